@@ -1,0 +1,218 @@
+"""Seeded synthetic inputs for the TLSPH step (arXiv 2602.15149).
+
+This module only lays out particles, materials, boundary conditions and
+notches.  It holds none of the method's arithmetic; both the CUDA library and
+the CPU oracle receive the same arrays from here.
+
+Recipes (the paper's own workloads use CAD geometry that is not available, so
+these lattices stand in for them at the same scale):
+
+* ``plate_2d``      -- 2D plane-strain elastic plate, square lattice
+  X = ((i + 1/2) dp, (j + 1/2) dp), no jitter; neo-Hookean; left edge clamped,
+  right edge pulled in x at ``v_pull`` with a linear ramp over ``ramp_steps``
+  steps (100 x 20 particles, dp = 1 mm is the full case).
+* ``block_3d``      -- 3D block, lattice jittered by U(-jitter dp, +jitter dp)
+  per axis from ``numpy.random.default_rng(seed)``; J2 plasticity; bottom face
+  fixed, top face pressed down at ``v_press`` (128 x 128 x 64 is the full case).
+* ``notched_plate`` -- 2D plate 0.1 x 0.04 m with an edge notch of length
+  0.05 m at mid-height, phase-field fracture, +-1 MPa traction on the top and
+  bottom rows (500 x 200 particles is the full case).
+* ``batched``       -- many independent 2D specimens of log-uniform size with
+  random materials and loading (512 specimens is the full case).
+
+The time step of every case is the CFL bound 0.3 h / c with
+c = sqrt((lambda + 2 mu)/rho) (the step the solvers take in their
+``cfl_static`` mode); the ramp lengths are given in those steps.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MODEL_NH, MODEL_J2 = 2, 3
+BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
+DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
+
+
+@dataclass
+class Material:
+    model: int = MODEL_NH
+    rho: float = 7850.0
+    E: float = 200e9
+    nu: float = 0.3
+    sigma_y0: float = 0.0
+    H_hard: float = 0.0
+    beta1: float = 0.2
+    beta2: float = 0.0
+    fracture: int = 0
+    Gc: float = 0.0
+    eps0: float = 0.0
+    s_lim: float = 0.1
+
+    def p_wave_speed(self) -> float:
+        """sqrt((lambda + 2 mu) / rho): the speed that sets the workload's step size."""
+        return math.sqrt(self.E * (1.0 - self.nu) / ((1.0 + self.nu) * (1.0 - 2.0 * self.nu)) / self.rho)
+
+
+@dataclass
+class BC:
+    mask: np.ndarray            # uint8 per particle
+    kind: int                   # BC_*
+    comp_mask: int              # bit k -> component k
+    value: tuple                # 3 values
+    t_start: float = 0.0
+    t_end: float = -1.0         # < 0: no end
+    ramp: float = 0.0           # linear ramp time, 0 = step
+    area: float = 0.0           # traction: area per particle
+
+
+@dataclass
+class Case:
+    name: str
+    dim: int
+    dp: float
+    h: float
+    cfl: float
+    dt_mode: int
+    fixed_dt: float
+    materials: list
+    X0: np.ndarray              # (n, dim) float64
+    vol: np.ndarray             # (n,) float64
+    v0: np.ndarray              # (n, dim) float64
+    material_id: np.ndarray     # (n,) int32
+    specimen_id: np.ndarray | None
+    bcs: list = field(default_factory=list)
+    notches: list = field(default_factory=list)
+    steps: int = 1000
+    precision: str = "fp32"     # "fp64" or "fp32" (fp32 fields, fp64 displacement)
+    gravity: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def n(self) -> int:
+        return int(self.X0.shape[0])
+
+
+def lattice(shape, dp, jitter=0.0, seed=0, origin=None):
+    """Particles at ((i + 1/2) dp, ...) with id = i + nx (j + ny k); optional uniform jitter."""
+    dim = len(shape)
+    idx = np.indices(shape[::-1]).reshape(dim, -1)[::-1].T.astype(np.float64)  # x fastest
+    X = (idx + 0.5) * dp
+    if origin is not None:
+        X = X + np.asarray(origin, dtype=np.float64)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        X = X + rng.uniform(-jitter * dp, jitter * dp, size=X.shape)
+    return np.ascontiguousarray(X), idx.astype(np.int64)
+
+
+def plate_2d(nx=100, ny=20, dp=1e-3, v_pull=1.0, ramp_steps=100, steps=1000, precision="fp64",
+             beta1=1.0, beta2=0.0):
+    """2D plane-strain Neo-Hookean plate, left edge clamped, right edge pulled (ramped)."""
+    X, idx = lattice((nx, ny), dp)
+    n = X.shape[0]
+    mat = Material(model=MODEL_NH, rho=7850.0, E=200e9, nu=0.3, beta1=beta1, beta2=beta2)
+    h = 1.5 * dp
+    dt = 0.3 * h / mat.p_wave_speed()
+    left = (idx[:, 0] == 0).astype(np.uint8)
+    right = (idx[:, 0] == nx - 1).astype(np.uint8)
+    bcs = [BC(left, BC_VEL, 0b11, (0.0, 0.0, 0.0)),
+           BC(right, BC_VEL, 0b01, (v_pull, 0.0, 0.0), ramp=ramp_steps * dt)]
+    return Case("plate_2d_nh", 2, dp, h, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
+                np.zeros((n, 2)), np.zeros(n, np.int32), None, bcs, [], steps, precision)
+
+
+def block_3d(nx=128, ny=128, nz=64, dp=1e-3, jitter=0.01, seed=2602, v_press=5.0, steps=2000,
+             precision="fp32", sigma_y0=250e6, H_hard=1e9, beta1=0.2):
+    """3D J2 block: bottom face fixed, top face pressed down at v_press."""
+    X, idx = lattice((nx, ny, nz), dp, jitter=jitter, seed=seed)
+    n = X.shape[0]
+    mat = Material(model=MODEL_J2, rho=7850.0, E=200e9, nu=0.3, sigma_y0=sigma_y0, H_hard=H_hard, beta1=beta1)
+    bottom = (idx[:, 2] == 0).astype(np.uint8)
+    top = (idx[:, 2] == nz - 1).astype(np.uint8)
+    bcs = [BC(bottom, BC_VEL, 0b111, (0.0, 0.0, 0.0)),
+           BC(top, BC_VEL, 0b100, (0.0, 0.0, -v_press))]
+    return Case("block_3d_j2", 3, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp ** 3),
+                np.zeros((n, 3)), np.zeros(n, np.int32), None, bcs, [], steps, precision)
+
+
+def notched_plate(nx=500, ny=200, width=0.1, height=0.04, notch_len=0.05, traction=1e6, steps=4000,
+                  precision="fp32", s_lim=0.1, beta1=0.2):
+    """2D phase-field plate with an edge notch at mid-height, pulled by +-traction on top/bottom rows."""
+    dp = width / nx
+    assert abs(dp * ny - height) < 1e-12 * height
+    X, idx = lattice((nx, ny), dp)
+    n = X.shape[0]
+    mat = Material(model=MODEL_NH, rho=2450.0, E=32e9, nu=0.2, beta1=beta1, fracture=1, Gc=3.0, eps0=2.0 * dp,
+                   s_lim=s_lim)
+    top = (idx[:, 1] == ny - 1).astype(np.uint8)
+    bot = (idx[:, 1] == 0).astype(np.uint8)
+    area = dp * 1.0  # unit thickness
+    bcs = [BC(top, BC_TRACTION, 0b10, (0.0, traction, 0.0), area=area),
+           BC(bot, BC_TRACTION, 0b10, (0.0, -traction, 0.0), area=area)]
+    y0 = 0.5 * height
+    notch = [(0.0, y0, 0.0), (notch_len, y0, 0.0), (notch_len, y0, 1.0), (0.0, y0, 1.0)]
+    return Case("notched_plate_pf", 2, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
+                np.zeros((n, 2)), np.zeros(n, np.int32), None, bcs, [np.array(notch, dtype=np.float64)], steps,
+                precision)
+
+
+def batched(nspec=512, n_min=500, n_max=50000, dp=1e-3, seed=0, steps=1000, precision="fp32"):
+    """Independent 2D specimens laid side by side (each its own specimen id).
+
+    Per specimen s (seeded by ``seed + s``): N_s = round(exp(U(ln n_min, ln n_max))), aspect U(1, 4),
+    E log-U(1, 200) GPa, nu U(0.2, 0.45), Neo-Hookean or J2 with p = 1/2 (sigma_y0 U(100, 500) MPa,
+    H = 1 GPa), rho = 7850, one clamped edge and a different loaded edge (velocity log-U(0.1, 5) m/s
+    along the edge normal, ramped over 100 steps).  Specimens are ordered by size.
+    """
+    specs = []
+    for s in range(nspec):
+        rng = np.random.default_rng(seed + s)
+        N = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        aspect = rng.uniform(1.0, 4.0)
+        ny = max(3, int(round(math.sqrt(N / aspect))))
+        nx = max(3, int(round(N / ny)))
+        E = math.exp(rng.uniform(math.log(1e9), math.log(200e9)))
+        nu = rng.uniform(0.2, 0.45)
+        j2 = rng.uniform() < 0.5
+        sy = rng.uniform(100e6, 500e6)
+        sides = rng.permutation(4)[:2]
+        rate = math.exp(rng.uniform(math.log(0.1), math.log(5.0)))
+        specs.append((nx * ny, nx, ny, E, nu, j2, sy, int(sides[0]), int(sides[1]), rate))
+    specs.sort(key=lambda t: t[0])
+    Xs, mids, sids, bc_clamp, bc_load, mats, loads = [], [], [], [], [], [], []
+    x_off = 0.0
+    for s, (N, nx, ny, E, nu, j2, sy, clamp, load, rate) in enumerate(specs):
+        X, idx = lattice((nx, ny), dp, origin=(x_off, 0.0))
+        x_off += (nx + 4) * dp  # specimens never touch (gap > support radius)
+        m = Material(model=MODEL_J2 if j2 else MODEL_NH, rho=7850.0, E=E, nu=nu, sigma_y0=sy if j2 else 0.0,
+                     H_hard=1e9 if j2 else 0.0, beta1=0.2)
+        mats.append(m)
+        edges = [idx[:, 0] == 0, idx[:, 0] == nx - 1, idx[:, 1] == 0, idx[:, 1] == ny - 1]
+        normals = [(-1.0, 0.0), (1.0, 0.0), (0.0, -1.0), (0.0, 1.0)]
+        Xs.append(X)
+        mids.append(np.full(X.shape[0], s, np.int32))
+        sids.append(np.full(X.shape[0], s, np.int32))
+        bc_clamp.append(edges[clamp])
+        bc_load.append(edges[load])
+        loads.append((load, rate, normals[load], m.p_wave_speed()))
+    X0 = np.concatenate(Xs)
+    n = X0.shape[0]
+    clamp_mask = np.concatenate(bc_clamp).astype(np.uint8)
+    bcs = [BC(clamp_mask, BC_VEL, 0b11, (0.0, 0.0, 0.0))]
+    # one loaded-edge BC per (direction) group; the ramp is in each specimen's own steps, so
+    # specimens are grouped by their velocity value and ramp time in the per-particle table
+    case = Case("batched_2d", 2, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, mats, X0, np.full(n, dp * dp),
+                np.zeros((n, 2)), np.concatenate(mids), np.concatenate(sids), bcs, [], steps, precision)
+    case.specimen_loads = []
+    off = 0
+    for s, X in enumerate(Xs):
+        load, rate, nrm, c = loads[s]
+        mask = np.zeros(n, np.uint8)
+        mask[off:off + X.shape[0]] = bc_load[s]
+        dt = 0.3 * case.h / c
+        case.specimen_loads.append(BC(mask, BC_VEL, 0b01 if nrm[0] != 0.0 else 0b10,
+                                      (rate * nrm[0], rate * nrm[1], 0.0), ramp=100 * dt))
+        off += X.shape[0]
+    return case

@@ -1,0 +1,24 @@
+"""Drive the FP64 oracle from a workload Case (test helper; imports only oracle/ and workloads)."""
+import numpy as np
+
+from oracle.oracle import Oracle, OracleMaterial
+from paper_2602_15149_b300 import workloads as W
+
+
+def oracle_material(m: W.Material) -> OracleMaterial:
+    return OracleMaterial(m.model, m.rho, m.E, m.nu, m.sigma_y0, m.H_hard, m.beta1, m.beta2, m.fracture, m.Gc,
+                          m.eps0, m.s_lim)
+
+
+def make_oracle(case: W.Case, build=True, method=None, **kw) -> Oracle:
+    o = Oracle(case.dim, case.h, cfl=case.cfl, dt_mode=case.dt_mode, fixed_dt=case.fixed_dt,
+               gravity=case.gravity, **kw)
+    o.set_materials([oracle_material(m) for m in case.materials])
+    o.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
+    for b in case.bcs:
+        o.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
+    for q in case.notches:
+        o.add_notch(q)
+    if build:
+        o.build_ref_neighbours(method)
+    return o

@@ -1,0 +1,551 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own formulas: closed forms,
+invariants, finite differences, brute force, or special cases that reduce to
+a textbook result.  None needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import oracle as O
+from paper_2602_15149_b300 import workloads as W
+from tests.oracle_cases import make_oracle, oracle_material
+
+STEEL_NH = O.OracleMaterial(model=O.MODEL_NH, rho=7850.0, E=200e9, nu=0.3, beta1=0.0)
+STEEL_J2 = O.OracleMaterial(model=O.MODEL_J2, rho=7850.0, E=200e9, nu=0.3, sigma_y0=250e6, H_hard=1e9, beta1=0.0)
+
+
+def lame(E, nu):
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    return lam, mu
+
+
+def rand_rotation(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q @ np.diag(np.sign(np.diag(r)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+# ---------------------------------------------------------------- kernel
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wendland_normalised_and_derivative(dim):
+    """Wendland C2 integrates to one (alpha_D) and dW/dr matches finite differences."""
+    h = 1.3e-3
+    r = np.linspace(0.0, 2 * h, 20001)
+    Wv = np.array([O.wendland(dim, h, x)[0] for x in r])
+    shell = 2 * math.pi * r if dim == 2 else 4 * math.pi * r * r
+    total = np.trapezoid(Wv * shell, r)
+    assert abs(total - 1.0) < 1e-6
+    for x in [0.1 * h, 0.7 * h, 1.3 * h, 1.9 * h]:
+        e = 1e-9 * h
+        fd = (O.wendland(dim, h, x + e)[0] - O.wendland(dim, h, x - e)[0]) / (2 * e)
+        assert abs(O.wendland(dim, h, x)[1] - fd) <= 1e-6 * abs(fd)
+    assert O.wendland(dim, h, 2 * h) == (0.0, 0.0)
+
+
+# ---------------------------------------------------------------- neighbours
+def _brute_rows(X, R):
+    n = X.shape[0]
+    rows = []
+    for i in range(n):
+        d = X - X[i]
+        r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+        if X.shape[1] == 3:
+            r2 = r2 + d[:, 2] * d[:, 2]
+        idx = np.nonzero(r2 < R * R)[0]
+        rows.append(idx[idx != i])
+    return rows
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_neighbours_equal_brute_force(dim):
+    """Cell-list and O(N^2) searches give bit-identical CSR; both equal a numpy brute force."""
+    if dim == 2:
+        case = W.plate_2d(nx=23, ny=9)
+    else:
+        case = W.block_3d(nx=9, ny=8, nz=7, jitter=0.01, seed=5)
+    a = make_oracle(case, method=0)
+    b = make_oracle(case, method=1)
+    rpa, cola = a.neighbours()
+    rpb, colb = b.neighbours()
+    assert np.array_equal(rpa, rpb) and np.array_equal(cola, colb)
+    rows = _brute_rows(case.X0, 2.0 * case.h)
+    for i, row in enumerate(rows):
+        assert np.array_equal(cola[rpa[i]:rpa[i + 1]], row)
+    # symmetry of the neighbour relation
+    pairs = set()
+    for i in range(case.n):
+        for j in cola[rpa[i]:rpa[i + 1]]:
+            pairs.add((i, int(j)))
+    assert all((j, i) in pairs for (i, j) in pairs)
+
+
+def test_cell_sort_permutation():
+    """The cell-sorted order is a permutation with ids ascending inside each cell."""
+    case = W.block_3d(nx=10, ny=7, nz=6, jitter=0.01, seed=1)
+    o = make_oracle(case)
+    p = o.perm()
+    assert np.array_equal(np.sort(p), np.arange(case.n))
+    cs = 2.0 * case.h * (1.0 + 2.0 ** -10)
+    xmin = case.X0.min(axis=0)
+    cell = np.floor((case.X0 - xmin) / cs).astype(np.int64)
+    nc = cell.max(axis=0) + 1
+    key = (cell[:, 2] * nc[1] + cell[:, 1]) * nc[0] + cell[:, 0]
+    k = key[p]
+    assert np.all(np.diff(k) >= 0)
+    same = np.diff(k) == 0
+    assert np.all(np.diff(p)[same] > 0)
+
+
+def test_notch_removes_exactly_crossing_bonds():
+    """Bonds whose reference segment crosses the notch segment inside it (relative margin 1e-9) are removed."""
+    case = W.notched_plate(nx=50, ny=20)
+    o = make_oracle(case)
+    rp, col = o.neighbours()
+    free = make_oracle(W.notched_plate(nx=50, ny=20), build=False)
+    # same particles without the notch
+    free2 = O.Oracle(2, case.h)
+    free2.set_materials([oracle_material(m) for m in case.materials])
+    free2.create_particles(case.X0, case.vol)
+    free2.build_ref_neighbours()
+    rp0, col0 = free2.neighbours()
+    y0, xt = 0.02, 0.05
+    X = case.X0
+    removed = 0
+    for i in range(case.n):
+        full = set(col0[rp0[i]:rp0[i + 1]].tolist())
+        cut = set(col[rp[i]:rp[i + 1]].tolist())
+        assert cut <= full
+        for j in full:
+            yi, yj = X[i, 1], X[j, 1]
+            crosses = (yi - y0) * (yj - y0) < 0
+            if crosses:
+                xc = X[i, 0] + (y0 - yi) * (X[j, 0] - X[i, 0]) / (yj - yi)
+                crosses = 1e-9 * xt < xc < (1 - 1e-9) * xt
+            assert (j not in cut) == crosses
+            removed += crosses
+    assert removed > 0
+    del free
+
+
+# ---------------------------------------------------------------- correction / deformation gradient
+@pytest.mark.parametrize("dim", [2, 3])
+def test_patch_test_linear_field(dim):
+    """Corrected gradients are exact for linear fields: u = A X + b gives F = I + A everywhere (edges too)."""
+    rng = np.random.default_rng(3)
+    case = W.plate_2d(nx=12, ny=9) if dim == 2 else W.block_3d(nx=7, ny=6, nz=5, jitter=0.05, seed=2)
+    o = make_oracle(case)
+    A = rng.normal(scale=1e-2, size=(dim, dim))
+    b = rng.normal(scale=1e-4, size=dim)
+    u = case.X0 @ A.T + b
+    o.write("U", u)
+    F = o.read("F")
+    expect = np.eye(3)
+    expect[:dim, :dim] += A
+    assert np.abs(F - expect).max() < 1e-12
+
+
+def test_volume_scaling_invariance():
+    """F does not change when every reference volume is scaled (the volume enters L and F inversely)."""
+    case = W.block_3d(nx=6, ny=6, nz=5, jitter=0.05, seed=9)
+    rng = np.random.default_rng(0)
+    u = rng.normal(scale=1e-5, size=case.X0.shape)
+    o1 = make_oracle(case)
+    o1.write("U", u)
+    case.vol = case.vol * 3.7
+    o2 = make_oracle(case)
+    o2.write("U", u)
+    assert np.abs(o1.read("F") - o2.read("F")).max() < 1e-12
+
+
+# ---------------------------------------------------------------- neo-Hookean
+def _psi_nh(F, s, mat):
+    _, pp, pm = O.nh_stress(F, s, mat)
+    return s * s * pp + pm
+
+
+@pytest.mark.parametrize("J_branch", ["tension", "compression"])
+def test_nh_stress_is_energy_derivative(J_branch):
+    """P = F S equals dpsi/dF (central differences), psi = s^2 psi+ + psi-, on both J branches."""
+    rng = np.random.default_rng(11 if J_branch == "tension" else 12)
+    for _ in range(5):
+        F = np.eye(3) + rng.normal(scale=0.05, size=(3, 3))
+        J = np.linalg.det(F)
+        target = 1.05 if J_branch == "tension" else 0.95
+        F = F * (target / J) ** (1 / 3)
+        s = 0.7
+        S, _, _ = O.nh_stress(F, s, STEEL_NH)
+        P = F @ S
+        e = 1e-7
+        fd = np.zeros((3, 3))
+        for a in range(3):
+            for b in range(3):
+                Fp, Fm = F.copy(), F.copy()
+                Fp[a, b] += e
+                Fm[a, b] -= e
+                fd[a, b] = (_psi_nh(Fp, s, STEEL_NH) - _psi_nh(Fm, s, STEEL_NH)) / (2 * e)
+        assert np.abs(P - fd).max() < 1e-5 * np.abs(P).max()
+
+
+def test_nh_frame_indifference_and_rest_state():
+    """P(QF) = Q P(F); psi(I) = 0 and S(I) = 0; a rigid rotation carries no stress."""
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        F = np.eye(3) + rng.normal(scale=0.1, size=(3, 3))
+        Q = rand_rotation(rng)
+        S1, p1, m1 = O.nh_stress(F, 0.8, STEEL_NH)
+        S2, p2, m2 = O.nh_stress(Q @ F, 0.8, STEEL_NH)
+        assert np.abs(Q @ F @ S2 - Q @ (F @ S1)).max() < 1e-9 * np.abs(F @ S1).max() + 1.0
+        assert abs(p1 - p2) < 1e-9 * abs(p1) + 1e-6
+        S0, pp, pm = O.nh_stress(Q, 1.0, STEEL_NH)
+        assert np.abs(S0).max() < 1e-14 * STEEL_NH.E and abs(pp) < 1e-14 * STEEL_NH.E and abs(pm) < 1e-14 * STEEL_NH.E
+
+
+def test_nh_small_strain_is_hooke():
+    """For small strain the NH second Piola-Kirchhoff stress tends to lambda tr(eps) I + 2 mu eps."""
+    lam, mu = lame(STEEL_NH.E, STEEL_NH.nu)
+    rng = np.random.default_rng(7)
+    eps = rng.normal(scale=1e-7, size=(3, 3))
+    eps = 0.5 * (eps + eps.T)
+    S, _, _ = O.nh_stress(np.eye(3) + eps, 1.0, STEEL_NH)
+    hooke = lam * np.trace(eps) * np.eye(3) + 2 * mu * eps
+    assert np.abs(S - hooke).max() < 1e-5 * np.abs(hooke).max()
+
+
+def test_nh_degradation_split():
+    """Degradation s^2 acts on the tensile energy only: in compression the volumetric stress survives s = 0."""
+    F = np.diag([0.98, 0.98, 0.98])
+    S0, pp, pm = O.nh_stress(F, 0.0, STEEL_NH)
+    S1, _, _ = O.nh_stress(F, 1.0, STEEL_NH)
+    assert np.allclose(S0, S1, rtol=1e-12)  # pure volumetric compression: no isochoric part
+    assert pm > 0 and abs(pp) < 1e-6
+    Ft = np.diag([1.02, 1.02, 1.02])
+    St, _, _ = O.nh_stress(Ft, 0.0, STEEL_NH)
+    assert np.abs(St).max() == 0.0
+
+
+# ---------------------------------------------------------------- matrix exponential
+def test_expm_matches_scipy_and_eigen():
+    rng = np.random.default_rng(5)
+    for scale in [1e-6, 1e-2, 0.3, 2.0, 8.0]:
+        A = rng.normal(scale=scale, size=(3, 3))
+        assert np.abs(O.expm(A) - sla.expm(A)).max() <= 1e-13 * np.abs(sla.expm(A)).max()
+        Sym = 0.5 * (A + A.T)
+        w, V = np.linalg.eigh(Sym)
+        ref = V @ np.diag(np.exp(w)) @ V.T
+        assert np.abs(O.expm(Sym) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- J2 plasticity
+def _sigma_eq_from_state(F, Fp, mat):
+    lam, mu = lame(mat.E, mat.nu)
+    C = F.T @ F
+    Fpi = np.linalg.inv(Fp)
+    Ce = Fpi.T @ C @ Fpi
+    Cb = np.linalg.det(F) ** (-2 / 3) * Ce
+    M = mu * (Cb - np.trace(Cb) / 3 * np.eye(3))
+    return math.sqrt(1.5 * np.sum(M * M))
+
+
+def test_j2_elastic_equals_neo_hooke():
+    """Below yield the J2 model is the (undegraded) neo-Hookean model: same energy split."""
+    rng = np.random.default_rng(2)
+    F = np.eye(3) + rng.normal(scale=2e-4, size=(3, 3))
+    r = O.j2_update(F, np.eye(3), 0.0, STEEL_J2)
+    S_nh, _, _ = O.nh_stress(F, 1.0, STEEL_NH)
+    assert r["dgamma"] == 0.0 and r["status"] == 0
+    assert np.abs(r["S"] - S_nh).max() < 1e-9 * np.abs(S_nh).max()
+
+
+def _trial_F(rng, e_dev, e_vol=0.0, rotate=True):
+    """F = Q exp(e_dev D + e_vol I) with D a random unit deviatoric symmetric direction."""
+    A = rng.normal(size=(3, 3))
+    D = 0.5 * (A + A.T)
+    D -= np.trace(D) / 3 * np.eye(3)
+    D /= np.linalg.norm(D)
+    F = sla.expm(e_dev * D + e_vol * np.eye(3))
+    return (rand_rotation(rng) @ F) if rotate else F
+
+
+def _plastic_state(rng):
+    """A plastic state (F_p, eps_p) reached by one earlier return from I."""
+    r = O.j2_update(_trial_F(rng, 0.0022), np.eye(3), 0.0, STEEL_J2)
+    assert r["status"] == 0 and r["dgamma"] > 0
+    return r["Fp"], r["ep"]
+
+
+def test_j2_return_on_yield_surface():
+    """After a plastic step sigma_eq = sigma_y(eps_p), det F_p = 1, and eps_p grows by dgamma."""
+    rng = np.random.default_rng(4)
+    nplastic = 0
+    for k in range(30):
+        Fp0, ep0 = _plastic_state(rng) if k % 2 else (np.eye(3), 0.0)
+        F = _trial_F(rng, rng.uniform(0.0005, 0.0025), rng.uniform(-2e-3, 2e-3))
+        r = O.j2_update(F, Fp0, ep0, STEEL_J2)
+        assert r["status"] == 0
+        if r["dgamma"] > 0:
+            nplastic += 1
+            sig = _sigma_eq_from_state(F, r["Fp"], STEEL_J2)
+            sy = STEEL_J2.sigma_y0 + STEEL_J2.H_hard * r["ep"]
+            assert abs(sig - sy) <= 1e-8 * sy
+            assert abs(np.linalg.det(r["Fp"]) - 1.0) < 1e-12
+            assert abs(r["ep"] - ep0 - r["dgamma"]) < 1e-15
+        else:
+            assert _sigma_eq_from_state(F, Fp0, STEEL_J2) <= STEEL_J2.sigma_y0 + STEEL_J2.H_hard * ep0
+    assert nplastic > 10
+
+
+def test_j2_small_strain_radial_return_limit():
+    """For small strain increments dgamma -> (sigma_tr - sigma_y) / (3 mu + H) (small-strain return map)."""
+    lam, mu = lame(STEEL_J2.E, STEEL_J2.nu)
+    e = 1.5e-3
+    F = np.diag([1 + e, 1 - 0.5 * e, 1 - 0.5 * e])  # isochoric to first order, past yield
+    sig_tr = _sigma_eq_from_state(F, np.eye(3), STEEL_J2)
+    r = O.j2_update(F, np.eye(3), 0.0, STEEL_J2)
+    pred = (sig_tr - STEEL_J2.sigma_y0) / (3 * mu + STEEL_J2.H_hard)
+    assert r["dgamma"] > 0
+    assert abs(r["dgamma"] - pred) < 5e-3 * pred
+
+
+def test_j2_frame_indifference_and_unloading():
+    rng = np.random.default_rng(8)
+    F = _trial_F(rng, 0.0022, 1e-3, rotate=False)
+    Q = rand_rotation(rng)
+    r1 = O.j2_update(F, np.eye(3), 0.0, STEEL_J2)
+    r2 = O.j2_update(Q @ F, np.eye(3), 0.0, STEEL_J2)
+    assert r1["dgamma"] > 0
+    assert abs(r1["dgamma"] - r2["dgamma"]) < 1e-10 * r1["dgamma"]
+    P1, P2 = F @ r1["S"], Q @ F @ r2["S"]
+    assert np.abs(P2 - Q @ P1).max() < 1e-8 * np.abs(P1).max()
+    # unloading from the plastic state is elastic
+    Fu = sla.fractional_matrix_power(F, 0.5).real
+    r3 = O.j2_update(Fu, r1["Fp"], r1["ep"], STEEL_J2)
+    assert r3["dgamma"] == 0.0
+
+
+def test_j2_converges_on_large_increments():
+    """Illinois with bracket doubling converges for trial stresses up to twice the yield stress.
+
+    (Beyond about 2 sigma_y the doubled bracket can step over the minimum of sigma_eq along the frozen
+    flow direction; explicit steps stay far below that.)"""
+    rng = np.random.default_rng(13)
+    for e in [0.0015, 0.002, 0.0025]:
+        F = _trial_F(rng, e, 2e-3)
+        r = O.j2_update(F, np.eye(3), 0.0, STEEL_J2)
+        assert r["status"] == 0 and r["iters"] < 40
+        sig = _sigma_eq_from_state(F, r["Fp"], STEEL_J2)
+        assert abs(sig - (STEEL_J2.sigma_y0 + STEEL_J2.H_hard * r["ep"])) <= 1e-8 * sig
+
+
+# ---------------------------------------------------------------- phase field
+def _pf_case(nx=30, ny=30):
+    case = W.notched_plate(nx=nx, ny=ny, width=nx * 1e-3, height=ny * 1e-3, notch_len=0.0, traction=0.0)
+    case.bcs = []
+    case.notches = []
+    return case
+
+
+def test_laplacian_exact_for_quadratics_interior():
+    """Corrected SPH Laplacian of s = a |X - c|^2 / 2 equals a d on symmetric interior neighbourhoods."""
+    case = _pf_case()
+    m = case.materials[0]
+    o = make_oracle(case)
+    a = 3.0
+    c = np.array([0.013, 0.017])
+    s = 1.0 - 0.5 * a * np.sum((case.X0 - c) ** 2, axis=1)
+    o.write("S", s)
+    o.step(1)
+    sdd = o.read("SDD")
+    cw = O.sound_speed(oracle_material(m))
+    e0 = m.eps0
+    lap = (sdd * 2 * e0 / cw ** 2 - (1 - s) / (2 * e0)) / (2 * e0)
+    R = 2 * case.h
+    X = case.X0
+    interior = (X[:, 0] > X[:, 0].min() + R) & (X[:, 0] < X[:, 0].max() - R) & \
+               (X[:, 1] > X[:, 1].min() + R) & (X[:, 1] < X[:, 1].max() - R)
+    assert interior.sum() > 100
+    assert np.abs(lap[interior] - (-a * 2)).max() < 1e-6 * 2 * a
+
+
+def test_phase_field_fixed_point_intact():
+    """s = 1, sdot = 0 with H = 0 is a fixed point (no load)."""
+    case = _pf_case(12, 10)
+    o = make_oracle(case)
+    o.step(50)
+    assert np.all(o.read("S") == 1.0) and np.all(o.read("SDOT") == 0.0)
+
+
+def test_phase_field_homogeneous_equilibrium():
+    """With a uniform history H the damage settles monotonically at s* = 1 / (1 + 4 eps0 H / Gc)."""
+    case = _pf_case(10, 10)
+    m = case.materials[0]
+    o = make_oracle(case)
+    Hh = 0.75 * m.Gc / m.eps0
+    o.write("H", np.full(case.n, Hh))
+    prev = 1.0
+    for _ in range(60):
+        o.step(100)
+        s = o.read("S")
+        assert np.all(s <= prev + 1e-15)
+        prev = s.max()
+    sstar = 1.0 / (1.0 + 4.0 * m.eps0 * Hh / m.Gc)
+    assert np.abs(s - sstar).max() < 1e-6
+    assert np.all(o.read("H") == Hh)
+
+
+def test_history_nondecreasing_and_s_bounds():
+    """H never decreases and s stays in [0, 1] on the notched plate under load."""
+    case = W.notched_plate(nx=50, ny=20, steps=300)
+    o = make_oracle(case)
+    Hprev = o.read("H")
+    for _ in range(6):
+        o.step(50)
+        Hn = o.read("H")
+        assert np.all(Hn >= Hprev)
+        Hprev = Hn
+        s = o.read("S")
+        assert s.min() >= 0.0 and s.max() <= 1.0
+    assert Hprev.max() > 0.0
+
+
+# ---------------------------------------------------------------- dynamics
+def test_momentum_conservation_without_viscosity():
+    """Internal forces are pairwise antisymmetric: sum m a = 0 for a free body (no viscosity, no BCs)."""
+    case = W.block_3d(nx=7, ny=6, nz=5, jitter=0.05, seed=4, beta1=0.0)
+    case.bcs = []
+    rng = np.random.default_rng(0)
+    o = make_oracle(case)
+    o.write("U", rng.normal(scale=2e-6, size=case.X0.shape))
+    o.step(1)
+    a = o.read("ACC")
+    m = case.materials[0].rho * case.vol
+    tot = (m[:, None] * a).sum(axis=0)
+    assert np.abs(tot).max() < 1e-10 * (m[:, None] * np.abs(a)).sum()
+
+
+def _free_body(beta1, nx=16, ny=12):
+    case = W.plate_2d(nx=nx, ny=ny, beta1=beta1, beta2=0.0)
+    case.bcs = []
+    X = case.X0
+    L = X[:, 0].max() - X[:, 0].min()
+    case.v0 = np.stack([0.5 * np.sin(math.pi * (X[:, 0] - X[:, 0].min()) / L), np.zeros(case.n)], axis=1)
+    return case
+
+
+def _staggered_energy(o, case):
+    """Energy of the staggered (leapfrog) reading of Algorithm 1: 1/2 m v_{n-1/2} . v_{n+1/2} + SE(u_n).
+
+    Algorithm 1 updates v from a(u_n) and then u with the new v, so the stored v is the half-step velocity;
+    this is the energy the scheme conserves for a conservative force.  Advances the oracle by one step.
+    """
+    m = case.materials[0].rho * case.vol
+    se = o.energies()["SE"]
+    v0 = o.read("V")
+    o.step(1)
+    v1 = o.read("V")
+    return 0.5 * np.sum(m[:, None] * v0 * v1) + se
+
+
+def test_energy_conserved_without_viscosity():
+    """Without viscosity the scheme's energy stays within 1e-6 of its start over 1000 steps (bounded drift)."""
+    case = _free_body(0.0)
+    o = make_oracle(case)
+    E0 = _staggered_energy(o, case)
+    worst = 0.0
+    for _ in range(20):
+        o.step(49)
+        worst = max(worst, abs(_staggered_energy(o, case) - E0) / E0)
+    assert worst < 1e-6
+
+
+def test_viscosity_dissipates_and_literal_sign_does_not():
+    """The dissipative reading of the viscosity (Pv = -J pi F^-T) lowers the energy; the printed sign adds to it."""
+    res = {}
+    for literal in (False, True):
+        case = _free_body(1.0)
+        o = make_oracle(case, visc_literal=literal)
+        E0 = _staggered_energy(o, case)
+        try:
+            o.step(300)
+            res[literal] = _staggered_energy(o, case) / E0
+        except RuntimeError:  # the literal sign feeds energy in until the run blows up
+            res[literal] = math.inf
+    assert res[False] < 0.99
+    assert res[True] > 1.0
+
+
+def test_elastic_wave_speed():
+    """With nu = 0 the P-wave front travels at sqrt(E/rho) (plane strain = 1D bar speed)."""
+    nx, ny, dp = 240, 6, 1e-3
+    case = W.plate_2d(nx=nx, ny=ny, dp=dp, beta1=0.2)
+    case.materials[0].nu = 0.0
+    X = case.X0
+    left = (np.isclose(X[:, 0], X[:, 0].min())).astype(np.uint8)
+    v0 = 0.1
+    case.bcs = [W.BC(left, W.BC_VEL, 0b01, (v0, 0.0, 0.0))]
+    o = make_oracle(case)
+    c_exact = math.sqrt(case.materials[0].E / case.materials[0].rho)
+    probe = np.isclose(X[:, 0], X[:, 0].min() + 150 * dp)
+    t_arrive = None
+    for _ in range(2000):
+        o.step(1)
+        if o.read("V")[probe, 0].mean() >= 0.5 * v0:
+            t_arrive = o.time()[0]
+            break
+    assert t_arrive is not None
+    c_meas = 150 * dp / t_arrive
+    assert abs(c_meas - c_exact) < 0.02 * c_exact
+
+
+def test_adaptive_dt_bound():
+    """Adaptive step: dt = C min(h / (c + |v|max), sqrt(h / |a|max)) from the previous step's maxima."""
+    case = _free_body(0.2)
+    case.dt_mode = W.DT_ADAPTIVE
+    o = make_oracle(case)
+    o.step(3)
+    v = o.read("V")
+    a = o.read("ACC")
+    o.step(1)
+    _, dt = o.time()
+    c = O.sound_speed(oracle_material(case.materials[0]))
+    vmax = np.sqrt((v ** 2).sum(axis=1)).max()
+    amax = np.sqrt((a ** 2).sum(axis=1)).max()
+    expect = case.cfl * min(case.h / (c + vmax), math.sqrt(case.h / amax))
+    assert abs(dt - expect) < 1e-14 * expect
+
+
+def test_velocity_bc_rigid_translation_has_no_stress():
+    """All particles driven at one velocity: F stays I and no internal force arises."""
+    case = W.plate_2d(nx=10, ny=6)
+    allm = np.ones(case.n, np.uint8)
+    case.bcs = [W.BC(allm, W.BC_VEL, 0b11, (0.3, -0.2, 0.0))]
+    o = make_oracle(case)
+    o.step(20)
+    F = o.read("F")
+    assert np.abs(F - np.eye(3)).max() < 1e-12
+    assert np.abs(o.read("ACC")).max() < 1e-3
+
+
+def test_force_bcs_balance_total_momentum():
+    """Internal forces cancel, so sum m a equals the applied load: traction t A per particle, point force in total."""
+    case = W.block_3d(nx=6, ny=5, nz=5, jitter=0.02, seed=3, beta1=0.0)
+    X = case.X0
+    top = (X[:, 2] > X[:, 2].max() - 0.5 * case.dp).astype(np.uint8)
+    side = (X[:, 0] < X[:, 0].min() + 0.5 * case.dp).astype(np.uint8)
+    area = case.dp ** 2
+    case.bcs = [W.BC(top, W.BC_TRACTION, 0b100, (0.0, 0.0, 2e6), area=area),
+                W.BC(side, W.BC_POINTFORCE, 0b001, (-50.0, 0.0, 0.0))]
+    o = make_oracle(case)
+    o.write("U", np.random.default_rng(1).normal(scale=1e-6, size=X.shape))
+    o.step(1)
+    m = case.materials[0].rho * case.vol
+    tot = (m[:, None] * o.read("ACC")).sum(axis=0)
+    expect = np.array([-50.0, 0.0, 2e6 * area * top.sum()])
+    scale = (m[:, None] * np.abs(o.read("ACC"))).sum()
+    assert np.abs(tot - expect).max() < 1e-9 * scale
