@@ -1,0 +1,303 @@
+"""Benchmark of the fused TLSPH step on B300: particle-steps/s at 1M particles and % of HBM roofline.
+
+Workload: the 3D finite-strain J2 block, 128 x 128 x 64 = 1,048,576 particles on a
+jittered lattice (dp = 1 mm, h = 1.5 dp, Wendland C2, E = 200 GPa, nu = 0.3,
+sigma_y0 = 250 MPa, H = 1 GPa), bottom face fixed, top face pressed at 5 m/s,
+FP32 fields with FP64 displacement accumulation.  A step is one pass of the whole
+hot path (deformation gradient, J2 return map, momentum with viscosity, update,
+next step size): 2 kernels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+method as plainly written, test infrastructure) on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_15149_b300 import workloads as W  # noqa: E402
+
+METRIC = "TL-SPH particle-steps/sec at 1M particles, % HBM roofline; surrogate vs plain"
+UNIT = "particle-steps/s"
+SHAPE = (128, 128, 64)
+FALLBACK_HBM_GBS = 6400.0
+
+# DRAM bytes per launch of the force-and-damage pass (k_pass2) from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel
+# sources it was taken on; reported as null once the kernels change.
+NCU_TRAFFIC = {"sources": None, "pass2_bytes_per_launch": None}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2602_15149_b300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def pass_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
+    """Algorithmic HBM bytes per launch of each pass (own reads / writes once, neighbour gathers
+    served on chip, neighbour indices read once per pass) for the library's layout."""
+    v4 = 4 * ts
+    q = 3 * v4 if dim == 3 else v4
+    nsym = 6 if dim == 3 else 3
+    p1 = n * (4 + 8 / 32 + v4 + v4 + nsym * ts + 2 + q + dim * dim * ts) + 4 * nnz
+    if j2:
+        p1 += n * 2 * 7 * ts
+    if frac:
+        p1 += n * (v4 + 2 * ts)
+    p2 = n * (4 + 8 / 32 + 3 * v4 + q + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4) + 4 * nnz
+    if visc:
+        p2 += n * dim * dim * ts
+    if frac:
+        p2 += n * (nsym * ts + 3 * ts)
+    return p1, p2
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(seconds=15.0, shape=(32, 32, 16)):
+    """The FP64 oracle as it stands on a bounded sample of the workload (same lattice recipe,
+    material and loading, smaller block): particle-steps/s on the host cores."""
+    from tests.oracle_cases import make_oracle
+    case = W.block_3d(nx=shape[0], ny=shape[1], nz=shape[2])
+    o = make_oracle(case)
+    o.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 1 or (time.perf_counter() - t0 < seconds and steps < 10000):
+        o.step(1)
+        steps += 1
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": case.n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"block_3d_j2 {shape[0]}x{shape[1]}x{shape[2]} = {case.n} particles, {steps} steps "
+                      f"after 1 warm-up step ({el:.1f} s), FP64 OpenMP"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    res = []
+    for _ in range(args.warmup):
+        oracle_sample(seconds=1.0, shape=(16, 16, 8))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res.append(oracle_sample(seconds=max(1.0, 60.0 / max(args.steps, 1)), shape=(32, 32, 16)))
+    el = time.perf_counter() - t0
+    val = statistics.median(r["value"] for r in res)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "block_3d_j2 sample 32x32x16 of the 128x128x64 J2 block (FP64 CPU oracle)",
+                       "particles": 32 * 32 * 16},
+            "cpu_baseline": dict(res[0], value=val),
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+
+    case = W.block_3d(*SHAPE, steps=args.steps)
+    n = case.n
+    g = tlsph.from_case(case, device=local, stream=stream.cuda_stream)
+    info = g.get_info()
+    nnz = info["nnz"]
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    g.step(args.warmup)
+    l0 = g.get_info()["kernel_launches"]
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        g.step_async(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    st = g.sync(check=False)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = g.get_info()["kernel_launches"] - l0
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * args.steps / (ms * 1e-3)
+
+    # per-kernel durations (CUDA events around each launch on the same stream)
+    g.set_option(tlsph.OPT_KERNEL_TIMING, 1)
+    g.step(min(args.steps, 200))
+    kt = g.kernel_times()
+    g.set_option(tlsph.OPT_KERNEL_TIMING, 0)
+    p1_bytes, p2_bytes = pass_bytes(3, nnz, n)
+    p1_ms = kt["pass1_ms"] / max(kt["pass1_launches"], 1)
+    p2_ms = kt["pass2_ms"] / max(kt["pass2_launches"], 1)
+    dom = "pass2" if p2_ms >= p1_ms else "pass1"
+    dom_bytes, dom_ms = (p2_bytes, p2_ms) if dom == "pass2" else (p1_bytes, p1_ms)
+    peak, peak_src = peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["pass2_bytes_per_launch"] if (dom == "pass2" and
+                                                          NCU_TRAFFIC["sources"] == source_hash()) else None
+    g.close()
+    torch.cuda.synchronize(dev)
+
+    # end to end through the C-ABI with host buffers: setup from host arrays, every step with
+    # its status read back, final displacement copied to the host
+    barrier()
+    t0 = time.perf_counter()
+    g2 = tlsph.from_case(case, device=local, stream=stream.cuda_stream)
+    for _ in range(args.steps):
+        g2.step(1)
+    u = g2.read_state("U")
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    g2.close()
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = n * (8 * 3 + 8 + 4 + 8 * 3) + sum(n for _ in case.bcs)
+    d2h = u.nbytes + 8 * 4 * args.steps
+
+    if rank != 0:
+        return 0
+    cpu = oracle_sample() if not args.no_cpu else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "block_3d_j2 128x128x64 jittered lattice, J2 plasticity, top pressed at 5 m/s "
+                               "(FP32 fields, FP64 displacement)", "particles": n, "neighbour_pairs": nnz,
+                   "mean_neighbours": nnz / n, "l2": "inputs larger than L2 (~1.3 GB of state), no flush",
+                   "parallelism": f"replicas x{ws} (independent blocks)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+                     "pass1_ms": p1_ms, "pass2_ms": p2_ms, "pass1_bytes": p1_bytes, "pass2_bytes": p2_bytes},
+        "clocks": clk.summary(),
+        "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": launches,
+        "status": int(st),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * tlsph.h -- C-ABI of the B300 (sm_103a) total-Lagrangian SPH solid step of
+ * arXiv 2602.15149 ("SoliDualSPHysics").
+ *
+ * The library computes, per time step and per particle, over neighbour lists
+ * fixed in the reference configuration:
+ *   - the deformation gradient F_i with the kernel-gradient correction L_i
+ *     (Sec. 2.4, eq. deformGradTLSPH and the corrected gradient L_i),
+ *   - the first Piola-Kirchhoff stress from compressible neo-Hookean
+ *     hyperelasticity (Sec. 2.3.2) or finite-strain J2 plasticity with
+ *     exponential-map return (Sec. 2.3.3),
+ *   - the symmetric momentum sum with artificial viscosity (Sec. 2.4,
+ *     eq. MomentumEqTLSPH, eq. artViscCoef),
+ *   - the hyperbolic phase-field damage and its degradation of the stress
+ *     (Sec. 2.2, eq. phasefieldddot, eq. phasefieldLapLacian),
+ *   - the explicit update of Algorithm 1 with velocity / force boundary
+ *     conditions (Sec. 2.5, Sec. 3.3.2) and the step bound eq. dt_criterion.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a tlsph_status and never aborts the process.  On an
+ *     error, tlsph_last_error() returns a one-line description.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     needs and keeps no pointer to caller memory after a call returns.
+ *     The library owns all device memory of a context and frees it in
+ *     tlsph_destroy().
+ *   - Particle arrays are in the caller's order (particle p = row p) on input
+ *     and on output; the library reorders internally (cell-sorted) and maps
+ *     back.  Vectors are `dim` consecutive doubles per particle; tensors are
+ *     9 doubles per particle, row-major 3x3 (plane strain embeds 2D in 3D with
+ *     F_zz = 1).
+ *   - Calls out of order return TLSPH_ERR_STATE (e.g. step before
+ *     build_ref_neighbours).  Calls on one context must not overlap.
+ *   - Work is enqueued on the context's CUDA stream; calls that return data
+ *     to the host synchronise that stream.
+ */
+#ifndef TLSPH_H
+#define TLSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlsph_ctx tlsph_ctx;
+
+typedef enum {
+    TLSPH_OK = 0,
+    TLSPH_ERR_ARG = -1,          /* invalid argument (null pointer, bad size, bad parameter) */
+    TLSPH_ERR_CUDA = -2,         /* a CUDA runtime call failed (no device, launch error, ...) */
+    TLSPH_ERR_OOM = -3,          /* device allocation failed */
+    TLSPH_ERR_SINGULAR_L = -4,   /* a particle's correction matrix is singular (too few neighbours) */
+    TLSPH_ERR_NONFINITE = -5,    /* a non-finite stress / acceleration was produced */
+    TLSPH_ERR_NOCONVERGE = -6,   /* the J2 return map failed to bracket or converge for some particle */
+    TLSPH_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up */
+    TLSPH_ERR_STATE = -8         /* call out of order */
+} tlsph_status;
+
+/* precision of the step */
+enum {
+    TLSPH_FP64 = 0,      /* every field and sum in FP64 */
+    TLSPH_FP32_U64 = 1   /* FP32 fields and neighbour sums, FP64 displacement accumulation */
+};
+/* time step, eq. dt_criterion (C_CFL = params.cfl) */
+enum {
+    TLSPH_DT_FIXED = 0,      /* params.fixed_dt for every specimen */
+    TLSPH_DT_ADAPTIVE = 1,   /* C min(h / (c + |v|max), sqrt(h / |a|max)) from the previous step, per specimen */
+    TLSPH_DT_CFL_STATIC = 2  /* C h / c per specimen (c = max sound speed of its materials) */
+};
+/* constitutive models (Sec. 3.3 <constitmodel>) */
+enum { TLSPH_MODEL_NH = 2, TLSPH_MODEL_J2 = 3 };
+/* boundary-condition kinds (Sec. 3.3.2 <bcvel>, <bcforce type=1|2|3>) */
+enum {
+    TLSPH_BC_VEL = 0,        /* masked velocity components are set to value * ramp(t_{n+1}) */
+    TLSPH_BC_TRACTION = 1,   /* a += value * ramp(t_n) * area / m_i   (type 2, N/m^2) */
+    TLSPH_BC_ACCEL = 2,      /* a += value * ramp(t_n)                (type 3, m/s^2) */
+    TLSPH_BC_POINTFORCE = 3  /* a += value * ramp(t_n) / (count * m_i) (type 1, N, shared by the masked particles) */
+};
+/* fields for tlsph_read_state / tlsph_write_state */
+enum {
+    TLSPH_FIELD_U = 0,      /* displacement, dim doubles per particle (read/write) */
+    TLSPH_FIELD_V = 1,      /* velocity, dim doubles (read/write) */
+    TLSPH_FIELD_X = 2,      /* current position X0 + u, dim doubles (read) */
+    TLSPH_FIELD_S = 3,      /* phase field s, 1 double (read/write) */
+    TLSPH_FIELD_SDOT = 4,   /* ds/dt, 1 double (read/write) */
+    TLSPH_FIELD_H = 5,      /* history functional H, 1 double (read/write) */
+    TLSPH_FIELD_EPSP = 6,   /* equivalent plastic strain, 1 double (read/write) */
+    TLSPH_FIELD_P = 7,      /* first Piola-Kirchhoff stress at the current state, 9 doubles (read) */
+    TLSPH_FIELD_F = 8,      /* deformation gradient at the current state, 9 doubles (read) */
+    TLSPH_FIELD_ACC = 11,   /* acceleration of the last step, dim doubles (read) */
+    TLSPH_FIELD_CPINV = 12, /* plastic state C_p^-1 = F_p^-1 F_p^-T, 9 doubles (read/write) */
+    TLSPH_FIELD_STATE = 100 /* opaque checkpoint blob of the whole evolving state (read/write, see tlsph_field_bytes) */
+};
+
+typedef struct {
+    int dim;            /* 2 (plane strain, x-y plane) or 3 */
+    int precision;      /* TLSPH_FP64 or TLSPH_FP32_U64 */
+    int integrator;     /* 1 = Algorithm 1 (the only one supported) */
+    double h;           /* smoothing length (Wendland C2, support R = support * h) */
+    double support;     /* 2.0 for Wendland C2 */
+    double cfl;         /* C_CFL */
+    int dt_mode;        /* TLSPH_DT_* */
+    double fixed_dt;    /* step for TLSPH_DT_FIXED */
+    double gravity[3];  /* body force per unit mass */
+    void *cuda_stream;  /* cudaStream_t to enqueue on; NULL = a stream the context creates */
+    int device;         /* CUDA device ordinal */
+} tlsph_params;
+
+typedef struct {
+    int model;          /* TLSPH_MODEL_NH or TLSPH_MODEL_J2 */
+    double rho, E, nu;  /* reference density, Young's modulus, Poisson's ratio */
+    double sigma_y0;    /* J2: initial yield stress */
+    double H_hard;      /* J2: linear hardening modulus */
+    double beta1, beta2;/* artificial viscosity factors (eq. artViscCoef) */
+    int fracture;       /* phase-field fracture on/off (ignored for J2, Sec. 3.3.1) */
+    double Gc, eps0;    /* critical energy release rate, phase-field length scale */
+    double s_lim;       /* soft-particle threshold s_l (eq. defGrad_phase) */
+} tlsph_material;
+
+typedef struct {
+    int64_t steps;          /* steps taken */
+    int64_t kernel_launches;/* kernels this context has launched */
+    int64_t noconverge;     /* J2 return maps that did not converge (cumulative) */
+    int64_t nonfinite;      /* particles with a non-finite stress or acceleration (cumulative) */
+    int64_t nnz;            /* neighbour pairs (directed) */
+    int64_t max_row;        /* largest neighbour count */
+    double bytes_per_step;  /* algorithmic HBM bytes of one step of this configuration */
+} tlsph_info;
+
+/* Create a context.  params is copied.  Errors: ERR_ARG (bad dim/h/precision),
+ * ERR_CUDA (device not available).  *out is NULL on error. */
+tlsph_status tlsph_create(const tlsph_params *params, tlsph_ctx **out);
+/* Free every device and host resource of the context (NULL is allowed). */
+void tlsph_destroy(tlsph_ctx *ctx);
+/* One-line description of the last error on this context ("" if none). */
+const char *tlsph_last_error(const tlsph_ctx *ctx);
+
+/* Material table (Sec. 3.3 keyword list); n >= 1, at most 65535 entries.
+ * Lame constants follow from (E, nu); kappa = lambda + 2 mu / 3 (Sec. 2.2). */
+tlsph_status tlsph_set_materials(tlsph_ctx *ctx, int n, const tlsph_material *materials);
+
+/* Particles in the reference configuration.  X0: n*dim doubles; vol: n
+ * reference volumes V0 (2D: area x unit thickness); v0: n*dim initial
+ * velocities or NULL (zero); material_id: n indices into the material table;
+ * specimen_id: n ids >= 0 of independent specimens or NULL (one specimen).
+ * Particles of different specimens never interact and each specimen has its
+ * own time and step size.  Resets boundary conditions and notches. */
+tlsph_status tlsph_create_particles(tlsph_ctx *ctx, int64_t n, const double *X0, const double *vol, const double *v0,
+                                    const int32_t *material_id, const int32_t *specimen_id);
+
+/* Boundary condition (Sec. 3.3.2) on the particles with mask[p] != 0 (n bytes).
+ * comp_mask bit k selects component k; value[3] in SI units; active for
+ * t_start <= t <= t_end (t_end < 0: no end), linearly ramped from 0 over
+ * ramp seconds after t_start (ramp <= 0: step); area is the surface area per
+ * particle for TLSPH_BC_TRACTION.  At most 4 conditions may cover one particle. */
+tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int comp_mask, const double value[3],
+                          double t_start, double t_end, double ramp, double area);
+
+/* Pre-existing notch (Sec. 3.3.1): quad[12] = p1..p4 (x, y, z).  3D: the
+ * planar convex quad p1..p4; 2D: the segment p1-p2 (x, y).  A reference bond
+ * whose segment crosses the notch inside it (relative margin 1e-9) is removed.
+ * At most 512 notches. */
+tlsph_status tlsph_add_notch(tlsph_ctx *ctx, const double quad[12]);
+
+/* Reference setup, once (Sec. 2.4): cell keys floor((X0 - Xmin) / (R (1 + 2^-10))),
+ * stable sort by (specimen, cell, id), neighbour lists {j != i : |X0j - X0i|^2 < R^2}
+ * (FP64, fixed summation order, no FMA) minus notch-crossing bonds, the correction
+ * tensors and the initial state.  Errors: ERR_SINGULAR_L if a correction matrix is
+ * singular, ERR_OOM, ERR_CUDA.  Calling it again rebuilds from the reference state. */
+tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *ctx);
+
+/* Advance every specimen by nsteps steps of Algorithm 1 (2 kernels per step),
+ * then synchronise and report device status: ERR_NONFINITE or ERR_NOCONVERGE
+ * if that happened in these steps (the state is still advanced). */
+tlsph_status tlsph_step(tlsph_ctx *ctx, int64_t nsteps);
+/* As tlsph_step but only enqueues the work (no synchronisation, no status). */
+tlsph_status tlsph_step_async(tlsph_ctx *ctx, int64_t nsteps);
+/* Synchronise the context's stream and report device status as tlsph_step. */
+tlsph_status tlsph_sync(tlsph_ctx *ctx);
+
+/* Copy a field in the caller's particle order into dst (bytes must equal
+ * tlsph_field_bytes(ctx, field)); dst is host memory, or device memory if
+ * dst_is_device.  F and P are evaluated at the current state without
+ * advancing it (J2: a trial return map from the stored plastic state). */
+tlsph_status tlsph_read_state(tlsph_ctx *ctx, int field, void *dst, size_t bytes, int dst_is_device);
+/* Overwrite a writable field from src (caller's order), see the field list. */
+tlsph_status tlsph_write_state(tlsph_ctx *ctx, int field, const void *src, size_t bytes, int src_is_device);
+/* Size in bytes of a field as read / written by the two calls above (-1 on error). */
+int64_t tlsph_field_bytes(const tlsph_ctx *ctx, int field);
+
+/* Energies of the current state (Sec. 3.5 energy tracking), FP64:
+ * out[0] kinetic sum m |v|^2 / 2, out[1] strain sum V psi_e (degraded),
+ * out[2] fracture sum V Gc ((1 - s)^2 / (4 eps0) + eps0 |grad s|^2),
+ * out[3] plastic work sum V (sigma_y0 eps_p + H eps_p^2 / 2),
+ * out[4] time of specimen 0, out[5] current step size of specimen 0. */
+tlsph_status tlsph_energies(tlsph_ctx *ctx, double out[6]);
+
+/* Time and current step size of one specimen. */
+tlsph_status tlsph_time(tlsph_ctx *ctx, int specimen, double *t, double *dt);
+
+/* Neighbour lists in the caller's order: row_ptr[n + 1] (int64) and col[cap]
+ * (int32 original ids, each row ascending).  cap >= tlsph_nnz(ctx). */
+tlsph_status tlsph_neighbours(tlsph_ctx *ctx, int64_t *row_ptr, int32_t *col, int64_t cap);
+/* Cell-sorted order: perm[k] = caller id of the k-th particle (n int64). */
+tlsph_status tlsph_permutation(tlsph_ctx *ctx, int64_t *perm);
+/* Number of directed neighbour pairs (-1 before the reference setup). */
+int64_t tlsph_nnz(const tlsph_ctx *ctx);
+
+/* Counters and sizes of the context. */
+tlsph_status tlsph_get_info(tlsph_ctx *ctx, tlsph_info *out);
+
+/* Options (value 0 = off, default; 1 = on):
+ *  TLSPH_OPT_KERNEL_TIMING: bracket every kernel of tlsph_step with CUDA events on the
+ *    context's stream; tlsph_kernel_times returns the summed milliseconds and launch
+ *    counts of the force-and-damage pass (ms[0], count[0]) and of the
+ *    deformation-gradient / stress pass (ms[1], count[1]) since the last call.
+ *  TLSPH_OPT_RECORD_ACC: keep the acceleration of each step for TLSPH_FIELD_ACC. */
+enum { TLSPH_OPT_KERNEL_TIMING = 1, TLSPH_OPT_RECORD_ACC = 2 };
+tlsph_status tlsph_set_option(tlsph_ctx *ctx, int option, int value);
+tlsph_status tlsph_kernel_times(tlsph_ctx *ctx, double ms[2], int64_t count[2]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLSPH_H */

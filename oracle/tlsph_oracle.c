@@ -584,7 +584,10 @@ static int notch_cuts(const orc_ctx *c, const double *P, const double *Q) {
 static int is_neighbour(const orc_ctx *c, int64_t i, int64_t j, double R2) {
     if (i == j || c->spec[i] != c->spec[j]) return 0;
     if (!(ref_r2(c, i, j) < R2)) return 0;
-    if (c->nnotch && notch_cuts(c, &c->X0[3 * i], &c->X0[3 * j])) return 0;
+    /* the segment is always taken from the lower to the higher id, so the
+     * relation stays symmetric whatever the rounding */
+    int64_t a = i < j ? i : j, b = i < j ? j : i;
+    if (c->nnotch && notch_cuts(c, &c->X0[3 * a], &c->X0[3 * b])) return 0;
     return 1;
 }
 

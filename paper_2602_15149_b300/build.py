@@ -1,0 +1,41 @@
+"""Build the sm_103a CUDA library ``_lib/libtlsph.so`` in-tree with nvcc."""
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB = os.path.join(HERE, "_lib", "libtlsph.so")
+SOURCES = [os.path.join(HERE, "csrc", "tlsph_capi.cu")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _inputs():
+    return glob.glob(os.path.join(HERE, "csrc", "*")) + [os.path.join(ROOT, "include", "tlsph.h")]
+
+
+def nvcc_command(out: str = LIB, extra=()):
+    return (["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+             "-ffp-contract=off", "-shared", "-o", out, *SOURCES] + list(extra))
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Compile if the library is missing or older than any source; return its path."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if not force and os.path.exists(LIB):
+        t = os.path.getmtime(LIB)
+        if all(os.path.getmtime(p) <= t for p in _inputs()):
+            return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = nvcc_command(tmp)
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_library(force=True, verbose=True))

@@ -1,0 +1,81 @@
+// Shared device types of the TLSPH library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "constitutive.cuh"
+
+namespace tl {
+
+template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
+
+__device__ __forceinline__ V4<float> ldg4(const V4<float> *p) {
+    float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+    return V4<float>{f.x, f.y, f.z, f.w};
+}
+__device__ __forceinline__ V4<double> ldg4(const V4<double> *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return V4<double>{a.x, a.y, b.x, b.y};
+}
+
+// Boundary condition record (Sec. 3.3.2).
+struct BCDev {
+    int kind, comp_mask;
+    double value[3];
+    double t_start, t_end, ramp, area, inv_count;
+};
+constexpr int kMaxBcPerParticle = 4;
+
+// factor of a condition at time t: < 0 when inactive, else the ramp value in [0, 1]
+__device__ __forceinline__ double bc_factor(const BCDev &b, double t) {
+    if (t < b.t_start) return -1.0;
+    if (b.t_end >= 0.0 && t > b.t_end) return -1.0;
+    if (b.ramp > 0.0) {
+        double f = (t - b.t_start) / b.ramp;
+        return f < 1.0 ? f : 1.0;
+    }
+    return 1.0;
+}
+
+enum { kFlagNonfinite = 0, kFlagNoconv = 1, kFlagSingular = 2, kFlagRowOverflow = 3, kNumFlags = 8 };
+
+// All pointers of a step (device memory, cell-sorted order).
+template <typename T> struct StepArgs {
+    int n;
+    const int64_t *slice_off;
+    const int *row_len;
+    const int *col;
+    const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
+    const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, -)
+    V4<T> *ug_next;
+    const V4<T> *vs_cur;   // (vx, vy, vz, s)
+    V4<T> *vs_next;
+    V4<T> *Q;              // P_i Ahat_i: 3D 3 records (9 values + m0 in [2].y), 2D 1 record
+    T *Vm;                 // J F^-T Ahat, dim*dim arrays of n
+    const T *Ahat;         // inverse of sum V w d d^T: 6 arrays of n (2D uses xx, yy, xy)
+    T *K;                  // J2 state C_p^-1 - I, 6 arrays of n
+    T *ep;                 // equivalent plastic strain
+    T *H;                  // history functional
+    T *sdot;               // phase-field rate
+    double *u64;           // FP64 displacement, 3 arrays of n
+    const uint16_t *mid;
+    const int *spec;
+    const uint16_t *bcgrp;     // 0 = no condition, else group g -> grp_bcs[4 g .. 4 g + 3]
+    const int16_t *grp_bcs;
+    const BCDev *bcs;
+    const MatT<T> *mats;
+    double *t, *dt, *cmax;     // per specimen
+    unsigned long long *vmax_bits, *amax_bits;  // per specimen, bits of a non-negative double
+    double *last_vmax, *last_amax;
+    unsigned int *done;
+    int *flags;
+    int nspec, dt_mode;
+    double hd, cfl, fixed_dt;
+    T h, inv2h, visc_eps;
+    T grav[3];
+    // diagnostics (may be null)
+    T *Fout, *Pout, *psi_out, *acc_out;
+};
+
+}  // namespace tl

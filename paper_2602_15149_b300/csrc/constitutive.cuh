@@ -1,0 +1,321 @@
+// Constitutive updates of the TLSPH step (device code).
+//
+// Both models take the displacement gradient G = F - I (so that small
+// strains keep their relative precision in FP32) and return the second
+// Piola-Kirchhoff stress S.
+//
+//  * Neo-Hookean with the J-split of the phase-field degradation (Sec. 2.3.2):
+//      S = s^2 (Svol + Siso)       J >= 1
+//      S = Svol + s^2 Siso         J <  1
+//    Svol = kappa/2 (J^2 - 1) C^-1, Siso = mu J^-2/3 (I - tr(C)/3 C^-1).  The
+//    stress is the derivative of the stated energy with respect to C/2 (the
+//    printed formula writes b^-1; C^-1 is the frame-indifferent derivative).
+//  * Finite-strain J2 plasticity (Sec. 2.3.3).  The plastic state is kept as
+//    C_p^-1 = F_p^-1 F_p^-T (stored as K = C_p^-1 - I): the stress, the trial
+//    state and the exponential-map update depend on F_p only through it.
+//    With A = C_p^-1 C (similar to the elastic C_e), the trial flow direction
+//    commutes with A, so the residual of the return map (eq. J2_residual) is a
+//    scalar function of the eigenvalues of A; the Illinois / regula-falsi
+//    iteration with bracket doubling runs on that scalar, and the accepted
+//    increment updates C_p^-1 <- exp(-2 dgamma N~) C_p^-1 with a scaling and
+//    squaring Taylor series, followed by the isochoric projection det = 1.
+#pragma once
+#include "tensor3.cuh"
+
+namespace tl {
+
+template <typename T> struct MatT {
+    int model;      // 2 NH, 3 J2
+    int fracture;   // phase field on
+    T rho, mu, kappa, sy0, Hh, beta1, beta2, c0, Gc, eps0, s_lim, mass_scale;
+};
+
+// x + x^2/2 - log(1 + x) (= (J^2 - 1)/2 - ln J with x = J - 1), series near 0
+template <typename T> __device__ __forceinline__ T xp_minus_log(T x) {
+    if (t_abs(x) < T(0.01)) {
+        // x^2 - x^3/3 + x^4/4 - ... - x^11/11
+        T r = T(-1.0 / 11.0);
+        r = r * x + T(1.0 / 10.0);
+        r = r * x - T(1.0 / 9.0);
+        r = r * x + T(1.0 / 8.0);
+        r = r * x - T(1.0 / 7.0);
+        r = r * x + T(1.0 / 6.0);
+        r = r * x - T(1.0 / 5.0);
+        r = r * x + T(1.0 / 4.0);
+        r = r * x - T(1.0 / 3.0);
+        r = r * x + T(1.0);
+        return r * x * x;
+    }
+    return x + T(0.5) * x * x - t_log1p(x);
+}
+
+// Kinematics shared by both models.
+template <typename T> struct Kin {
+    M3<T> E2;    // C - I = G + G^T + G^T G
+    M3<T> Ci;    // C^-1
+    T Jm1;       // J - 1
+    T Jm23;      // J^-2/3
+    T Jm23m1;    // J^-2/3 - 1
+};
+template <typename T> __device__ __forceinline__ Kin<T> kinematics(const M3<T> &G) {
+    Kin<T> k;
+    k.E2 = mul_tn(G, G);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) k.E2.a[3 * i + j] += G.a[3 * i + j] + G.a[3 * j + i];
+    k.Jm1 = det_eye_plus_m1(G);
+    M3<T> C = k.E2;
+    C.a[0] += T(1);
+    C.a[4] += T(1);
+    C.a[8] += T(1);
+    inverse(C, k.Ci);
+    T lJ = t_log1p(k.Jm1);
+    k.Jm23m1 = t_expm1(T(-2.0 / 3.0) * lJ);
+    k.Jm23 = T(1) + k.Jm23m1;
+    return k;
+}
+
+// Neo-Hookean stress and energy split.  psi_plus / psi_minus of eq. ksipNH / ksinNH.
+template <typename T>
+__device__ __forceinline__ void nh_stress(const Kin<T> &k, T s, const MatT<T> &m, M3<T> &S, T &psi_plus, T &psi_minus) {
+    T trE2 = trace(k.E2);
+    M3<T> dE = k.E2;
+    dE.a[0] -= trE2 / T(3);
+    dE.a[4] -= trE2 / T(3);
+    dE.a[8] -= trE2 / T(3);
+    // Siso = mu J^-2/3 (I - tr C / 3 C^-1) = mu J^-2/3 C^-1 dev(C - I)
+    M3<T> Siso = sym_part(mul(k.Ci, dE));
+    T fi = m.mu * k.Jm23;
+    T fv = T(0.5) * m.kappa * k.Jm1 * (k.Jm1 + T(2));
+    T U = T(0.5) * m.kappa * xp_minus_log(k.Jm1);
+    T psibar = T(0.5) * m.mu * (T(3) * k.Jm23m1 + k.Jm23 * trE2);
+    T s2 = s * s;
+    T cv, ci;
+    if (k.Jm1 >= T(0)) {
+        cv = s2 * fv;
+        ci = s2 * fi;
+        psi_plus = U + psibar;
+        psi_minus = T(0);
+    } else {
+        cv = fv;
+        ci = s2 * fi;
+        psi_plus = psibar;
+        psi_minus = U;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; q++) S.a[q] = cv * k.Ci.a[q] + ci * Siso.a[q];
+}
+
+// Eigenvalues of a traceless 3x3 matrix with real spectrum (trigonometric form).
+template <typename T> __device__ __forceinline__ void eig_traceless(const M3<T> &B, T q2, T e[3]) {
+    T p = q2 / T(6);
+    if (!(p > T(0))) {
+        e[0] = e[1] = e[2] = T(0);
+        return;
+    }
+    T q = T(0.5) * det(B);
+    T sp = t_sqrt(p);
+    T r = q / (p * sp);
+    r = t_min(T(1), t_max(T(-1), r));
+    T phi = t_acos(r) / T(3);
+    T two_sp = T(2) * sp;
+    e[0] = two_sp * t_cos(phi);
+    e[1] = two_sp * t_cos(phi + T(2.0943951023931953));
+    e[2] = -e[0] - e[1];
+}
+
+// exp(X) - I by scaling and squaring of a Taylor series (order 6 in FP32, 12 in FP64).
+template <typename T> __device__ __forceinline__ M3<T> expm1_mat(const M3<T> &X) {
+    T nrm2 = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) nrm2 += X.a[q] * X.a[q];
+    int ks = 0;
+    T scale = T(1);
+    while (nrm2 * scale * scale > T(1.0 / 64.0) && ks < 40) {
+        scale *= T(0.5);
+        ks++;
+    }
+    M3<T> B;
+#pragma unroll
+    for (int q = 0; q < 9; q++) B.a[q] = X.a[q] * scale;
+    constexpr int order = sizeof(T) == 4 ? 6 : 12;
+    // Horner: E1 = B (I + B/2 (I + B/3 (... (I + B/order))))
+    M3<T> R = m3_eye<T>();
+#pragma unroll
+    for (int m = order; m >= 2; m--) {
+        M3<T> t = mul(B, R);
+        T inv = T(1) / T(m);
+#pragma unroll
+        for (int q = 0; q < 9; q++) R.a[q] = t.a[q] * inv;
+        R.a[0] += T(1);
+        R.a[4] += T(1);
+        R.a[8] += T(1);
+    }
+    M3<T> E1 = mul(B, R);
+    for (int s = 0; s < ks; s++) {  // expm1(2Y) = E1 (E1 + 2 I)
+        M3<T> sq = mul(E1, E1);
+#pragma unroll
+        for (int q = 0; q < 9; q++) E1.a[q] = T(2) * E1.a[q] + sq.a[q];
+    }
+    return E1;
+}
+
+template <typename T> struct J2Tol;
+template <> struct J2Tol<float> {
+    static constexpr float res = 1e-5f, width = 1e-7f;
+    static constexpr int maxit = 100;
+};
+template <> struct J2Tol<double> {
+    static constexpr double res = 1e-10, width = 1e-14;
+    static constexpr int maxit = 100;
+};
+
+// Residual r(dgamma) of eq. J2_residual in the eigenbasis of A = C_p^-1 C.
+template <typename T> struct J2Res {
+    T delta[3], n[3], c_eq, sy0, Hh, epn;
+    __device__ __forceinline__ T operator()(T dg) const {
+        T dp[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) dp[a] = delta[a] + (T(1) + delta[a]) * t_expm1(T(-2) * dg * n[a]);
+        T mean = (dp[0] + dp[1] + dp[2]) / T(3);
+        T s2 = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; a++) s2 += (dp[a] - mean) * (dp[a] - mean);
+        return c_eq * t_sqrt(s2) - (sy0 + Hh * (epn + dg));
+    }
+};
+
+// J2 update.  K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.  Returns 0, or 1 if the
+// bracket / iteration did not converge (the state is still updated with the last iterate).
+template <typename T>
+__device__ __forceinline__ int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6out[6], T &ep_out,
+                                         M3<T> &S, T &dgamma) {
+    M3<T> K;
+    K.a[0] = K6[0]; K.a[4] = K6[1]; K.a[8] = K6[2];
+    K.a[1] = K.a[3] = K6[3];
+    K.a[2] = K.a[6] = K6[4];
+    K.a[5] = K.a[7] = K6[5];
+    // D = A - I = K + E2 + K E2
+    M3<T> D = mul(K, k.E2);
+#pragma unroll
+    for (int q = 0; q < 9; q++) D.a[q] += K.a[q] + k.E2.a[q];
+    T trD3 = trace(D) / T(3);
+    M3<T> dev = D;
+    dev.a[0] -= trD3;
+    dev.a[4] -= trD3;
+    dev.a[8] -= trD3;
+    T q2 = t_max(trace_mul(dev, dev), T(0));
+    T c_eq = T(1.2247448713915890) * m.mu * k.Jm23;  // sqrt(3/2) mu J^-2/3
+    T sig_tr = c_eq * t_sqrt(q2);
+    T syn = m.sy0 + m.Hh * ep;
+    T f = sig_tr - syn;
+    int status = 0;
+    T dg = T(0);
+#pragma unroll
+    for (int q = 0; q < 6; q++) K6out[q] = K6[q];
+    if (f > T(0)) {
+        J2Res<T> r;
+        T e[3];
+        eig_traceless(dev, q2, e);
+        T kn = T(1.5) * m.mu * k.Jm23 / sig_tr;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r.delta[a] = e[a] + trD3;
+            r.n[a] = kn * e[a];
+        }
+        r.c_eq = c_eq;
+        r.sy0 = m.sy0;
+        r.Hh = m.Hh;
+        r.epn = ep;
+        // bracket: L = 0, R = max((sigma_tr - sigma_y) / (3 mu + H), eps), doubled until r(R) <= 0
+        T L = T(0), rL = f;
+        T eps_b = T(1e-12) * syn / m.mu;
+        T R = t_max(f / (T(3) * m.mu + m.Hh), eps_b);
+        T rR = r(R);
+        for (int nd = 0; rR > T(0) && nd < 60; nd++) {
+            R *= T(2);
+            rR = r(R);
+        }
+        if (!(rR <= T(0))) status = 1;
+        T x = R;
+        if (rR != T(0) && status == 0) {
+            int it = 0;
+            for (; it < J2Tol<T>::maxit; it++) {
+                T den = rR - rL;
+                x = den != T(0) ? R - rR * (R - L) / den : T(0.5) * (L + R);
+                T rx = r(x);
+                if (t_abs(rx) <= J2Tol<T>::res * m.sy0 || t_abs(R - L) <= J2Tol<T>::width * t_abs(R)) break;
+                if ((rx < T(0) && rR > T(0)) || (rx > T(0) && rR < T(0))) {
+                    L = R;
+                    rL = rR;
+                } else {
+                    rL = T(0.5) * rL;
+                }
+                R = x;
+                rR = rx;
+            }
+            if (it == J2Tol<T>::maxit) status = 1;
+        }
+        dg = x;
+        // C_p^-1 <- exp(-2 dg N~) C_p^-1, N~ = (3 mu J^-2/3 / (2 sigma_tr)) dev(A)
+        M3<T> X;
+        T sc = T(-2) * dg * kn;
+#pragma unroll
+        for (int q = 0; q < 9; q++) X.a[q] = sc * dev.a[q];
+        M3<T> E1 = expm1_mat(X);
+        M3<T> E1K = mul(E1, K);
+        M3<T> Kn;
+#pragma unroll
+        for (int q = 0; q < 9; q++) Kn.a[q] = K.a[q] + E1.a[q] + E1K.a[q];
+        Kn = sym_part(Kn);
+        // isochoric projection det(C_p^-1) = 1
+        T detm1 = det_eye_plus_m1(Kn);
+        T fm1 = t_expm1(-t_log1p(detm1) / T(3));
+#pragma unroll
+        for (int q = 0; q < 9; q++) Kn.a[q] = Kn.a[q] * (T(1) + fm1);
+        Kn.a[0] += fm1;
+        Kn.a[4] += fm1;
+        Kn.a[8] += fm1;
+        K = Kn;
+        K6out[0] = K.a[0]; K6out[1] = K.a[4]; K6out[2] = K.a[8];
+        K6out[3] = K.a[1]; K6out[4] = K.a[2]; K6out[5] = K.a[5];
+        // stress from the updated state
+        D = mul(K, k.E2);
+#pragma unroll
+        for (int q = 0; q < 9; q++) D.a[q] += K.a[q] + k.E2.a[q];
+        trD3 = trace(D) / T(3);
+        dev = D;
+        dev.a[0] -= trD3;
+        dev.a[4] -= trD3;
+        dev.a[8] -= trD3;
+    }
+    ep_out = ep + dg;
+    dgamma = dg;
+    // S = mu J^-2/3 (C_p^-1 - tr(A)/3 C^-1) + kappa/2 (J^2 - 1) C^-1 = mu J^-2/3 C^-1 dev(D)^T + ...
+    M3<T> Siso = sym_part(mul(k.Ci, transpose(dev)));
+    T fi = m.mu * k.Jm23;
+    T fv = T(0.5) * m.kappa * k.Jm1 * (k.Jm1 + T(2));
+#pragma unroll
+    for (int q = 0; q < 9; q++) S.a[q] = fi * Siso.a[q] + fv * k.Ci.a[q];
+    return status;
+}
+
+// Strain energy of the J2 model, psi_vol(J) + psi_iso(Cbar_e) (evaluated at a given C_p^-1).
+template <typename T> __device__ __forceinline__ T j2_energy(const Kin<T> &k, const T K6[6], const MatT<T> &m) {
+    // tr(C_e) = tr(C_p^-1 C) = 3 + tr(D)
+    M3<T> K;
+    K.a[0] = K6[0]; K.a[4] = K6[1]; K.a[8] = K6[2];
+    K.a[1] = K.a[3] = K6[3];
+    K.a[2] = K.a[6] = K6[4];
+    K.a[5] = K.a[7] = K6[5];
+    M3<T> D = mul(K, k.E2);
+#pragma unroll
+    for (int q = 0; q < 9; q++) D.a[q] += K.a[q] + k.E2.a[q];
+    T trD = trace(D);
+    T vol = T(0.5) * m.kappa * xp_minus_log(k.Jm1);
+    T iso = T(0.5) * m.mu * (T(3) * k.Jm23m1 + k.Jm23 * trD);
+    return vol + iso;
+}
+
+}  // namespace tl

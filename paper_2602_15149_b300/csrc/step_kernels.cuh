@@ -1,0 +1,577 @@
+// The two kernels of one TLSPH step (Algorithm 1) and their diagnostics.
+//
+// Pass 1 (one thread per particle, SELL-32 neighbour slices):
+//   F_i = I + B_i Ahat_i,  B_i = sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T
+// which is eq. deformGradTLSPH with the corrected gradient L_i gradW_ij =
+// w_ij Ahat_i (X_j - X_i); soft particles (s_i <= s_l) take F = I
+// (eq. defGrad_phase).  Then the stress (NH / J2), the history functional,
+// and the per-particle matrices pass 2 needs:
+//   Q_i = P_i Ahat_i,  Vm_i = J_i F_i^-T Ahat_i.
+// Pass 2 (same layout):
+//   a_i = (1/rho_i) [Q_i sum_j V_j w d + sum_j V_j w Q_j d]   (eq. MomentumEqTLSPH, symmetric form)
+//       - Vm_i sum_j m_j pi_ij w d                            (eq. artViscCoef, Pv = -J pi F^-T)
+//   lap s_i = -2 Ahat_i : sum_j (s_i - s_j) V_j w d d^T / r^2  (eq. phasefieldLapLacian)
+// plus body and boundary forces, the phase-field acceleration
+// (eq. phasefieldddot), the Algorithm 1 update, and the per-specimen maxima of
+// |v| and |a| for the next step size; the last block to finish advances the
+// specimen clocks (eq. dt_criterion).
+#pragma once
+#include "common.cuh"
+
+namespace tl {
+
+template <typename T, int DIM> __device__ __forceinline__ void load_ahat(const T *Ahat, int n, int i, T A[3][3]) {
+    if (DIM == 3) {
+        A[0][0] = Ahat[i];
+        A[1][1] = Ahat[n + i];
+        A[2][2] = Ahat[2 * n + i];
+        A[0][1] = A[1][0] = Ahat[3 * n + i];
+        A[0][2] = A[2][0] = Ahat[4 * n + i];
+        A[1][2] = A[2][1] = Ahat[5 * n + i];
+    } else {
+        A[0][0] = Ahat[i];
+        A[1][1] = Ahat[n + i];
+        A[0][1] = A[1][0] = Ahat[3 * n + i];
+    }
+}
+
+template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
+
+// ---------------------------------------------------------------- pass 1
+template <typename T, int DIM, bool FRAC, bool DIAG>
+__global__ void __launch_bounds__(128) k_pass1(StepArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int n = a.n;
+    const int64_t base = a.slice_off[i >> 5] + (i & 31);
+    const int len = a.row_len[i];
+    const V4<T> xi = a.X0V[i];
+    const V4<T> ui = a.ug_cur[i];
+    T B[DIM][DIM];
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) B[p][q] = T(0);
+    const int *cp = a.col + base;
+    for (int k = 0; k < len; k++) {
+        const int j = __ldg(cp + 32 * k);
+        const V4<T> xj = ldg4(a.X0V + j);
+        const V4<T> uj = ldg4(a.ug_cur + j);
+        T d[DIM], du[DIM];
+        d[0] = xj.x - xi.x;
+        d[1] = xj.y - xi.y;
+        du[0] = uj.x - ui.x;
+        du[1] = uj.y - ui.y;
+        if (DIM == 3) {
+            d[DIM - 1] = xj.z - xi.z;
+            du[DIM - 1] = uj.z - ui.z;
+        }
+        T r2 = d[0] * d[0] + d[1] * d[1];
+        if (DIM == 3) r2 += d[DIM - 1] * d[DIM - 1];
+        const T t = t_max(T(1) - t_sqrt(r2) * a.inv2h, T(0));
+        const T Vj = DIM == 3 ? xj.w : xj.z;
+        const T aw = t * t * t * Vj;
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            const T c = aw * du[p];
+#pragma unroll
+            for (int q = 0; q < DIM; q++) B[p][q] += c * d[q];
+        }
+    }
+    T A[3][3];
+    load_ahat<T, DIM>(a.Ahat, n, i, A);
+    M3<T> G = m3_zero<T>();
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            T s = T(0);
+#pragma unroll
+            for (int r = 0; r < DIM; r++) s += B[p][r] * A[r][q];
+            G(p, q) = s;
+        }
+    const MatT<T> m = a.mats[a.mid[i]];
+    T s = T(1);
+    const bool frac = FRAC && m.fracture;
+    if (frac) {
+        s = a.vs_cur[i].w;
+        if (s <= m.s_lim) G = m3_zero<T>();
+    }
+    const Kin<T> kin = kinematics(G);
+    M3<T> S;
+    T psi = T(0);
+    if (m.model == 3) {
+        T K6[6], K6o[6], epo, dg;
+#pragma unroll
+        for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+        const T ep = a.ep[i];
+        const int st = j2_update(kin, K6, ep, m, K6o, epo, S, dg);
+        if (DIAG) {
+            psi = j2_energy(kin, K6o, m);
+        } else {
+            if (dg > T(0)) {
+#pragma unroll
+                for (int q = 0; q < 6; q++) a.K[q * n + i] = K6o[q];
+                a.ep[i] = epo;
+            }
+            if (st) atomicAdd(&a.flags[kFlagNoconv], 1);
+        }
+    } else {
+        T pp, pm;
+        nh_stress(kin, s, m, S, pp, pm);
+        psi = s * s * pp + pm;
+        if (!DIAG && frac && pp > a.H[i]) a.H[i] = pp;  // eq. irreversibility
+    }
+    // P = F S
+    M3<T> F = G;
+    F.a[0] += T(1);
+    F.a[4] += T(1);
+    F.a[8] += T(1);
+    const M3<T> P = mul(F, S);
+    if (DIAG) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            a.Fout[q * n + i] = F.a[q];
+            a.Pout[q * n + i] = P.a[q];
+        }
+        a.psi_out[i] = psi;
+        return;
+    }
+    // Q = P Ahat (in-plane block), Vm = J F^-T Ahat
+    M3<T> Fi;
+    inverse(F, Fi);
+    const T J = T(1) + kin.Jm1;
+    T Qm[DIM][DIM], Vm[DIM][DIM];
+    bool ok = true;
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            T s1 = T(0), s2 = T(0);
+#pragma unroll
+            for (int r = 0; r < DIM; r++) {
+                s1 += P(p, r) * A[r][q];
+                s2 += Fi(r, p) * A[r][q];
+            }
+            Qm[p][q] = s1;
+            Vm[p][q] = J * s2;
+            ok = ok && finite_t(s1) && finite_t(s2);
+        }
+    if (!ok) atomicAdd(&a.flags[kFlagNonfinite], 1);
+    if (DIM == 3) {
+        const T mi = m.rho * xi.w;
+        a.Q[3 * i] = V4<T>{Qm[0][0], Qm[0][1], Qm[0][DIM - 1], Qm[1][0]};
+        a.Q[3 * i + 1] = V4<T>{Qm[1][1], Qm[1][DIM - 1], Qm[DIM - 1][0], Qm[DIM - 1][1]};
+        a.Q[3 * i + 2] = V4<T>{Qm[DIM - 1][DIM - 1], mi, T(0), T(0)};
+    } else {
+        a.Q[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[1][0], Qm[1][1]};
+    }
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) a.Vm[(p * DIM + q) * n + i] = Vm[p][q];
+}
+
+// ---------------------------------------------------------------- pass 2
+template <typename T, int DIM, bool FRAC, bool VISC>
+__global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
+    __shared__ int s_sp;
+    __shared__ double s_v[4], s_a[4];
+    __shared__ bool s_last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < a.n;
+    const int n = a.n;
+    double vmag = 0.0, amag = 0.0;
+    int sp = 0;
+    if (active) {
+        sp = a.spec[i];
+        const int64_t base = a.slice_off[i >> 5] + (i & 31);
+        const int len = a.row_len[i];
+        const V4<T> xi = a.X0V[i];
+        const V4<T> ui = a.ug_cur[i];
+        const V4<T> vsi = a.vs_cur[i];
+        const MatT<T> m = a.mats[a.mid[i]];
+        const bool frac = FRAC && m.fracture;
+        const T irho = T(1) / m.rho;
+        const T cvis = m.beta1 * m.c0;
+        T s1[DIM], s2[DIM], s3[DIM], Tl[DIM == 3 ? 6 : 3];
+#pragma unroll
+        for (int p = 0; p < DIM; p++) s1[p] = s2[p] = s3[p] = T(0);
+#pragma unroll
+        for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
+        const int *cp = a.col + base;
+        for (int k = 0; k < len; k++) {
+            const int j = __ldg(cp + 32 * k);
+            const V4<T> xj = ldg4(a.X0V + j);
+            T d[DIM];
+            d[0] = xj.x - xi.x;
+            d[1] = xj.y - xi.y;
+            if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
+            T r2 = d[0] * d[0] + d[1] * d[1];
+            if (DIM == 3) r2 += d[DIM - 1] * d[DIM - 1];
+            const T t = t_max(T(1) - t_sqrt(r2) * a.inv2h, T(0));
+            const T w = t * t * t;
+            const T Vj = DIM == 3 ? xj.w : xj.z;
+            const T aw = w * Vj;
+            T Qd[DIM];
+            T mj;
+            if (DIM == 3) {
+                const V4<T> q0 = ldg4(a.Q + 3 * j), q1 = ldg4(a.Q + 3 * j + 1), q2 = ldg4(a.Q + 3 * j + 2);
+                Qd[0] = q0.x * d[0] + q0.y * d[1] + q0.z * d[DIM - 1];
+                Qd[1] = q0.w * d[0] + q1.x * d[1] + q1.y * d[DIM - 1];
+                Qd[DIM - 1] = q1.z * d[0] + q1.w * d[1] + q2.x * d[DIM - 1];
+                mj = q2.y;
+            } else {
+                const V4<T> q0 = ldg4(a.Q + j);
+                Qd[0] = q0.x * d[0] + q0.y * d[1];
+                Qd[1] = q0.z * d[0] + q0.w * d[1];
+                mj = xj.w;
+            }
+#pragma unroll
+            for (int p = 0; p < DIM; p++) {
+                s1[p] += aw * d[p];
+                s2[p] += aw * Qd[p];
+            }
+            if (VISC || frac) {
+                const V4<T> vsj = ldg4(a.vs_cur + j);
+                if (VISC) {
+                    const V4<T> uj = ldg4(a.ug_cur + j);
+                    T dv[DIM], dx[DIM];
+                    dv[0] = vsj.x - vsi.x;
+                    dv[1] = vsj.y - vsi.y;
+                    dx[0] = d[0] + (uj.x - ui.x);
+                    dx[1] = d[1] + (uj.y - ui.y);
+                    if (DIM == 3) {
+                        dv[DIM - 1] = vsj.z - vsi.z;
+                        dx[DIM - 1] = d[DIM - 1] + (uj.z - ui.z);
+                    }
+                    T vx = dv[0] * dx[0] + dv[1] * dx[1];
+                    T vX = dv[0] * d[0] + dv[1] * d[1];
+                    if (DIM == 3) {
+                        vx += dv[DIM - 1] * dx[DIM - 1];
+                        vX += dv[DIM - 1] * d[DIM - 1];
+                    }
+                    if (vx < T(0)) {  // pair in relative compression
+                        const T G = a.h * vX / (r2 + a.visc_eps);
+                        const T pi = (m.beta2 * G - cvis) * G * irho;
+                        const T c = mj * pi * w;
+#pragma unroll
+                        for (int p = 0; p < DIM; p++) s3[p] += c * d[p];
+                    }
+                }
+                if (frac) {
+                    const T c = (vsi.w - vsj.w) * aw / r2;
+                    Tl[0] += c * d[0] * d[0];
+                    Tl[1] += c * d[1] * d[1];
+                    if (DIM == 3) {
+                        Tl[2] += c * d[2] * d[2];
+                        Tl[3] += c * d[0] * d[1];
+                        Tl[4] += c * d[0] * d[2];
+                        Tl[5] += c * d[1] * d[2];
+                    } else {
+                        Tl[2] += c * d[0] * d[1];
+                    }
+                }
+            }
+        }
+        // own matrices
+        T Qi[DIM][DIM];
+        if (DIM == 3) {
+            const V4<T> q0 = a.Q[3 * i], q1 = a.Q[3 * i + 1], q2 = a.Q[3 * i + 2];
+            Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
+            Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
+            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = q2.x;
+        } else {
+            const V4<T> q0 = a.Q[i];
+            Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
+        }
+        T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            T f = s2[p];
+#pragma unroll
+            for (int q = 0; q < DIM; q++) f += Qi[p][q] * s1[q];
+            acc[p] = f * irho;
+            if (VISC) {
+                T v = T(0);
+#pragma unroll
+                for (int q = 0; q < DIM; q++) v += a.Vm[(p * DIM + q) * n + i] * s3[q];
+                acc[p] -= v;
+            }
+            acc[p] += a.grav[p];
+        }
+        const double t_n = a.t[sp], dt = a.dt[sp], t_1 = t_n + dt;
+        const int g = a.bcgrp[i];
+        const T mass = DIM == 3 ? m.rho * xi.w : xi.w;
+        double vset[3];
+        int vmask = 0;
+        if (g) {
+            for (int b = 0; b < kMaxBcPerParticle; b++) {
+                const int id = a.grp_bcs[4 * g + b];
+                if (id < 0) break;
+                const BCDev bc = a.bcs[id];
+                if (bc.kind == 0) {  // velocity: value at t_{n+1}
+                    const double f = bc_factor(bc, t_1);
+                    if (f < 0.0) continue;
+                    for (int p = 0; p < DIM; p++)
+                        if (bc.comp_mask & (1 << p)) {
+                            vset[p] = f * bc.value[p];
+                            vmask |= 1 << p;
+                        }
+                } else {  // forces at t_n
+                    const double f = bc_factor(bc, t_n);
+                    if (f < 0.0) continue;
+                    for (int p = 0; p < DIM; p++) {
+                        if (!(bc.comp_mask & (1 << p))) continue;
+                        const double val = f * bc.value[p];
+                        if (bc.kind == 1) acc[p] += (T)(val * bc.area / (double)mass);
+                        else if (bc.kind == 2) acc[p] += (T)val;
+                        else acc[p] += (T)(val * bc.inv_count / (double)mass);
+                    }
+                }
+            }
+        }
+        // phase field (eq. phasefieldddot)
+        T s_new = vsi.w;
+        if (frac) {
+            T A[3][3];
+            load_ahat<T, DIM>(a.Ahat, n, i, A);
+            T AT;
+            if (DIM == 3)
+                AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + A[2][2] * Tl[2] +
+                     T(2) * (A[0][1] * Tl[3] + A[0][2] * Tl[4] + A[1][2] * Tl[5]);
+            else
+                AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
+            const T lap = T(-2) * AT;
+            const T Hh = a.H[i], si = vsi.w, sd = a.sdot[i];
+            const T e0 = m.eps0;
+            const T sdd = m.c0 * m.c0 / (T(2) * e0) *
+                          (T(2) * e0 * lap + (T(1) - si) / (T(2) * e0) -
+                           T(2) * t_sqrt(T(4) * e0 * Hh / m.Gc + T(1)) / m.c0 * sd - T(2) * si * Hh / m.Gc);
+            const T sd_new = sd + (T)dt * sdd;
+            a.sdot[i] = sd_new;
+            s_new = t_min(T(1), t_max(T(0), si + (T)dt * sd_new));
+        }
+        // Algorithm 1 update
+        T vn[3] = {vsi.x, vsi.y, vsi.z};
+        const T dtT = (T)dt;
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            vn[p] = vn[p] + dtT * acc[p];
+            if (vmask & (1 << p)) vn[p] = (T)vset[p];
+        }
+        double un[3];
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            un[p] = a.u64[p * n + i] + dt * (double)vn[p];
+            a.u64[p * n + i] = un[p];
+        }
+        a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), T(0)};
+        a.vs_next[i] = V4<T>{vn[0], vn[1], DIM == 3 ? vn[DIM - 1] : T(0), s_new};
+        if (a.acc_out)
+#pragma unroll
+            for (int p = 0; p < DIM; p++) a.acc_out[p * n + i] = acc[p];
+        T vv = T(0), aa = T(0);
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            vv += vn[p] * vn[p];
+            aa += acc[p] * acc[p];
+        }
+        vmag = (double)t_sqrt(vv);
+        amag = (double)t_sqrt(aa);
+        if (!(isfinite(vmag) && isfinite(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
+    }
+    // per-specimen maxima of |v_{n+1}| and |a_n|
+    if (threadIdx.x == 0) s_sp = sp;
+    __syncthreads();
+    const bool uniform = __syncthreads_and(!active || sp == s_sp);
+    if (uniform) {
+        double v = vmag, ac = amag;
+        for (int o = 16; o > 0; o >>= 1) {
+            v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            ac = fmax(ac, __shfl_xor_sync(0xffffffffu, ac, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_v[threadIdx.x >> 5] = v;
+            s_a[threadIdx.x >> 5] = ac;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+                v = fmax(v, s_v[q]);
+                ac = fmax(ac, s_a[q]);
+            }
+            atomicMax(&a.vmax_bits[s_sp], (unsigned long long)__double_as_longlong(v));
+            atomicMax(&a.amax_bits[s_sp], (unsigned long long)__double_as_longlong(ac));
+        }
+    } else if (active) {
+        atomicMax(&a.vmax_bits[sp], (unsigned long long)__double_as_longlong(vmag));
+        atomicMax(&a.amax_bits[sp], (unsigned long long)__double_as_longlong(amag));
+    }
+    // the last block to finish advances the clocks and picks the next step size
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int q = threadIdx.x; q < a.nspec; q += blockDim.x) {
+            const double dts = a.dt[q];
+            a.t[q] = a.t[q] + dts;
+            const double vm = __longlong_as_double((long long)atomicExch(&a.vmax_bits[q], 0ull));
+            const double am = __longlong_as_double((long long)atomicExch(&a.amax_bits[q], 0ull));
+            a.last_vmax[q] = vm;
+            a.last_amax[q] = am;
+            if (a.dt_mode == 1) {
+                const double dtv = a.hd / (a.cmax[q] + vm);
+                const double dta = am > 0.0 ? sqrt(a.hd / am) : INFINITY;
+                a.dt[q] = a.cfl * (dtv < dta ? dtv : dta);
+            }
+        }
+        if (threadIdx.x == 0) *a.done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- diagnostics
+// grad s and the energy densities of the current state (FP64 sums).
+template <typename T, int DIM, bool FRAC>
+__global__ void __launch_bounds__(128) k_energy(StepArgs<T> a, double *out) {
+    __shared__ double red[4][4];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double e[4] = {0, 0, 0, 0};
+    if (i < a.n) {
+        const int n = a.n;
+        const MatT<T> m = a.mats[a.mid[i]];
+        const V4<T> xi = a.X0V[i];
+        const V4<T> vsi = a.vs_cur[i];
+        const double V = DIM == 3 ? (double)xi.w : (double)xi.z;
+        const double vv = (double)vsi.x * vsi.x + (double)vsi.y * vsi.y + (double)vsi.z * vsi.z;
+        e[0] = 0.5 * (double)m.rho * V * vv;
+        e[1] = V * (double)a.psi_out[i];
+        if (m.model == 3) {
+            const double ep = a.ep[i];
+            e[3] = V * ((double)m.sy0 * ep + 0.5 * (double)m.Hh * ep * ep);
+        }
+        if (FRAC && m.fracture) {
+            const int64_t base = a.slice_off[i >> 5] + (i & 31);
+            const int len = a.row_len[i];
+            double gs[3] = {0, 0, 0};
+            for (int k = 0; k < len; k++) {
+                const int j = a.col[base + 32 * k];
+                const V4<T> xj = a.X0V[j];
+                double d[3] = {(double)(xj.x - xi.x), (double)(xj.y - xi.y), DIM == 3 ? (double)(xj.z - xi.z) : 0.0};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double t = fmax(1.0 - r * (double)a.inv2h, 0.0);
+                double Vj = DIM == 3 ? (double)xj.w : (double)xj.z;
+                double c = Vj * t * t * t * ((double)a.vs_cur[j].w - (double)vsi.w);
+                for (int p = 0; p < 3; p++) gs[p] += c * d[p];
+            }
+            T A[3][3];
+            load_ahat<T, DIM>(a.Ahat, n, i, A);
+            double g2 = 0.0;
+            for (int p = 0; p < DIM; p++) {
+                double gp = 0.0;
+                for (int q = 0; q < DIM; q++) gp += (double)A[p][q] * gs[q];
+                g2 += gp * gp;
+            }
+            const double om = 1.0 - (double)vsi.w;
+            e[2] = V * (double)m.Gc * (om * om / (4.0 * (double)m.eps0) + (double)m.eps0 * g2);
+        }
+    }
+    for (int q = 0; q < 4; q++)
+        for (int o = 16; o > 0; o >>= 1) e[q] += __shfl_xor_sync(0xffffffffu, e[q], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; q++) red[q][threadIdx.x >> 5] = e[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; q++) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[q][w];
+            atomicAdd(&out[q], s);
+        }
+}
+
+// ---------------------------------------------------------------- gathers to / from the caller's order
+// out[perm[k] * nc + c] = src_c[k] for c < nc, sources given as nc strided arrays of T.
+template <typename S>
+__global__ void k_to_caller(int64_t n, int nc, const S *src, int64_t cstride, const int *perm, double *out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    for (int c = 0; c < nc; c++) out[p * nc + c] = (double)src[c * cstride + k];
+}
+template <typename S>
+__global__ void k_from_caller(int64_t n, int nc, const double *in, const int *perm, S *dst, int64_t cstride) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    for (int c = 0; c < nc; c++) dst[c * cstride + k] = (S)in[p * nc + c];
+}
+// V4 records (vs, ug): component c of record k
+template <typename T>
+__global__ void k_v4_to_caller(int64_t n, int nc, int c0, const V4<T> *src, const int *perm, double *out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    const T *r = reinterpret_cast<const T *>(src + k);
+    for (int c = 0; c < nc; c++) out[p * nc + c] = (double)r[c0 + c];
+}
+template <typename T>
+__global__ void k_v4_from_caller(int64_t n, int nc, int c0, const double *in, const int *perm, V4<T> *dst) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    T *r = reinterpret_cast<T *>(dst + k);
+    for (int c = 0; c < nc; c++) r[c0 + c] = (T)in[p * nc + c];
+}
+// current position X0 + u (FP64) to the caller
+__global__ void k_x_to_caller(int64_t n, int dim, const double *X0d, const double *u64, const int *perm, double *out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    for (int c = 0; c < dim; c++) out[p * dim + c] = X0d[c * n + k] + u64[c * n + k];
+}
+// u64 (FP64) -> gathered copy ug
+template <typename T> __global__ void k_refresh_ug(int64_t n, int dim, const double *u64, V4<T> *ug) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    ug[k] = V4<T>{(T)u64[k], (T)u64[n + k], dim == 3 ? (T)u64[2 * n + k] : T(0), T(0)};
+}
+// C_p^-1 = I + K (9 components) to the caller
+template <typename T> __global__ void k_cpinv_to_caller(int64_t n, const T *K, const int *perm, double *out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+    for (int c = 0; c < 9; c++) out[p * 9 + c] = (double)K[map[c] * n + k] + ((c % 4) == 0 ? 1.0 : 0.0);
+}
+template <typename T> __global__ void k_cpinv_from_caller(int64_t n, const double *in, const int *perm, T *K) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    const int src[6] = {0, 4, 8, 1, 2, 5};
+    for (int q = 0; q < 6; q++) K[q * n + k] = (T)(in[p * 9 + src[q]] - ((src[q] % 4) == 0 ? 1.0 : 0.0));
+}
+// caller CSR: row lengths in caller order, then rows mapped to caller ids and sorted
+__global__ void k_rowlen_caller(int64_t n, const int *row_len, const int *perm, int64_t *len_out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) len_out[perm[k]] = row_len[k];
+}
+__global__ void k_rows_caller(int64_t n, const int64_t *row_ptr, const int *col, const int *perm, const int64_t *rp_out,
+                              int *col_out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t b = row_ptr[k], e = row_ptr[k + 1], o = rp_out[perm[k]];
+    for (int64_t q = 0; q < e - b; q++) col_out[o + q] = perm[col[b + q]];
+    for (int64_t x = 1; x < e - b; x++) {  // insertion sort: rows are short
+        int v = col_out[o + x];
+        int64_t y = x - 1;
+        while (y >= 0 && col_out[o + y] > v) {
+            col_out[o + y + 1] = col_out[o + y];
+            y--;
+        }
+        col_out[o + y + 1] = v;
+    }
+}
+
+}  // namespace tl

@@ -1,0 +1,1109 @@
+// C-ABI of the TLSPH library (include/tlsph.h): context, device memory,
+// reference setup and the step loop.  Every operation of the method runs in
+// the kernels of setup_kernels.cuh and step_kernels.cuh; this file only
+// allocates, copies, orders launches and reports status.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tlsph.h"
+#include "setup_kernels.cuh"
+#include "step_kernels.cuh"
+
+using namespace tl;
+
+namespace {
+
+constexpr int kThreads = 128;
+inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+struct BCHost {
+    int kind, comp_mask;
+    double value[3];
+    double t_start, t_end, ramp, area;
+    std::vector<uint8_t> mask;
+    int64_t count;
+};
+
+}  // namespace
+
+struct tlsph_ctx {
+    tlsph_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<tlsph_material> mats;
+    int64_t n = 0;
+    int nspec = 1;
+    std::vector<double> X0h;  // n * 3, caller order
+    std::vector<double> volh, v0h;
+    std::vector<int32_t> midh, spech;
+    std::vector<BCHost> bcs;
+    std::vector<double> notches;
+    bool built = false;
+    int parity = 0;
+    int64_t steps = 0, launches = 0, nnz = 0;
+    int max_row = 0;
+    int64_t nslice = 0, sell_total = 0;
+    bool has_j2 = false, has_frac = false, has_visc = false;
+    bool record_acc = false;
+    double bytes_per_step = 0.0;
+    // device memory
+    std::vector<void *> allocs;
+    double *X0d = nullptr;  // sorted FP64 reference positions, 3 arrays
+    int *perm = nullptr;    // sorted k -> caller id
+    int64_t *row_ptr = nullptr;
+    int *col = nullptr, *row_len = nullptr, *sell = nullptr;
+    int64_t *slice_off = nullptr;
+    void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr}, *Q = nullptr, *Vm = nullptr;
+    void *Ahat = nullptr, *K = nullptr, *ep = nullptr, *H = nullptr, *sdot = nullptr;
+    double *u64 = nullptr;
+    uint16_t *mid = nullptr, *bcgrp = nullptr;
+    int *spec = nullptr;
+    int16_t *grp_bcs = nullptr;
+    BCDev *bcdev = nullptr;
+    void *matsdev = nullptr;
+    double *t = nullptr, *dt = nullptr, *cmax = nullptr, *last_v = nullptr, *last_a = nullptr;
+    unsigned long long *vmax = nullptr, *amax = nullptr;
+    unsigned int *done = nullptr;
+    int *flags = nullptr;
+    void *Fd = nullptr, *Pd = nullptr, *psid = nullptr, *accd = nullptr;
+    double *energy = nullptr;
+    int64_t flags_seen[kNumFlags] = {0};
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pending;  // (kind, event index of start); stop = start + 1
+    size_t ev_next = 0;
+    double ms[2] = {0, 0};
+    int64_t cnt[2] = {0, 0};
+};
+
+namespace {
+
+tlsph_status fail(tlsph_ctx *c, tlsph_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(c, TLSPH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+#define CKL()                                                                                        \
+    do {                                                                                             \
+        c->launches++;                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                                         \
+        if (e_ != cudaSuccess) return fail(c, TLSPH_ERR_CUDA, "launch: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P> tlsph_status dalloc(tlsph_ctx *c, P **ptr, size_t bytes) {
+    void *q = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TLSPH_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *ptr = reinterpret_cast<P *>(q);
+    return TLSPH_OK;
+}
+#define DA(ptr, bytes)                                  \
+    do {                                                \
+        tlsph_status s_ = dalloc(c, &(ptr), (bytes));   \
+        if (s_ != TLSPH_OK) return s_;                  \
+    } while (0)
+
+void free_device(tlsph_ctx *c) {
+    for (void *q : c->allocs) cudaFree(q);
+    c->allocs.clear();
+    c->X0d = nullptr;
+    c->perm = nullptr;
+    c->Fd = c->Pd = c->psid = c->accd = nullptr;
+    c->built = false;
+}
+
+void lame(const tlsph_material &m, double &lam, double &mu, double &kap) {
+    lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+    mu = m.E / (2.0 * (1.0 + m.nu));
+    kap = lam + 2.0 * mu / 3.0;
+}
+double sound_speed(const tlsph_material &m) {
+    double lam, mu, kap;
+    lame(m, lam, mu, kap);
+    return sqrt((kap + 4.0 * mu / 3.0) / m.rho);
+}
+
+tlsph_status scan_exclusive(tlsph_ctx *c, int64_t m, const int64_t *in, int64_t *out) {
+    // recursive block scan
+    int64_t nb = (m + kScanBlock - 1) / kScanBlock;
+    if (nb <= 1) {
+        k_scan_block<<<1, kScanBlock, 0, c->stream>>>(m, in, out, nullptr);
+        CKL();
+        return TLSPH_OK;
+    }
+    int64_t *bs = nullptr, *bscan = nullptr;
+    DA(bs, nb * sizeof(int64_t));
+    DA(bscan, nb * sizeof(int64_t));
+    k_scan_block<<<(unsigned)nb, kScanBlock, 0, c->stream>>>(m, in, out, bs);
+    CKL();
+    tlsph_status st = scan_exclusive(c, nb, bs, bscan);
+    if (st != TLSPH_OK) return st;
+    k_scan_add<<<(unsigned)nb, kScanBlock, 0, c->stream>>>(m, out, bscan);
+    CKL();
+    return TLSPH_OK;
+}
+
+template <typename T> __global__ void k_init_sorted(int64_t n, int dim, const int *perm, const double *X0c,
+                                                    const double *volc, const double *v0c, const int *midc,
+                                                    const int *specc, const uint16_t *grpc, const MatT<T> *mats,
+                                                    const double *center, double *X0d, V4<T> *X0V, V4<T> *vs,
+                                                    uint16_t *mid, int *spec, uint16_t *bcgrp) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t p = perm[k];
+    double x[3] = {0, 0, 0};
+    for (int q = 0; q < dim; q++) x[q] = X0c[3 * p + q];
+    for (int q = 0; q < 3; q++) X0d[q * n + k] = x[q];
+    double V = volc[p];
+    int m = midc[p];
+    T xs[3];
+    for (int q = 0; q < 3; q++) xs[q] = (T)(x[q] - center[q]);
+    if (dim == 3) X0V[k] = V4<T>{xs[0], xs[1], xs[2], (T)V};
+    else X0V[k] = V4<T>{xs[0], xs[1], (T)V, (T)((double)mats[m].rho * V)};
+    double v[3] = {0, 0, 0};
+    if (v0c)
+        for (int q = 0; q < dim; q++) v[q] = v0c[dim * p + q];
+    vs[k] = V4<T>{(T)v[0], (T)v[1], (T)v[2], T(1)};
+    mid[k] = (uint16_t)m;
+    spec[k] = specc ? specc[p] : 0;
+    bcgrp[k] = grpc[p];
+}
+
+template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
+    StepArgs<T> a{};
+    const int cur = c->parity, nxt = c->parity ^ 1;
+    a.n = (int)c->n;
+    a.slice_off = c->slice_off;
+    a.row_len = c->row_len;
+    a.col = c->sell;
+    a.X0V = (const V4<T> *)c->X0V;
+    a.ug_cur = (const V4<T> *)c->ug[cur];
+    a.ug_next = (V4<T> *)c->ug[nxt];
+    a.vs_cur = (const V4<T> *)c->vs[cur];
+    a.vs_next = (V4<T> *)c->vs[nxt];
+    a.Q = (V4<T> *)c->Q;
+    a.Vm = (T *)c->Vm;
+    a.Ahat = (const T *)c->Ahat;
+    a.K = (T *)c->K;
+    a.ep = (T *)c->ep;
+    a.H = (T *)c->H;
+    a.sdot = (T *)c->sdot;
+    a.u64 = c->u64;
+    a.mid = c->mid;
+    a.spec = c->spec;
+    a.bcgrp = c->bcgrp;
+    a.grp_bcs = c->grp_bcs;
+    a.bcs = c->bcdev;
+    a.mats = (const MatT<T> *)c->matsdev;
+    a.t = c->t;
+    a.dt = c->dt;
+    a.cmax = c->cmax;
+    a.vmax_bits = c->vmax;
+    a.amax_bits = c->amax;
+    a.last_vmax = c->last_v;
+    a.last_amax = c->last_a;
+    a.done = c->done;
+    a.flags = c->flags;
+    a.nspec = c->nspec;
+    a.dt_mode = c->p.dt_mode;
+    a.hd = c->p.h;
+    a.cfl = c->p.cfl;
+    a.fixed_dt = c->p.fixed_dt;
+    a.h = (T)c->p.h;
+    a.inv2h = (T)(1.0 / (c->p.support * c->p.h));
+    a.visc_eps = (T)(0.001 * c->p.h * c->p.h);
+    for (int q = 0; q < 3; q++) a.grav[q] = (T)c->p.gravity[q];
+    a.Fout = (T *)c->Fd;
+    a.Pout = (T *)c->Pd;
+    a.psi_out = (T *)c->psid;
+    a.acc_out = c->record_acc ? (T *)c->accd : nullptr;
+    return a;
+}
+
+// algorithmic HBM bytes of one step (neighbour gathers served from L2 / L1)
+double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
+    const int d = c->p.dim;
+    const double n = (double)c->n, nnz = (double)c->nnz;
+    const double v4 = 4.0 * ts;
+    const double q = d == 3 ? 3 * v4 : v4;
+    double p1 = 4 + 8.0 / 32 + v4 /*X0V*/ + v4 /*ug*/ + (d == 3 ? 6 : 3) * ts /*Ahat*/ + 2 /*mid*/ + q /*Q w*/ +
+                d * d * ts /*Vm w*/;
+    if (c->has_j2) p1 += 2 * 7 * ts;               // K, ep read + write
+    if (c->has_frac) p1 += v4 /*s*/ + 2 * ts;      // H read + write
+    double p2 = 4 + 8.0 / 32 + v4 + v4 /*ug r*/ + v4 /*vs r*/ + q /*Q own*/ + 2 + 4 + 2 + 2 * 8.0 * d /*u64 r/w*/ +
+                v4 /*ug w*/ + v4 /*vs w*/;
+    if (c->has_visc) p2 += d * d * ts;
+    if (c->has_frac) p2 += (d == 3 ? 6 : 3) * ts + ts + 2 * ts;  // Ahat, H, sdot r/w
+    return n * (p1 + p2) + 2.0 * 4.0 * nnz;        // + neighbour indices of both passes
+}
+
+template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
+    const int64_t n = c->n;
+    const int dim = c->p.dim;
+    free_device(c);
+    cudaStream_t s = c->stream;
+    // ---- inputs (caller order)
+    double *X0c, *volc, *v0c = nullptr, *bbox;
+    int *midc, *specc;
+    uint16_t *grpc;
+    DA(X0c, n * 3 * sizeof(double));
+    DA(volc, n * sizeof(double));
+    DA(midc, n * sizeof(int));
+    DA(specc, n * sizeof(int));
+    DA(grpc, n * sizeof(uint16_t));
+    DA(bbox, 6 * sizeof(double));
+    CK(cudaMemcpyAsync(X0c, c->X0h.data(), n * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(volc, c->volh.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(midc, c->midh.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(specc, c->spech.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (!c->v0h.empty()) {
+        DA(v0c, n * dim * sizeof(double));
+        CK(cudaMemcpyAsync(v0c, c->v0h.data(), n * dim * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    // ---- boundary-condition groups
+    std::vector<uint16_t> grph(n, 0);
+    std::map<std::vector<int>, int> groups;
+    std::vector<int16_t> grp_tab(4, -1);
+    for (int64_t pi = 0; pi < n; pi++) {
+        std::vector<int> ids;
+        for (size_t b = 0; b < c->bcs.size(); b++)
+            if (c->bcs[b].mask[pi]) ids.push_back((int)b);
+        if (ids.empty()) continue;
+        if (ids.size() > (size_t)kMaxBcPerParticle)
+            return fail(c, TLSPH_ERR_ARG, "particle %lld is covered by more than %d boundary conditions", (long long)pi,
+                        kMaxBcPerParticle);
+        auto it = groups.find(ids);
+        int g;
+        if (it == groups.end()) {
+            g = (int)groups.size() + 1;
+            if (g > 65535) return fail(c, TLSPH_ERR_ARG, "too many distinct boundary-condition groups");
+            groups[ids] = g;
+            for (int q = 0; q < 4; q++) grp_tab.push_back(q < (int)ids.size() ? (int16_t)ids[q] : (int16_t)-1);
+        } else {
+            g = it->second;
+        }
+        grph[pi] = (uint16_t)g;
+    }
+    CK(cudaMemcpyAsync(grpc, grph.data(), n * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+    DA(c->grp_bcs, grp_tab.size() * sizeof(int16_t));
+    CK(cudaMemcpyAsync(c->grp_bcs, grp_tab.data(), grp_tab.size() * sizeof(int16_t), cudaMemcpyHostToDevice, s));
+    std::vector<BCDev> bch(std::max<size_t>(c->bcs.size(), 1));
+    for (size_t b = 0; b < c->bcs.size(); b++) {
+        const BCHost &h = c->bcs[b];
+        BCDev &d = bch[b];
+        d.kind = h.kind;
+        d.comp_mask = h.comp_mask;
+        for (int q = 0; q < 3; q++) d.value[q] = h.value[q];
+        d.t_start = h.t_start;
+        d.t_end = h.t_end;
+        d.ramp = h.ramp;
+        d.area = h.area;
+        d.inv_count = h.count > 0 ? 1.0 / (double)h.count : 0.0;
+    }
+    DA(c->bcdev, bch.size() * sizeof(BCDev));
+    CK(cudaMemcpyAsync(c->bcdev, bch.data(), bch.size() * sizeof(BCDev), cudaMemcpyHostToDevice, s));
+    // ---- materials
+    std::vector<MatT<T>> mt(c->mats.size());
+    c->has_j2 = c->has_frac = c->has_visc = false;
+    for (size_t k = 0; k < c->mats.size(); k++) {
+        const tlsph_material &m = c->mats[k];
+        double lam, mu, kap;
+        lame(m, lam, mu, kap);
+        MatT<T> &d = mt[k];
+        d.model = m.model;
+        d.fracture = (m.model != TLSPH_MODEL_J2 && m.fracture) ? 1 : 0;
+        d.rho = (T)m.rho;
+        d.mu = (T)mu;
+        d.kappa = (T)kap;
+        d.sy0 = (T)m.sigma_y0;
+        d.Hh = (T)m.H_hard;
+        d.beta1 = (T)m.beta1;
+        d.beta2 = (T)m.beta2;
+        d.c0 = (T)sound_speed(m);
+        d.Gc = (T)m.Gc;
+        d.eps0 = (T)m.eps0;
+        d.s_lim = (T)m.s_lim;
+        d.mass_scale = T(1);
+    }
+    std::vector<char> used(c->mats.size(), 0);
+    for (int64_t pi = 0; pi < n; pi++) used[c->midh[pi]] = 1;
+    for (size_t k = 0; k < c->mats.size(); k++)
+        if (used[k]) {
+            if (c->mats[k].model == TLSPH_MODEL_J2) c->has_j2 = true;
+            if (mt[k].fracture) c->has_frac = true;
+            if (c->mats[k].beta1 != 0.0 || c->mats[k].beta2 != 0.0) c->has_visc = true;
+        }
+    DA(c->matsdev, mt.size() * sizeof(MatT<T>));
+    CK(cudaMemcpyAsync(c->matsdev, mt.data(), mt.size() * sizeof(MatT<T>), cudaMemcpyHostToDevice, s));
+    // ---- notches
+    double *notchd = nullptr;
+    int nn = (int)(c->notches.size() / 12);
+    if (nn) {
+        DA(notchd, c->notches.size() * sizeof(double));
+        CK(cudaMemcpyAsync(notchd, c->notches.data(), c->notches.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    // ---- cell grid (same formulas as the specification of the predicate)
+    k_bbox<<<1, 1024, 0, s>>>(n, dim, X0c, bbox);
+    CKL();
+    double bb[6];
+    CK(cudaMemcpyAsync(bb, bbox, sizeof bb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double R = c->p.support * c->p.h, R2 = R * R;
+    CellGrid g;
+    g.dim = dim;
+    g.cs = R * (1.0 + ldexp(1.0, -10));
+    double center[3];
+    for (int k = 0; k < 3; k++) {
+        g.xmin[k] = bb[k];
+        g.nc[k] = (int64_t)floor((bb[3 + k] - bb[k]) / g.cs) + 1;
+        center[k] = 0.5 * (bb[k] + bb[3 + k]);
+    }
+    double *centerd;
+    DA(centerd, 3 * sizeof(double));
+    CK(cudaMemcpyAsync(centerd, center, sizeof center, cudaMemcpyHostToDevice, s));
+    double maxkey = ((double)c->nspec * g.nc[2] * g.nc[1] * g.nc[0]);
+    if (!(maxkey < 9.0e18)) return fail(c, TLSPH_ERR_ARG, "cell grid too large");
+    int bits = 1;
+    while (bits < 64 && (double)(1ull << bits) < maxkey) bits++;
+    // ---- keys and stable sort
+    unsigned long long *key[2];
+    int *val[2];
+    DA(key[0], n * 8);
+    DA(key[1], n * 8);
+    DA(val[0], n * 4);
+    DA(val[1], n * 4);
+    k_cell_keys<<<blocks_for(n), kThreads, 0, s>>>(n, g, X0c, specc, key[0], val[0]);
+    CKL();
+    const int64_t nblk = (n + kSortTile - 1) / kSortTile;
+    int64_t *hist, *hoff;
+    DA(hist, 256 * nblk * sizeof(int64_t));
+    DA(hoff, 256 * nblk * sizeof(int64_t));
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nblk, 32, 0, s>>>(n, key[cur], shift, hist);
+        CKL();
+        tlsph_status st = scan_exclusive(c, 256 * nblk, hist, hoff);
+        if (st != TLSPH_OK) return st;
+        k_radix_scatter<<<(unsigned)nblk, 32, 0, s>>>(n, key[cur], val[cur], shift, hoff, key[cur ^ 1], val[cur ^ 1]);
+        CKL();
+        cur ^= 1;
+    }
+    c->perm = val[cur];
+    unsigned long long *skey = key[cur];
+    // ---- sorted particle arrays
+    DA(c->X0d, 3 * n * sizeof(double));
+    DA(c->X0V, n * sizeof(V4<T>));
+    DA(c->vs[0], n * sizeof(V4<T>));
+    DA(c->vs[1], n * sizeof(V4<T>));
+    DA(c->ug[0], n * sizeof(V4<T>));
+    DA(c->ug[1], n * sizeof(V4<T>));
+    DA(c->mid, n * sizeof(uint16_t));
+    DA(c->spec, n * sizeof(int));
+    DA(c->bcgrp, n * sizeof(uint16_t));
+    k_init_sorted<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->perm, X0c, volc, v0c, midc, specc, grpc,
+                                                        (const MatT<T> *)c->matsdev, centerd, c->X0d, (V4<T> *)c->X0V,
+                                                        (V4<T> *)c->vs[0], c->mid, c->spec, c->bcgrp);
+    CKL();
+    CK(cudaMemsetAsync(c->ug[0], 0, n * sizeof(V4<T>), s));
+    CK(cudaMemsetAsync(c->ug[1], 0, n * sizeof(V4<T>), s));
+    CK(cudaMemcpyAsync(c->vs[1], c->vs[0], n * sizeof(V4<T>), cudaMemcpyDeviceToDevice, s));
+    // ---- neighbours (count, scan, fill)
+    DA(c->row_len, n * sizeof(int));
+    DA(c->row_ptr, (n + 1) * sizeof(int64_t));
+    NotchSet ns{notchd, nn};
+    k_neighbours<false><<<blocks_for(n), kThreads, 0, s>>>(n, g, R2, skey, c->X0d, c->perm, ns, c->row_len, nullptr,
+                                                           nullptr);
+    CKL();
+    int64_t *len64;
+    DA(len64, (n + 1) * sizeof(int64_t));
+    int *maxrow;
+    DA(maxrow, sizeof(int));
+    CK(cudaMemsetAsync(maxrow, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(len64, 0, (n + 1) * sizeof(int64_t), s));
+    k_widen_rows<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_len, len64, maxrow);
+    CKL();
+    CK(cudaMemcpyAsync(&c->max_row, maxrow, sizeof(int), cudaMemcpyDeviceToHost, s));
+    tlsph_status st = scan_exclusive(c, n + 1, len64, c->row_ptr);
+    if (st != TLSPH_OK) return st;
+    CK(cudaMemcpyAsync(&c->nnz, c->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->nnz >= (int64_t)1 << 31) return fail(c, TLSPH_ERR_ARG, "too many neighbour pairs for 32-bit indices");
+    DA(c->col, std::max<int64_t>(c->nnz, 1) * sizeof(int));
+    k_neighbours<true><<<blocks_for(n), kThreads, 0, s>>>(n, g, R2, skey, c->X0d, c->perm, ns, c->row_len, c->row_ptr,
+                                                          c->col);
+    CKL();
+    // ---- flags, correction tensors
+    DA(c->flags, kNumFlags * sizeof(int));
+    CK(cudaMemsetAsync(c->flags, 0, kNumFlags * sizeof(int), s));
+    for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = 0;
+    DA(c->Ahat, 6 * n * sizeof(T));
+    k_correction<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->row_ptr, c->col, (const V4<T> *)c->X0V,
+                                                       1.0 / R, (T *)c->Ahat, c->flags);
+    CKL();
+    // ---- SELL-32 layout
+    c->nslice = (n + 31) / 32;
+    int64_t *slen;
+    DA(slen, (c->nslice + 1) * sizeof(int64_t));
+    CK(cudaMemsetAsync(slen, 0, (c->nslice + 1) * sizeof(int64_t), s));
+    k_slice_len<<<blocks_for(c->nslice), kThreads, 0, s>>>(n, c->nslice, c->row_len, slen);
+    CKL();
+    DA(c->slice_off, (c->nslice + 1) * sizeof(int64_t));
+    st = scan_exclusive(c, c->nslice + 1, slen, c->slice_off);
+    if (st != TLSPH_OK) return st;
+    CK(cudaMemcpyAsync(&c->sell_total, c->slice_off + c->nslice, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    DA(c->sell, std::max<int64_t>(c->sell_total, 1) * sizeof(int));
+    k_sell_pad<<<blocks_for(std::max<int64_t>(c->sell_total, 1)), kThreads, 0, s>>>(c->sell_total, c->sell, 0);
+    CKL();
+    k_sell_fill<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, c->slice_off, c->sell);
+    CKL();
+    // ---- state
+    DA(c->u64, 3 * n * sizeof(double));
+    CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
+    DA(c->Q, (dim == 3 ? 3 : 1) * n * sizeof(V4<T>));
+    CK(cudaMemsetAsync(c->Q, 0, (dim == 3 ? 3 : 1) * n * sizeof(V4<T>), s));
+    DA(c->Vm, dim * dim * n * sizeof(T));
+    DA(c->K, 6 * n * sizeof(T));
+    CK(cudaMemsetAsync(c->K, 0, 6 * n * sizeof(T), s));
+    DA(c->ep, n * sizeof(T));
+    CK(cudaMemsetAsync(c->ep, 0, n * sizeof(T), s));
+    DA(c->H, n * sizeof(T));
+    CK(cudaMemsetAsync(c->H, 0, n * sizeof(T), s));
+    DA(c->sdot, n * sizeof(T));
+    CK(cudaMemsetAsync(c->sdot, 0, n * sizeof(T), s));
+    DA(c->accd, dim * n * sizeof(T));
+    CK(cudaMemsetAsync(c->accd, 0, dim * n * sizeof(T), s));
+    DA(c->energy, 8 * sizeof(double));
+    // ---- per-specimen clocks (eq. dt_criterion)
+    const int ns_ = c->nspec;
+    std::vector<double> cm(ns_, 0.0), vm0(ns_, 0.0), t0(ns_, 0.0), dt0(ns_, 0.0);
+    for (int64_t pi = 0; pi < n; pi++) {
+        int sp = c->spech.empty() ? 0 : c->spech[pi];
+        double cs = sound_speed(c->mats[c->midh[pi]]);
+        if (cs > cm[sp]) cm[sp] = cs;
+        double vv = 0.0;
+        for (int k = 0; k < 3; k++) {
+            double x = (!c->v0h.empty() && k < dim) ? c->v0h[dim * pi + k] : 0.0;
+            vv += x * x;
+        }
+        vv = sqrt(vv);
+        if (vv > vm0[sp]) vm0[sp] = vv;
+    }
+    for (int sp = 0; sp < ns_; sp++) {
+        const double h = c->p.h;
+        if (c->p.dt_mode == TLSPH_DT_FIXED) dt0[sp] = c->p.fixed_dt;
+        else if (c->p.dt_mode == TLSPH_DT_CFL_STATIC) dt0[sp] = c->p.cfl * h / cm[sp];
+        else dt0[sp] = c->p.cfl * (h / (cm[sp] + vm0[sp]));
+    }
+    DA(c->t, ns_ * sizeof(double));
+    DA(c->dt, ns_ * sizeof(double));
+    DA(c->cmax, ns_ * sizeof(double));
+    DA(c->last_v, ns_ * sizeof(double));
+    DA(c->last_a, ns_ * sizeof(double));
+    DA(c->vmax, ns_ * sizeof(unsigned long long));
+    DA(c->amax, ns_ * sizeof(unsigned long long));
+    DA(c->done, sizeof(unsigned int));
+    CK(cudaMemcpyAsync(c->t, t0.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->dt, dt0.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->cmax, cm.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->last_v, 0, ns_ * sizeof(double), s));
+    CK(cudaMemsetAsync(c->last_a, 0, ns_ * sizeof(double), s));
+    CK(cudaMemsetAsync(c->vmax, 0, ns_ * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->amax, 0, ns_ * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->done, 0, sizeof(unsigned int), s));
+    int hf[kNumFlags];
+    CK(cudaMemcpyAsync(hf, c->flags, sizeof hf, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->parity = 0;
+    c->steps = 0;
+    c->bytes_per_step = algorithmic_bytes(c, sizeof(T));
+    if (hf[kFlagSingular]) return fail(c, TLSPH_ERR_SINGULAR_L, "%d particles have a singular correction matrix",
+                                       hf[kFlagSingular]);
+    c->built = true;
+    return TLSPH_OK;
+}
+
+int timing_event(tlsph_ctx *c) {
+    if (c->ev_next + 2 > c->ev_pool.size()) {
+        for (int q = 0; q < 256; q++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->ev_pool.push_back(e);
+        }
+    }
+    int k = (int)c->ev_next;
+    c->ev_next += 2;
+    return k;
+}
+
+void collect_timing(tlsph_ctx *c) {
+    for (auto &pr : c->ev_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]) == cudaSuccess) {
+            c->ms[pr.first] += ms;
+            c->cnt[pr.first]++;
+        }
+    }
+    c->ev_pending.clear();
+    c->ev_next = 0;
+}
+
+template <typename T, int DIM, bool FRAC>
+tlsph_status step_dim(tlsph_ctx *c, int64_t nsteps) {
+    const unsigned nb = blocks_for(c->n);
+    for (int64_t k = 0; k < nsteps; k++) {
+        StepArgs<T> a = make_args<T>(c);
+        int e1 = -1, e2 = -1;
+        if (c->timing) {
+            if (c->ev_next + 4 > 4096) {
+                cudaStreamSynchronize(c->stream);
+                collect_timing(c);
+            }
+            e1 = timing_event(c);
+            cudaEventRecord(c->ev_pool[e1], c->stream);
+        }
+        k_pass1<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        if (c->timing) {
+            cudaEventRecord(c->ev_pool[e1 + 1], c->stream);
+            c->ev_pending.push_back({1, e1});
+            e2 = timing_event(c);
+            cudaEventRecord(c->ev_pool[e2], c->stream);
+        }
+        if (c->has_visc) k_pass2<T, DIM, FRAC, true><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_pass2<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        if (c->timing) {
+            cudaEventRecord(c->ev_pool[e2 + 1], c->stream);
+            c->ev_pending.push_back({0, e2});
+        }
+        c->parity ^= 1;
+        c->steps++;
+    }
+    return TLSPH_OK;
+}
+
+template <typename T> tlsph_status step_impl(tlsph_ctx *c, int64_t nsteps) {
+    if (c->p.dim == 3) return c->has_frac ? step_dim<T, 3, true>(c, nsteps) : step_dim<T, 3, false>(c, nsteps);
+    return c->has_frac ? step_dim<T, 2, true>(c, nsteps) : step_dim<T, 2, false>(c, nsteps);
+}
+
+template <typename T> tlsph_status diag_pass(tlsph_ctx *c) {
+    const int64_t n = c->n;
+    if (!c->Fd) {
+        DA(c->Fd, 9 * n * sizeof(T));
+        DA(c->Pd, 9 * n * sizeof(T));
+        DA(c->psid, n * sizeof(T));
+    }
+    StepArgs<T> a = make_args<T>(c);
+    const unsigned nb = blocks_for(n);
+    if (c->p.dim == 3) {
+        if (c->has_frac) k_pass1<T, 3, true, true><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_pass1<T, 3, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+    } else {
+        if (c->has_frac) k_pass1<T, 2, true, true><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_pass1<T, 2, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+    }
+    CKL();
+    return TLSPH_OK;
+}
+
+template <typename T> tlsph_status energies_impl(tlsph_ctx *c, double *out) {
+    tlsph_status st = diag_pass<T>(c);
+    if (st != TLSPH_OK) return st;
+    CK(cudaMemsetAsync(c->energy, 0, 8 * sizeof(double), c->stream));
+    StepArgs<T> a = make_args<T>(c);
+    const unsigned nb = blocks_for(c->n);
+    if (c->p.dim == 3) {
+        if (c->has_frac) k_energy<T, 3, true><<<nb, kThreads, 0, c->stream>>>(a, c->energy);
+        else k_energy<T, 3, false><<<nb, kThreads, 0, c->stream>>>(a, c->energy);
+    } else {
+        if (c->has_frac) k_energy<T, 2, true><<<nb, kThreads, 0, c->stream>>>(a, c->energy);
+        else k_energy<T, 2, false><<<nb, kThreads, 0, c->stream>>>(a, c->energy);
+    }
+    CKL();
+    double e[4];
+    CK(cudaMemcpyAsync(e, c->energy, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&out[4], c->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&out[5], c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < 4; q++) out[q] = e[q];
+    return TLSPH_OK;
+}
+
+int field_comps(const tlsph_ctx *c, int field) {
+    switch (field) {
+    case TLSPH_FIELD_U:
+    case TLSPH_FIELD_V:
+    case TLSPH_FIELD_X:
+    case TLSPH_FIELD_ACC: return c->p.dim;
+    case TLSPH_FIELD_S:
+    case TLSPH_FIELD_SDOT:
+    case TLSPH_FIELD_H:
+    case TLSPH_FIELD_EPSP: return 1;
+    case TLSPH_FIELD_P:
+    case TLSPH_FIELD_F:
+    case TLSPH_FIELD_CPINV: return 9;
+    default: return -1;
+    }
+}
+
+size_t state_bytes(const tlsph_ctx *c) {
+    const size_t ts = c->p.precision == TLSPH_FP64 ? 8 : 4, n = (size_t)c->n;
+    return 64 + n * (3 * 8 + 2 * 4 * ts + ts * (1 + 1 + 6 + 1)) + (size_t)c->nspec * 2 * 8;
+}
+
+template <typename T> tlsph_status read_impl(tlsph_ctx *c, int field, double *dst /* device, caller order */) {
+    const int64_t n = c->n;
+    const int dim = c->p.dim;
+    const unsigned nb = blocks_for(n);
+    cudaStream_t s = c->stream;
+    switch (field) {
+    case TLSPH_FIELD_U: k_to_caller<double><<<nb, kThreads, 0, s>>>(n, dim, c->u64, n, c->perm, dst); break;
+    case TLSPH_FIELD_X: k_x_to_caller<<<nb, kThreads, 0, s>>>(n, dim, c->X0d, c->u64, c->perm, dst); break;
+    case TLSPH_FIELD_V:
+        k_v4_to_caller<T><<<nb, kThreads, 0, s>>>(n, dim, 0, (const V4<T> *)c->vs[c->parity], c->perm, dst);
+        break;
+    case TLSPH_FIELD_S:
+        k_v4_to_caller<T><<<nb, kThreads, 0, s>>>(n, 1, 3, (const V4<T> *)c->vs[c->parity], c->perm, dst);
+        break;
+    case TLSPH_FIELD_SDOT: k_to_caller<T><<<nb, kThreads, 0, s>>>(n, 1, (const T *)c->sdot, n, c->perm, dst); break;
+    case TLSPH_FIELD_H: k_to_caller<T><<<nb, kThreads, 0, s>>>(n, 1, (const T *)c->H, n, c->perm, dst); break;
+    case TLSPH_FIELD_EPSP: k_to_caller<T><<<nb, kThreads, 0, s>>>(n, 1, (const T *)c->ep, n, c->perm, dst); break;
+    case TLSPH_FIELD_ACC: k_to_caller<T><<<nb, kThreads, 0, s>>>(n, dim, (const T *)c->accd, n, c->perm, dst); break;
+    case TLSPH_FIELD_CPINV: k_cpinv_to_caller<T><<<nb, kThreads, 0, s>>>(n, (const T *)c->K, c->perm, dst); break;
+    case TLSPH_FIELD_F:
+    case TLSPH_FIELD_P: {
+        tlsph_status st = diag_pass<T>(c);
+        if (st != TLSPH_OK) return st;
+        k_to_caller<T><<<nb, kThreads, 0, s>>>(n, 9, (const T *)(field == TLSPH_FIELD_F ? c->Fd : c->Pd), n, c->perm,
+                                                dst);
+        break;
+    }
+    default: return fail(c, TLSPH_ERR_ARG, "field %d cannot be read", field);
+    }
+    CKL();
+    return TLSPH_OK;
+}
+
+template <typename T> tlsph_status write_impl(tlsph_ctx *c, int field, const double *src /* device */) {
+    const int64_t n = c->n;
+    const int dim = c->p.dim;
+    const unsigned nb = blocks_for(n);
+    cudaStream_t s = c->stream;
+    switch (field) {
+    case TLSPH_FIELD_U:
+        k_from_caller<double><<<nb, kThreads, 0, s>>>(n, dim, src, c->perm, c->u64, n);
+        CKL();
+        k_refresh_ug<T><<<nb, kThreads, 0, s>>>(n, dim, c->u64, (V4<T> *)c->ug[c->parity]);
+        break;
+    case TLSPH_FIELD_V: k_v4_from_caller<T><<<nb, kThreads, 0, s>>>(n, dim, 0, src, c->perm, (V4<T> *)c->vs[c->parity]); break;
+    case TLSPH_FIELD_S: k_v4_from_caller<T><<<nb, kThreads, 0, s>>>(n, 1, 3, src, c->perm, (V4<T> *)c->vs[c->parity]); break;
+    case TLSPH_FIELD_SDOT: k_from_caller<T><<<nb, kThreads, 0, s>>>(n, 1, src, c->perm, (T *)c->sdot, n); break;
+    case TLSPH_FIELD_H: k_from_caller<T><<<nb, kThreads, 0, s>>>(n, 1, src, c->perm, (T *)c->H, n); break;
+    case TLSPH_FIELD_EPSP: k_from_caller<T><<<nb, kThreads, 0, s>>>(n, 1, src, c->perm, (T *)c->ep, n); break;
+    case TLSPH_FIELD_CPINV: k_cpinv_from_caller<T><<<nb, kThreads, 0, s>>>(n, src, c->perm, (T *)c->K); break;
+    default: return fail(c, TLSPH_ERR_ARG, "field %d cannot be written", field);
+    }
+    CKL();
+    return TLSPH_OK;
+}
+
+// checkpoint blob: header, u64, ug, vs, sdot, H, K, ep, t, dt (sorted order)
+template <typename T> tlsph_status state_io(tlsph_ctx *c, char *blob /* host */, bool save) {
+    const size_t n = (size_t)c->n, ts = sizeof(T);
+    struct Part { void *p; size_t bytes; };
+    Part parts[] = {{c->u64, 3 * n * 8},          {c->ug[c->parity], n * sizeof(V4<T>)},
+                    {c->vs[c->parity], n * sizeof(V4<T>)}, {c->sdot, n * ts},
+                    {c->H, n * ts},               {c->K, 6 * n * ts},
+                    {c->ep, n * ts},              {c->t, (size_t)c->nspec * 8},
+                    {c->dt, (size_t)c->nspec * 8}};
+    int64_t hdr[8] = {0x54534c50485354LL, (int64_t)n, c->p.precision, c->nspec, c->steps, c->p.dim, 0, 0};
+    cudaStream_t s = c->stream;
+    if (save) {
+        memcpy(blob, hdr, sizeof hdr);
+    } else {
+        int64_t h2[8];
+        memcpy(h2, blob, sizeof h2);
+        if (h2[0] != hdr[0] || h2[1] != hdr[1] || h2[2] != hdr[2] || h2[3] != hdr[3] || h2[5] != hdr[5])
+            return fail(c, TLSPH_ERR_ARG, "checkpoint does not match this context");
+        c->steps = h2[4];
+    }
+    size_t off = 64;
+    for (const Part &pt : parts) {
+        if (save) CK(cudaMemcpyAsync(blob + off, pt.p, pt.bytes, cudaMemcpyDeviceToHost, s));
+        else CK(cudaMemcpyAsync(pt.p, blob + off, pt.bytes, cudaMemcpyHostToDevice, s));
+        off += pt.bytes;
+    }
+    CK(cudaStreamSynchronize(s));
+    return TLSPH_OK;
+}
+
+tlsph_status check_flags(tlsph_ctx *c) {
+    int hf[kNumFlags];
+    CK(cudaMemcpyAsync(hf, c->flags, sizeof hf, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t dn = hf[kFlagNonfinite] - c->flags_seen[kFlagNonfinite];
+    int64_t dc = hf[kFlagNoconv] - c->flags_seen[kFlagNoconv];
+    for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = hf[q];
+    if (dn > 0) return fail(c, TLSPH_ERR_NONFINITE, "%lld non-finite stresses or accelerations", (long long)dn);
+    if (dc > 0) return fail(c, TLSPH_ERR_NOCONVERGE, "%lld J2 return maps did not converge", (long long)dc);
+    return TLSPH_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C-ABI
+extern "C" {
+
+tlsph_status tlsph_create(const tlsph_params *params, tlsph_ctx **out) {
+    if (!out) return TLSPH_ERR_ARG;
+    *out = nullptr;
+    if (!params || (params->dim != 2 && params->dim != 3) || !(params->h > 0.0) || !(params->support > 0.0) ||
+        (params->precision != TLSPH_FP64 && params->precision != TLSPH_FP32_U64) ||
+        (params->integrator != 0 && params->integrator != 1) || params->dt_mode < 0 || params->dt_mode > 2 ||
+        (params->dt_mode == TLSPH_DT_FIXED && !(params->fixed_dt > 0.0)) ||
+        (params->dt_mode != TLSPH_DT_FIXED && !(params->cfl > 0.0)))
+        return TLSPH_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || params->device < 0 || params->device >= ndev) {
+        cudaGetLastError();
+        return TLSPH_ERR_CUDA;
+    }
+    if (cudaSetDevice(params->device) != cudaSuccess) return TLSPH_ERR_CUDA;
+    tlsph_ctx *c = new tlsph_ctx();
+    c->p = *params;
+    if (params->cuda_stream) {
+        c->stream = (cudaStream_t)params->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return TLSPH_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return TLSPH_OK;
+}
+
+void tlsph_destroy(tlsph_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->p.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_device(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *tlsph_last_error(const tlsph_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+tlsph_status tlsph_set_materials(tlsph_ctx *c, int n, const tlsph_material *m) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (n <= 0 || n > 65535 || !m) return fail(c, TLSPH_ERR_ARG, "bad material table");
+    for (int i = 0; i < n; i++) {
+        if (!(m[i].E > 0.0) || !(m[i].nu > -1.0 && m[i].nu < 0.5) || !(m[i].rho > 0.0))
+            return fail(c, TLSPH_ERR_ARG, "material %d: need E > 0, -1 < nu < 0.5, rho > 0", i);
+        if (m[i].model != TLSPH_MODEL_NH && m[i].model != TLSPH_MODEL_J2)
+            return fail(c, TLSPH_ERR_ARG, "material %d: unknown model %d", i, m[i].model);
+        if (m[i].model == TLSPH_MODEL_J2 && !(m[i].sigma_y0 > 0.0))
+            return fail(c, TLSPH_ERR_ARG, "material %d: J2 needs sigma_y0 > 0", i);
+        if (m[i].fracture && m[i].model != TLSPH_MODEL_J2 && (!(m[i].Gc > 0.0) || !(m[i].eps0 > 0.0)))
+            return fail(c, TLSPH_ERR_ARG, "material %d: fracture needs Gc > 0 and eps0 > 0", i);
+    }
+    c->mats.assign(m, m + n);
+    c->built = false;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_create_particles(tlsph_ctx *c, int64_t n, const double *X0, const double *vol, const double *v0,
+                                    const int32_t *material_id, const int32_t *specimen_id) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (c->mats.empty()) return fail(c, TLSPH_ERR_STATE, "set_materials must come before create_particles");
+    if (n <= 0 || n >= (int64_t)1 << 31 || !X0 || !vol || !material_id)
+        return fail(c, TLSPH_ERR_ARG, "create_particles: bad size or null array");
+    const int d = c->p.dim;
+    c->n = n;
+    c->X0h.assign(3 * n, 0.0);
+    c->volh.assign(vol, vol + n);
+    c->midh.assign(material_id, material_id + n);
+    c->spech.assign(n, 0);
+    c->v0h.clear();
+    if (v0) c->v0h.assign(v0, v0 + n * d);
+    c->nspec = 1;
+    for (int64_t i = 0; i < n; i++) {
+        for (int k = 0; k < d; k++) {
+            double x = X0[d * i + k];
+            if (!std::isfinite(x)) return fail(c, TLSPH_ERR_ARG, "particle %lld: non-finite position", (long long)i);
+            c->X0h[3 * i + k] = x;
+        }
+        if (!(vol[i] > 0.0)) return fail(c, TLSPH_ERR_ARG, "particle %lld: volume must be > 0", (long long)i);
+        if (material_id[i] < 0 || material_id[i] >= (int)c->mats.size())
+            return fail(c, TLSPH_ERR_ARG, "particle %lld: material id out of range", (long long)i);
+        if (specimen_id) {
+            if (specimen_id[i] < 0) return fail(c, TLSPH_ERR_ARG, "particle %lld: negative specimen id", (long long)i);
+            c->spech[i] = specimen_id[i];
+            c->nspec = std::max(c->nspec, specimen_id[i] + 1);
+        }
+    }
+    c->bcs.clear();
+    c->notches.clear();
+    free_device(c);
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_add_bc(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_mask, const double value[3],
+                          double t_start, double t_end, double ramp, double area) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (c->n <= 0) return fail(c, TLSPH_ERR_STATE, "create_particles must come before add_bc");
+    if (!mask || !value || kind < 0 || kind > 3) return fail(c, TLSPH_ERR_ARG, "add_bc: bad kind or null array");
+    if (c->bcs.size() >= 32767) return fail(c, TLSPH_ERR_ARG, "too many boundary conditions");
+    BCHost b;
+    b.kind = kind;
+    b.comp_mask = comp_mask;
+    for (int q = 0; q < 3; q++) b.value[q] = value[q];
+    b.t_start = t_start;
+    b.t_end = t_end;
+    b.ramp = ramp;
+    b.area = area;
+    b.mask.assign(mask, mask + c->n);
+    b.count = 0;
+    for (int64_t i = 0; i < c->n; i++) b.count += mask[i] ? 1 : 0;
+    c->bcs.push_back(std::move(b));
+    c->built = false;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_add_notch(tlsph_ctx *c, const double quad[12]) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!quad || c->notches.size() / 12 >= 512) return fail(c, TLSPH_ERR_ARG, "add_notch: null or more than 512");
+    c->notches.insert(c->notches.end(), quad, quad + 12);
+    c->built = false;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (c->n <= 0 || c->mats.empty()) return fail(c, TLSPH_ERR_STATE, "no particles");
+    cudaSetDevice(c->p.device);
+    tlsph_status st = c->p.precision == TLSPH_FP64 ? build_impl<double>(c) : build_impl<float>(c);
+    if (st != TLSPH_OK && st != TLSPH_ERR_SINGULAR_L) free_device(c);
+    return st;
+}
+
+tlsph_status tlsph_step_async(tlsph_ctx *c, int64_t nsteps) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before step");
+    if (nsteps < 0) return fail(c, TLSPH_ERR_ARG, "negative step count");
+    return c->p.precision == TLSPH_FP64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
+}
+
+tlsph_status tlsph_sync(tlsph_ctx *c) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    return check_flags(c);
+}
+
+tlsph_status tlsph_step(tlsph_ctx *c, int64_t nsteps) {
+    tlsph_status st = tlsph_step_async(c, nsteps);
+    if (st != TLSPH_OK) return st;
+    return check_flags(c);
+}
+
+int64_t tlsph_field_bytes(const tlsph_ctx *c, int field) {
+    if (!c || c->n <= 0) return -1;
+    if (field == TLSPH_FIELD_STATE) return c->built ? (int64_t)state_bytes(c) : -1;
+    int nc = field_comps(c, field);
+    return nc < 0 ? -1 : (int64_t)nc * c->n * 8;
+}
+
+tlsph_status tlsph_read_state(tlsph_ctx *c, int field, void *dst, size_t bytes, int dst_is_device) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before read_state");
+    int64_t need = tlsph_field_bytes(c, field);
+    if (need < 0) return fail(c, TLSPH_ERR_ARG, "unknown field %d", field);
+    if (!dst || bytes != (size_t)need) return fail(c, TLSPH_ERR_ARG, "read_state: need %lld bytes", (long long)need);
+    if (field == TLSPH_FIELD_STATE) {
+        if (dst_is_device) return fail(c, TLSPH_ERR_ARG, "the checkpoint blob is host memory");
+        return c->p.precision == TLSPH_FP64 ? state_io<double>(c, (char *)dst, true)
+                                            : state_io<float>(c, (char *)dst, true);
+    }
+    double *dev = (double *)dst;
+    double *tmp = nullptr;
+    if (!dst_is_device) {
+        if (cudaMalloc(&tmp, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, TLSPH_ERR_OOM, "read_state staging buffer");
+        }
+        dev = tmp;
+    }
+    tlsph_status st = c->p.precision == TLSPH_FP64 ? read_impl<double>(c, field, dev) : read_impl<float>(c, field, dev);
+    if (st == TLSPH_OK && !dst_is_device) {
+        cudaError_t e = cudaMemcpyAsync(dst, dev, need, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(c, TLSPH_ERR_CUDA, "read_state copy: %s", cudaGetErrorString(e));
+    } else if (st == TLSPH_OK) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(c, TLSPH_ERR_CUDA, "read_state: %s", cudaGetErrorString(e));
+    }
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
+tlsph_status tlsph_write_state(tlsph_ctx *c, int field, const void *src, size_t bytes, int src_is_device) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before write_state");
+    int64_t need = tlsph_field_bytes(c, field);
+    if (need < 0) return fail(c, TLSPH_ERR_ARG, "unknown field %d", field);
+    if (!src || bytes != (size_t)need) return fail(c, TLSPH_ERR_ARG, "write_state: need %lld bytes", (long long)need);
+    if (field == TLSPH_FIELD_STATE) {
+        if (src_is_device) return fail(c, TLSPH_ERR_ARG, "the checkpoint blob is host memory");
+        return c->p.precision == TLSPH_FP64 ? state_io<double>(c, (char *)src, false)
+                                            : state_io<float>(c, (char *)src, false);
+    }
+    const double *dev = (const double *)src;
+    double *tmp = nullptr;
+    if (!src_is_device) {
+        if (cudaMalloc(&tmp, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, TLSPH_ERR_OOM, "write_state staging buffer");
+        }
+        cudaMemcpyAsync(tmp, src, need, cudaMemcpyHostToDevice, c->stream);
+        dev = tmp;
+    }
+    tlsph_status st =
+        c->p.precision == TLSPH_FP64 ? write_impl<double>(c, field, dev) : write_impl<float>(c, field, dev);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (st == TLSPH_OK && e != cudaSuccess) st = fail(c, TLSPH_ERR_CUDA, "write_state: %s", cudaGetErrorString(e));
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
+tlsph_status tlsph_energies(tlsph_ctx *c, double out[6]) {
+    if (!c || !out) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    return c->p.precision == TLSPH_FP64 ? energies_impl<double>(c, out) : energies_impl<float>(c, out);
+}
+
+tlsph_status tlsph_time(tlsph_ctx *c, int specimen, double *t, double *dt) {
+    if (!c || !t || !dt) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    if (specimen < 0 || specimen >= c->nspec) return fail(c, TLSPH_ERR_ARG, "specimen out of range");
+    CK(cudaMemcpyAsync(t, c->t + specimen, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dt, c->dt + specimen, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return TLSPH_OK;
+}
+
+int64_t tlsph_nnz(const tlsph_ctx *c) { return (c && c->built) ? c->nnz : -1; }
+
+tlsph_status tlsph_neighbours(tlsph_ctx *c, int64_t *row_ptr, int32_t *col, int64_t cap) {
+    if (!c || !row_ptr || !col) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    if (cap < c->nnz) return fail(c, TLSPH_ERR_ARG, "cap < nnz (%lld)", (long long)c->nnz);
+    const int64_t n = c->n;
+    int64_t *len, *rp;
+    int *co;
+    size_t mark = c->allocs.size();
+    DA(len, (n + 1) * 8);
+    DA(rp, (n + 1) * 8);
+    DA(co, std::max<int64_t>(c->nnz, 1) * 4);
+    CK(cudaMemsetAsync(len, 0, (n + 1) * 8, c->stream));
+    k_rowlen_caller<<<blocks_for(n), kThreads, 0, c->stream>>>(n, c->row_len, c->perm, len);
+    CKL();
+    tlsph_status st = scan_exclusive(c, n + 1, len, rp);
+    if (st != TLSPH_OK) return st;
+    k_rows_caller<<<blocks_for(n), kThreads, 0, c->stream>>>(n, c->row_ptr, c->col, c->perm, rp, co);
+    CKL();
+    CK(cudaMemcpyAsync(row_ptr, rp, (n + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(col, co, c->nnz * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    while (c->allocs.size() > mark) {
+        cudaFree(c->allocs.back());
+        c->allocs.pop_back();
+    }
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_permutation(tlsph_ctx *c, int64_t *perm) {
+    if (!c || !perm) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    std::vector<int> p(c->n);
+    CK(cudaMemcpyAsync(p.data(), c->perm, c->n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t k = 0; k < c->n; k++) perm[k] = p[k];
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_get_info(tlsph_ctx *c, tlsph_info *out) {
+    if (!c || !out) return TLSPH_ERR_ARG;
+    out->steps = c->steps;
+    out->kernel_launches = c->launches;
+    out->nnz = c->built ? c->nnz : -1;
+    out->max_row = c->max_row;
+    out->bytes_per_step = c->bytes_per_step;
+    out->noconverge = out->nonfinite = 0;
+    if (c->built) {
+        int hf[kNumFlags];
+        CK(cudaMemcpyAsync(hf, c->flags, sizeof hf, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out->noconverge = hf[kFlagNoconv];
+        out->nonfinite = hf[kFlagNonfinite];
+    }
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (option == TLSPH_OPT_KERNEL_TIMING) {
+        if (c->timing && !value) {
+            cudaStreamSynchronize(c->stream);
+            collect_timing(c);
+        }
+        c->timing = value != 0;
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_RECORD_ACC) {
+        c->record_acc = value != 0;
+        return TLSPH_OK;
+    }
+    return fail(c, TLSPH_ERR_ARG, "unknown option %d", option);
+}
+
+tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[2], int64_t count[2]) {
+    if (!c || !ms || !count) return TLSPH_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    for (int q = 0; q < 2; q++) {
+        ms[q] = c->ms[q];
+        count[q] = c->cnt[q];
+        c->ms[q] = 0.0;
+        c->cnt[q] = 0;
+    }
+    return TLSPH_OK;
+}
+
+}  // extern "C"

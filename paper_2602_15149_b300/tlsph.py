@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C-ABI in ``include/tlsph.h`` (argument marshalling only).
+
+Every computation runs in ``_lib/libtlsph.so`` (sm_103a CUDA).  There is no
+fallback: if the library is missing this module raises on load.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtlsph.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_SINGULAR_L, ERR_NONFINITE, ERR_NOCONVERGE, ERR_TIMEOUT, ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+FP64, FP32_U64 = 0, 1
+DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
+MODEL_NH, MODEL_J2 = 2, 3
+BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
+FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "ACC": 11, "CPINV": 12,
+         "STATE": 100}
+OPT_KERNEL_TIMING, OPT_RECORD_ACC = 1, 2
+
+# every entry point declared in include/tlsph.h
+EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_materials", "tlsph_create_particles",
+           "tlsph_add_bc", "tlsph_add_notch", "tlsph_build_ref_neighbours", "tlsph_step", "tlsph_step_async",
+           "tlsph_sync", "tlsph_read_state", "tlsph_write_state", "tlsph_field_bytes", "tlsph_energies", "tlsph_time",
+           "tlsph_neighbours", "tlsph_permutation", "tlsph_nnz", "tlsph_get_info", "tlsph_set_option",
+           "tlsph_kernel_times"]
+
+
+class Params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("precision", C.c_int), ("integrator", C.c_int), ("h", C.c_double),
+                ("support", C.c_double), ("cfl", C.c_double), ("dt_mode", C.c_int), ("fixed_dt", C.c_double),
+                ("gravity", C.c_double * 3), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+
+
+class Material(C.Structure):
+    _fields_ = [("model", C.c_int), ("rho", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("sigma_y0", C.c_double), ("H_hard", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("fracture", C.c_int), ("Gc", C.c_double), ("eps0", C.c_double), ("s_lim", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("noconverge", C.c_int64),
+                ("nonfinite", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int64), ("bytes_per_step", C.c_double)]
+
+
+class TLSPHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tlsph status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtlsph.so and declare the C signatures (raises if the library is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2602_15149_b300.build.build_library()")
+    lib = C.CDLL(path)
+    P, D, I64, I32, U8, V = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32), \
+        C.POINTER(C.c_uint8), C.c_void_p
+    sig = {
+        "tlsph_create": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
+        "tlsph_destroy": (None, [P]),
+        "tlsph_last_error": (C.c_char_p, [P]),
+        "tlsph_set_materials": (C.c_int, [P, C.c_int, C.POINTER(Material)]),
+        "tlsph_create_particles": (C.c_int, [P, C.c_int64, D, D, D, I32, I32]),
+        "tlsph_add_bc": (C.c_int, [P, U8, C.c_int, C.c_int, D, C.c_double, C.c_double, C.c_double, C.c_double]),
+        "tlsph_add_notch": (C.c_int, [P, D]),
+        "tlsph_build_ref_neighbours": (C.c_int, [P]),
+        "tlsph_step": (C.c_int, [P, C.c_int64]),
+        "tlsph_step_async": (C.c_int, [P, C.c_int64]),
+        "tlsph_sync": (C.c_int, [P]),
+        "tlsph_read_state": (C.c_int, [P, C.c_int, V, C.c_size_t, C.c_int]),
+        "tlsph_write_state": (C.c_int, [P, C.c_int, V, C.c_size_t, C.c_int]),
+        "tlsph_field_bytes": (C.c_int64, [P, C.c_int]),
+        "tlsph_energies": (C.c_int, [P, D]),
+        "tlsph_time": (C.c_int, [P, C.c_int, D, D]),
+        "tlsph_neighbours": (C.c_int, [P, I64, I32, C.c_int64]),
+        "tlsph_permutation": (C.c_int, [P, I64]),
+        "tlsph_nnz": (C.c_int64, [P]),
+        "tlsph_get_info": (C.c_int, [P, C.POINTER(Info)]),
+        "tlsph_set_option": (C.c_int, [P, C.c_int, C.c_int]),
+        "tlsph_kernel_times": (C.c_int, [P, D, I64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _d(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class TLSPH:
+    """One TLSPH context on a CUDA device (methods carry the C-ABI names without the prefix)."""
+
+    def __init__(self, dim, h, precision=FP32_U64, cfl=0.3, dt_mode=DT_CFL_STATIC, fixed_dt=0.0,
+                 gravity=(0.0, 0.0, 0.0), support=2.0, device=0, stream=None):
+        self.lib = load_library()
+        p = Params(dim, precision, 1, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity),
+                   stream, device)
+        ctx = C.c_void_p()
+        st = self.lib.tlsph_create(C.byref(p), C.byref(ctx))
+        if st != OK:
+            raise TLSPHError(st, "tlsph_create failed (no CUDA device or bad parameters)")
+        self.ctx = ctx
+        self.dim = dim
+        self.precision = precision
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.tlsph_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def _ck(self, st, what=""):
+        if st != OK:
+            raise TLSPHError(st, f"{what}: {self.last_error()}")
+        return st
+
+    def last_error(self) -> str:
+        return self.lib.tlsph_last_error(self.ctx).decode()
+
+    def set_materials(self, mats):
+        arr = (Material * len(mats))(*[Material(m.model, m.rho, m.E, m.nu, m.sigma_y0, m.H_hard, m.beta1, m.beta2,
+                                                m.fracture, m.Gc, m.eps0, m.s_lim) for m in mats])
+        self._ck(self.lib.tlsph_set_materials(self.ctx, len(mats), arr), "set_materials")
+
+    def create_particles(self, X0, vol, v0=None, material_id=None, specimen_id=None):
+        X0 = np.ascontiguousarray(X0, np.float64)
+        n = X0.shape[0]
+        vol = np.ascontiguousarray(vol, np.float64)
+        mid = np.zeros(n, np.int32) if material_id is None else np.ascontiguousarray(material_id, np.int32)
+        v0a = None if v0 is None else np.ascontiguousarray(v0, np.float64)
+        sid = None if specimen_id is None else np.ascontiguousarray(specimen_id, np.int32)
+        I32 = C.POINTER(C.c_int32)
+        self._ck(self.lib.tlsph_create_particles(self.ctx, n, _d(X0), _d(vol), None if v0a is None else _d(v0a),
+                                                 mid.ctypes.data_as(I32),
+                                                 None if sid is None else sid.ctypes.data_as(I32)),
+                 "create_particles")
+        self.n = n
+
+    def add_bc(self, mask, kind, comp_mask, value, t_start=0.0, t_end=-1.0, ramp=0.0, area=0.0):
+        m = np.ascontiguousarray(mask, np.uint8)
+        val = np.zeros(3)
+        val[:len(value)] = value
+        self._ck(self.lib.tlsph_add_bc(self.ctx, m.ctypes.data_as(C.POINTER(C.c_uint8)), kind, comp_mask, _d(val),
+                                       t_start, t_end, ramp, area), "add_bc")
+
+    def add_notch(self, quad):
+        q = np.ascontiguousarray(quad, np.float64).reshape(12)
+        self._ck(self.lib.tlsph_add_notch(self.ctx, _d(q)), "add_notch")
+
+    def build_ref_neighbours(self):
+        self._ck(self.lib.tlsph_build_ref_neighbours(self.ctx), "build_ref_neighbours")
+
+    def step(self, nsteps=1, check=True):
+        st = self.lib.tlsph_step(self.ctx, nsteps)
+        if check:
+            self._ck(st, "step")
+        return st
+
+    def step_async(self, nsteps=1):
+        self._ck(self.lib.tlsph_step_async(self.ctx, nsteps), "step_async")
+
+    def sync(self, check=True):
+        st = self.lib.tlsph_sync(self.ctx)
+        if check:
+            self._ck(st, "sync")
+        return st
+
+    def field_bytes(self, field: str) -> int:
+        return int(self.lib.tlsph_field_bytes(self.ctx, FIELD[field]))
+
+    def read_state(self, field: str, out=None):
+        """Read a field in the caller's order into a new numpy array, or into ``out``
+        (a numpy array, or a torch CUDA tensor of float64 for a device-side read)."""
+        nb = self.field_bytes(field)
+        if field == "STATE":
+            buf = np.zeros(nb, np.uint8) if out is None else out
+            self._ck(self.lib.tlsph_read_state(self.ctx, FIELD[field], buf.ctypes.data, nb, 0), "read_state")
+            return buf
+        if out is not None and hasattr(out, "data_ptr"):
+            self._ck(self.lib.tlsph_read_state(self.ctx, FIELD[field], out.data_ptr(), nb, 1), "read_state")
+            return out
+        a = np.zeros(nb // 8) if out is None else out
+        self._ck(self.lib.tlsph_read_state(self.ctx, FIELD[field], a.ctypes.data, nb, 0), "read_state " + field)
+        per = nb // 8 // self.n
+        if per == 9:
+            return a.reshape(self.n, 3, 3)
+        return a.reshape(self.n, per) if per > 1 else a
+
+    def write_state(self, field: str, values):
+        nb = self.field_bytes(field)
+        if hasattr(values, "data_ptr"):
+            self._ck(self.lib.tlsph_write_state(self.ctx, FIELD[field], values.data_ptr(), nb, 1), "write_state")
+            return
+        a = np.ascontiguousarray(values, np.uint8 if field == "STATE" else np.float64)
+        self._ck(self.lib.tlsph_write_state(self.ctx, FIELD[field], a.ctypes.data, nb, 0), "write_state " + field)
+
+    def energies(self):
+        out = np.zeros(6)
+        self._ck(self.lib.tlsph_energies(self.ctx, _d(out)), "energies")
+        return {"KE": out[0], "SE": out[1], "FE": out[2], "PW": out[3], "t": out[4], "dt": out[5]}
+
+    def time(self, specimen=0):
+        t, dt = C.c_double(), C.c_double()
+        self._ck(self.lib.tlsph_time(self.ctx, specimen, C.byref(t), C.byref(dt)), "time")
+        return t.value, dt.value
+
+    def nnz(self) -> int:
+        return int(self.lib.tlsph_nnz(self.ctx))
+
+    def neighbours(self):
+        nnz = self.nnz()
+        rp = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(max(nnz, 1), np.int32)
+        self._ck(self.lib.tlsph_neighbours(self.ctx, rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           col.ctypes.data_as(C.POINTER(C.c_int32)), nnz), "neighbours")
+        return rp, col[:nnz]
+
+    def permutation(self):
+        p = np.zeros(self.n, np.int64)
+        self._ck(self.lib.tlsph_permutation(self.ctx, p.ctypes.data_as(C.POINTER(C.c_int64))), "permutation")
+        return p
+
+    def get_info(self) -> dict:
+        info = Info()
+        self._ck(self.lib.tlsph_get_info(self.ctx, C.byref(info)), "get_info")
+        return {k: getattr(info, k) for k, _ in Info._fields_}
+
+    def set_option(self, option: int, value: int):
+        self._ck(self.lib.tlsph_set_option(self.ctx, option, value), "set_option")
+
+    def kernel_times(self):
+        ms = np.zeros(2)
+        cnt = np.zeros(2, np.int64)
+        self._ck(self.lib.tlsph_kernel_times(self.ctx, _d(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
+                 "kernel_times")
+        return {"pass2_ms": ms[0], "pass2_launches": int(cnt[0]), "pass1_ms": ms[1], "pass1_launches": int(cnt[1])}
+
+
+def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
+    """Create a context from a :class:`workloads.Case` (marshalling only)."""
+    prec = precision if precision is not None else (FP64 if case.precision == "fp64" else FP32_U64)
+    t = TLSPH(case.dim, case.h, prec, case.cfl, case.dt_mode, case.fixed_dt, case.gravity, device=device,
+              stream=stream)
+    t.set_materials(case.materials)
+    t.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
+    for b in case.bcs:
+        t.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
+    for q in case.notches:
+        t.add_notch(q)
+    if build:
+        t.build_ref_neighbours()
+    return t

@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/tlsph.h declares.
+
+No compute calls are made here (no GPU needed): only argument validation that
+returns before any device work.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2602_15149_b300 import build, tlsph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(tlsph_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return tlsph.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = declared_functions()
+    assert len(decl) >= 20
+    missing = [n for n in decl if not hasattr(lib, n)]
+    assert not missing
+    assert sorted(tlsph.EXPORTS) == decl
+
+
+def test_argument_errors_without_device_work(lib):
+    ctx = ctypes.c_void_p()
+    bad = tlsph.Params(4, 1, 1, 1e-3, 2.0, 0.3, 2, 0.0, (ctypes.c_double * 3)(0, 0, 0), None, 0)
+    assert lib.tlsph_create(ctypes.byref(bad), ctypes.byref(ctx)) == tlsph.ERR_ARG
+    neg_h = tlsph.Params(3, 1, 1, -1.0, 2.0, 0.3, 2, 0.0, (ctypes.c_double * 3)(0, 0, 0), None, 0)
+    assert lib.tlsph_create(ctypes.byref(neg_h), ctypes.byref(ctx)) == tlsph.ERR_ARG
+    assert lib.tlsph_create(None, ctypes.byref(ctx)) == tlsph.ERR_ARG
+    assert lib.tlsph_step(None, 1) == tlsph.ERR_ARG
+    assert lib.tlsph_nnz(None) == -1
+    assert lib.tlsph_field_bytes(None, 0) == -1
+    lib.tlsph_destroy(None)
+
+
+def test_library_targets_sm103a():
+    cmd = build.nvcc_command()
+    assert "arch=compute_103a,code=sm_103a" in " ".join(cmd)
+    assert os.path.exists(build.LIB)
