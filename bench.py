@@ -190,7 +190,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
 
-    case = W.block_3d(*SHAPE, steps=args.steps)
+    shape = tuple(int(x) for x in args.shape.split(","))
+    case = W.block_3d(*shape, steps=args.steps)
     n = case.n
     g = tlsph.from_case(case, device=local, stream=stream.cuda_stream)
     info = g.get_info()
@@ -263,8 +264,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "block_3d_j2 128x128x64 jittered lattice, J2 plasticity, top pressed at 5 m/s "
-                               "(FP32 fields, FP64 displacement)", "particles": n, "neighbour_pairs": nnz,
+        "config": {"workload": f"block_3d_j2 {'x'.join(map(str, shape))} jittered lattice, J2 plasticity, top "
+                               "pressed at 5 m/s (FP32 fields, FP64 displacement)", "particles": n, "neighbour_pairs": nnz,
                    "mean_neighbours": nnz / n, "l2": "inputs larger than L2 (~1.3 GB of state), no flush",
                    "parallelism": f"replicas x{ws} (independent blocks)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -291,6 +292,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
+                    help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -21,7 +21,7 @@ MODEL_NH, MODEL_J2 = 2, 3
 BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
 FIELDS = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "FP": 9,
-          "L": 10, "ACC": 11, "CPINV": 12, "SDD": 13}
+          "L": 10, "ACC": 11, "CPINV": 12, "SDD": 13, "LAP": 14}
 
 
 class _Params(C.Structure):

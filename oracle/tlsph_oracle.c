@@ -88,6 +88,7 @@ typedef struct orc_ctx {
     int64_t n;
     int nspec;
     double *X0, *vol, *u, *v, *acc, *s, *sdot, *sdd, *Hh, *Fp, *ep;
+    double *lap, *pf_b, *pf_k, *pf_g;  /* phase-field terms of the current step */
     int32_t *mid, *spec;
     double *F, *P, *L;           /* per-particle 3x3 (L: in-plane block) */
     int32_t *status;             /* per-particle return-map status */
@@ -410,7 +411,7 @@ orc_ctx *orc_create(const orc_params *p) {
 
 static void free_particles(orc_ctx *c) {
     free(c->X0); free(c->vol); free(c->u); free(c->v); free(c->acc); free(c->s); free(c->sdot);
-    free(c->sdd); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
+    free(c->sdd); free(c->lap); free(c->pf_b); free(c->pf_k); free(c->pf_g); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
     free(c->P); free(c->L); free(c->status); free(c->row_ptr); free(c->col); free(c->perm);
     free(c->t); free(c->dt); free(c->vmax); free(c->amax); free(c->cmax);
     for (int b = 0; b < c->nbc; b++) free(c->bc[b].mask);
@@ -454,6 +455,10 @@ int orc_create_particles(orc_ctx *c, int64_t n, const double *X0, const double *
     c->s = xcalloc(n, sizeof(double));
     c->sdot = xcalloc(n, sizeof(double));
     c->sdd = xcalloc(n, sizeof(double));
+    c->lap = xcalloc(n, sizeof(double));
+    c->pf_b = xcalloc(n, sizeof(double));
+    c->pf_k = xcalloc(n, sizeof(double));
+    c->pf_g = xcalloc(n, sizeof(double));
     c->Hh = xcalloc(n, sizeof(double));
     c->Fp = xcalloc(n * 9, sizeof(double));
     c->ep = xcalloc(n, sizeof(double));
@@ -965,13 +970,24 @@ static int one_step(orc_ctx *c) {
             }
         }
         for (int k = 0; k < 3; k++) c->acc[3 * i + k] = k < d ? a[k] : 0.0;
-        if (is_fracture(c, i)) { /* eq. phasefieldddot */
-            double e0 = mi->eps0, Gc = mi->Gc, s = c->s[i], Hh = c->Hh[i];
-            c->sdd[i] = c0 * c0 / (2.0 * e0) *
-                        (2.0 * e0 * lap + (1.0 - s) / (2.0 * e0) -
-                         2.0 * sqrt(4.0 * e0 * Hh / Gc + 1.0) / c0 * c->sdot[i] - 2.0 * s * Hh / Gc);
-        } else {
-            c->sdd[i] = 0.0;
+        c->lap[i] = lap;
+        if (is_fracture(c, i)) {
+            /* eq. phasefieldddot: sdd = r - gamma sdot, with
+             *   r = c^2/(2 eps0) (2 eps0 lap + (1 - s)/(2 eps0) - 2 s H/Gc)   (all terms but the damping),
+             *   gamma = (c/eps0) sqrt(4 eps0 H/Gc + 1)                     (the damping of M, eq. Mparameter1),
+             *   k = c^2/(2 eps0) (1/(2 eps0) + 2 H/Gc)                     (-dr/ds).
+             * reading: the local terms are taken at the new time level,
+             *   sdot_{n+1} = (sdot_n + dt r_n) / (1 + dt gamma + dt^2 k),  s_{n+1} = s_n + dt sdot_{n+1}.
+             * The explicit update of Algorithm 1 diverges once dt gamma > 2, which crack tips
+             * reach, contradicting the monotone, non-wave-like evolution M is chosen for
+             * (Sec. 2.2); the fixed points are unchanged. */
+            double e0 = mi->eps0, Gc = mi->Gc, Hh = c->Hh[i], s = c->s[i];
+            double r = c0 * c0 / (2.0 * e0) * (2.0 * e0 * lap + (1.0 - s) / (2.0 * e0) - 2.0 * s * Hh / Gc);
+            double k = c0 * c0 / (2.0 * e0) * (1.0 / (2.0 * e0) + 2.0 * Hh / Gc);
+            double gam = c0 / e0 * sqrt(4.0 * e0 * Hh / Gc + 1.0);
+            c->pf_b[i] = r;
+            c->pf_k[i] = k;
+            c->pf_g[i] = gam;
         }
     }
     /* Step 3-4: boundary conditions and update (Algorithm 1) */
@@ -1003,7 +1019,10 @@ static int one_step(orc_ctx *c) {
         if (vv > c->vmax[sp]) c->vmax[sp] = vv;
         if (aa > c->amax[sp]) c->amax[sp] = aa;
         if (is_fracture(c, i)) {
-            c->sdot[i] = c->sdot[i] + dt * c->sdd[i];
+            double sd1 = (c->sdot[i] + dt * c->pf_b[i]) /
+                         (1.0 + dt * c->pf_g[i] + dt * dt * c->pf_k[i]);
+            c->sdd[i] = (sd1 - c->sdot[i]) / dt;
+            c->sdot[i] = sd1;
             double sn = c->s[i] + dt * c->sdot[i];
             c->s[i] = sn < 0.0 ? 0.0 : (sn > 1.0 ? 1.0 : sn); /* reading: s kept in [0, 1] */
         }
@@ -1044,6 +1063,7 @@ int orc_step(orc_ctx *c, int64_t nsteps) {
 #define ORC_F_ACC 11
 #define ORC_F_CPINV 12
 #define ORC_F_SDD 13
+#define ORC_F_LAP 14
 
 /* F and P evaluated at the current state without committing the state
  * (J2 runs a trial return map from the stored F_p). */
@@ -1080,6 +1100,7 @@ int orc_read(orc_ctx *c, int field, double *out) {
     case ORC_F_SDOT: memcpy(out, c->sdot, sizeof(double) * n); return ORC_OK;
     case ORC_F_H: memcpy(out, c->Hh, sizeof(double) * n); return ORC_OK;
     case ORC_F_SDD: memcpy(out, c->sdd, sizeof(double) * n); return ORC_OK;
+    case ORC_F_LAP: memcpy(out, c->lap, sizeof(double) * n); return ORC_OK;
     case ORC_F_EPSP: memcpy(out, c->ep, sizeof(double) * n); return ORC_OK;
     case ORC_F_FP: memcpy(out, c->Fp, sizeof(double) * 9 * n); return ORC_OK;
     case ORC_F_L: memcpy(out, c->L, sizeof(double) * 9 * n); return ORC_OK;

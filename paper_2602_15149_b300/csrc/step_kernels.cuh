@@ -344,11 +344,14 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
                 AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
             const T lap = T(-2) * AT;
             const T Hh = a.H[i], si = vsi.w, sd = a.sdot[i];
-            const T e0 = m.eps0;
-            const T sdd = m.c0 * m.c0 / (T(2) * e0) *
-                          (T(2) * e0 * lap + (T(1) - si) / (T(2) * e0) -
-                           T(2) * t_sqrt(T(4) * e0 * Hh / m.Gc + T(1)) / m.c0 * sd - T(2) * si * Hh / m.Gc);
-            const T sd_new = sd + (T)dt * sdd;
+            const T e0 = m.eps0, c2e = m.c0 * m.c0 / (T(2) * e0);
+            // eq. phasefieldddot with its local terms at the new time level:
+            // sdot_{n+1} = (sdot_n + dt r_n) / (1 + dt gamma + dt^2 k)
+            const T r = c2e * (T(2) * e0 * lap + (T(1) - si) / (T(2) * e0) - T(2) * si * Hh / m.Gc);
+            const T kk = c2e * (T(1) / (T(2) * e0) + T(2) * Hh / m.Gc);
+            const T gam = m.c0 / e0 * t_sqrt(T(4) * e0 * Hh / m.Gc + T(1));
+            const T dts = (T)dt;
+            const T sd_new = (sd + dts * r) / (T(1) + dts * gam + dts * dts * kk);
             a.sdot[i] = sd_new;
             s_new = t_min(T(1), t_max(T(0), si + (T)dt * sd_new));
         }
