@@ -163,7 +163,7 @@ tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int com
  * At most 512 notches. */
 tlsph_status tlsph_add_notch(tlsph_ctx *ctx, const double quad[12]);
 
-/* Reference setup, once (Sec. 2.4): cell keys floor((X0 - Xmin) / (R (1 + 2^-10))),
+/* Reference setup, once (Sec. 2.4): cell keys floor((X0 - Xmin) / (R/3) + 1/2),
  * stable sort by (specimen, cell, id), neighbour lists {j != i : |X0j - X0i|^2 < R^2}
  * (FP64, fixed summation order, no FMA) minus notch-crossing bonds, the correction
  * tensors and the initial state.  Errors: ERR_SINGULAR_L if a correction matrix is

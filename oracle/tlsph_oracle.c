@@ -603,11 +603,16 @@ static int cmp_keyid(const void *a, const void *b) {
     return x->id < y->id ? -1 : (x->id > y->id);
 }
 
-/* Cell of size R (1 + 2^-10) so that every pair with r0 < R lies in
- * adjacent cells even after rounding of the cell coordinate. */
+/* Cells of size R/3 centred on the planes X = Xmin + k R/3, cell coordinate
+ * floor((X - Xmin) / (R/3) + 1/2).  A pair with r0 < R is at most 3 cells
+ * apart per axis; the search covers 4 to absorb the rounding of the cell
+ * coordinate.  reading (the paper only says that particles are sorted by
+ * cell): cells this fine hold about one particle of a lattice of spacing R/3,
+ * so the cell-sorted order is the lattice order. */
+#define CELL_RANGE 4
 static void cell_setup(orc_ctx *c) {
     double R = c->p.support * c->p.h;
-    c->cell_size = R * (1.0 + ldexp(1.0, -10));
+    c->cell_size = R / 3.0;
     for (int k = 0; k < 3; k++) {
         double mn = INFINITY, mx = -INFINITY;
         for (int64_t i = 0; i < c->n; i++) {
@@ -617,12 +622,12 @@ static void cell_setup(orc_ctx *c) {
         }
         if (k >= c->p.dim) { mn = 0.0; mx = 0.0; }
         c->xmin[k] = mn;
-        c->ncell[k] = (int64_t)floor((mx - mn) / c->cell_size) + 1;
+        c->ncell[k] = (int64_t)floor((mx - mn) / c->cell_size + 0.5) + 1;
     }
 }
 static void cell_of(const orc_ctx *c, int64_t i, int64_t *cc) {
     for (int k = 0; k < 3; k++)
-        cc[k] = k < c->p.dim ? (int64_t)floor((c->X0[3 * i + k] - c->xmin[k]) / c->cell_size) : 0;
+        cc[k] = k < c->p.dim ? (int64_t)floor((c->X0[3 * i + k] - c->xmin[k]) / c->cell_size + 0.5) : 0;
 }
 static int64_t cell_key(const orc_ctx *c, int64_t spec, const int64_t *cc) {
     return ((spec * c->ncell[2] + cc[2]) * c->ncell[1] + cc[1]) * c->ncell[0] + cc[0];
@@ -675,10 +680,10 @@ int orc_build_neighbours(orc_ctx *c, int method) {
         } else {
             int64_t cc[3];
             cell_of(c, i, cc);
-            int dz0 = c->p.dim == 3 ? -1 : 0, dz1 = c->p.dim == 3 ? 1 : 0;
+            int dz0 = c->p.dim == 3 ? -CELL_RANGE : 0, dz1 = c->p.dim == 3 ? CELL_RANGE : 0;
             for (int dz = dz0; dz <= dz1; dz++)
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
+                for (int dy = -CELL_RANGE; dy <= CELL_RANGE; dy++)
+                    for (int dx = -CELL_RANGE; dx <= CELL_RANGE; dx++) {
                         int64_t q[3] = {cc[0] + dx, cc[1] + dy, cc[2] + dz};
                         if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= c->ncell[0] || q[1] >= c->ncell[1] ||
                             q[2] >= c->ncell[2])

@@ -31,7 +31,7 @@ template <typename T> struct MatT {
 };
 
 // x + x^2/2 - log(1 + x) (= (J^2 - 1)/2 - ln J with x = J - 1), series near 0
-template <typename T> __device__ __forceinline__ T xp_minus_log(T x) {
+template <typename T> TL_HD T xp_minus_log(T x) {
     if (t_abs(x) < T(0.01)) {
         // x^2 - x^3/3 + x^4/4 - ... - x^11/11
         T r = T(-1.0 / 11.0);
@@ -49,6 +49,20 @@ template <typename T> __device__ __forceinline__ T xp_minus_log(T x) {
     return x + T(0.5) * x * x - t_log1p(x);
 }
 
+// tr(I + X) - 3 det(I + X)^(1/3) without first-order cancellation (for X with real
+// spectrum): with a = 1 + tr X / 3 and B = dev X, det(a I + B) = a^3 (1 + x),
+// x = -tr(B^2) / (2 a^2) + det(B) / a^3, so the difference is -3 a ((1 + x)^(1/3) - 1).
+template <typename T> TL_HD T iso_excess(const M3<T> &X) {
+    const T t3 = trace(X) / T(3);
+    const T a = T(1) + t3;
+    M3<T> B = X;
+    B.a[0] -= t3;
+    B.a[4] -= t3;
+    B.a[8] -= t3;
+    const T x = -trace_mul(B, B) / (T(2) * a * a) + det(B) / (a * a * a);
+    return T(-3) * a * t_expm1(t_log1p(x) / T(3));
+}
+
 // Kinematics shared by both models.
 template <typename T> struct Kin {
     M3<T> E2;    // C - I = G + G^T + G^T G
@@ -57,7 +71,7 @@ template <typename T> struct Kin {
     T Jm23;      // J^-2/3
     T Jm23m1;    // J^-2/3 - 1
 };
-template <typename T> __device__ __forceinline__ Kin<T> kinematics(const M3<T> &G) {
+template <typename T> TL_HD Kin<T> kinematics(const M3<T> &G) {
     Kin<T> k;
     k.E2 = mul_tn(G, G);
 #pragma unroll
@@ -78,7 +92,7 @@ template <typename T> __device__ __forceinline__ Kin<T> kinematics(const M3<T> &
 
 // Neo-Hookean stress and energy split.  psi_plus / psi_minus of eq. ksipNH / ksinNH.
 template <typename T>
-__device__ __forceinline__ void nh_stress(const Kin<T> &k, T s, const MatT<T> &m, M3<T> &S, T &psi_plus, T &psi_minus) {
+TL_HD void nh_stress(const Kin<T> &k, T s, const MatT<T> &m, M3<T> &S, T &psi_plus, T &psi_minus) {
     T trE2 = trace(k.E2);
     M3<T> dE = k.E2;
     dE.a[0] -= trE2 / T(3);
@@ -89,7 +103,8 @@ __device__ __forceinline__ void nh_stress(const Kin<T> &k, T s, const MatT<T> &m
     T fi = m.mu * k.Jm23;
     T fv = T(0.5) * m.kappa * k.Jm1 * (k.Jm1 + T(2));
     T U = T(0.5) * m.kappa * xp_minus_log(k.Jm1);
-    T psibar = T(0.5) * m.mu * (T(3) * k.Jm23m1 + k.Jm23 * trE2);
+    // psibar = mu/2 (tr bbar - 3) = mu/2 J^-2/3 (tr C - 3 J^2/3)
+    T psibar = T(0.5) * m.mu * k.Jm23 * iso_excess(k.E2);
     T s2 = s * s;
     T cv, ci;
     if (k.Jm1 >= T(0)) {
@@ -108,7 +123,7 @@ __device__ __forceinline__ void nh_stress(const Kin<T> &k, T s, const MatT<T> &m
 }
 
 // Eigenvalues of a traceless 3x3 matrix with real spectrum (trigonometric form).
-template <typename T> __device__ __forceinline__ void eig_traceless(const M3<T> &B, T q2, T e[3]) {
+template <typename T> TL_HD void eig_traceless(const M3<T> &B, T q2, T e[3]) {
     T p = q2 / T(6);
     if (!(p > T(0))) {
         e[0] = e[1] = e[2] = T(0);
@@ -126,7 +141,7 @@ template <typename T> __device__ __forceinline__ void eig_traceless(const M3<T> 
 }
 
 // exp(X) - I by scaling and squaring of a Taylor series (order 6 in FP32, 12 in FP64).
-template <typename T> __device__ __forceinline__ M3<T> expm1_mat(const M3<T> &X) {
+template <typename T> TL_HD M3<T> expm1_mat(const M3<T> &X) {
     T nrm2 = T(0);
 #pragma unroll
     for (int q = 0; q < 9; q++) nrm2 += X.a[q] * X.a[q];
@@ -174,7 +189,7 @@ template <> struct J2Tol<double> {
 // Residual r(dgamma) of eq. J2_residual in the eigenbasis of A = C_p^-1 C.
 template <typename T> struct J2Res {
     T delta[3], n[3], c_eq, sy0, Hh, epn;
-    __device__ __forceinline__ T operator()(T dg) const {
+    TL_HD T operator()(T dg) const {
         T dp[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) dp[a] = delta[a] + (T(1) + delta[a]) * t_expm1(T(-2) * dg * n[a]);
@@ -189,7 +204,7 @@ template <typename T> struct J2Res {
 // J2 update.  K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.  Returns 0, or 1 if the
 // bracket / iteration did not converge (the state is still updated with the last iterate).
 template <typename T>
-__device__ __forceinline__ int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6out[6], T &ep_out,
+TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6out[6], T &ep_out,
                                          M3<T> &S, T &dgamma) {
     M3<T> K;
     K.a[0] = K6[0]; K.a[4] = K6[1]; K.a[8] = K6[2];
@@ -231,14 +246,20 @@ __device__ __forceinline__ int j2_update(const Kin<T> &k, const T K6[6], T ep, c
         // bracket: L = 0, R = max((sigma_tr - sigma_y) / (3 mu + H), eps), doubled until r(R) <= 0
         T L = T(0), rL = f;
         T eps_b = T(1e-12) * syn / m.mu;
-        T R = t_max(f / (T(3) * m.mu + m.Hh), eps_b);
+        const T R0 = t_max(f / (T(3) * m.mu + m.Hh), eps_b);
+        T R = R0;
         T rR = r(R);
         for (int nd = 0; rR > T(0) && nd < 60; nd++) {
             R *= T(2);
             rR = r(R);
         }
-        if (!(rR <= T(0))) status = 1;
         T x = R;
+        if (!(rR <= T(0))) {
+            // no bracket (a trial far outside the yield surface): keep the state finite with the
+            // small-strain estimate and report the particle as non-converged
+            status = 1;
+            x = R0;
+        }
         if (rR != T(0) && status == 0) {
             int it = 0;
             for (; it < J2Tol<T>::maxit; it++) {
@@ -302,7 +323,7 @@ __device__ __forceinline__ int j2_update(const Kin<T> &k, const T K6[6], T ep, c
 }
 
 // Strain energy of the J2 model, psi_vol(J) + psi_iso(Cbar_e) (evaluated at a given C_p^-1).
-template <typename T> __device__ __forceinline__ T j2_energy(const Kin<T> &k, const T K6[6], const MatT<T> &m) {
+template <typename T> TL_HD T j2_energy(const Kin<T> &k, const T K6[6], const MatT<T> &m) {
     // tr(C_e) = tr(C_p^-1 C) = 3 + tr(D)
     M3<T> K;
     K.a[0] = K6[0]; K.a[4] = K6[1]; K.a[8] = K6[2];
@@ -312,9 +333,8 @@ template <typename T> __device__ __forceinline__ T j2_energy(const Kin<T> &k, co
     M3<T> D = mul(K, k.E2);
 #pragma unroll
     for (int q = 0; q < 9; q++) D.a[q] += K.a[q] + k.E2.a[q];
-    T trD = trace(D);
     T vol = T(0.5) * m.kappa * xp_minus_log(k.Jm1);
-    T iso = T(0.5) * m.mu * (T(3) * k.Jm23m1 + k.Jm23 * trD);
+    T iso = T(0.5) * m.mu * k.Jm23 * iso_excess(D);  // mu/2 (tr Cbar_e - 3), det C_e = J^2
     return vol + iso;
 }
 

@@ -42,15 +42,20 @@ __global__ void k_bbox(int64_t n, int dim, const double *X /* n*3, orig order */
     }
 }
 
+// Cells of size R/3 centred on the planes X = Xmin + k R/3: coordinate
+// floor((X - Xmin) / cs + 1/2); a pair with r0 < R is at most 3 cells apart per
+// axis, and the search covers kCellRange = 4 to absorb rounding.  On a lattice of
+// spacing R/3 every cell holds one particle, so the sorted order is lattice order.
+constexpr int kCellRange = 4;
 struct CellGrid {
     double xmin[3];
-    double cs;          // cell size R (1 + 2^-10)
+    double cs;          // cell size R / 3
     int64_t nc[3];      // cells per axis
     int dim;
 };
 
 __device__ __forceinline__ int64_t cell_coord(double x, double xmin, double cs) {
-    return (int64_t)floor(__ddiv_rn(__dsub_rn(x, xmin), cs));
+    return (int64_t)floor(__dadd_rn(__ddiv_rn(__dsub_rn(x, xmin), cs), 0.5));
 }
 
 // key = ((spec nz + cz) ny + cy) nx + cx
@@ -219,14 +224,14 @@ __global__ void k_neighbours(int64_t n, CellGrid g, double R2, const unsigned lo
     int64_t sp = (int64_t)(r / (unsigned long long)g.nc[2]);
     int cnt = 0;
     int64_t out = FILL ? row_ptr[k] : 0;
-    const int dz0 = g.dim == 3 ? -1 : 0, dz1 = g.dim == 3 ? 1 : 0;
+    const int dz0 = g.dim == 3 ? -kCellRange : 0, dz1 = g.dim == 3 ? kCellRange : 0;
     for (int dz = dz0; dz <= dz1; dz++) {
         int64_t z = cz + dz;
         if (z < 0 || z >= g.nc[2]) continue;
-        for (int dy = -1; dy <= 1; dy++) {
+        for (int dy = -kCellRange; dy <= kCellRange; dy++) {
             int64_t y = cy + dy;
             if (y < 0 || y >= g.nc[1]) continue;
-            int64_t x0 = max(cx - 1, (int64_t)0), x1 = min(cx + 1, g.nc[0] - 1);
+            int64_t x0 = max(cx - kCellRange, (int64_t)0), x1 = min(cx + kCellRange, g.nc[0] - 1);
             unsigned long long kb = (unsigned long long)((((sp * g.nc[2] + z) * g.nc[1] + y) * g.nc[0]) + x0);
             unsigned long long ke = kb + (unsigned long long)(x1 - x0 + 1);
             int64_t lo = lower_bound_u64(skey, n, kb), hi = lower_bound_u64(skey, n, ke);

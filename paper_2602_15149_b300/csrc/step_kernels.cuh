@@ -39,7 +39,7 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 
 // ---------------------------------------------------------------- pass 1
 template <typename T, int DIM, bool FRAC, bool DIAG>
-__global__ void __launch_bounds__(128) k_pass1(StepArgs<T> a) {
+__global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int n = a.n;
@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(128) k_pass1(StepArgs<T> a) {
 #pragma unroll
         for (int q = 0; q < DIM; q++) B[p][q] = T(0);
     const int *cp = a.col + base;
+#pragma unroll 4
     for (int k = 0; k < len; k++) {
         const int j = __ldg(cp + 32 * k);
         const V4<T> xj = ldg4(a.X0V + j);
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
 #pragma unroll
         for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
         const int *cp = a.col + base;
+#pragma unroll 4
         for (int k = 0; k < len; k++) {
             const int j = __ldg(cp + 32 * k);
             const V4<T> xj = ldg4(a.X0V + j);

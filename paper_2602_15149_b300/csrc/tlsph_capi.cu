@@ -374,11 +374,11 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     const double R = c->p.support * c->p.h, R2 = R * R;
     CellGrid g;
     g.dim = dim;
-    g.cs = R * (1.0 + ldexp(1.0, -10));
+    g.cs = R / 3.0;
     double center[3];
     for (int k = 0; k < 3; k++) {
         g.xmin[k] = bb[k];
-        g.nc[k] = (int64_t)floor((bb[3 + k] - bb[k]) / g.cs) + 1;
+        g.nc[k] = (int64_t)floor((bb[3 + k] - bb[k]) / g.cs + 0.5) + 1;
         center[k] = 0.5 * (bb[k] + bb[3 + k]);
     }
     double *centerd;

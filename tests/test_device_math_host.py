@@ -1,0 +1,106 @@
+"""The library's constitutive device code, compiled for the host, against the FP64 oracle.
+
+tests/native/constitutive_host.cu includes csrc/constitutive.cuh unchanged and is built
+with nvcc as host code, so the GPU's NH and J2 (C_p^-1 form) arithmetic is checked on
+the CPU in both FP64 and FP32, without a GPU.
+"""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.test_oracle_pins import STEEL_J2, STEEL_NH, _plastic_state, _trial_F
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "native", "constitutive_host.cu")
+LIB = os.path.join(HERE, "native", "_build", "libconstitutive_host.so")
+
+
+@pytest.fixture(scope="module")
+def hc():
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    deps = [SRC] + [os.path.join(HERE, "..", "paper_2602_15149_b300", "csrc", f)
+                    for f in ("constitutive.cuh", "tensor3.cuh")]
+    if not os.path.exists(LIB) or any(os.path.getmtime(d) > os.path.getmtime(LIB) for d in deps):
+        subprocess.check_call(["nvcc", "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-o", LIB, SRC])
+    lib = C.CDLL(LIB)
+    D = C.POINTER(C.c_double)
+    for f in (lib.hc_j2_d, lib.hc_j2_f):
+        f.argtypes = [D, D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, D, D, D, D]
+    for f in (lib.hc_nh_d, lib.hc_nh_f):
+        f.argtypes = [D, C.c_double, C.c_double, C.c_double, D, D, D]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _j2(fn, F, Fp0, ep0):
+    Fpi = np.linalg.inv(Fp0)
+    K = Fpi @ Fpi.T - np.eye(3)
+    K6 = np.array([K[0, 0], K[1, 1], K[2, 2], K[0, 1], K[0, 2], K[1, 2]])
+    G = np.ascontiguousarray(F - np.eye(3)).ravel()
+    K6o, S = np.zeros(6), np.zeros(9)
+    epo, dg = C.c_double(), C.c_double()
+    st = fn(_p(G), _p(K6), ep0, STEEL_J2.E, STEEL_J2.nu, STEEL_J2.sigma_y0, STEEL_J2.H_hard, _p(K6o), C.byref(epo),
+            _p(S), C.byref(dg))
+    Ko = np.array([[K6o[0], K6o[3], K6o[4]], [K6o[3], K6o[1], K6o[5]], [K6o[4], K6o[5], K6o[2]]]) + np.eye(3)
+    return st, S.reshape(3, 3), epo.value, Ko
+
+
+@pytest.mark.parametrize("prec,tol", [("d", 1e-9), ("f", 2e-3)])
+def test_j2_cpinv_form_matches_fp_oracle(hc, prec, tol):
+    """Stress, plastic strain and C_p^-1 of the device return map equal the oracle's F_p return map."""
+    fn = hc.hc_j2_d if prec == "d" else hc.hc_j2_f
+    rng = np.random.default_rng(0)
+    nplastic = 0
+    for k in range(200):
+        Fp0, ep0 = _plastic_state(rng) if k % 2 else (np.eye(3), 0.0)
+        F = _trial_F(rng, rng.uniform(0.0005, 0.0025), rng.uniform(-2e-3, 2e-3))
+        ro = O.j2_update(F, Fp0, ep0, STEEL_J2)
+        st, S, ep, Cpi = _j2(fn, F, Fp0, ep0)
+        assert st == 0
+        scale = np.abs(ro["S"]).max()
+        assert np.abs(S - ro["S"]).max() <= tol * scale
+        assert abs(ep - ro["ep"]) <= tol * max(ro["ep"], 1e-3)
+        Fpi = np.linalg.inv(ro["Fp"])
+        assert np.abs(Cpi - Fpi @ Fpi.T).max() <= tol
+        nplastic += ro["dgamma"] > 0
+    assert nplastic > 50
+
+
+def test_j2_no_bracket_stays_finite(hc):
+    """Far outside the return map's regime the device code flags the point and keeps a finite state."""
+    rng = np.random.default_rng(1)
+    flagged = 0
+    for _ in range(20):
+        G = rng.normal(scale=3e-3, size=(3, 3))
+        st, S, ep, Cpi = _j2(hc.hc_j2_d, np.eye(3) + G, np.eye(3), 0.0)
+        assert np.all(np.isfinite(S)) and np.isfinite(ep)
+        flagged += st
+    assert flagged > 0
+
+
+@pytest.mark.parametrize("prec,tol", [("d", 1e-11), ("f", 1e-5)])
+def test_nh_matches_oracle(hc, prec, tol):
+    fn = hc.hc_nh_d if prec == "d" else hc.hc_nh_f
+    rng = np.random.default_rng(2)
+    for scale in [1e-5, 1e-3, 5e-2]:
+        for _ in range(20):
+            F = np.eye(3) + rng.normal(scale=scale, size=(3, 3))
+            s = rng.uniform(0.2, 1.0)
+            So, ppo, pmo = O.nh_stress(F, s, STEEL_NH)
+            S, pp, pm = np.zeros(9), C.c_double(), C.c_double()
+            fn(_p(np.ascontiguousarray(F - np.eye(3)).ravel()), s, STEEL_NH.E, STEEL_NH.nu, _p(S), C.byref(pp),
+               C.byref(pm))
+            # (the oracle's literal I - tr C / 3 C^-1 cancels to ~1e-15 E in FP64 near F = I)
+            assert np.abs(S.reshape(3, 3) - So).max() <= tol * np.abs(So).max() + 1e-15 * STEEL_NH.E
+            # the tensile energy drives damage: relative accuracy even at tiny strain (the oracle's
+            # literal mu/2 (J^-2/3 tr C - 3) itself cancels to ~1e-15 E in FP64)
+            floor = 1e-15 * STEEL_NH.E
+            assert abs(pp.value - ppo) <= 50 * tol * abs(ppo) + floor
+            assert abs(pm.value - pmo) <= 50 * tol * abs(pmo) + floor

@@ -87,20 +87,22 @@ def test_cell_neighbours_equal_brute_force(dim):
 
 
 def test_cell_sort_permutation():
-    """The cell-sorted order is a permutation with ids ascending inside each cell."""
+    """The cell-sorted order is a permutation with ids ascending inside each cell; on a lattice of spacing
+    R/3 it is the lattice order itself."""
     case = W.block_3d(nx=10, ny=7, nz=6, jitter=0.01, seed=1)
     o = make_oracle(case)
     p = o.perm()
     assert np.array_equal(np.sort(p), np.arange(case.n))
-    cs = 2.0 * case.h * (1.0 + 2.0 ** -10)
+    cs = 2.0 * case.h / 3.0
     xmin = case.X0.min(axis=0)
-    cell = np.floor((case.X0 - xmin) / cs).astype(np.int64)
+    cell = np.floor((case.X0 - xmin) / cs + 0.5).astype(np.int64)
     nc = cell.max(axis=0) + 1
     key = (cell[:, 2] * nc[1] + cell[:, 1]) * nc[0] + cell[:, 0]
     k = key[p]
     assert np.all(np.diff(k) >= 0)
     same = np.diff(k) == 0
     assert np.all(np.diff(p)[same] > 0)
+    assert np.array_equal(p, np.arange(case.n))  # jittered lattice: one particle per cell, lattice order
 
 
 def test_notch_removes_exactly_crossing_bonds():
