@@ -220,6 +220,32 @@ enum { TLSPH_OPT_KERNEL_TIMING = 1, TLSPH_OPT_RECORD_ACC = 2 };
 tlsph_status tlsph_set_option(tlsph_ctx *ctx, int option, int value);
 tlsph_status tlsph_kernel_times(tlsph_ctx *ctx, double ms[2], int64_t count[2]);
 
+/* Largest particle count accepted by tlsph_cell_sort_noalloc. */
+#define TLSPH_NOALLOC_MAX_PARTICLES 131072
+
+/* Cell-sorted order of n particles without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc (code running in
+ * a memory pool it does not own, or under a driver that forbids allocation while it holds
+ * the device).  It computes the same permutation as tlsph_build_ref_neighbours followed by
+ * tlsph_permutation (cells of size R/3 = support h / 3, stable by (specimen, cell, id)).
+ *   device       CUDA device ordinal; it is current for the calling thread only during the call
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = the legacy default stream)
+ *   X0           device pointer, n * dim doubles, caller order
+ *   specimen_id  device pointer, n int32 >= 0, or NULL (one specimen)
+ *   perm         device pointer, n int32 out: perm[k] = caller id of the k-th particle
+ * Work is only enqueued; perm is ready when the stream reaches it.  Scratch memory is one
+ * fixed device array of about 3.3 MB inside the library (room for
+ * TLSPH_NOALLOC_MAX_PARTICLES particles), held by every device that loads the library
+ * until the process exits.  Every call shares that array, so calls that overlap on the GPU
+ * (on different streams, or from different threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Errors: TLSPH_ERR_ARG if n < 1 or
+ * n > TLSPH_NOALLOC_MAX_PARTICLES, dim is not 2 or 3, h or support <= 0, or a required
+ * pointer is NULL; TLSPH_ERR_CUDA if the device or the scratch address is unavailable or
+ * a launch fails. */
+tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, int64_t n, int dim, double h, double support,
+                                     const double *X0, const int32_t *specimen_id, int32_t *perm);
+
 #ifdef __cplusplus
 }
 #endif

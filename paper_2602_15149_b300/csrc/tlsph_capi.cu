@@ -1107,3 +1107,153 @@ tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[2], int64_t count[2]) {
 }
 
 }  // extern "C"
+
+// ===================================================================== allocation-free cell sort
+// A variant of the reference setup's cell sort for callers that cannot allocate device
+// memory (for example code that runs inside a memory pool it does not own, or a driver
+// that forbids cudaMalloc while it holds the device).  Its scratch lives in one file-scope
+// device array of fixed size, shared by every call on a device; nothing is allocated.
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNAMax = TLSPH_NOALLOC_MAX_PARTICLES;
+constexpr int64_t kNABlk = (kNAMax + kSortTile - 1) / kSortTile;
+
+struct NAScratch {
+    unsigned long long keys[2][kNAMax];
+    int vals[2][kNAMax];
+    int64_t hist[256 * kNABlk];
+    int64_t hoff[256 * kNABlk];
+    int64_t bsum[64];
+    int64_t bscan[64];
+    double bbox[8];
+    CellGrid grid;
+};
+
+// every GPU that loads the library holds this array until the process exits
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NAScratch)];
+
+std::mutex g_na_mutex;
+void *g_na_ptr[128] = {nullptr};
+
+__global__ void k_na_bbox(int64_t n, int dim, const double *X, double *out) {
+    __shared__ double smin[3][32], smax[3][32];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = 0; k < dim; k++) {
+            double x = X[dim * i + k];
+            mn[k] = fmin(mn[k], x);
+            mx[k] = fmax(mx[k], x);
+        }
+    for (int k = 0; k < 3; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fmin(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmax(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int k = 0; k < 3; k++) {
+            smin[k][w] = mn[k];
+            smax[k][w] = mx[k];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < 3; k++) {
+            double a = INFINITY, b = -INFINITY;
+            for (int q = 0; q < nw; q++) {
+                a = fmin(a, smin[k][q]);
+                b = fmax(b, smax[k][q]);
+            }
+            if (k >= dim) a = b = 0.0;
+            out[k] = a;
+            out[3 + k] = b;
+        }
+    }
+}
+
+// the same grid as the context's reference setup: cells R/3, nc = floor((max - min) / cs + 1/2) + 1
+__global__ void k_na_grid(int dim, double cs, const double *bbox, CellGrid *g) {
+    g->dim = dim;
+    g->cs = cs;
+    for (int k = 0; k < 3; k++) {
+        g->xmin[k] = bbox[k];
+        g->nc[k] = (int64_t)floor(__dadd_rn(__ddiv_rn(__dsub_rn(bbox[3 + k], bbox[k]), cs), 0.5)) + 1;
+    }
+}
+
+__global__ void k_na_keys(int64_t n, int dim, const double *X, const int32_t *spec, const CellGrid *gp,
+                          unsigned long long *key, int *id) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CellGrid g = *gp;
+    int64_t c[3] = {0, 0, 0};
+    for (int k = 0; k < dim; k++) c[k] = cell_coord(X[dim * i + k], g.xmin[k], g.cs);
+    int64_t sp = spec ? (int64_t)spec[i] : 0;
+    key[i] = (unsigned long long)((((sp * g.nc[2] + c[2]) * g.nc[1] + c[1]) * g.nc[0]) + c[0]);
+    id[i] = (int)i;
+}
+
+__global__ void k_na_copy(int64_t n, const int *src, int32_t *dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+
+}  // namespace
+
+extern "C" tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, int64_t n, int dim, double h,
+                                                double support, const double *X0, const int32_t *specimen_id,
+                                                int32_t *perm) {
+    if (n < 1 || n > kNAMax || (dim != 2 && dim != 3) || !(h > 0.0) || !(support > 0.0) || !X0 || !perm ||
+        device < 0 || device >= 128)
+        return TLSPH_ERR_ARG;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        return TLSPH_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return TLSPH_ERR_CUDA;
+    }
+    tlsph_status st = TLSPH_OK;
+    NAScratch *sc = nullptr;
+    {
+        // set-up, once per device, with that device current: the device address of the scratch
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_ptr[device]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                st = TLSPH_ERR_CUDA;
+            } else {
+                g_na_ptr[device] = p;
+            }
+        }
+        sc = reinterpret_cast<NAScratch *>(g_na_ptr[device]);
+    }
+    if (st == TLSPH_OK) {
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        const int64_t nblk = (n + kSortTile - 1) / kSortTile;
+        const int64_t m = 256 * nblk;
+        const unsigned nb = (unsigned)((m + kScanBlock - 1) / kScanBlock);
+        k_na_bbox<<<1, 1024, 0, s>>>(n, dim, X0, sc->bbox);
+        k_na_grid<<<1, 1, 0, s>>>(dim, support * h / 3.0, sc->bbox, &sc->grid);
+        k_na_keys<<<blocks_for(n), kThreads, 0, s>>>(n, dim, X0, specimen_id, &sc->grid, sc->keys[0], sc->vals[0]);
+        // stable LSD radix sort over all 64 key bits: 8 passes, the result lands in buffer 0
+        for (int pass = 0; pass < 8; pass++) {
+            const int cur = pass & 1, shift = 8 * pass;
+            k_radix_hist<<<(unsigned)nblk, 32, 0, s>>>(n, sc->keys[cur], shift, sc->hist);
+            k_scan_block<<<nb, kScanBlock, 0, s>>>(m, sc->hist, sc->hoff, sc->bsum);
+            k_scan_block<<<1, kScanBlock, 0, s>>>((int64_t)nb, sc->bsum, sc->bscan, nullptr);
+            k_scan_add<<<nb, kScanBlock, 0, s>>>(m, sc->hoff, sc->bscan);
+            k_radix_scatter<<<(unsigned)nblk, 32, 0, s>>>(n, sc->keys[cur], sc->vals[cur], shift, sc->hoff,
+                                                          sc->keys[cur ^ 1], sc->vals[cur ^ 1]);
+        }
+        k_na_copy<<<blocks_for(n), kThreads, 0, s>>>(n, sc->vals[0], perm);
+        if (cudaGetLastError() != cudaSuccess) st = TLSPH_ERR_CUDA;
+    }
+    cudaSetDevice(prev);
+    return st;
+}

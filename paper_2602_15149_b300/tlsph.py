@@ -28,7 +28,8 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_add_bc", "tlsph_add_notch", "tlsph_build_ref_neighbours", "tlsph_step", "tlsph_step_async",
            "tlsph_sync", "tlsph_read_state", "tlsph_write_state", "tlsph_field_bytes", "tlsph_energies", "tlsph_time",
            "tlsph_neighbours", "tlsph_permutation", "tlsph_nnz", "tlsph_get_info", "tlsph_set_option",
-           "tlsph_kernel_times"]
+           "tlsph_kernel_times", "tlsph_cell_sort_noalloc"]
+NOALLOC_MAX_PARTICLES = 131072
 
 
 class Params(C.Structure):
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "tlsph_get_info": (C.c_int, [P, C.POINTER(Info)]),
         "tlsph_set_option": (C.c_int, [P, C.c_int, C.c_int]),
         "tlsph_kernel_times": (C.c_int, [P, D, I64]),
+        "tlsph_cell_sort_noalloc": (C.c_int, [C.c_int, V, C.c_int64, C.c_int, C.c_double, C.c_double, V, V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -252,6 +254,16 @@ class TLSPH:
         self._ck(self.lib.tlsph_kernel_times(self.ctx, _d(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
                  "kernel_times")
         return {"pass2_ms": ms[0], "pass2_launches": int(cnt[0]), "pass1_ms": ms[1], "pass1_launches": int(cnt[1])}
+
+
+def cell_sort_noalloc(X0, perm, h, support=2.0, specimen_id=None, device=0, stream=None) -> int:
+    """tlsph_cell_sort_noalloc on caller-owned device buffers (torch CUDA tensors): X0 (n, dim)
+    float64, perm (n,) int32 out, specimen_id (n,) int32 or None.  Returns the status; the
+    library allocates nothing."""
+    lib = load_library()
+    n, dim = int(X0.shape[0]), int(X0.shape[1])
+    return lib.tlsph_cell_sort_noalloc(device, stream, n, dim, h, support, X0.data_ptr(),
+                                       None if specimen_id is None else specimen_id.data_ptr(), perm.data_ptr())
 
 
 def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
