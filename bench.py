@@ -38,10 +38,10 @@ UNIT = "particle-steps/s"
 SHAPE = (128, 128, 64)
 FALLBACK_HBM_GBS = 6400.0
 
-# DRAM bytes per launch of the force-and-damage pass (k_pass2) from one ncu capture
+# DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel
 # sources it was taken on; reported as null once the kernels change.
-NCU_TRAFFIC = {"sources": None, "pass2_bytes_per_launch": None}
+NCU_TRAFFIC = {"sources": None, "pass2": None, "gradient": None, "stress": None}
 
 
 def source_hash() -> str:
@@ -59,23 +59,23 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def pass_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
-    """Algorithmic HBM bytes per launch of each pass (own reads / writes once, neighbour gathers
-    served on chip, neighbour indices read once per pass) for the library's layout."""
-    v4 = 4 * ts
-    q = 3 * v4 if dim == 3 else v4
-    nsym = 6 if dim == 3 else 3
-    p1 = n * (4 + 8 / 32 + v4 + v4 + nsym * ts + 2 + q + dim * dim * ts) + 4 * nnz
+def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
+    """Algorithmic HBM bytes per launch of each kernel of a step (every particle's own records
+    read / written once, neighbour gathers served on chip, neighbour indices read once per
+    neighbour pass) for the library's layout.  Mirrors algorithmic_bytes() in tlsph_capi.cu."""
+    v4, nsym, q = 4 * ts, (6 if dim == 3 else 3), dim * dim * ts
+    grad = n * (4 + 8 / 32 + 2 * v4 + nsym * ts + dim * dim * ts) + 4 * nnz
+    stress = n * (dim * dim * ts + nsym * ts + 2 + q + dim * dim * ts)
     if j2:
-        p1 += n * 2 * 7 * ts
+        stress += n * 2 * 7 * ts
     if frac:
-        p1 += n * (v4 + 2 * ts)
+        stress += n * (v4 + 2 * ts)
     p2 = n * (4 + 8 / 32 + 3 * v4 + q + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4) + 4 * nnz
     if visc:
         p2 += n * dim * dim * ts
     if frac:
         p2 += n * (nsym * ts + 3 * ts)
-    return p1, p2
+    return {"gradient": grad, "stress": stress, "pass2": p2}
 
 
 class ClockSampler:
@@ -227,15 +227,14 @@ def run_ours(args):
     g.step(min(args.steps, 200))
     kt = g.kernel_times()
     g.set_option(tlsph.OPT_KERNEL_TIMING, 0)
-    p1_bytes, p2_bytes = pass_bytes(3, nnz, n)
-    p1_ms = kt["pass1_ms"] / max(kt["pass1_launches"], 1)
-    p2_ms = kt["pass2_ms"] / max(kt["pass2_launches"], 1)
-    dom = "pass2" if p2_ms >= p1_ms else "pass1"
-    dom_bytes, dom_ms = (p2_bytes, p2_ms) if dom == "pass2" else (p1_bytes, p1_ms)
+    kb = kernel_bytes(3, nnz, n)
+    kms = {k: kt[k + "_ms"] / max(kt[k + "_launches"], 1) for k in ("gradient", "stress", "pass2")}
+    dom = max(kms, key=kms.get)
+    dom_bytes, dom_ms = kb[dom], kms[dom]
     peak, peak_src = peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC["pass2_bytes_per_launch"] if (dom == "pass2" and
-                                                          NCU_TRAFFIC["sources"] == source_hash()) else None
+    traffic = NCU_TRAFFIC.get(dom) if NCU_TRAFFIC.get("sources") == source_hash() else None
+    step_bytes = sum(kb.values())
     g.close()
     torch.cuda.synchronize(dev)
 
@@ -271,7 +270,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
-                     "pass1_ms": p1_ms, "pass2_ms": p2_ms, "pass1_bytes": p1_bytes, "pass2_bytes": p2_bytes},
+                     "kernel_ms": kms, "kernel_bytes": kb,
+                     "step_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},
         "clocks": clk.summary(),
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps},

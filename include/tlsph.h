@@ -170,7 +170,7 @@ tlsph_status tlsph_add_notch(tlsph_ctx *ctx, const double quad[12]);
  * singular, ERR_OOM, ERR_CUDA.  Calling it again rebuilds from the reference state. */
 tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *ctx);
 
-/* Advance every specimen by nsteps steps of Algorithm 1 (2 kernels per step),
+/* Advance every specimen by nsteps steps of Algorithm 1 (3 kernels per step),
  * then synchronise and report device status: ERR_NONFINITE or ERR_NOCONVERGE
  * if that happened in these steps (the state is still advanced). */
 tlsph_status tlsph_step(tlsph_ctx *ctx, int64_t nsteps);
@@ -212,13 +212,13 @@ tlsph_status tlsph_get_info(tlsph_ctx *ctx, tlsph_info *out);
 
 /* Options (value 0 = off, default; 1 = on):
  *  TLSPH_OPT_KERNEL_TIMING: bracket every kernel of tlsph_step with CUDA events on the
- *    context's stream; tlsph_kernel_times returns the summed milliseconds and launch
- *    counts of the force-and-damage pass (ms[0], count[0]) and of the
- *    deformation-gradient / stress pass (ms[1], count[1]) since the last call.
+ *    context's stream; tlsph_kernel_times returns the summed milliseconds and launch counts
+ *    since the last call of the force-and-damage pass (ms[0], count[0]), the
+ *    deformation-gradient pass (ms[1], count[1]) and the stress pass (ms[2], count[2]).
  *  TLSPH_OPT_RECORD_ACC: keep the acceleration of each step for TLSPH_FIELD_ACC. */
 enum { TLSPH_OPT_KERNEL_TIMING = 1, TLSPH_OPT_RECORD_ACC = 2 };
 tlsph_status tlsph_set_option(tlsph_ctx *ctx, int option, int value);
-tlsph_status tlsph_kernel_times(tlsph_ctx *ctx, double ms[2], int64_t count[2]);
+tlsph_status tlsph_kernel_times(tlsph_ctx *ctx, double ms[3], int64_t count[3]);
 
 /* Largest particle count accepted by tlsph_cell_sort_noalloc. */
 #define TLSPH_NOALLOC_MAX_PARTICLES 131072

@@ -19,6 +19,22 @@ __device__ __forceinline__ V4<double> ldg4(const V4<double> *p) {
     return V4<double>{a.x, a.y, b.x, b.y};
 }
 
+// Bulk prefetch of a contiguous global range into L2 by the TMA unit (one instruction,
+// no registers).  ptr 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+// Lane 0 of each warp prefetches the warp's SELL slice of neighbour indices (slices start
+// on 128-byte boundaries and hold 32 x slice_len ints).
+__device__ __forceinline__ void prefetch_slice(const int *col, const int64_t *slice_off, int i) {
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t s = i >> 5;
+        const int64_t b = slice_off[s], e = slice_off[s + 1];
+        if (e > b) prefetch_l2_bulk(col + b, (uint32_t)((e - b) * sizeof(int)));
+    }
+}
+
 // Boundary condition record (Sec. 3.3.2).
 struct BCDev {
     int kind, comp_mask;
@@ -47,11 +63,13 @@ template <typename T> struct StepArgs {
     const int *row_len;
     const int *col;
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
-    const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, -)
+    const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, m0 in 3D)
     V4<T> *ug_next;
     const V4<T> *vs_cur;   // (vx, vy, vz, s)
     V4<T> *vs_next;
-    V4<T> *Q;              // P_i Ahat_i: 3D 3 records (9 values + m0 in [2].y), 2D 1 record
+    V4<T> *Qa, *Qb;        // P_i Ahat_i: 3D (q00 q01 q02 q10), (q11 q12 q20 q21); 2D Qa = (q00 q01 q10 q11)
+    T *Qc;                 // 3D q22
+    T *G;                  // F - I from k_gradient, dim*dim arrays of n
     T *Vm;                 // J F^-T Ahat, dim*dim arrays of n
     const T *Ahat;         // inverse of sum V w d d^T: 6 arrays of n (2D uses xx, yy, xy)
     T *K;                  // J2 state C_p^-1 - I, 6 arrays of n

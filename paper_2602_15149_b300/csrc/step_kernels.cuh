@@ -1,6 +1,6 @@
 // The two kernels of one TLSPH step (Algorithm 1) and their diagnostics.
 //
-// Pass 1 (one thread per particle, SELL-32 neighbour slices):
+// Pass 1 (k_gradient + k_stress; one thread per particle, SELL-32 neighbour slices):
 //   F_i = I + B_i Ahat_i,  B_i = sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T
 // which is eq. deformGradTLSPH with the corrected gradient L_i gradW_ij =
 // w_ij Ahat_i (X_j - X_i); soft particles (s_i <= s_l) take F = I
@@ -37,11 +37,14 @@ template <typename T, int DIM> __device__ __forceinline__ void load_ahat(const T
 
 template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
 
-// ---------------------------------------------------------------- pass 1
-template <typename T, int DIM, bool FRAC, bool DIAG>
-__global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
+// ---------------------------------------------------------------- pass 1a: deformation gradient
+// G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i.  Register-light so
+// that many warps keep neighbour gathers in flight.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128, 8) k_gradient(StepArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    prefetch_slice(a.col, a.slice_off, i);
     const int n = a.n;
     const int64_t base = a.slice_off[i >> 5] + (i & 31);
     const int len = a.row_len[i];
@@ -81,7 +84,6 @@ __global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
     }
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, n, i, A);
-    M3<T> G = m3_zero<T>();
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
@@ -89,8 +91,23 @@ __global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
             T s = T(0);
 #pragma unroll
             for (int r = 0; r < DIM; r++) s += B[p][r] * A[r][q];
-            G(p, q) = s;
+            a.G[(p * DIM + q) * n + i] = s;
         }
+}
+
+// ---------------------------------------------------------------- pass 1b: stress
+// Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and the
+// per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i.
+template <typename T, int DIM, bool FRAC, bool DIAG>
+__global__ void __launch_bounds__(128) k_stress(StepArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int n = a.n;
+    M3<T> G = m3_zero<T>();
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
     const MatT<T> m = a.mats[a.mid[i]];
     T s = T(1);
     const bool frac = FRAC && m.fracture;
@@ -138,7 +155,8 @@ __global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
         a.psi_out[i] = psi;
         return;
     }
-    // Q = P Ahat (in-plane block), Vm = J F^-T Ahat
+    T A[3][3];
+    load_ahat<T, DIM>(a.Ahat, n, i, A);
     M3<T> Fi;
     inverse(F, Fi);
     const T J = T(1) + kin.Jm1;
@@ -160,12 +178,11 @@ __global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
         }
     if (!ok) atomicAdd(&a.flags[kFlagNonfinite], 1);
     if (DIM == 3) {
-        const T mi = m.rho * xi.w;
-        a.Q[3 * i] = V4<T>{Qm[0][0], Qm[0][1], Qm[0][DIM - 1], Qm[1][0]};
-        a.Q[3 * i + 1] = V4<T>{Qm[1][1], Qm[1][DIM - 1], Qm[DIM - 1][0], Qm[DIM - 1][1]};
-        a.Q[3 * i + 2] = V4<T>{Qm[DIM - 1][DIM - 1], mi, T(0), T(0)};
+        a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[0][DIM - 1], Qm[1][0]};
+        a.Qb[i] = V4<T>{Qm[1][1], Qm[1][DIM - 1], Qm[DIM - 1][0], Qm[DIM - 1][1]};
+        a.Qc[i] = Qm[DIM - 1][DIM - 1];
     } else {
-        a.Q[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[1][0], Qm[1][1]};
+        a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[1][0], Qm[1][1]};
     }
 #pragma unroll
     for (int p = 0; p < DIM; p++)
@@ -175,7 +192,7 @@ __global__ void __launch_bounds__(128, 6) k_pass1(StepArgs<T> a) {
 
 // ---------------------------------------------------------------- pass 2
 template <typename T, int DIM, bool FRAC, bool VISC>
-__global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
+__global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
     __shared__ int s_sp;
     __shared__ double s_v[4], s_a[4];
     __shared__ bool s_last;
@@ -185,6 +202,7 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
     double vmag = 0.0, amag = 0.0;
     int sp = 0;
     if (active) {
+        prefetch_slice(a.col, a.slice_off, i);
         sp = a.spec[i];
         const int64_t base = a.slice_off[i >> 5] + (i & 31);
         const int len = a.row_len[i];
@@ -216,18 +234,16 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
             const T Vj = DIM == 3 ? xj.w : xj.z;
             const T aw = w * Vj;
             T Qd[DIM];
-            T mj;
             if (DIM == 3) {
-                const V4<T> q0 = ldg4(a.Q + 3 * j), q1 = ldg4(a.Q + 3 * j + 1), q2 = ldg4(a.Q + 3 * j + 2);
+                const V4<T> q0 = ldg4(a.Qa + j), q1 = ldg4(a.Qb + j);
+                const T q2 = __ldg(a.Qc + j);
                 Qd[0] = q0.x * d[0] + q0.y * d[1] + q0.z * d[DIM - 1];
                 Qd[1] = q0.w * d[0] + q1.x * d[1] + q1.y * d[DIM - 1];
-                Qd[DIM - 1] = q1.z * d[0] + q1.w * d[1] + q2.x * d[DIM - 1];
-                mj = q2.y;
+                Qd[DIM - 1] = q1.z * d[0] + q1.w * d[1] + q2 * d[DIM - 1];
             } else {
-                const V4<T> q0 = ldg4(a.Q + j);
+                const V4<T> q0 = ldg4(a.Qa + j);
                 Qd[0] = q0.x * d[0] + q0.y * d[1];
                 Qd[1] = q0.z * d[0] + q0.w * d[1];
-                mj = xj.w;
             }
 #pragma unroll
             for (int p = 0; p < DIM; p++) {
@@ -238,6 +254,7 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
                 const V4<T> vsj = ldg4(a.vs_cur + j);
                 if (VISC) {
                     const V4<T> uj = ldg4(a.ug_cur + j);
+                    const T mj = DIM == 3 ? uj.w : xj.w;  // reference mass m0_j
                     T dv[DIM], dx[DIM];
                     dv[0] = vsj.x - vsi.x;
                     dv[1] = vsj.y - vsi.y;
@@ -279,12 +296,12 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
         // own matrices
         T Qi[DIM][DIM];
         if (DIM == 3) {
-            const V4<T> q0 = a.Q[3 * i], q1 = a.Q[3 * i + 1], q2 = a.Q[3 * i + 2];
+            const V4<T> q0 = a.Qa[i], q1 = a.Qb[i];
             Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
             Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
-            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = q2.x;
+            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = a.Qc[i];
         } else {
-            const V4<T> q0 = a.Q[i];
+            const V4<T> q0 = a.Qa[i];
             Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
         }
         T acc[3] = {T(0), T(0), T(0)};
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(128) k_pass2(StepArgs<T> a) {
             un[p] = a.u64[p * n + i] + dt * (double)vn[p];
             a.u64[p * n + i] = un[p];
         }
-        a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), T(0)};
+        a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), DIM == 3 ? mass : T(0)};
         a.vs_next[i] = V4<T>{vn[0], vn[1], DIM == 3 ? vn[DIM - 1] : T(0), s_new};
         if (a.acc_out)
 #pragma unroll
@@ -540,7 +557,7 @@ __global__ void k_x_to_caller(int64_t n, int dim, const double *X0d, const doubl
 template <typename T> __global__ void k_refresh_ug(int64_t n, int dim, const double *u64, V4<T> *ug) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
-    ug[k] = V4<T>{(T)u64[k], (T)u64[n + k], dim == 3 ? (T)u64[2 * n + k] : T(0), T(0)};
+    ug[k] = V4<T>{(T)u64[k], (T)u64[n + k], dim == 3 ? (T)u64[2 * n + k] : T(0), ug[k].w};
 }
 // C_p^-1 = I + K (9 components) to the caller
 template <typename T> __global__ void k_cpinv_to_caller(int64_t n, const T *K, const int *perm, double *out) {

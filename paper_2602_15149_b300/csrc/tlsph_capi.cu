@@ -60,7 +60,8 @@ struct tlsph_ctx {
     int64_t *row_ptr = nullptr;
     int *col = nullptr, *row_len = nullptr, *sell = nullptr;
     int64_t *slice_off = nullptr;
-    void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr}, *Q = nullptr, *Vm = nullptr;
+    void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr}, *Vm = nullptr;
+    void *Qa = nullptr, *Qb = nullptr, *Qc = nullptr, *G = nullptr;
     void *Ahat = nullptr, *K = nullptr, *ep = nullptr, *H = nullptr, *sdot = nullptr;
     double *u64 = nullptr;
     uint16_t *mid = nullptr, *bcgrp = nullptr;
@@ -80,8 +81,8 @@ struct tlsph_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> ev_pending;  // (kind, event index of start); stop = start + 1
     size_t ev_next = 0;
-    double ms[2] = {0, 0};
-    int64_t cnt[2] = {0, 0};
+    double ms[3] = {0, 0, 0};
+    int64_t cnt[3] = {0, 0, 0};
 };
 
 namespace {
@@ -170,7 +171,8 @@ template <typename T> __global__ void k_init_sorted(int64_t n, int dim, const in
                                                     const double *volc, const double *v0c, const int *midc,
                                                     const int *specc, const uint16_t *grpc, const MatT<T> *mats,
                                                     const double *center, double *X0d, V4<T> *X0V, V4<T> *vs,
-                                                    uint16_t *mid, int *spec, uint16_t *bcgrp) {
+                                                    V4<T> *ug0, V4<T> *ug1, uint16_t *mid, int *spec,
+                                                    uint16_t *bcgrp) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
     int64_t p = perm[k];
@@ -187,6 +189,10 @@ template <typename T> __global__ void k_init_sorted(int64_t n, int dim, const in
     if (v0c)
         for (int q = 0; q < dim; q++) v[q] = v0c[dim * p + q];
     vs[k] = V4<T>{(T)v[0], (T)v[1], (T)v[2], T(1)};
+    // gathered displacement starts at zero; in 3D its 4th slot carries the reference mass m0
+    const T m0 = dim == 3 ? (T)((double)mats[m].rho * V) : T(0);
+    ug0[k] = V4<T>{T(0), T(0), T(0), m0};
+    ug1[k] = V4<T>{T(0), T(0), T(0), m0};
     mid[k] = (uint16_t)m;
     spec[k] = specc ? specc[p] : 0;
     bcgrp[k] = grpc[p];
@@ -204,7 +210,10 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.ug_next = (V4<T> *)c->ug[nxt];
     a.vs_cur = (const V4<T> *)c->vs[cur];
     a.vs_next = (V4<T> *)c->vs[nxt];
-    a.Q = (V4<T> *)c->Q;
+    a.Qa = (V4<T> *)c->Qa;
+    a.Qb = (V4<T> *)c->Qb;
+    a.Qc = (T *)c->Qc;
+    a.G = (T *)c->G;
     a.Vm = (T *)c->Vm;
     a.Ahat = (const T *)c->Ahat;
     a.K = (T *)c->K;
@@ -243,21 +252,20 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     return a;
 }
 
-// algorithmic HBM bytes of one step (neighbour gathers served from L2 / L1)
+// Algorithmic HBM bytes of one step: every particle's own records read / written once,
+// neighbour gathers served on chip, neighbour indices read once per neighbour pass.
 double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
     const int d = c->p.dim;
     const double n = (double)c->n, nnz = (double)c->nnz;
-    const double v4 = 4.0 * ts;
-    const double q = d == 3 ? 3 * v4 : v4;
-    double p1 = 4 + 8.0 / 32 + v4 /*X0V*/ + v4 /*ug*/ + (d == 3 ? 6 : 3) * ts /*Ahat*/ + 2 /*mid*/ + q /*Q w*/ +
-                d * d * ts /*Vm w*/;
-    if (c->has_j2) p1 += 2 * 7 * ts;               // K, ep read + write
-    if (c->has_frac) p1 += v4 /*s*/ + 2 * ts;      // H read + write
-    double p2 = 4 + 8.0 / 32 + v4 + v4 /*ug r*/ + v4 /*vs r*/ + q /*Q own*/ + 2 + 4 + 2 + 2 * 8.0 * d /*u64 r/w*/ +
-                v4 /*ug w*/ + v4 /*vs w*/;
-    if (c->has_visc) p2 += d * d * ts;
-    if (c->has_frac) p2 += (d == 3 ? 6 : 3) * ts + ts + 2 * ts;  // Ahat, H, sdot r/w
-    return n * (p1 + p2) + 2.0 * 4.0 * nnz;        // + neighbour indices of both passes
+    const double v4 = 4.0 * ts, nsym = d == 3 ? 6 : 3, q = d * d * ts;
+    const double grad = n * (4 + 8.0 / 32 + 2 * v4 + nsym * ts + d * d * ts) + 4.0 * nnz;
+    double stress = n * (d * d * ts + nsym * ts + 2 + q + d * d * ts);
+    if (c->has_j2) stress += n * 2 * 7 * ts;
+    if (c->has_frac) stress += n * (v4 + 2 * ts);
+    double p2 = n * (4 + 8.0 / 32 + 3 * v4 + q + 2 + 4 + 2 + 2 * 8.0 * d + 2 * v4) + 4.0 * nnz;
+    if (c->has_visc) p2 += n * d * d * ts;
+    if (c->has_frac) p2 += n * (nsym * ts + 3 * ts);
+    return grad + stress + p2;
 }
 
 template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
@@ -425,10 +433,9 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     DA(c->bcgrp, n * sizeof(uint16_t));
     k_init_sorted<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->perm, X0c, volc, v0c, midc, specc, grpc,
                                                         (const MatT<T> *)c->matsdev, centerd, c->X0d, (V4<T> *)c->X0V,
-                                                        (V4<T> *)c->vs[0], c->mid, c->spec, c->bcgrp);
+                                                        (V4<T> *)c->vs[0], (V4<T> *)c->ug[0], (V4<T> *)c->ug[1],
+                                                        c->mid, c->spec, c->bcgrp);
     CKL();
-    CK(cudaMemsetAsync(c->ug[0], 0, n * sizeof(V4<T>), s));
-    CK(cudaMemsetAsync(c->ug[1], 0, n * sizeof(V4<T>), s));
     CK(cudaMemcpyAsync(c->vs[1], c->vs[0], n * sizeof(V4<T>), cudaMemcpyDeviceToDevice, s));
     // ---- neighbours (count, scan, fill)
     DA(c->row_len, n * sizeof(int));
@@ -483,8 +490,11 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     // ---- state
     DA(c->u64, 3 * n * sizeof(double));
     CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
-    DA(c->Q, (dim == 3 ? 3 : 1) * n * sizeof(V4<T>));
-    CK(cudaMemsetAsync(c->Q, 0, (dim == 3 ? 3 : 1) * n * sizeof(V4<T>), s));
+    DA(c->Qa, n * sizeof(V4<T>));
+    DA(c->Qb, (dim == 3 ? n : 1) * sizeof(V4<T>));
+    DA(c->Qc, (dim == 3 ? n : 1) * sizeof(T));
+    CK(cudaMemsetAsync(c->Qa, 0, n * sizeof(V4<T>), s));
+    DA(c->G, dim * dim * n * sizeof(T));
     DA(c->Vm, dim * dim * n * sizeof(T));
     DA(c->K, 6 * n * sizeof(T));
     CK(cudaMemsetAsync(c->K, 0, 6 * n * sizeof(T), s));
@@ -576,30 +586,35 @@ tlsph_status step_dim(tlsph_ctx *c, int64_t nsteps) {
     const unsigned nb = blocks_for(c->n);
     for (int64_t k = 0; k < nsteps; k++) {
         StepArgs<T> a = make_args<T>(c);
-        int e1 = -1, e2 = -1;
-        if (c->timing) {
-            if (c->ev_next + 4 > 4096) {
-                cudaStreamSynchronize(c->stream);
-                collect_timing(c);
-            }
-            e1 = timing_event(c);
-            cudaEventRecord(c->ev_pool[e1], c->stream);
+        int ev[3] = {-1, -1, -1};
+        if (c->timing && c->ev_next + 6 > 4096) {
+            cudaStreamSynchronize(c->stream);
+            collect_timing(c);
         }
-        k_pass1<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        // timing category: 0 force-and-damage pass, 1 deformation gradient, 2 stress
+        auto start = [&](int cat) {
+            if (!c->timing) return;
+            ev[cat] = timing_event(c);
+            cudaEventRecord(c->ev_pool[ev[cat]], c->stream);
+        };
+        auto stop = [&](int cat) {
+            if (!c->timing) return;
+            cudaEventRecord(c->ev_pool[ev[cat] + 1], c->stream);
+            c->ev_pending.push_back({cat, ev[cat]});
+        };
+        start(1);
+        k_gradient<T, DIM><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
-        if (c->timing) {
-            cudaEventRecord(c->ev_pool[e1 + 1], c->stream);
-            c->ev_pending.push_back({1, e1});
-            e2 = timing_event(c);
-            cudaEventRecord(c->ev_pool[e2], c->stream);
-        }
+        stop(1);
+        start(2);
+        k_stress<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        stop(2);
+        start(0);
         if (c->has_visc) k_pass2<T, DIM, FRAC, true><<<nb, kThreads, 0, c->stream>>>(a);
         else k_pass2<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
-        if (c->timing) {
-            cudaEventRecord(c->ev_pool[e2 + 1], c->stream);
-            c->ev_pending.push_back({0, e2});
-        }
+        stop(0);
         c->parity ^= 1;
         c->steps++;
     }
@@ -621,11 +636,15 @@ template <typename T> tlsph_status diag_pass(tlsph_ctx *c) {
     StepArgs<T> a = make_args<T>(c);
     const unsigned nb = blocks_for(n);
     if (c->p.dim == 3) {
-        if (c->has_frac) k_pass1<T, 3, true, true><<<nb, kThreads, 0, c->stream>>>(a);
-        else k_pass1<T, 3, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 3><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        if (c->has_frac) k_stress<T, 3, true, true><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_stress<T, 3, false, true><<<nb, kThreads, 0, c->stream>>>(a);
     } else {
-        if (c->has_frac) k_pass1<T, 2, true, true><<<nb, kThreads, 0, c->stream>>>(a);
-        else k_pass1<T, 2, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 2><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        if (c->has_frac) k_stress<T, 2, true, true><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_stress<T, 2, false, true><<<nb, kThreads, 0, c->stream>>>(a);
     }
     CKL();
     return TLSPH_OK;
@@ -1093,11 +1112,11 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
     return fail(c, TLSPH_ERR_ARG, "unknown option %d", option);
 }
 
-tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[2], int64_t count[2]) {
+tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[3], int64_t count[3]) {
     if (!c || !ms || !count) return TLSPH_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream));
     collect_timing(c);
-    for (int q = 0; q < 2; q++) {
+    for (int q = 0; q < 3; q++) {
         ms[q] = c->ms[q];
         count[q] = c->cnt[q];
         c->ms[q] = 0.0;

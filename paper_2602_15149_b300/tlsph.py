@@ -249,11 +249,12 @@ class TLSPH:
         self._ck(self.lib.tlsph_set_option(self.ctx, option, value), "set_option")
 
     def kernel_times(self):
-        ms = np.zeros(2)
-        cnt = np.zeros(2, np.int64)
+        ms = np.zeros(3)
+        cnt = np.zeros(3, np.int64)
         self._ck(self.lib.tlsph_kernel_times(self.ctx, _d(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
                  "kernel_times")
-        return {"pass2_ms": ms[0], "pass2_launches": int(cnt[0]), "pass1_ms": ms[1], "pass1_launches": int(cnt[1])}
+        return {"pass2_ms": ms[0], "pass2_launches": int(cnt[0]), "gradient_ms": ms[1],
+                "gradient_launches": int(cnt[1]), "stress_ms": ms[2], "stress_launches": int(cnt[2])}
 
 
 def cell_sort_noalloc(X0, perm, h, support=2.0, specimen_id=None, device=0, stream=None) -> int:
