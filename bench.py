@@ -178,6 +178,37 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(args, device, stream):
+    """The batched form: 512 independent 2D specimens (log-uniform 500-50k particles, random
+    materials and loading) stepped together; execution mode and block picked by the autotuner."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    case = W.batched(nspec=args.batch_specimens, steps=args.steps)
+    t0 = time.perf_counter()
+    g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    best, allt = g.autotune(trial_steps=5)
+    g.step(args.warmup)
+    steps = max(10, min(args.steps, 1000))
+    dev = torch.device("cuda", device)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = g.sync(check=False)
+    ms = e0.elapsed_time(e1)
+    info = g.get_info()
+    g.close()
+    return {"workload": f"batched_2d {args.batch_specimens} specimens, {case.n} particles, "
+                        f"log-uniform 500-50k each, NH/J2, own clocks", "particles": case.n,
+            "specimens": args.batch_specimens, "steps": steps, "ms_per_step": ms / steps,
+            "value": case.n * steps / (ms * 1e-3), "unit": UNIT, "tuned": best, "candidates": allt,
+            "setup_s": setup_s, "status": int(st), "mean_neighbours": info["nnz"] / case.n}
+
+
 def run_ours(args):
     import torch
     from paper_2602_15149_b300 import tlsph
@@ -256,6 +287,7 @@ def run_ours(args):
     h2d = n * (8 * 3 + 8 + 4 + 8 * 3) + sum(n for _ in case.bcs)
     d2h = u.nbytes + 8 * 4 * args.steps
 
+    batched = measure_batched(args, local, stream) if not args.no_batched else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -276,6 +308,7 @@ def run_ours(args):
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": launches,
+        "batched": batched,
         "status": int(st),
         "cpu_baseline": cpu,
     }
@@ -292,6 +325,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
+    ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()

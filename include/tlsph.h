@@ -216,9 +216,36 @@ tlsph_status tlsph_get_info(tlsph_ctx *ctx, tlsph_info *out);
  *    since the last call of the force-and-damage pass (ms[0], count[0]), the
  *    deformation-gradient pass (ms[1], count[1]) and the stress pass (ms[2], count[2]).
  *  TLSPH_OPT_RECORD_ACC: keep the acceleration of each step for TLSPH_FIELD_ACC. */
-enum { TLSPH_OPT_KERNEL_TIMING = 1, TLSPH_OPT_RECORD_ACC = 2 };
+enum {
+    TLSPH_OPT_KERNEL_TIMING = 1,
+    TLSPH_OPT_RECORD_ACC = 2,
+    TLSPH_OPT_MODE = 3,         /* execution mode, value TLSPH_MODE_* (default TLSPH_MODE_LAUNCH) */
+    TLSPH_OPT_BLOCK = 4,        /* threads per block: 64, 128 (default) or 256 */
+    TLSPH_OPT_BARRIER_TEST = 5  /* testing: the persistent mode's grid barrier waits for one block more than it
+                                   launches, so every wait runs out after about a second and tlsph_step /
+                                   tlsph_sync return TLSPH_ERR_TIMEOUT (the context stays usable) */
+};
+/* How a step is executed:
+ *  TLSPH_MODE_LAUNCH:     three kernel launches per step (deformation gradient, stress, force and damage);
+ *  TLSPH_MODE_GRAPH:      the same kernels replayed from a CUDA graph of two steps (fewer launch gaps);
+ *  TLSPH_MODE_PERSISTENT: one cooperative launch runs all the steps of a tlsph_step call with grid-wide
+ *                         barriers between the phases (each bounded to about a second of waiting). */
+enum { TLSPH_MODE_LAUNCH = 0, TLSPH_MODE_GRAPH = 1, TLSPH_MODE_PERSISTENT = 2 };
 tlsph_status tlsph_set_option(tlsph_ctx *ctx, int option, int value);
 tlsph_status tlsph_kernel_times(tlsph_ctx *ctx, double ms[3], int64_t count[3]);
+
+typedef struct {
+    int mode;            /* TLSPH_MODE_* */
+    int block;           /* threads per block */
+    double ms_per_step;  /* measured over the trial (INFINITY if the candidate failed) */
+} tlsph_tuning;
+/* Autotuner: run each execution mode / block size (LAUNCH 64, 128, 256; GRAPH 128;
+ * PERSISTENT 128, 256) for 2 warm-up steps and trial_steps timed steps, each from the same
+ * snapshot of the current state, and select the fastest for later steps.  The state, time
+ * and step count are restored afterwards (the tuning steps leave no trace).  best and
+ * all (6 entries, order above) may be NULL.  Needs a temporary device buffer of the size
+ * of the evolving state. */
+tlsph_status tlsph_autotune(tlsph_ctx *ctx, int trial_steps, tlsph_tuning *best, tlsph_tuning *all);
 
 /* Largest particle count accepted by tlsph_cell_sort_noalloc. */
 #define TLSPH_NOALLOC_MAX_PARTICLES 131072

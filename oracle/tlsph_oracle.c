@@ -49,7 +49,7 @@
 #define ORC_DT_ADAPTIVE 1
 #define ORC_DT_CFL_STATIC 2
 
-#define ORC_MAX_BC 16
+#define ORC_MAX_BC 256
 #define ORC_MAX_NOTCH 512
 
 typedef struct {

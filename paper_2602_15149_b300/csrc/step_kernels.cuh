@@ -41,10 +41,7 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i.  Register-light so
 // that many warps keep neighbour gathers in flight.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128, 8) k_gradient(StepArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    prefetch_slice(a.col, a.slice_off, i);
+__device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[DIM][DIM]) {
     const int n = a.n;
     const int64_t base = a.slice_off[i >> 5] + (i & 31);
     const int len = a.row_len[i];
@@ -91,23 +88,34 @@ __global__ void __launch_bounds__(128, 8) k_gradient(StepArgs<T> a) {
             T s = T(0);
 #pragma unroll
             for (int r = 0; r < DIM; r++) s += B[p][r] * A[r][q];
-            a.G[(p * DIM + q) * n + i] = s;
+            Gm[p][q] = s;
         }
+}
+
+template <typename T, int DIM, int BS>
+__global__ void __launch_bounds__(BS, 1024 / BS) k_gradient(StepArgs<T> a) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= a.n) return;
+    prefetch_slice(a.col, a.slice_off, i);
+    T Gm[DIM][DIM];
+    dev_gradient<T, DIM>(a, i, Gm);
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) a.G[(p * DIM + q) * a.n + i] = Gm[p][q];
 }
 
 // ---------------------------------------------------------------- pass 1b: stress
 // Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and the
 // per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i.
 template <typename T, int DIM, bool FRAC, bool DIAG>
-__global__ void __launch_bounds__(128) k_stress(StepArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+__device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T Gm[DIM][DIM]) {
     const int n = a.n;
     M3<T> G = m3_zero<T>();
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
-        for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
+        for (int q = 0; q < DIM; q++) G(p, q) = Gm[p][q];
     const MatT<T> m = a.mats[a.mid[i]];
     T s = T(1);
     const bool frac = FRAC && m.fracture;
@@ -190,20 +198,24 @@ __global__ void __launch_bounds__(128) k_stress(StepArgs<T> a) {
         for (int q = 0; q < DIM; q++) a.Vm[(p * DIM + q) * n + i] = Vm[p][q];
 }
 
+template <typename T, int DIM, bool FRAC, bool DIAG, int BS>
+__global__ void __launch_bounds__(BS) k_stress(StepArgs<T> a) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= a.n) return;
+    T Gm[DIM][DIM];
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * a.n + i];
+    dev_stress<T, DIM, FRAC, DIAG>(a, i, Gm);
+}
+
 // ---------------------------------------------------------------- pass 2
 template <typename T, int DIM, bool FRAC, bool VISC>
-__global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
-    __shared__ int s_sp;
-    __shared__ double s_v[4], s_a[4];
-    __shared__ bool s_last;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < a.n;
+__device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &vmag, double &amag) {
     const int n = a.n;
-    double vmag = 0.0, amag = 0.0;
-    int sp = 0;
-    if (active) {
-        prefetch_slice(a.col, a.slice_off, i);
-        sp = a.spec[i];
+    const int sp = a.spec[i];
+    {
         const int64_t base = a.slice_off[i >> 5] + (i & 31);
         const int len = a.row_len[i];
         const V4<T> xi = a.X0V[i];
@@ -403,7 +415,15 @@ __global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
         amag = (double)t_sqrt(aa);
         if (!(isfinite(vmag) && isfinite(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
     }
-    // per-specimen maxima of |v_{n+1}| and |a_n|
+}
+
+// Per-specimen maxima of |v_{n+1}| and |a_n| of one block (one atomic per block when the
+// block holds a single specimen).
+template <typename T, int BS>
+__device__ __forceinline__ void dev_block_maxima(const StepArgs<T> &a, bool active, int sp, double vmag,
+                                                 double amag) {
+    __shared__ int s_sp;
+    __shared__ double s_v[BS / 32], s_a[BS / 32];
     if (threadIdx.x == 0) s_sp = sp;
     __syncthreads();
     const bool uniform = __syncthreads_and(!active || sp == s_sp);
@@ -419,7 +439,7 @@ __global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+            for (int q = 1; q < BS / 32; q++) {
                 v = fmax(v, s_v[q]);
                 ac = fmax(ac, s_a[q]);
             }
@@ -430,13 +450,13 @@ __global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
         atomicMax(&a.vmax_bits[sp], (unsigned long long)__double_as_longlong(vmag));
         atomicMax(&a.amax_bits[sp], (unsigned long long)__double_as_longlong(amag));
     }
-    // the last block to finish advances the clocks and picks the next step size
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
+}
+
+// Advance every specimen's clock by its step and pick the next step size (eq. dt_criterion),
+// after all of the step's maxima are in; run by the threads of one block.
+template <typename T> __device__ __forceinline__ void dev_finalize(const StepArgs<T> &a) {
+    {
         for (int q = threadIdx.x; q < a.nspec; q += blockDim.x) {
             const double dts = a.dt[q];
             a.t[q] = a.t[q] + dts;
@@ -450,8 +470,119 @@ __global__ void __launch_bounds__(128, 8) k_pass2(StepArgs<T> a) {
                 a.dt[q] = a.cfl * (dtv < dta ? dtv : dta);
             }
         }
+    }
+}
+
+template <typename T, int DIM, bool FRAC, bool VISC, int BS>
+__global__ void __launch_bounds__(BS, 1024 / BS) k_pass2(StepArgs<T> a) {
+    __shared__ bool s_last;
+    const int i = blockIdx.x * BS + threadIdx.x;
+    const bool active = i < a.n;
+    double vmag = 0.0, amag = 0.0;
+    int sp = 0;
+    if (active) {
+        prefetch_slice(a.col, a.slice_off, i);
+        sp = a.spec[i];
+        dev_pass2<T, DIM, FRAC, VISC>(a, i, vmag, amag);
+    }
+    dev_block_maxima<T, BS>(a, active, sp, vmag, amag);
+    // the last block to finish advances the clocks and picks the next step size
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        dev_finalize(a);
         if (threadIdx.x == 0) *a.done = 0u;
     }
+}
+
+// ---------------------------------------------------------------- persistent step loop
+// Bounded grid barrier of a cooperative launch: every block arrives once per phase; a
+// block that waits longer than limit_cycles (about a second) flags kFlagTimeout and all
+// blocks leave the kernel at their next barrier.
+struct GridBarrier {
+    unsigned int *count;
+    unsigned int *gen;
+    unsigned int expected;
+    long long limit_cycles;
+};
+
+template <typename T> __device__ __forceinline__ bool grid_sync(const GridBarrier &b, int *flags) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = b.gen;
+        volatile int *vflag = flags + kFlagTimeout;
+        int ok = *vflag == 0;
+        if (ok) {
+            const unsigned int g0 = *vgen;
+            __threadfence();
+            const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+            if (arrived == b.expected) {
+                atomicExch(b.count, 0u);
+                __threadfence();
+                atomicAdd(b.gen, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*vgen == g0) {
+                    if (*vflag != 0 || clock64() - t0 > b.limit_cycles) {
+                        atomicAdd(flags + kFlagTimeout, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// nsteps steps in one cooperative launch: phase A (gradient + stress per particle, no
+// neighbour dependency between them), barrier, phase B (force, damage, update), barrier.
+// Block 0 advances the clocks of the previous step while phase A runs.
+template <typename T, int DIM, bool FRAC, bool VISC, int BS>
+__global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps, GridBarrier bar) {
+    const int n = a.n;
+    const int stride = gridDim.x * BS;
+    for (int step = 0; step < nsteps; step++) {
+        for (int base = blockIdx.x * BS; base < n; base += stride) {
+            const int i = base + threadIdx.x;
+            if (i < n) {
+                prefetch_slice(a.col, a.slice_off, i);
+                T Gm[DIM][DIM];
+                dev_gradient<T, DIM>(a, i, Gm);
+                dev_stress<T, DIM, FRAC, false>(a, i, Gm);
+            }
+        }
+        if (step > 0 && blockIdx.x == 0) dev_finalize(a);
+        if (!grid_sync<T>(bar, a.flags)) return;
+        for (int base = blockIdx.x * BS; base < n; base += stride) {
+            const int i = base + threadIdx.x;
+            const bool active = i < n;
+            double vmag = 0.0, amag = 0.0;
+            int sp = 0;
+            if (active) {
+                prefetch_slice(a.col, a.slice_off, i);
+                sp = a.spec[i];
+                dev_pass2<T, DIM, FRAC, VISC>(a, i, vmag, amag);
+            }
+            dev_block_maxima<T, BS>(a, active, sp, vmag, amag);
+        }
+        // ping-pong: the new displacement and velocity become current
+        const V4<T> *u0 = a.ug_cur, *v0 = a.vs_cur;
+        a.ug_cur = a.ug_next;
+        a.vs_cur = a.vs_next;
+        a.ug_next = const_cast<V4<T> *>(u0);
+        a.vs_next = const_cast<V4<T> *>(v0);
+        if (!grid_sync<T>(bar, a.flags)) return;
+    }
+    if (nsteps > 0 && blockIdx.x == 0) dev_finalize(a);
 }
 
 // ---------------------------------------------------------------- diagnostics

@@ -26,7 +26,7 @@ struct BCHost {
     int kind, comp_mask;
     double value[3];
     double t_start, t_end, ramp, area;
-    std::vector<uint8_t> mask;
+    std::vector<int64_t> ids;  // the masked particles (kept as a list: a batch has one condition per specimen)
     int64_t count;
 };
 
@@ -76,6 +76,11 @@ struct tlsph_ctx {
     void *Fd = nullptr, *Pd = nullptr, *psid = nullptr, *accd = nullptr;
     double *energy = nullptr;
     int64_t flags_seen[kNumFlags] = {0};
+    // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
+    int mode = 0, bs = 128;
+    cudaGraphExec_t gexec = nullptr;
+    unsigned int *bar = nullptr;
+    bool barrier_test = false;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -127,12 +132,19 @@ template <typename P> tlsph_status dalloc(tlsph_ctx *c, P **ptr, size_t bytes) {
         if (s_ != TLSPH_OK) return s_;                  \
     } while (0)
 
+void drop_graph(tlsph_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
 void free_device(tlsph_ctx *c) {
+    drop_graph(c);
     for (void *q : c->allocs) cudaFree(q);
     c->allocs.clear();
     c->X0d = nullptr;
     c->perm = nullptr;
     c->Fd = c->Pd = c->psid = c->accd = nullptr;
+    c->bar = nullptr;
     c->built = false;
 }
 
@@ -170,21 +182,14 @@ tlsph_status scan_exclusive(tlsph_ctx *c, int64_t m, const int64_t *in, int64_t 
 template <typename T> __global__ void k_init_sorted(int64_t n, int dim, const int *perm, const double *X0c,
                                                     const double *volc, const double *v0c, const int *midc,
                                                     const int *specc, const uint16_t *grpc, const MatT<T> *mats,
-                                                    const double *center, double *X0d, V4<T> *X0V, V4<T> *vs,
-                                                    V4<T> *ug0, V4<T> *ug1, uint16_t *mid, int *spec,
-                                                    uint16_t *bcgrp) {
+                                                    double *X0d, V4<T> *vs, V4<T> *ug0, V4<T> *ug1, uint16_t *mid,
+                                                    int *spec, uint16_t *bcgrp, int *first, int *last) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
     int64_t p = perm[k];
-    double x[3] = {0, 0, 0};
-    for (int q = 0; q < dim; q++) x[q] = X0c[3 * p + q];
-    for (int q = 0; q < 3; q++) X0d[q * n + k] = x[q];
-    double V = volc[p];
-    int m = midc[p];
-    T xs[3];
-    for (int q = 0; q < 3; q++) xs[q] = (T)(x[q] - center[q]);
-    if (dim == 3) X0V[k] = V4<T>{xs[0], xs[1], xs[2], (T)V};
-    else X0V[k] = V4<T>{xs[0], xs[1], (T)V, (T)((double)mats[m].rho * V)};
+    for (int q = 0; q < 3; q++) X0d[q * n + k] = q < dim ? X0c[3 * p + q] : 0.0;
+    const double V = volc[p];
+    const int m = midc[p];
     double v[3] = {0, 0, 0};
     if (v0c)
         for (int q = 0; q < dim; q++) v[q] = v0c[dim * p + q];
@@ -194,8 +199,34 @@ template <typename T> __global__ void k_init_sorted(int64_t n, int dim, const in
     ug0[k] = V4<T>{T(0), T(0), T(0), m0};
     ug1[k] = V4<T>{T(0), T(0), T(0), m0};
     mid[k] = (uint16_t)m;
-    spec[k] = specc ? specc[p] : 0;
+    const int sp = specc ? specc[p] : 0;
+    spec[k] = sp;
     bcgrp[k] = grpc[p];
+    atomicMin(&first[sp], (int)k);
+    atomicMax(&last[sp], (int)k);
+}
+
+// Reference positions in the step's precision, relative to an origin inside each specimen
+// (the particle in the middle of its sorted range): small coordinates keep the relative
+// precision of X_j - X_i in FP32, and a specimen gets the same values alone or in a batch.
+template <typename T> __global__ void k_build_x0v(int64_t n, int dim, const double *X0d, const double *volc,
+                                                  const int *perm, const int *spec, const int *first,
+                                                  const int *last, const MatT<T> *mats, const uint16_t *mid,
+                                                  V4<T> *X0V) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int sp = spec[k];
+    const int64_t o = ((int64_t)first[sp] + (int64_t)last[sp]) / 2;
+    T xs[3];
+    for (int q = 0; q < 3; q++) xs[q] = (T)(X0d[q * n + k] - X0d[q * n + o]);
+    const double V = volc[perm[k]];
+    if (dim == 3) X0V[k] = V4<T>{xs[0], xs[1], xs[2], (T)V};
+    else X0V[k] = V4<T>{xs[0], xs[1], (T)V, (T)((double)mats[mid[k]].rho * V)};
+}
+
+__global__ void k_fill_int(int64_t n, int *p, int v) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n) p[k] = v;
 }
 
 template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
@@ -295,10 +326,11 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     std::vector<uint16_t> grph(n, 0);
     std::map<std::vector<int>, int> groups;
     std::vector<int16_t> grp_tab(4, -1);
+    std::vector<std::vector<int>> per(n);
+    for (size_t b = 0; b < c->bcs.size(); b++)
+        for (int64_t pi : c->bcs[b].ids) per[pi].push_back((int)b);
     for (int64_t pi = 0; pi < n; pi++) {
-        std::vector<int> ids;
-        for (size_t b = 0; b < c->bcs.size(); b++)
-            if (c->bcs[b].mask[pi]) ids.push_back((int)b);
+        const std::vector<int> &ids = per[pi];
         if (ids.empty()) continue;
         if (ids.size() > (size_t)kMaxBcPerParticle)
             return fail(c, TLSPH_ERR_ARG, "particle %lld is covered by more than %d boundary conditions", (long long)pi,
@@ -383,15 +415,10 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     CellGrid g;
     g.dim = dim;
     g.cs = R / 3.0;
-    double center[3];
     for (int k = 0; k < 3; k++) {
         g.xmin[k] = bb[k];
         g.nc[k] = (int64_t)floor((bb[3 + k] - bb[k]) / g.cs + 0.5) + 1;
-        center[k] = 0.5 * (bb[k] + bb[3 + k]);
     }
-    double *centerd;
-    DA(centerd, 3 * sizeof(double));
-    CK(cudaMemcpyAsync(centerd, center, sizeof center, cudaMemcpyHostToDevice, s));
     double maxkey = ((double)c->nspec * g.nc[2] * g.nc[1] * g.nc[0]);
     if (!(maxkey < 9.0e18)) return fail(c, TLSPH_ERR_ARG, "cell grid too large");
     int bits = 1;
@@ -431,10 +458,20 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     DA(c->mid, n * sizeof(uint16_t));
     DA(c->spec, n * sizeof(int));
     DA(c->bcgrp, n * sizeof(uint16_t));
+    int *sfirst, *slast;
+    DA(sfirst, c->nspec * sizeof(int));
+    DA(slast, c->nspec * sizeof(int));
+    k_fill_int<<<blocks_for(c->nspec), kThreads, 0, s>>>(c->nspec, sfirst, (int)n);
+    CKL();
+    k_fill_int<<<blocks_for(c->nspec), kThreads, 0, s>>>(c->nspec, slast, -1);
+    CKL();
     k_init_sorted<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->perm, X0c, volc, v0c, midc, specc, grpc,
-                                                        (const MatT<T> *)c->matsdev, centerd, c->X0d, (V4<T> *)c->X0V,
-                                                        (V4<T> *)c->vs[0], (V4<T> *)c->ug[0], (V4<T> *)c->ug[1],
-                                                        c->mid, c->spec, c->bcgrp);
+                                                        (const MatT<T> *)c->matsdev, c->X0d, (V4<T> *)c->vs[0],
+                                                        (V4<T> *)c->ug[0], (V4<T> *)c->ug[1], c->mid, c->spec,
+                                                        c->bcgrp, sfirst, slast);
+    CKL();
+    k_build_x0v<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->X0d, volc, c->perm, c->spec, sfirst, slast,
+                                                      (const MatT<T> *)c->matsdev, c->mid, (V4<T> *)c->X0V);
     CKL();
     CK(cudaMemcpyAsync(c->vs[1], c->vs[0], n * sizeof(V4<T>), cudaMemcpyDeviceToDevice, s));
     // ---- neighbours (count, scan, fill)
@@ -536,6 +573,8 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     DA(c->vmax, ns_ * sizeof(unsigned long long));
     DA(c->amax, ns_ * sizeof(unsigned long long));
     DA(c->done, sizeof(unsigned int));
+    DA(c->bar, 2 * sizeof(unsigned int));
+    CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned int), s));
     CK(cudaMemcpyAsync(c->t, t0.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->dt, dt0.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->cmax, cm.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -581,44 +620,132 @@ void collect_timing(tlsph_ctx *c) {
     c->ev_next = 0;
 }
 
-template <typename T, int DIM, bool FRAC>
-tlsph_status step_dim(tlsph_ctx *c, int64_t nsteps) {
-    const unsigned nb = blocks_for(c->n);
+// ---- one step as three kernel launches (gradient, stress, force-and-damage)
+template <typename T, int DIM, bool FRAC, int BS>
+tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
+    const unsigned nb = blocks_for(c->n, BS);
     for (int64_t k = 0; k < nsteps; k++) {
         StepArgs<T> a = make_args<T>(c);
         int ev[3] = {-1, -1, -1};
-        if (c->timing && c->ev_next + 6 > 4096) {
+        if (timing && c->ev_next + 6 > 4096) {
             cudaStreamSynchronize(c->stream);
             collect_timing(c);
         }
         // timing category: 0 force-and-damage pass, 1 deformation gradient, 2 stress
         auto start = [&](int cat) {
-            if (!c->timing) return;
+            if (!timing) return;
             ev[cat] = timing_event(c);
             cudaEventRecord(c->ev_pool[ev[cat]], c->stream);
         };
         auto stop = [&](int cat) {
-            if (!c->timing) return;
+            if (!timing) return;
             cudaEventRecord(c->ev_pool[ev[cat] + 1], c->stream);
             c->ev_pending.push_back({cat, ev[cat]});
         };
         start(1);
-        k_gradient<T, DIM><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, DIM, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
         stop(1);
         start(2);
-        k_stress<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        k_stress<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
         stop(2);
         start(0);
-        if (c->has_visc) k_pass2<T, DIM, FRAC, true><<<nb, kThreads, 0, c->stream>>>(a);
-        else k_pass2<T, DIM, FRAC, false><<<nb, kThreads, 0, c->stream>>>(a);
+        if (c->has_visc) k_pass2<T, DIM, FRAC, true, BS><<<nb, BS, 0, c->stream>>>(a);
+        else k_pass2<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
         stop(0);
         c->parity ^= 1;
         c->steps++;
     }
     return TLSPH_OK;
+}
+
+// ---- steps replayed from a CUDA graph holding two steps (the ping-pong returns to parity 0)
+template <typename T, int DIM, bool FRAC, int BS>
+tlsph_status step_graph(tlsph_ctx *c, int64_t nsteps) {
+    if (nsteps > 0 && c->parity == 1) {
+        tlsph_status st = step_launches<T, DIM, FRAC, BS>(c, 1, false);
+        if (st != TLSPH_OK) return st;
+        nsteps--;
+    }
+    if (nsteps >= 2 && !c->gexec) {
+        cudaGraph_t g = nullptr;
+        const int par = c->parity;
+        const int64_t steps = c->steps, launches = c->launches;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        tlsph_status st = step_launches<T, DIM, FRAC, BS>(c, 2, false);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->parity = par;
+        c->steps = steps;
+        c->launches = launches;
+        if (st != TLSPH_OK) return st;
+        if (e != cudaSuccess) return fail(c, TLSPH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, TLSPH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    for (; nsteps >= 2; nsteps -= 2) {
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+        c->launches += 6;
+        c->steps += 2;
+    }
+    if (nsteps) return step_launches<T, DIM, FRAC, BS>(c, nsteps, false);
+    return TLSPH_OK;
+}
+
+// ---- steps in one cooperative persistent launch (all blocks resident, bounded grid barriers)
+template <typename T, int DIM, bool FRAC, bool VISC, int BS>
+tlsph_status step_persistent_v(tlsph_ctx *c, int64_t nsteps) {
+    auto kern = k_persistent<T, DIM, FRAC, VISC, BS>;
+    int per_sm = 0, nsm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, 0));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->p.device));
+    const int64_t tiles = (c->n + BS - 1) / BS;
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * nsm, tiles);
+    if (grid < 1) return fail(c, TLSPH_ERR_CUDA, "persistent kernel cannot be resident");
+    GridBarrier bar{c->bar, c->bar + 1, (unsigned)grid + (c->barrier_test ? 1u : 0u), 2000000000LL};
+    while (nsteps > 0) {
+        const int chunk = (int)std::min<int64_t>(nsteps, 1 << 20);
+        StepArgs<T> a = make_args<T>(c);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(BS);
+        cfg.stream = c->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, kern, a, chunk, bar));
+        CKL();
+        if (chunk & 1) c->parity ^= 1;
+        c->steps += chunk;
+        nsteps -= chunk;
+    }
+    return TLSPH_OK;
+}
+
+template <typename T, int DIM, bool FRAC, int BS>
+tlsph_status step_mode(tlsph_ctx *c, int64_t nsteps) {
+    if (c->mode == TLSPH_MODE_GRAPH && !c->timing) return step_graph<T, DIM, FRAC, BS>(c, nsteps);
+    if (c->mode == TLSPH_MODE_PERSISTENT) {
+        if (BS == 64) return fail(c, TLSPH_ERR_ARG, "the persistent mode needs a block of 128 or 256");
+        return c->has_visc ? step_persistent_v<T, DIM, FRAC, true, (BS < 128 ? 128 : BS)>(c, nsteps)
+                           : step_persistent_v<T, DIM, FRAC, false, (BS < 128 ? 128 : BS)>(c, nsteps);
+    }
+    return step_launches<T, DIM, FRAC, BS>(c, nsteps, c->timing);
+}
+
+template <typename T, int DIM, bool FRAC> tlsph_status step_dim(tlsph_ctx *c, int64_t nsteps) {
+    switch (c->bs) {
+    case 64: return step_mode<T, DIM, FRAC, 64>(c, nsteps);
+    case 256: return step_mode<T, DIM, FRAC, 256>(c, nsteps);
+    default: return step_mode<T, DIM, FRAC, 128>(c, nsteps);
+    }
 }
 
 template <typename T> tlsph_status step_impl(tlsph_ctx *c, int64_t nsteps) {
@@ -636,15 +763,15 @@ template <typename T> tlsph_status diag_pass(tlsph_ctx *c) {
     StepArgs<T> a = make_args<T>(c);
     const unsigned nb = blocks_for(n);
     if (c->p.dim == 3) {
-        k_gradient<T, 3><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 3, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
-        if (c->has_frac) k_stress<T, 3, true, true><<<nb, kThreads, 0, c->stream>>>(a);
-        else k_stress<T, 3, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+        if (c->has_frac) k_stress<T, 3, true, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_stress<T, 3, false, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
     } else {
-        k_gradient<T, 2><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 2, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
-        if (c->has_frac) k_stress<T, 2, true, true><<<nb, kThreads, 0, c->stream>>>(a);
-        else k_stress<T, 2, false, true><<<nb, kThreads, 0, c->stream>>>(a);
+        if (c->has_frac) k_stress<T, 2, true, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        else k_stress<T, 2, false, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
     }
     CKL();
     return TLSPH_OK;
@@ -787,9 +914,114 @@ tlsph_status check_flags(tlsph_ctx *c) {
     CK(cudaStreamSynchronize(c->stream));
     int64_t dn = hf[kFlagNonfinite] - c->flags_seen[kFlagNonfinite];
     int64_t dc = hf[kFlagNoconv] - c->flags_seen[kFlagNoconv];
+    int64_t dt = hf[kFlagTimeout] - c->flags_seen[kFlagTimeout];
     for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = hf[q];
+    if (dt > 0) {
+        // a persistent launch gave up at a barrier: its steps are incomplete; reset the
+        // barrier and the timeout flag so that the context stays usable
+        CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned int), c->stream));
+        CK(cudaMemsetAsync(c->flags + kFlagTimeout, 0, sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->flags_seen[kFlagTimeout] = 0;
+        return fail(c, TLSPH_ERR_TIMEOUT, "a grid barrier of the persistent step gave up after its time limit");
+    }
     if (dn > 0) return fail(c, TLSPH_ERR_NONFINITE, "%lld non-finite stresses or accelerations", (long long)dn);
     if (dc > 0) return fail(c, TLSPH_ERR_NOCONVERGE, "%lld J2 return maps did not converge", (long long)dc);
+    return TLSPH_OK;
+}
+
+// Autotuner: time every execution mode / block size on the live problem for a few steps,
+// each from the same snapshot of the evolving state, keep the fastest, restore the state.
+struct Snap {
+    void *p;
+    size_t bytes;
+};
+template <typename T> std::vector<Snap> snap_parts(tlsph_ctx *c) {
+    const size_t n = (size_t)c->n, ns = (size_t)c->nspec, ts = sizeof(T);
+    return {{c->u64, 3 * n * 8},       {c->ug[c->parity], n * sizeof(V4<T>)}, {c->vs[c->parity], n * sizeof(V4<T>)},
+            {c->sdot, n * ts},         {c->H, n * ts},                         {c->K, 6 * n * ts},
+            {c->ep, n * ts},           {c->t, ns * 8},                         {c->dt, ns * 8},
+            {c->vmax, ns * 8},         {c->amax, ns * 8},                      {c->last_v, ns * 8},
+            {c->last_a, ns * 8},       {c->flags, kNumFlags * sizeof(int)},     {c->done, sizeof(unsigned int)},
+            {c->bar, 2 * sizeof(unsigned int)}};
+}
+
+template <typename T>
+tlsph_status autotune_impl(tlsph_ctx *c, int trial, tlsph_tuning *best, tlsph_tuning *all) {
+    std::vector<Snap> parts = snap_parts<T>(c);
+    size_t total = 0;
+    for (const Snap &q : parts) total += (q.bytes + 255) / 256 * 256;
+    char *snap = nullptr;
+    if (cudaMalloc(&snap, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TLSPH_ERR_OOM, "autotune snapshot");
+    }
+    const int par = c->parity, mode0 = c->mode, bs0 = c->bs;
+    const int64_t steps = c->steps;
+    int64_t seen[kNumFlags];
+    for (int q = 0; q < kNumFlags; q++) seen[q] = c->flags_seen[q];
+    auto copy_all = [&](bool save) {
+        size_t off = 0;
+        for (const Snap &q : parts) {
+            if (save) cudaMemcpyAsync(snap + off, q.p, q.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            else cudaMemcpyAsync(q.p, snap + off, q.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            off += (q.bytes + 255) / 256 * 256;
+        }
+    };
+    auto restore = [&]() {
+        c->parity = par;  // the snapshot holds the buffers of this parity
+        copy_all(false);
+        c->steps = steps;
+        for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = seen[q];
+        drop_graph(c);
+    };
+    copy_all(true);
+    const int cand[6][2] = {{TLSPH_MODE_LAUNCH, 64},  {TLSPH_MODE_LAUNCH, 128},     {TLSPH_MODE_LAUNCH, 256},
+                            {TLSPH_MODE_GRAPH, 128},  {TLSPH_MODE_PERSISTENT, 128}, {TLSPH_MODE_PERSISTENT, 256}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = INFINITY;
+    int bi = -1;
+    const bool timing = c->timing;
+    c->timing = false;
+    for (int k = 0; k < 6; k++) {
+        c->mode = cand[k][0];
+        c->bs = cand[k][1];
+        drop_graph(c);
+        double ms_step = INFINITY;
+        tlsph_status st = step_impl<T>(c, 2);
+        if (st == TLSPH_OK) {
+            cudaEventRecord(e0, c->stream);
+            st = step_impl<T>(c, trial);
+            cudaEventRecord(e1, c->stream);
+        }
+        if (st == TLSPH_OK && cudaStreamSynchronize(c->stream) == cudaSuccess && check_flags(c) == TLSPH_OK) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_step = ms / trial;
+        }
+        cudaGetLastError();
+        if (all) all[k] = tlsph_tuning{cand[k][0], cand[k][1], ms_step};
+        if (ms_step < best_ms) {
+            best_ms = ms_step;
+            bi = k;
+        }
+        restore();
+    }
+    c->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(snap);
+    if (bi < 0) {
+        c->mode = mode0;
+        c->bs = bs0;
+        return fail(c, TLSPH_ERR_CUDA, "no execution mode ran");
+    }
+    c->mode = cand[bi][0];
+    c->bs = cand[bi][1];
+    if (best) *best = tlsph_tuning{c->mode, c->bs, best_ms};
     return TLSPH_OK;
 }
 
@@ -908,9 +1140,9 @@ tlsph_status tlsph_add_bc(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_
     b.t_end = t_end;
     b.ramp = ramp;
     b.area = area;
-    b.mask.assign(mask, mask + c->n);
-    b.count = 0;
-    for (int64_t i = 0; i < c->n; i++) b.count += mask[i] ? 1 : 0;
+    for (int64_t i = 0; i < c->n; i++)
+        if (mask[i]) b.ids.push_back(i);
+    b.count = (int64_t)b.ids.size();
     c->bcs.push_back(std::move(b));
     c->built = false;
     return TLSPH_OK;
@@ -1107,9 +1339,34 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
     }
     if (option == TLSPH_OPT_RECORD_ACC) {
         c->record_acc = value != 0;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_MODE) {
+        if (value < TLSPH_MODE_LAUNCH || value > TLSPH_MODE_PERSISTENT) return fail(c, TLSPH_ERR_ARG, "bad mode");
+        c->mode = value;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_BLOCK) {
+        if (value != 64 && value != 128 && value != 256) return fail(c, TLSPH_ERR_ARG, "block must be 64, 128 or 256");
+        c->bs = value;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_BARRIER_TEST) {
+        c->barrier_test = value != 0;
         return TLSPH_OK;
     }
     return fail(c, TLSPH_ERR_ARG, "unknown option %d", option);
+}
+
+tlsph_status tlsph_autotune(tlsph_ctx *c, int trial_steps, tlsph_tuning *best, tlsph_tuning *all) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before autotune");
+    if (trial_steps < 1) return fail(c, TLSPH_ERR_ARG, "trial_steps must be >= 1");
+    return c->p.precision == TLSPH_FP64 ? autotune_impl<double>(c, trial_steps, best, all)
+                                        : autotune_impl<float>(c, trial_steps, best, all);
 }
 
 tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[3], int64_t count[3]) {

@@ -21,14 +21,16 @@ MODEL_NH, MODEL_J2 = 2, 3
 BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "ACC": 11, "CPINV": 12,
          "STATE": 100}
-OPT_KERNEL_TIMING, OPT_RECORD_ACC = 1, 2
+OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST = 1, 2, 3, 4, 5
+MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
+MODE_NAMES = {MODE_LAUNCH: "launch", MODE_GRAPH: "graph", MODE_PERSISTENT: "persistent"}
 
 # every entry point declared in include/tlsph.h
 EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_materials", "tlsph_create_particles",
            "tlsph_add_bc", "tlsph_add_notch", "tlsph_build_ref_neighbours", "tlsph_step", "tlsph_step_async",
            "tlsph_sync", "tlsph_read_state", "tlsph_write_state", "tlsph_field_bytes", "tlsph_energies", "tlsph_time",
            "tlsph_neighbours", "tlsph_permutation", "tlsph_nnz", "tlsph_get_info", "tlsph_set_option",
-           "tlsph_kernel_times", "tlsph_cell_sort_noalloc"]
+           "tlsph_kernel_times", "tlsph_cell_sort_noalloc", "tlsph_autotune"]
 NOALLOC_MAX_PARTICLES = 131072
 
 
@@ -47,6 +49,10 @@ class Material(C.Structure):
 class Info(C.Structure):
     _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("noconverge", C.c_int64),
                 ("nonfinite", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int64), ("bytes_per_step", C.c_double)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("mode", C.c_int), ("block", C.c_int), ("ms_per_step", C.c_double)]
 
 
 class TLSPHError(RuntimeError):
@@ -92,6 +98,7 @@ def load_library(path: str = LIB_PATH):
         "tlsph_set_option": (C.c_int, [P, C.c_int, C.c_int]),
         "tlsph_kernel_times": (C.c_int, [P, D, I64]),
         "tlsph_cell_sort_noalloc": (C.c_int, [C.c_int, V, C.c_int64, C.c_int, C.c_double, C.c_double, V, V, V]),
+        "tlsph_autotune": (C.c_int, [P, C.c_int, C.POINTER(Tuning), C.POINTER(Tuning)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -248,6 +255,15 @@ class TLSPH:
     def set_option(self, option: int, value: int):
         self._ck(self.lib.tlsph_set_option(self.ctx, option, value), "set_option")
 
+    def autotune(self, trial_steps=10):
+        """Time every execution mode / block size on the live problem and keep the fastest
+        (the state is restored); returns (best, all) as dicts."""
+        best = Tuning()
+        allt = (Tuning * 6)()
+        self._ck(self.lib.tlsph_autotune(self.ctx, trial_steps, C.byref(best), allt), "autotune")
+        conv = lambda t: {"mode": MODE_NAMES[t.mode], "block": t.block, "ms_per_step": t.ms_per_step}
+        return conv(best), [conv(t) for t in allt]
+
     def kernel_times(self):
         ms = np.zeros(3)
         cnt = np.zeros(3, np.int64)
@@ -274,7 +290,7 @@ def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
               stream=stream)
     t.set_materials(case.materials)
     t.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
-    for b in case.bcs:
+    for b in list(case.bcs) + list(getattr(case, "specimen_loads", [])):
         t.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
     for q in case.notches:
         t.add_notch(q)

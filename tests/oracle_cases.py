@@ -15,7 +15,7 @@ def make_oracle(case: W.Case, build=True, method=None, **kw) -> Oracle:
                gravity=case.gravity, **kw)
     o.set_materials([oracle_material(m) for m in case.materials])
     o.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
-    for b in case.bcs:
+    for b in list(case.bcs) + list(getattr(case, "specimen_loads", [])):
         o.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
     for q in case.notches:
         o.add_notch(q)
