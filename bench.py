@@ -5,9 +5,14 @@ jittered lattice (dp = 1 mm, h = 1.5 dp, Wendland C2, E = 200 GPa, nu = 0.3,
 sigma_y0 = 250 MPa, H = 1 GPa), bottom face fixed, top face pressed at 5 m/s,
 FP32 fields with FP64 displacement accumulation.  A step is one pass of the whole
 hot path (deformation gradient, J2 return map, momentum with viscosity, update,
-next step size): 2 kernels.
+next step size): 3 kernels (k_gradient, k_stress, k_pass2).
+
+Beside the headline it measures the batched form (512 independent 2D specimens in one
+autotuned launch) and the learned form (the J2 update served by a network trained on
+return-map samples of this block, against the plain step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--no-batched] [--no-surrogate] [--no-cpu]
 
 Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
 method as plainly written, test infrastructure) on a bounded sample of the
@@ -37,6 +42,8 @@ METRIC = "TL-SPH particle-steps/sec at 1M particles, % HBM roofline; surrogate v
 UNIT = "particle-steps/s"
 SHAPE = (128, 128, 64)
 FALLBACK_HBM_GBS = 6400.0
+FALLBACK_BF16_TFLOPS = 1400.0
+MLP_FLOP_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16)  # 73,728
 
 # DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel
@@ -57,6 +64,15 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    """Dense bf16 tensor peak in TFLOP/s: the sustained figure (the MLP runs inside a long step)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured (sustained)"
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
@@ -209,6 +225,82 @@ def measure_batched(args, device, stream):
             "setup_s": setup_s, "status": int(st), "mean_neighbours": info["nnz"] / case.n}
 
 
+def timed_steps(g, steps, stream, dev):
+    import torch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = g.sync(check=False)
+    return e0.elapsed_time(e1), int(st)
+
+
+def measure_surrogate(args, shape, device, stream, plain):
+    """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
+    the GPU, then the block stepped with the network in the J2 update (both scopes), against the
+    plain step.  Stress error of held-out samples is judged by the exact return map."""
+    import torch
+    from paper_2602_15149_b300 import surrogate, tlsph
+
+    dev = torch.device("cuda", device)
+    case = W.block_3d(*shape, steps=args.steps)
+    n = case.n
+    every = 20
+    points = max(1, args.steps // every)
+    t0 = time.perf_counter()
+    x, y = surrogate.generate_samples(case, n_target=args.sur_samples, steps=args.steps, every=every,
+                                      stride_elastic=16, stride_plastic=8, device=device,
+                                      stream=stream.cuda_stream, per_call=2 * args.sur_samples // points)
+    gen_s = time.perf_counter() - t0
+    m = x.shape[0]
+    perm = torch.randperm(m, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+    x, y = x.index_select(0, perm), y.index_select(0, perm)
+    ntr = int(0.95 * m)
+    net, info = surrogate.train(x[:ntr], y[:ntr], epochs=args.sur_epochs, batch=4096, lr=2e-3, device=device,
+                                time_budget_s=args.sur_train_s)
+    err = surrogate.stress_error(net, x[ntr:], y[ntr:], case.materials[0].sigma_y0)
+    del x, y
+    torch.cuda.empty_cache()
+
+    exact = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    exact.step(args.steps)
+    ue, epe = exact.read_state("U"), exact.read_state("EPSP")
+    exact.close()
+    out = {"workload": f"block_3d_j2 {'x'.join(map(str, shape))}, same as the plain step",
+           "samples": m, "train_samples": ntr, "sample_gen_s": gen_s, "training": info, "stress_error": err,
+           "network": "16-128-128-128-16 SiLU, bf16 weights, fp32 accumulation (mma.sync m16n8k16)"}
+    for name, scope in (("all", tlsph.SURROGATE_ALL), ("plastic", tlsph.SURROGATE_PLASTIC)):
+        g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+        g.set_surrogate(net, scope)
+        g.step(args.warmup)
+        ms, st = timed_steps(g, args.steps - args.warmup, stream, dev)
+        steps_t = args.steps - args.warmup
+        used, outside, elastic = g.surrogate_counts()
+        us, eps = g.read_state("U"), g.read_state("EPSP")
+        g.set_option(tlsph.OPT_KERNEL_TIMING, 1)
+        g.step(min(args.steps, 100))
+        kt = g.kernel_times()
+        g.close()
+        stress_ms = kt["stress_ms"] / max(kt["stress_launches"], 1)
+        mlp_rows = used / max(args.steps, 1)  # network rows per launch (warm-up + timed steps)
+        tflops = MLP_FLOP_PER_ROW * mlp_rows / (stress_ms * 1e-3) / 1e12
+        peak, src = bf16_peak()
+        out[name] = {"ms_per_step": ms / steps_t, "value": n * steps_t / (ms * 1e-3), "unit": UNIT,
+                     "vs_plain": (n * steps_t / (ms * 1e-3)) / plain["value"],
+                     "status": st, "rows_network": used, "rows_outside_envelope": outside,
+                     "rows_elastic_exact": elastic,
+                     "network_fraction": used / max(used + outside + elastic, 1),
+                     "stress_kernel_ms": stress_ms, "plain_stress_kernel_ms": plain["stress_ms"],
+                     "rel_l2_u_vs_exact": float(np.linalg.norm(us - ue) / np.linalg.norm(ue)),
+                     "max_abs_eps_p_diff": float(np.abs(eps - epe).max()),
+                     "tensor": {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                                "peak_source": src, "flop_per_row": MLP_FLOP_PER_ROW,
+                                "rows_per_launch": mlp_rows}}
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2602_15149_b300 import tlsph
@@ -265,6 +357,7 @@ def run_ours(args):
     peak, peak_src = peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = NCU_TRAFFIC.get(dom) if NCU_TRAFFIC.get("sources") == source_hash() else None
+    plain = {"value": n * args.steps / (ms * 1e-3), "stress_ms": kms["stress"]}
     step_bytes = sum(kb.values())
     g.close()
     torch.cuda.synchronize(dev)
@@ -288,6 +381,7 @@ def run_ours(args):
     d2h = u.nbytes + 8 * 4 * args.steps
 
     batched = measure_batched(args, local, stream) if not args.no_batched else None
+    sur = measure_surrogate(args, shape, local, stream, plain) if not args.no_surrogate else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -309,6 +403,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": launches,
         "batched": batched,
+        "surrogate": sur,
         "status": int(st),
         "cpu_baseline": cpu,
     }
@@ -327,6 +422,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
     ap.add_argument("--batch-specimens", type=int, default=512)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
+    ap.add_argument("--sur-epochs", type=int, default=4)
+    ap.add_argument("--sur-train-s", type=float, default=60.0, help="training time limit (s)")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()

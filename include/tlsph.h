@@ -247,6 +247,69 @@ typedef struct {
  * of the evolving state. */
 tlsph_status tlsph_autotune(tlsph_ctx *ctx, int trial_steps, tlsph_tuning *best, tlsph_tuning *all);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned constitutive surrogate of the J2 return map (an addition to the paper's method).
+ * Network: 16 -> 128 -> 128 -> 128 -> 16, SiLU after the hidden layers, linear output;
+ * layer l maps a row x to x W_l^T + b_l.  Rows of features (16 floats):
+ *   x = (F row-major 9, b_e^tr xx yy zz xy xz yz, eps_p^n),  b_e^tr = F C_p^-1 F^T (trial elastic
+ *       left Cauchy-Green tensor of Sec. 2.3.3 with F_p frozen),
+ *   y = (P row-major 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map: the
+ *       updated state enters as increments (zero in elastic steps, small in plastic ones), so the
+ *       network's relative error does not accumulate in the plastic state.
+ * Parameters (37,264 floats, packed): W0 (128 x 16), b0 (128), W1 (128 x 128), b1, W2 (128 x 128),
+ * b2, W3 (16 x 128), b3 (16).  Normalisation (96 floats): input mean (16), input std (16), output
+ * mean (16), output std (16), and the envelope of normalised inputs: lower (16), upper (16).
+ * Training runs on the GPU: BF16 tensor-core GEMMs (FP32 accumulation), FP32 master weights,
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8), loss = mean squared error of normalised outputs.
+ * All array arguments of the tlsph_mlp_* calls are device pointers unless marked host.
+ * --------------------------------------------------------------------------------------- */
+typedef struct tlsph_mlp tlsph_mlp;
+/* A network with zero parameters and identity normalisation; batch = rows per training step
+ * (a multiple of 16, at most 2^20).  cuda_stream NULL = a stream of its own. */
+tlsph_status tlsph_mlp_create(int device, void *cuda_stream, int batch, tlsph_mlp **out);
+void tlsph_mlp_destroy(tlsph_mlp *mlp);
+const char *tlsph_mlp_last_error(const tlsph_mlp *mlp);
+/* host arrays of 37,264 floats (resets the Adam moments) */
+tlsph_status tlsph_mlp_set_params(tlsph_mlp *mlp, const float *params);
+tlsph_status tlsph_mlp_get_params(tlsph_mlp *mlp, float *params);
+/* host arrays of 96 floats */
+tlsph_status tlsph_mlp_set_normalization(tlsph_mlp *mlp, const float norm[96]);
+tlsph_status tlsph_mlp_get_normalization(tlsph_mlp *mlp, float norm[96]);
+/* Mean / standard deviation of n rows of x and y, and the envelope [min, max] of the normalised
+ * x widened by margin times its width on each side. */
+tlsph_status tlsph_mlp_fit_normalization(tlsph_mlp *mlp, int64_t n, const float *x, const float *y, float margin);
+/* One Adam step on `batch` rows of raw x and y (normalised inside); *loss (host, may be NULL) is
+ * the batch loss before the step. */
+tlsph_status tlsph_mlp_train_step(tlsph_mlp *mlp, const float *x, const float *y, float lr, float *loss);
+/* Loss and gradient of `batch` rows without updating: grads (host, 37,264 floats, packed like the
+ * parameters) and *loss (host) may each be NULL. */
+tlsph_status tlsph_mlp_gradients(tlsph_mlp *mlp, const float *x, const float *y, float *grads, float *loss);
+/* y = network(x) for n raw rows (denormalised outputs); outside[r] (may be NULL) = 1 when row r
+ * lies outside the envelope. */
+tlsph_status tlsph_mlp_forward(tlsph_mlp *mlp, int64_t n, const float *x, float *y, int32_t *outside);
+/* Scope of the surrogate in the J2 update. */
+#define TLSPH_SURROGATE_ALL 0     /* every J2 particle inside the envelope takes the network */
+#define TLSPH_SURROGATE_PLASTIC 1 /* only those whose trial state yields (f > 0); elastic trial
+                                     states keep the exact (closed-form) update */
+/* Use the network in the J2 update of an FP32 context (NULL = exact return map only).  A J2
+ * particle without phase field whose normalised features lie inside the envelope (and, with
+ * TLSPH_SURROGATE_PLASTIC, whose trial state yields) takes P from the network and its state from
+ * the network's increments: C_p^-1 += F^-1 (b_e^{n+1} - b_e^tr) F^-T followed by the projection
+ * det C_p^-1 = 1 (eq. Fp_iso_proj), eps_p += max(0, increment).  All others keep the exact
+ * update.  The weights are copied; later changes to mlp need another call.  The step then runs
+ * in TLSPH_MODE_LAUNCH.  TLSPH_ERR_ARG for an FP64 context or an unknown scope. */
+tlsph_status tlsph_set_surrogate(tlsph_ctx *ctx, const tlsph_mlp *mlp, int scope);
+/* Cumulative since tlsph_set_surrogate: counts[0] particle updates served by the network,
+ * counts[1] J2 updates that fell outside the envelope (exact return map), counts[2] elastic
+ * trial states kept exact under TLSPH_SURROGATE_PLASTIC. */
+tlsph_status tlsph_surrogate_counts(tlsph_ctx *ctx, int64_t counts[3]);
+/* Return-map samples of the current state without advancing it: every J2 particle is a
+ * candidate, kept with probability 1/stride_elastic (elastic step) or 1/stride_plastic (plastic
+ * step) by a hash of its index and salt.  Rows go to x, y (device, cap x 16 floats each) in
+ * particle order; *count (host) = rows written (at most cap). */
+tlsph_status tlsph_j2_samples(tlsph_ctx *ctx, int stride_elastic, int stride_plastic, unsigned salt, float *x,
+                              float *y, int64_t cap, int64_t *count);
+
 /* Largest particle count accepted by tlsph_cell_sort_noalloc. */
 #define TLSPH_NOALLOC_MAX_PARTICLES 131072
 

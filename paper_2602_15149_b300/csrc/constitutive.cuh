@@ -201,30 +201,46 @@ template <typename T> struct J2Res {
     }
 };
 
+// Trial state of the J2 update: C_p^-1 held fixed, D = A - I with A = C_p^-1 C, its deviator,
+// the trial equivalent stress sigma_tr = sqrt(3/2) mu J^-2/3 |dev D| and the yield function
+// f = sigma_tr - (sigma_y0 + H eps_p) whose sign decides elastic / plastic ahead of eq. J2_residual.
+// K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.
+template <typename T> struct J2Trial {
+    M3<T> K, D, dev;
+    T trD3, q2, c_eq, sig_tr, syn, f;
+};
+template <typename T> TL_HD J2Trial<T> j2_trial(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m) {
+    J2Trial<T> t;
+    t.K.a[0] = K6[0]; t.K.a[4] = K6[1]; t.K.a[8] = K6[2];
+    t.K.a[1] = t.K.a[3] = K6[3];
+    t.K.a[2] = t.K.a[6] = K6[4];
+    t.K.a[5] = t.K.a[7] = K6[5];
+    // D = A - I = K + E2 + K E2
+    t.D = mul(t.K, k.E2);
+#pragma unroll
+    for (int q = 0; q < 9; q++) t.D.a[q] += t.K.a[q] + k.E2.a[q];
+    t.trD3 = trace(t.D) / T(3);
+    t.dev = t.D;
+    t.dev.a[0] -= t.trD3;
+    t.dev.a[4] -= t.trD3;
+    t.dev.a[8] -= t.trD3;
+    t.q2 = t_max(trace_mul(t.dev, t.dev), T(0));
+    t.c_eq = T(1.2247448713915890) * m.mu * k.Jm23;  // sqrt(3/2) mu J^-2/3
+    t.sig_tr = t.c_eq * t_sqrt(t.q2);
+    t.syn = m.sy0 + m.Hh * ep;
+    t.f = t.sig_tr - t.syn;
+    return t;
+}
+
 // J2 update.  K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.  Returns 0, or 1 if the
 // bracket / iteration did not converge (the state is still updated with the last iterate).
 template <typename T>
 TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6out[6], T &ep_out,
                                          M3<T> &S, T &dgamma) {
-    M3<T> K;
-    K.a[0] = K6[0]; K.a[4] = K6[1]; K.a[8] = K6[2];
-    K.a[1] = K.a[3] = K6[3];
-    K.a[2] = K.a[6] = K6[4];
-    K.a[5] = K.a[7] = K6[5];
-    // D = A - I = K + E2 + K E2
-    M3<T> D = mul(K, k.E2);
-#pragma unroll
-    for (int q = 0; q < 9; q++) D.a[q] += K.a[q] + k.E2.a[q];
-    T trD3 = trace(D) / T(3);
-    M3<T> dev = D;
-    dev.a[0] -= trD3;
-    dev.a[4] -= trD3;
-    dev.a[8] -= trD3;
-    T q2 = t_max(trace_mul(dev, dev), T(0));
-    T c_eq = T(1.2247448713915890) * m.mu * k.Jm23;  // sqrt(3/2) mu J^-2/3
-    T sig_tr = c_eq * t_sqrt(q2);
-    T syn = m.sy0 + m.Hh * ep;
-    T f = sig_tr - syn;
+    const J2Trial<T> tr = j2_trial(k, K6, ep, m);
+    M3<T> K = tr.K, D = tr.D, dev = tr.dev;
+    T trD3 = tr.trD3;
+    const T q2 = tr.q2, c_eq = tr.c_eq, sig_tr = tr.sig_tr, syn = tr.syn, f = tr.f;
     int status = 0;
     T dg = T(0);
 #pragma unroll

@@ -17,6 +17,7 @@
 // specimen clocks (eq. dt_criterion).
 #pragma once
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace tl {
 
@@ -106,6 +107,9 @@ __global__ void __launch_bounds__(BS, 1024 / BS) k_gradient(StepArgs<T> a) {
 }
 
 // ---------------------------------------------------------------- pass 1b: stress
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J);
+
 // Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and the
 // per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i.
 template <typename T, int DIM, bool FRAC, bool DIAG>
@@ -163,11 +167,17 @@ __device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T 
         a.psi_out[i] = psi;
         return;
     }
+    dev_write_qvm<T, DIM>(a, i, F, P, T(1) + kin.Jm1);
+}
+
+// Per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i (in-plane block).
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J) {
+    const int n = a.n;
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, n, i, A);
     M3<T> Fi;
     inverse(F, Fi);
-    const T J = T(1) + kin.Jm1;
     T Qm[DIM][DIM], Vm[DIM][DIM];
     bool ok = true;
 #pragma unroll
@@ -583,6 +593,206 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
         if (!grid_sync<T>(bar, a.flags)) return;
     }
     if (nsteps > 0 && blockIdx.x == 0) dev_finalize(a);
+}
+
+// ---------------------------------------------------------------- learned constitutive surrogate
+// Features of a J2 material point (rows of 16): x = (F row-major 9, b_e^tr xx yy zz xy xz yz,
+// eps_p^n) with the trial elastic left Cauchy-Green tensor b_e^tr = F C_p^-1 F^T, and targets
+// y = (P 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map: the updated
+// state enters as increments, which vanish in elastic steps and stay small in plastic ones,
+// so that the network's relative error does not accumulate in the state.
+__device__ __forceinline__ void sym_to6(const M3<float> &b, float *o) {
+    o[0] = b.a[0];
+    o[1] = b.a[4];
+    o[2] = b.a[8];
+    o[3] = b.a[1];
+    o[4] = b.a[2];
+    o[5] = b.a[5];
+}
+template <typename T> __device__ __forceinline__ M3<T> left_cg(const M3<T> &F, const T K6[6]) {
+    M3<T> Cp;  // C_p^-1 = I + K
+    Cp.a[0] = T(1) + K6[0]; Cp.a[4] = T(1) + K6[1]; Cp.a[8] = T(1) + K6[2];
+    Cp.a[1] = Cp.a[3] = K6[3];
+    Cp.a[2] = Cp.a[6] = K6[4];
+    Cp.a[5] = Cp.a[7] = K6[5];
+    return mul(mul(F, Cp), transpose(F));
+}
+
+// Return-map samples of the current state (after k_gradient): every J2 particle whose hash
+// falls in 1 / stride_el (elastic step) or 1 / stride_pl (plastic step).  WRITE = false marks
+// the kept particles (flag[i] = 0 / 1); WRITE = true writes them at row offset[i] (the
+// exclusive scan of the flags), in particle order.
+template <typename T, int DIM, bool WRITE>
+__global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsigned salt, int64_t *flag,
+                             const int64_t *offset, float *x, float *y, int64_t cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int n = a.n;
+    const MatT<T> m = a.mats[a.mid[i]];
+    if (m.model != 3) {
+        if (!WRITE) flag[i] = 0;
+        return;
+    }
+    M3<T> G = m3_zero<T>();
+    for (int p = 0; p < DIM; p++)
+        for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
+    const Kin<T> kin = kinematics(G);
+    T K6[6], K6o[6], epo, dg;
+    for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+    const T ep = a.ep[i];
+    M3<T> S;
+    j2_update(kin, K6, ep, m, K6o, epo, S, dg);
+    const unsigned h = (unsigned)i * 2654435761u ^ (salt * 2246822519u + 0x9e3779b9u);
+    const unsigned stride = dg > T(0) ? (unsigned)stride_pl : (unsigned)stride_el;
+    const bool keep = ((h >> 7) % stride) == 0u;
+    if (!WRITE) {
+        flag[i] = keep ? 1 : 0;
+        return;
+    }
+    if (!keep || offset[i] >= cap) return;
+    M3<T> F = G;
+    F.a[0] += T(1);
+    F.a[4] += T(1);
+    F.a[8] += T(1);
+    const M3<T> P = mul(F, S);
+    const M3<T> btr = left_cg(F, K6), bnew = left_cg(F, K6o);
+    float *xr = x + 16 * offset[i], *yr = y + 16 * offset[i];
+    M3<float> bf, bd;
+    for (int q = 0; q < 9; q++) {
+        xr[q] = (float)F.a[q];
+        yr[q] = (float)P.a[q];
+        bf.a[q] = (float)btr.a[q];
+        bd.a[q] = (float)(bnew.a[q] - btr.a[q]);
+    }
+    sym_to6(bf, xr + 9);
+    sym_to6(bd, yr + 9);
+    xr[15] = (float)ep;
+    yr[15] = (float)(epo - ep);
+}
+
+// Pass 1b with the surrogate (FP32): every block loads the network into shared memory once
+// and walks tiles of 128 particles.  A J2 particle (without phase field) whose normalised
+// features lie inside the training envelope takes P and the increments of its state from the
+// network (BF16 tensor cores, FP32 accumulation); with scope 1 only particles whose trial
+// state yields do, and elastic trial states keep the exact update.  All others take the exact
+// constitutive update.  A tile in which no particle uses the network skips the forward pass.
+// counters: [0] network, [1] J2 outside the envelope, [2] elastic trial states (scope 1).
+template <int DIM, bool FRAC>
+__global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, SurrogateDev s,
+                                                       unsigned long long *counters) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
+    mlp_load_params(sm, s);
+    __syncthreads();
+    const int n = a.n, ntiles = (n + 127) / 128;
+    int n_mlp = 0, n_out = 0, n_el = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * 128 + threadIdx.x;
+        const bool active = i < n;
+        float Gm[DIM][DIM];
+        bool use = false;
+        float xn[16];
+        if (active) {
+            for (int p = 0; p < DIM; p++)
+                for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * n + i];
+            const MatT<float> m = a.mats[a.mid[i]];
+            if (m.model == 3 && !(FRAC && m.fracture)) {
+                M3<float> G = m3_zero<float>();
+                for (int p = 0; p < DIM; p++)
+                    for (int q = 0; q < DIM; q++) G(p, q) = Gm[p][q];
+                float K6[6];
+                for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+                const float ep = a.ep[i];
+                bool plastic = true;
+                if (s.scope == 1) {
+                    const Kin<float> kin = kinematics(G);
+                    plastic = j2_trial(kin, K6, ep, m).f > 0.0f;
+                }
+                if (plastic) {
+                    M3<float> F = G;
+                    F.a[0] += 1.0f;
+                    F.a[4] += 1.0f;
+                    F.a[8] += 1.0f;
+                    const M3<float> btr = left_cg(F, K6);
+                    float xr[16];
+                    for (int q = 0; q < 9; q++) xr[q] = F.a[q];
+                    sym_to6(btr, xr + 9);
+                    xr[15] = ep;
+                    use = s.enabled != 0;
+                    for (int c = 0; c < 16; c++) {
+                        xn[c] = (xr[c] - s.in_mean[c]) / s.in_std[c];
+                        use = use && xn[c] >= s.env_lo[c] && xn[c] <= s.env_hi[c];
+                    }
+                    n_out += use ? 0 : 1;
+                } else {
+                    n_el++;
+                }
+            }
+        }
+        for (int c = 0; c < 16; c++) sm.X[threadIdx.x][c] = __float2bfloat16_rn(use ? xn[c] : 0.0f);
+        if (__syncthreads_or(use)) {  // block-uniform
+            mlp_forward_block(sm);
+            __syncthreads();
+        }
+        if (active) {
+            if (use) {
+                float yr[16];
+                for (int c = 0; c < 16; c++) yr[c] = sm.Y[threadIdx.x][c] * s.out_std[c] + s.out_mean[c];
+                M3<float> G = m3_zero<float>(), P, db;
+                for (int p = 0; p < DIM; p++)
+                    for (int q = 0; q < DIM; q++) G(p, q) = Gm[p][q];
+                for (int q = 0; q < 9; q++) P.a[q] = yr[q];
+                db.a[0] = yr[9]; db.a[4] = yr[10]; db.a[8] = yr[11];
+                db.a[1] = db.a[3] = yr[12];
+                db.a[2] = db.a[6] = yr[13];
+                db.a[5] = db.a[7] = yr[14];
+                if (DIM == 2) {  // plane strain: keep the in-plane block structure
+                    P.a[2] = P.a[5] = P.a[6] = P.a[7] = 0.0f;
+                    db.a[2] = db.a[6] = db.a[5] = db.a[7] = 0.0f;
+                }
+                M3<float> F = G;
+                F.a[0] += 1.0f;
+                F.a[4] += 1.0f;
+                F.a[8] += 1.0f;
+                // b_e^{n+1} = b_e^tr + db with b_e^tr = F C_p^-1 F^T, so C_p^-1 grows by F^-1 db F^-T
+                // (added to C_p^-1 - I directly: no cancellation), then det C_p^-1 = 1 as in
+                // eq. Fp_iso_proj
+                M3<float> Fi;
+                inverse(F, Fi);
+                const M3<float> dK = sym_part(mul(mul(Fi, db), transpose(Fi)));
+                M3<float> Kn;
+                Kn.a[0] = a.K[0 * n + i]; Kn.a[4] = a.K[1 * n + i]; Kn.a[8] = a.K[2 * n + i];
+                Kn.a[1] = Kn.a[3] = a.K[3 * n + i];
+                Kn.a[2] = Kn.a[6] = a.K[4 * n + i];
+                Kn.a[5] = Kn.a[7] = a.K[5 * n + i];
+                for (int q = 0; q < 9; q++) Kn.a[q] += dK.a[q];
+                const float fm1 = expm1f(-log1pf(det_eye_plus_m1(Kn)) / 3.0f);
+                for (int q = 0; q < 9; q++) Kn.a[q] = Kn.a[q] * (1.0f + fm1);
+                a.K[0 * n + i] = Kn.a[0] + fm1;
+                a.K[1 * n + i] = Kn.a[4] + fm1;
+                a.K[2 * n + i] = Kn.a[8] + fm1;
+                a.K[3 * n + i] = Kn.a[1];
+                a.K[4 * n + i] = Kn.a[2];
+                a.K[5 * n + i] = Kn.a[5];
+                a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
+                dev_write_qvm<float, DIM>(a, i, F, P, 1.0f + det_eye_plus_m1(G));
+                n_mlp++;
+            } else {
+                dev_stress<float, DIM, FRAC, false>(a, i, Gm);
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
+        n_out += __shfl_xor_sync(0xffffffffu, n_out, o);
+        n_el += __shfl_xor_sync(0xffffffffu, n_el, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&counters[0], (unsigned long long)n_mlp);
+        atomicAdd(&counters[1], (unsigned long long)n_out);
+        atomicAdd(&counters[2], (unsigned long long)n_el);
+    }
 }
 
 // ---------------------------------------------------------------- diagnostics

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/tlsph.h"
@@ -76,6 +77,12 @@ struct tlsph_ctx {
     void *Fd = nullptr, *Pd = nullptr, *psid = nullptr, *accd = nullptr;
     double *energy = nullptr;
     int64_t flags_seen[kNumFlags] = {0};
+    // learned constitutive surrogate attached to the context (FP32 steps only)
+    bool sur_on = false;
+    __nv_bfloat16 *sur_W = nullptr;
+    float *sur_bias = nullptr, *sur_norm = nullptr;
+    unsigned long long *sur_count = nullptr;  // network, outside the envelope, elastic trial
+    int sur_scope = 0;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
     cudaGraphExec_t gexec = nullptr;
@@ -145,6 +152,10 @@ void free_device(tlsph_ctx *c) {
     c->perm = nullptr;
     c->Fd = c->Pd = c->psid = c->accd = nullptr;
     c->bar = nullptr;
+    c->sur_W = nullptr;
+    c->sur_bias = c->sur_norm = nullptr;
+    c->sur_count = nullptr;
+    c->sur_on = false;
     c->built = false;
 }
 
@@ -620,6 +631,37 @@ void collect_timing(tlsph_ctx *c) {
     c->ev_next = 0;
 }
 
+SurrogateDev sur_dev(const tlsph_ctx *c) {
+    SurrogateDev d{};
+    d.W = c->sur_W;
+    d.bias = c->sur_bias;
+    d.in_mean = c->sur_norm;
+    d.in_std = c->sur_norm + 16;
+    d.out_mean = c->sur_norm + 32;
+    d.out_std = c->sur_norm + 48;
+    d.env_lo = c->sur_norm + 64;
+    d.env_hi = c->sur_norm + 80;
+    d.enabled = c->sur_on ? 1 : 0;
+    d.scope = c->sur_scope;
+    return d;
+}
+
+template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const StepArgs<float> &a) {
+    auto kern = k_stress_sur<DIM, FRAC>;
+    static bool attr_set[2][2] = {{false, false}, {false, false}};
+    if (!attr_set[DIM - 2][FRAC]) {
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
+        attr_set[DIM - 2][FRAC] = true;
+    }
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->p.device));
+    const int64_t tiles = (c->n + 127) / 128;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, tiles));
+    kern<<<grid, 128, sizeof(MlpSmem), c->stream>>>(a, sur_dev(c), c->sur_count);
+    CKL();
+    return TLSPH_OK;
+}
+
 // ---- one step as three kernel launches (gradient, stress, force-and-damage)
 template <typename T, int DIM, bool FRAC, int BS>
 tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
@@ -647,8 +689,18 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
         CKL();
         stop(1);
         start(2);
-        k_stress<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
-        CKL();
+        bool done_sur = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (c->sur_on) {
+                tlsph_status st = launch_stress_sur<DIM, FRAC>(c, a);
+                if (st != TLSPH_OK) return st;
+                done_sur = true;
+            }
+        }
+        if (!done_sur) {
+            k_stress<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
+            CKL();
+        }
         stop(2);
         start(0);
         if (c->has_visc) k_pass2<T, DIM, FRAC, true, BS><<<nb, BS, 0, c->stream>>>(a);
@@ -1533,3 +1585,419 @@ extern "C" tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, i
     cudaSetDevice(prev);
     return st;
 }
+
+
+// ===================================================================== learned constitutive surrogate
+struct tlsph_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int batch = 0;
+    std::string err;
+    std::vector<void *> allocs;
+    float *P = nullptr, *G = nullptr, *m = nullptr, *v = nullptr;  // master parameters, gradient, Adam moments
+    __nv_bfloat16 *Wb = nullptr, *W1T = nullptr, *W2T = nullptr, *W3T = nullptr;
+    float *biasc = nullptr, *norm = nullptr;
+    __nv_bfloat16 *Xb, *A0, *A1, *A2, *dZb, *dZT, *AT, *XbT, *doutb, *doutT;
+    float *Yn, *Z0, *Z1, *Z2, *out, *dout, *dA, *dZf, *loss;
+    double *stat_d;
+    float *stat_f;
+    int64_t t = 0;
+};
+
+namespace {
+
+tlsph_status mfail(tlsph_mlp *m, tlsph_status st, const char *msg) {
+    if (m) m->err = msg;
+    return st;
+}
+#define MK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return mfail(m, TLSPH_ERR_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P> tlsph_status malloc_m(tlsph_mlp *m, P **ptr, size_t bytes) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return mfail(m, TLSPH_ERR_OOM, "cudaMalloc");
+    }
+    m->allocs.push_back(q);
+    *ptr = reinterpret_cast<P *>(q);
+    return TLSPH_OK;
+}
+#define MA(ptr, bytes)                                     \
+    do {                                                   \
+        tlsph_status s_ = malloc_m(m, &(ptr), (bytes));    \
+        if (s_ != TLSPH_OK) return s_;                     \
+    } while (0)
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// refresh the bf16 weights, their transposes and the contiguous biases from the master copy
+tlsph_status mlp_refresh(tlsph_mlp *m) {
+    cudaStream_t s = m->stream;
+    k_f32_to_bf16<<<nblk(kHid * kIn), 256, 0, s>>>(kHid * kIn, m->P + kOffW0, m->Wb);
+    k_f32_to_bf16<<<nblk(kHid * kHid), 256, 0, s>>>(kHid * kHid, m->P + kOffW1, m->Wb + kHid * kIn);
+    k_f32_to_bf16<<<nblk(kHid * kHid), 256, 0, s>>>(kHid * kHid, m->P + kOffW2, m->Wb + kHid * kIn + kHid * kHid);
+    k_f32_to_bf16<<<nblk(kOut * kHid), 256, 0, s>>>(kOut * kHid, m->P + kOffW3,
+                                                   m->Wb + kHid * kIn + 2 * kHid * kHid);
+    const dim3 tb(32, 8);
+    k_transpose_bf16<<<dim3(kHid / 32, kHid / 32), tb, 0, s>>>(kHid, kHid, m->Wb + kHid * kIn, m->W1T);
+    k_transpose_bf16<<<dim3(kHid / 32, kHid / 32), tb, 0, s>>>(kHid, kHid, m->Wb + kHid * kIn + kHid * kHid, m->W2T);
+    k_transpose_bf16<<<dim3(kHid / 32, 1), tb, 0, s>>>(kOut, kHid, m->Wb + kHid * kIn + 2 * kHid * kHid, m->W3T);
+    MK(cudaMemcpyAsync(m->biasc, m->P + kOffB0, kHid * 4, cudaMemcpyDeviceToDevice, s));
+    MK(cudaMemcpyAsync(m->biasc + kHid, m->P + kOffB1, kHid * 4, cudaMemcpyDeviceToDevice, s));
+    MK(cudaMemcpyAsync(m->biasc + 2 * kHid, m->P + kOffB2, kHid * 4, cudaMemcpyDeviceToDevice, s));
+    MK(cudaMemcpyAsync(m->biasc + 3 * kHid, m->P + kOffB3, kOut * 4, cudaMemcpyDeviceToDevice, s));
+    MK(cudaGetLastError());
+    return TLSPH_OK;
+}
+
+template <int EPI>
+void gemm(tlsph_mlp *m, int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
+          float *C, __nv_bfloat16 *Aout) {
+    const int warps = (M / 16) * ((N + 31) / 32);
+    k_gemm_bf16<EPI><<<(unsigned)((warps + 3) / 4), 128, 0, m->stream>>>(M, N, K, A, B, bias, C, Aout);
+}
+void transpose(tlsph_mlp *m, int rows, int cols, const __nv_bfloat16 *in, __nv_bfloat16 *out) {
+    k_transpose_bf16<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, m->stream>>>(rows, cols, in, out);
+}
+
+// forward + backward of one batch of raw rows; gradients into m->G, loss into m->loss
+tlsph_status mlp_fwd_bwd(tlsph_mlp *m, const float *x, const float *y) {
+    const int B = m->batch;
+    cudaStream_t s = m->stream;
+    const float *nm = m->norm;
+    k_normalize<<<nblk((int64_t)B * 16), 256, 0, s>>>(B, x, nm, nm + 16, nullptr, m->Xb);
+    k_normalize<<<nblk((int64_t)B * 16), 256, 0, s>>>(B, y, nm + 32, nm + 48, m->Yn, nullptr);
+    const __nv_bfloat16 *W0 = m->Wb, *W1 = m->Wb + kHid * kIn, *W2 = W1 + kHid * kHid, *W3 = W2 + kHid * kHid;
+    gemm<1>(m, B, kHid, kIn, m->Xb, W0, m->biasc, m->Z0, m->A0);
+    gemm<1>(m, B, kHid, kHid, m->A0, W1, m->biasc + kHid, m->Z1, m->A1);
+    gemm<1>(m, B, kHid, kHid, m->A1, W2, m->biasc + 2 * kHid, m->Z2, m->A2);
+    gemm<0>(m, B, kOut, kHid, m->A2, W3, m->biasc + 3 * kHid, m->out, nullptr);
+    MK(cudaMemsetAsync(m->loss, 0, 4, s));
+    k_mse_grad<<<nblk((int64_t)B * kOut), 256, 0, s>>>((int64_t)B * kOut, m->out, m->Yn, m->dout, m->doutb, m->loss);
+    // layer 3
+    transpose(m, B, kOut, m->doutb, m->doutT);
+    transpose(m, B, kHid, m->A2, m->AT);
+    gemm<0>(m, kOut, kHid, B, m->doutT, m->AT, nullptr, m->G + kOffW3, nullptr);
+    k_colsum<<<kOut, 256, 0, s>>>(B, kOut, m->dout, m->G + kOffB3);
+    gemm<0>(m, B, kHid, kOut, m->doutb, m->W3T, nullptr, m->dA, nullptr);
+    // layers 2, 1, 0
+    const float *Zs[3] = {m->Z0, m->Z1, m->Z2};
+    const __nv_bfloat16 *Ain[3] = {m->Xb, m->A0, m->A1};
+    const __nv_bfloat16 *WT[3] = {nullptr, m->W1T, m->W2T};
+    const int offW[3] = {kOffW0, kOffW1, kOffW2}, offB[3] = {kOffB0, kOffB1, kOffB2}, nin[3] = {kIn, kHid, kHid};
+    for (int l = 2; l >= 0; l--) {
+        k_silu_back_f32<<<nblk((int64_t)B * kHid), 256, 0, s>>>((int64_t)B * kHid, m->dA, Zs[l], m->dZf);
+        k_f32_to_bf16<<<nblk((int64_t)B * kHid), 256, 0, s>>>((int64_t)B * kHid, m->dZf, m->dZb);
+        transpose(m, B, kHid, m->dZb, m->dZT);
+        transpose(m, B, nin[l], Ain[l], l == 0 ? m->XbT : m->AT);
+        gemm<0>(m, kHid, nin[l], B, m->dZT, l == 0 ? m->XbT : m->AT, nullptr, m->G + offW[l], nullptr);
+        k_colsum<<<kHid, 256, 0, s>>>(B, kHid, m->dZf, m->G + offB[l]);
+        if (l > 0) gemm<0>(m, B, kHid, kHid, m->dZb, WT[l], nullptr, m->dA, nullptr);
+    }
+    MK(cudaGetLastError());
+    return TLSPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tlsph_status tlsph_mlp_create(int device, void *cuda_stream, int batch, tlsph_mlp **out) {
+    if (!out) return TLSPH_ERR_ARG;
+    *out = nullptr;
+    if (batch < 16 || batch % 16 || batch > (1 << 20)) return TLSPH_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return TLSPH_ERR_CUDA;
+    }
+    tlsph_mlp *m = new tlsph_mlp();
+    m->device = device;
+    m->batch = batch;
+    if (cuda_stream) m->stream = (cudaStream_t)cuda_stream;
+    else if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) == cudaSuccess) m->own_stream = true;
+    const size_t B = (size_t)batch;
+    tlsph_status st = TLSPH_OK;
+#define MAX(ptr, bytes)                          \
+    if (st == TLSPH_OK) st = malloc_m(m, &(ptr), (bytes));
+    MAX(m->P, kNumParams * 4) MAX(m->G, kNumParams * 4) MAX(m->m, kNumParams * 4) MAX(m->v, kNumParams * 4)
+    MAX(m->Wb, kNumWeights * 2) MAX(m->W1T, kHid * kHid * 2) MAX(m->W2T, kHid * kHid * 2) MAX(m->W3T, kHid * kOut * 2)
+    MAX(m->biasc, (3 * kHid + kOut) * 4) MAX(m->norm, 96 * 4)
+    MAX(m->Xb, B * kIn * 2) MAX(m->A0, B * kHid * 2) MAX(m->A1, B * kHid * 2) MAX(m->A2, B * kHid * 2)
+    MAX(m->dZb, B * kHid * 2) MAX(m->dZT, B * kHid * 2) MAX(m->AT, B * kHid * 2) MAX(m->XbT, B * kIn * 2)
+    MAX(m->doutb, B * kOut * 2) MAX(m->doutT, B * kOut * 2)
+    MAX(m->Yn, B * kOut * 4) MAX(m->Z0, B * kHid * 4) MAX(m->Z1, B * kHid * 4) MAX(m->Z2, B * kHid * 4)
+    MAX(m->out, B * kOut * 4) MAX(m->dout, B * kOut * 4) MAX(m->dA, B * kHid * 4) MAX(m->dZf, B * kHid * 4)
+    MAX(m->loss, 4) MAX(m->stat_d, 64 * 8) MAX(m->stat_f, 64 * 4)
+#undef MAX
+    if (st != TLSPH_OK) {
+        tlsph_mlp_destroy(m);
+        return st;
+    }
+    cudaMemsetAsync(m->P, 0, kNumParams * 4, m->stream);
+    cudaMemsetAsync(m->m, 0, kNumParams * 4, m->stream);
+    cudaMemsetAsync(m->v, 0, kNumParams * 4, m->stream);
+    std::vector<float> nrm(96, 0.0f);
+    for (int c = 0; c < 16; c++) {
+        nrm[16 + c] = 1.0f;
+        nrm[48 + c] = 1.0f;
+        nrm[64 + c] = -INFINITY;
+        nrm[80 + c] = INFINITY;
+    }
+    cudaMemcpyAsync(m->norm, nrm.data(), 96 * 4, cudaMemcpyHostToDevice, m->stream);
+    st = mlp_refresh(m);
+    if (st == TLSPH_OK && cudaStreamSynchronize(m->stream) != cudaSuccess) st = TLSPH_ERR_CUDA;
+    if (st != TLSPH_OK) {
+        tlsph_mlp_destroy(m);
+        return st;
+    }
+    *out = m;
+    return TLSPH_OK;
+}
+
+void tlsph_mlp_destroy(tlsph_mlp *m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (void *q : m->allocs) cudaFree(q);
+    if (m->own_stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+const char *tlsph_mlp_last_error(const tlsph_mlp *m) { return m ? m->err.c_str() : "null network"; }
+
+tlsph_status tlsph_mlp_set_params(tlsph_mlp *m, const float *params) {
+    if (!m || !params) return TLSPH_ERR_ARG;
+    MK(cudaMemcpyAsync(m->P, params, kNumParams * 4, cudaMemcpyHostToDevice, m->stream));
+    MK(cudaMemsetAsync(m->m, 0, kNumParams * 4, m->stream));
+    MK(cudaMemsetAsync(m->v, 0, kNumParams * 4, m->stream));
+    m->t = 0;
+    tlsph_status st = mlp_refresh(m);
+    if (st != TLSPH_OK) return st;
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_get_params(tlsph_mlp *m, float *params) {
+    if (!m || !params) return TLSPH_ERR_ARG;
+    MK(cudaMemcpyAsync(params, m->P, kNumParams * 4, cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_set_normalization(tlsph_mlp *m, const float norm[96]) {
+    if (!m || !norm) return TLSPH_ERR_ARG;
+    for (int c = 0; c < 16; c++)
+        if (!(norm[16 + c] > 0.0f) || !(norm[48 + c] > 0.0f)) return mfail(m, TLSPH_ERR_ARG, "std must be > 0");
+    MK(cudaMemcpyAsync(m->norm, norm, 96 * 4, cudaMemcpyHostToDevice, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_get_normalization(tlsph_mlp *m, float norm[96]) {
+    if (!m || !norm) return TLSPH_ERR_ARG;
+    MK(cudaMemcpyAsync(norm, m->norm, 96 * 4, cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_fit_normalization(tlsph_mlp *m, int64_t n, const float *x, const float *y, float margin) {
+    if (!m || !x || !y || n < 2 || !(margin >= 0.0f)) return TLSPH_ERR_ARG;
+    cudaStream_t s = m->stream;
+    float st_h[6][16];
+    double mean[2][16], sd[2][16];
+    for (int which = 0; which < 2; which++) {
+        MK(cudaMemsetAsync(m->stat_d, 0, 32 * 8, s));
+        std::vector<float> init(32);
+        for (int c = 0; c < 16; c++) {
+            init[c] = INFINITY;
+            init[16 + c] = -INFINITY;
+        }
+        // the ordered-int encoding of the min / max starts from +inf / -inf
+        std::vector<int> enc(32);
+        for (int c = 0; c < 32; c++) {
+            int b;
+            memcpy(&b, &init[c], 4);
+            enc[c] = b < 0 ? (int)(0x80000000u - (unsigned)b) : b;
+        }
+        MK(cudaMemcpyAsync(m->stat_f, enc.data(), 32 * 4, cudaMemcpyHostToDevice, s));
+        k_col_stats<<<dim3(64, 16), 256, 0, s>>>(n, which ? y : x, m->stat_d, m->stat_d + 16, m->stat_f,
+                                                  m->stat_f + 16);
+        MK(cudaGetLastError());
+        double sums[32];
+        int mm[32];
+        MK(cudaMemcpyAsync(sums, m->stat_d, 32 * 8, cudaMemcpyDeviceToHost, s));
+        MK(cudaMemcpyAsync(mm, m->stat_f, 32 * 4, cudaMemcpyDeviceToHost, s));
+        MK(cudaStreamSynchronize(s));
+        for (int c = 0; c < 16; c++) {
+            const double mu = sums[c] / (double)n;
+            double var = sums[16 + c] / (double)n - mu * mu;
+            if (var < 0.0) var = 0.0;
+            double sdev = sqrt(var);
+            if (!(sdev > 1e-12 * std::max(1.0, fabs(mu)))) sdev = std::max(1.0, fabs(mu)) * 1e-6;
+            mean[which][c] = mu;
+            sd[which][c] = sdev;
+            if (which == 0) {
+                float lo, hi;
+                int a = mm[c], b = mm[16 + c];
+                if (a < 0) a = (int)(0x80000000u - (unsigned)a);
+                if (b < 0) b = (int)(0x80000000u - (unsigned)b);
+                memcpy(&lo, &a, 4);
+                memcpy(&hi, &b, 4);
+                const double nlo = (lo - mu) / sdev, nhi = (hi - mu) / sdev, w = nhi - nlo;
+                st_h[4][c] = (float)(nlo - margin * w);
+                st_h[5][c] = (float)(nhi + margin * w);
+            }
+        }
+    }
+    for (int c = 0; c < 16; c++) {
+        st_h[0][c] = (float)mean[0][c];
+        st_h[1][c] = (float)sd[0][c];
+        st_h[2][c] = (float)mean[1][c];
+        st_h[3][c] = (float)sd[1][c];
+    }
+    MK(cudaMemcpyAsync(m->norm, st_h, 96 * 4, cudaMemcpyHostToDevice, s));
+    MK(cudaStreamSynchronize(s));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_gradients(tlsph_mlp *m, const float *x, const float *y, float *grads, float *loss) {
+    if (!m || !x || !y) return TLSPH_ERR_ARG;
+    tlsph_status st = mlp_fwd_bwd(m, x, y);
+    if (st != TLSPH_OK) return st;
+    if (grads) MK(cudaMemcpyAsync(grads, m->G, kNumParams * 4, cudaMemcpyDeviceToHost, m->stream));
+    if (loss) MK(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_train_step(tlsph_mlp *m, const float *x, const float *y, float lr, float *loss) {
+    if (!m || !x || !y || !(lr > 0.0f)) return TLSPH_ERR_ARG;
+    tlsph_status st = mlp_fwd_bwd(m, x, y);
+    if (st != TLSPH_OK) return st;
+    m->t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)m->t), c2 = 1.0f - powf(b2, (float)m->t);
+    k_adam<<<nblk(kNumParams), 256, 0, m->stream>>>(kNumParams, m->P, m->G, m->m, m->v, lr, b1, b2, 1e-8f, c1, c2);
+    MK(cudaGetLastError());
+    st = mlp_refresh(m);
+    if (st != TLSPH_OK) return st;
+    if (loss) {
+        MK(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
+        MK(cudaStreamSynchronize(m->stream));
+    }
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y, int32_t *outside) {
+    if (!m || !x || !y || n < 1) return TLSPH_ERR_ARG;
+    SurrogateDev d{};
+    d.W = m->Wb;
+    d.bias = m->biasc;
+    d.in_mean = m->norm;
+    d.in_std = m->norm + 16;
+    d.out_mean = m->norm + 32;
+    d.out_std = m->norm + 48;
+    d.env_lo = m->norm + 64;
+    d.env_hi = m->norm + 80;
+    d.enabled = 1;
+    static bool attr = false;
+    if (!attr) {
+        MK(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
+        attr = true;
+    }
+    k_mlp_forward<<<(unsigned)((n + 127) / 128), 128, sizeof(MlpSmem), m->stream>>>(n, x, y, d, outside);
+    MK(cudaGetLastError());
+    MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before set_surrogate");
+    if (!m) {
+        c->sur_on = false;
+        return TLSPH_OK;
+    }
+    if (scope != TLSPH_SURROGATE_ALL && scope != TLSPH_SURROGATE_PLASTIC)
+        return fail(c, TLSPH_ERR_ARG, "unknown surrogate scope %d", scope);
+    if (c->p.precision != TLSPH_FP32_U64) return fail(c, TLSPH_ERR_ARG, "the surrogate runs in the FP32 step only");
+    if (!c->sur_W) {
+        DA(c->sur_W, kNumWeights * 2);
+        DA(c->sur_bias, (3 * kHid + kOut) * 4);
+        DA(c->sur_norm, 96 * 4);
+        DA(c->sur_count, 3 * sizeof(unsigned long long));
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(c->sur_W, m->Wb, kNumWeights * 2, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sur_bias, m->biasc, (3 * kHid + kOut) * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sur_norm, m->norm, 96 * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(c->sur_count, 0, 3 * sizeof(unsigned long long), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->sur_on = true;
+    c->sur_scope = scope;
+    c->mode = TLSPH_MODE_LAUNCH;
+    drop_graph(c);
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_surrogate_counts(tlsph_ctx *c, int64_t counts[3]) {
+    if (!c || !counts) return TLSPH_ERR_ARG;
+    unsigned long long h[3] = {0, 0, 0};
+    if (c->sur_count) {
+        CK(cudaMemcpyAsync(h, c->sur_count, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    for (int q = 0; q < 3; q++) counts[q] = (int64_t)h[q];
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plastic, unsigned salt, float *x,
+                              float *y, int64_t cap, int64_t *count) {
+    if (!c || !x || !y || !count || cap < 0 || stride_elastic < 1 || stride_plastic < 1) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
+    const int64_t n = c->n;
+    int64_t *flag, *off;
+    size_t mark = c->allocs.size();
+    DA(flag, (n + 1) * sizeof(int64_t));
+    DA(off, (n + 1) * sizeof(int64_t));
+    CK(cudaMemsetAsync(flag + n, 0, sizeof(int64_t), c->stream));
+    const unsigned nb = blocks_for(n);
+    auto run = [&](auto tag, auto dimc) -> tlsph_status {
+        using T = decltype(tag);
+        constexpr int D = decltype(dimc)::value;
+        StepArgs<T> a = make_args<T>(c);
+        k_gradient<T, D, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        CKL();
+        k_j2_samples<T, D, false><<<nb, kThreads, 0, c->stream>>>(a, stride_elastic, stride_plastic, salt, flag,
+                                                                   nullptr, x, y, cap);
+        CKL();
+        tlsph_status st = scan_exclusive(c, n + 1, flag, off);
+        if (st != TLSPH_OK) return st;
+        k_j2_samples<T, D, true><<<nb, kThreads, 0, c->stream>>>(a, stride_elastic, stride_plastic, salt, flag, off,
+                                                                  x, y, cap);
+        CKL();
+        return TLSPH_OK;
+    };
+    tlsph_status st;
+    if (c->p.precision == TLSPH_FP64)
+        st = c->p.dim == 3 ? run(double(), std::integral_constant<int, 3>()) : run(double(), std::integral_constant<int, 2>());
+    else
+        st = c->p.dim == 3 ? run(float(), std::integral_constant<int, 3>()) : run(float(), std::integral_constant<int, 2>());
+    if (st != TLSPH_OK) return st;
+    int64_t h = 0;
+    CK(cudaMemcpyAsync(&h, off + n, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = std::min<int64_t>(h, cap);
+    while (c->allocs.size() > mark) {
+        cudaFree(c->allocs.back());
+        c->allocs.pop_back();
+    }
+    return TLSPH_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,13 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_add_bc", "tlsph_add_notch", "tlsph_build_ref_neighbours", "tlsph_step", "tlsph_step_async",
            "tlsph_sync", "tlsph_read_state", "tlsph_write_state", "tlsph_field_bytes", "tlsph_energies", "tlsph_time",
            "tlsph_neighbours", "tlsph_permutation", "tlsph_nnz", "tlsph_get_info", "tlsph_set_option",
-           "tlsph_kernel_times", "tlsph_cell_sort_noalloc", "tlsph_autotune"]
+           "tlsph_kernel_times", "tlsph_cell_sort_noalloc", "tlsph_autotune", "tlsph_mlp_create",
+           "tlsph_mlp_destroy", "tlsph_mlp_last_error", "tlsph_mlp_set_params", "tlsph_mlp_get_params",
+           "tlsph_mlp_set_normalization", "tlsph_mlp_get_normalization", "tlsph_mlp_fit_normalization",
+           "tlsph_mlp_train_step", "tlsph_mlp_gradients", "tlsph_mlp_forward", "tlsph_set_surrogate",
+           "tlsph_surrogate_counts", "tlsph_j2_samples"]
+MLP_NUM_PARAMS = 37264
+SURROGATE_ALL, SURROGATE_PLASTIC = 0, 1
 NOALLOC_MAX_PARTICLES = 131072
 
 
@@ -99,6 +105,20 @@ def load_library(path: str = LIB_PATH):
         "tlsph_kernel_times": (C.c_int, [P, D, I64]),
         "tlsph_cell_sort_noalloc": (C.c_int, [C.c_int, V, C.c_int64, C.c_int, C.c_double, C.c_double, V, V, V]),
         "tlsph_autotune": (C.c_int, [P, C.c_int, C.POINTER(Tuning), C.POINTER(Tuning)]),
+        "tlsph_mlp_create": (C.c_int, [C.c_int, V, C.c_int, C.POINTER(C.c_void_p)]),
+        "tlsph_mlp_destroy": (None, [P]),
+        "tlsph_mlp_last_error": (C.c_char_p, [P]),
+        "tlsph_mlp_set_params": (C.c_int, [P, V]),
+        "tlsph_mlp_get_params": (C.c_int, [P, V]),
+        "tlsph_mlp_set_normalization": (C.c_int, [P, V]),
+        "tlsph_mlp_get_normalization": (C.c_int, [P, V]),
+        "tlsph_mlp_fit_normalization": (C.c_int, [P, C.c_int64, V, V, C.c_float]),
+        "tlsph_mlp_train_step": (C.c_int, [P, V, V, C.c_float, C.POINTER(C.c_float)]),
+        "tlsph_mlp_gradients": (C.c_int, [P, V, V, V, C.POINTER(C.c_float)]),
+        "tlsph_mlp_forward": (C.c_int, [P, C.c_int64, V, V, V]),
+        "tlsph_set_surrogate": (C.c_int, [P, P, C.c_int]),
+        "tlsph_surrogate_counts": (C.c_int, [P, I64]),
+        "tlsph_j2_samples": (C.c_int, [P, C.c_int, C.c_int, C.c_uint, V, V, C.c_int64, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -264,6 +284,25 @@ class TLSPH:
         conv = lambda t: {"mode": MODE_NAMES[t.mode], "block": t.block, "ms_per_step": t.ms_per_step}
         return conv(best), [conv(t) for t in allt]
 
+    def set_surrogate(self, mlp, scope=None):
+        """Attach a network (None detaches); scope SURROGATE_ALL (default) or SURROGATE_PLASTIC."""
+        scope = SURROGATE_ALL if scope is None else scope
+        self._ck(self.lib.tlsph_set_surrogate(self.ctx, None if mlp is None else mlp.h, scope), "set_surrogate")
+
+    def surrogate_counts(self):
+        """(network, outside the envelope, elastic trial kept exact), cumulative."""
+        c = np.zeros(3, np.int64)
+        self._ck(self.lib.tlsph_surrogate_counts(self.ctx, c.ctypes.data_as(C.POINTER(C.c_int64))), "surrogate_counts")
+        return int(c[0]), int(c[1]), int(c[2])
+
+    def j2_samples(self, x, y, stride_elastic=1, stride_plastic=1, salt=0):
+        """Return-map samples of the current state into torch CUDA float32 tensors x, y (cap x 16);
+        returns the number of rows written."""
+        cnt = np.zeros(1, np.int64)
+        self._ck(self.lib.tlsph_j2_samples(self.ctx, stride_elastic, stride_plastic, salt, x.data_ptr(), y.data_ptr(),
+                                           int(x.shape[0]), cnt.ctypes.data_as(C.POINTER(C.c_int64))), "j2_samples")
+        return int(cnt[0])
+
     def kernel_times(self):
         ms = np.zeros(3)
         cnt = np.zeros(3, np.int64)
@@ -271,6 +310,86 @@ class TLSPH:
                  "kernel_times")
         return {"pass2_ms": ms[0], "pass2_launches": int(cnt[0]), "gradient_ms": ms[1],
                 "gradient_launches": int(cnt[1]), "stress_ms": ms[2], "stress_launches": int(cnt[2])}
+
+
+class MLP:
+    """The surrogate network on a CUDA device (tlsph_mlp_*); data arguments are torch CUDA tensors."""
+
+    def __init__(self, batch=4096, device=0, stream=None):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.tlsph_mlp_create(device, stream, batch, C.byref(h))
+        if st != OK:
+            raise TLSPHError(st, "tlsph_mlp_create failed")
+        self.h = h
+        self.batch = batch
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tlsph_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _ck(self, st, what):
+        if st != OK:
+            raise TLSPHError(st, f"{what}: {self.lib.tlsph_mlp_last_error(self.h).decode()}")
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, np.float32)
+        assert a.size == MLP_NUM_PARAMS
+        self._ck(self.lib.tlsph_mlp_set_params(self.h, a.ctypes.data), "set_params")
+
+    def get_params(self):
+        a = np.zeros(MLP_NUM_PARAMS, np.float32)
+        self._ck(self.lib.tlsph_mlp_get_params(self.h, a.ctypes.data), "get_params")
+        return a
+
+    def set_normalization(self, norm):
+        a = np.ascontiguousarray(norm, np.float32).reshape(96)
+        self._ck(self.lib.tlsph_mlp_set_normalization(self.h, a.ctypes.data), "set_normalization")
+
+    def get_normalization(self):
+        a = np.zeros(96, np.float32)
+        self._ck(self.lib.tlsph_mlp_get_normalization(self.h, a.ctypes.data), "get_normalization")
+        return a
+
+    def fit_normalization(self, x, y, margin=0.02):
+        self._ck(self.lib.tlsph_mlp_fit_normalization(self.h, int(x.shape[0]), x.data_ptr(), y.data_ptr(),
+                                                      float(margin)), "fit_normalization")
+
+    def train_step(self, x, y, lr):
+        loss = C.c_float()
+        self._ck(self.lib.tlsph_mlp_train_step(self.h, x.data_ptr(), y.data_ptr(), float(lr), C.byref(loss)),
+                 "train_step")
+        return loss.value
+
+    def gradients(self, x, y):
+        g = np.zeros(MLP_NUM_PARAMS, np.float32)
+        loss = C.c_float()
+        self._ck(self.lib.tlsph_mlp_gradients(self.h, x.data_ptr(), y.data_ptr(), g.ctypes.data, C.byref(loss)),
+                 "gradients")
+        return loss.value, g
+
+    def forward(self, x, y, outside=None):
+        self._ck(self.lib.tlsph_mlp_forward(self.h, int(x.shape[0]), x.data_ptr(), y.data_ptr(),
+                                            None if outside is None else outside.data_ptr()), "forward")
+
+
+def pack_params(params):
+    """[(W0, b0), ..., (W3, b3)] -> the packed float32 layout of the C-ABI."""
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+
+def unpack_params(p, sizes=(16, 128, 128, 128, 16)):
+    out, off = [], 0
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        W = p[off:off + n_in * n_out].reshape(n_out, n_in)
+        off += n_in * n_out
+        b = p[off:off + n_out]
+        off += n_out
+        out.append((W, b))
+    return out
 
 
 def cell_sort_noalloc(X0, perm, h, support=2.0, specimen_id=None, device=0, stream=None) -> int:
