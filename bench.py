@@ -78,7 +78,8 @@ def bf16_peak():
 def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
     """Algorithmic HBM bytes per launch of each kernel of a step (every particle's own records
     read / written once, neighbour gathers served on chip, neighbour indices read once per
-    neighbour pass) for the library's layout.  Mirrors algorithmic_bytes() in tlsph_capi.cu."""
+    neighbour pass: 4 B per pair, the CSR definition, also when the kernels walk the stencil
+    layout) for the library's layout.  Mirrors algorithmic_bytes() in tlsph_capi.cu."""
     v4, nsym, q = 4 * ts, (6 if dim == 3 else 3), dim * dim * ts
     grad = n * (4 + 8 / 32 + 2 * v4 + nsym * ts + dim * dim * ts) + 4 * nnz
     stress = n * (dim * dim * ts + nsym * ts + 2 + q + dim * dim * ts)
@@ -86,7 +87,7 @@ def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
         stress += n * 2 * 7 * ts
     if frac:
         stress += n * (v4 + 2 * ts)
-    p2 = n * (4 + 8 / 32 + 3 * v4 + q + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4) + 4 * nnz
+    p2 = n * (4 + 8 / 32 + 4 * v4 + q + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4) + 4 * nnz  # incl. first moment S1
     if visc:
         p2 += n * dim * dim * ts
     if frac:
@@ -392,6 +393,8 @@ def run_ours(args):
         "config": {"workload": f"block_3d_j2 {'x'.join(map(str, shape))} jittered lattice, J2 plasticity, top "
                                "pressed at 5 m/s (FP32 fields, FP64 displacement)", "particles": n, "neighbour_pairs": nnz,
                    "mean_neighbours": nnz / n, "l2": "inputs larger than L2 (~1.3 GB of state), no flush",
+                   "neighbour_layout": (f"stencil ({info['stencil']} differences, 16 B row masks)"
+                                        if info["stencil"] else "SELL-32 CSR rows"),
                    "parallelism": f"replicas x{ws} (independent blocks)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,

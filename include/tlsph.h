@@ -126,6 +126,7 @@ typedef struct {
     int64_t nnz;            /* neighbour pairs (directed) */
     int64_t max_row;        /* largest neighbour count */
     double bytes_per_step;  /* algorithmic HBM bytes of one step of this configuration */
+    int64_t stencil;        /* entries of the stencil neighbour layout in use (0 = SELL-32 rows) */
 } tlsph_info;
 
 /* Create a context.  params is copied.  Errors: ERR_ARG (bad dim/h/precision),
@@ -221,10 +222,21 @@ enum {
     TLSPH_OPT_RECORD_ACC = 2,
     TLSPH_OPT_MODE = 3,         /* execution mode, value TLSPH_MODE_* (default TLSPH_MODE_LAUNCH) */
     TLSPH_OPT_BLOCK = 4,        /* threads per block: 64, 128 (default) or 256 */
-    TLSPH_OPT_BARRIER_TEST = 5  /* testing: the persistent mode's grid barrier waits for one block more than it
+    TLSPH_OPT_BARRIER_TEST = 5, /* testing: the persistent mode's grid barrier waits for one block more than it
                                    launches, so every wait runs out after about a second and tlsph_step /
                                    tlsph_sync return TLSPH_ERR_TIMEOUT (the context stays usable) */
+    TLSPH_OPT_NEIGHBOUR_LAYOUT = 6 /* value TLSPH_LAYOUT_*: how the step kernels walk the neighbour rows */
 };
+/* Neighbour layouts.  The reference setup always builds CSR rows (tlsph_neighbours) and their
+ * SELL-32 copy.  When the pair differences j - i of the cell-sorted particles take at most 128
+ * distinct values (a lattice in lattice order: one particle per fine cell, the cells filling a
+ * box), it also builds the stencil layout: the sorted differences and one bit mask per row.
+ * Both visit every row's neighbours in ascending sorted index, so they give bit-identical
+ * steps; the stencil one reads no index stream and its gathers coalesce.
+ *  TLSPH_LAYOUT_AUTO: the stencil layout when it was built (default), else SELL-32;
+ *  TLSPH_LAYOUT_CSR:  SELL-32 rows always. */
+#define TLSPH_LAYOUT_AUTO 0
+#define TLSPH_LAYOUT_CSR 1
 /* How a step is executed:
  *  TLSPH_MODE_LAUNCH:     three kernel launches per step (deformation gradient, stress, force and damage);
  *  TLSPH_MODE_GRAPH:      the same kernels replayed from a CUDA graph of two steps (fewer launch gaps);

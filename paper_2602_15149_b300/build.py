@@ -17,8 +17,11 @@ def _inputs():
 
 
 def nvcc_command(out: str = LIB, extra=()):
-    return (["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
-             "-ffp-contract=off", "-shared", "-o", out, *SOURCES] + list(extra))
+    # --fmad=false: no implicit multiply-add contraction, so a kernel's rounding does not depend
+    # on the code around it (execution modes and block sizes give bit-identical steps); the hot
+    # loops write their fused multiply-adds explicitly.
+    return (["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
+             "-Xcompiler", "-ffp-contract=off", "-shared", "-o", out, *SOURCES] + list(extra))
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:

@@ -62,7 +62,11 @@ template <typename T> struct StepArgs {
     const int64_t *slice_off;
     const int *row_len;
     const int *col;
+    const unsigned *nmask;  // stencil layout: row masks, ceil(nsten / 32) arrays of n
+    const int *soff;       // stencil differences j - i, ascending
+    int nsten;             // stencil entries; 0 = SELL-32 rows
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
+    const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) (reference configuration)
     const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, m0 in 3D)
     V4<T> *ug_next;
     const V4<T> *vs_cur;   // (vx, vy, vz, s)

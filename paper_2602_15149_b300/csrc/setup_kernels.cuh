@@ -342,4 +342,62 @@ __global__ void k_sell_pad(int64_t total, int *sell, int v) {
     if (i < total) sell[i] = v;
 }
 
+// ---------------------------------------------------------------- stencil layout
+// On a lattice in lattice order (one particle per fine cell, cells filling a box) the index
+// difference j - i of a neighbour pair takes few distinct values: the lattice offsets within
+// the support.  D = the sorted distinct differences; when |D| <= kMaxStencil every row is a
+// bit mask over D (bit s set iff (i, i + D[s]) is a pair).  A row visits D in ascending order,
+// which is the ascending column order of its CSR row: both layouts visit the same pairs in
+// the same order.  The k-th visit of 32 consecutive rows reads 32 consecutive particles.
+constexpr int kMaxStencil = 128;
+constexpr int64_t kStencilSpan = (int64_t)1 << 22;  // |j - i| the difference bitmap covers
+
+// Set bit (d + kStencilSpan) of the bitmap for every pair difference d; *far counts pairs
+// beyond the span.  The bit is read first so that repeated differences cost no atomic.
+__global__ void k_stencil_diffs(int64_t n, const int64_t *row_ptr, const int *col, unsigned *bitmap, int *far) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+        const int64_t d = (int64_t)col[k] - i;
+        if (d < -kStencilSpan || d >= kStencilSpan) {
+            atomicAdd(far, 1);
+            continue;
+        }
+        const uint64_t b = (uint64_t)(d + kStencilSpan);
+        const unsigned bit = 1u << (b & 31);
+        if (!(((volatile unsigned *)bitmap)[b >> 5] & bit)) atomicOr(&bitmap[b >> 5], bit);
+    }
+}
+
+// Row masks over D (ascending, nsten entries): words w = 0 .. ceil(nsten / 32) - 1 at
+// mask[w n + i].  A difference missing from D or a row out of ascending order counts in *bad.
+__global__ void k_stencil_mask(int64_t n, const int64_t *row_ptr, const int *col, const int *D, int nsten,
+                               unsigned *mask, int *bad) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int s = 0;
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+        const int64_t d = (int64_t)col[k] - i;
+        while (s < nsten && (int64_t)D[s] < d) s++;
+        if (s == nsten || (int64_t)D[s] != d) {
+            atomicAdd(bad, 1);
+            return;
+        }
+        const unsigned bit = 1u << (s & 31);
+        switch (s >> 5) {
+        case 0: m0 |= bit; break;
+        case 1: m1 |= bit; break;
+        case 2: m2 |= bit; break;
+        default: m3 |= bit; break;
+        }
+        s++;  // strictly ascending rows: the next pair lies further on
+    }
+    const int nw = (nsten + 31) / 32;
+    mask[i] = m0;
+    if (nw > 1) mask[n + i] = m1;
+    if (nw > 2) mask[2 * n + i] = m2;
+    if (nw > 3) mask[3 * n + i] = m3;
+}
+
 }  // namespace tl

@@ -38,14 +38,63 @@ template <typename T, int DIM> __device__ __forceinline__ void load_ahat(const T
 
 template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isfinite(x); }
 
+// Visit the neighbours j of particle i in ascending sorted index, calling pair(j, on).  Stencil
+// layout (a.nsten > 0): the warp's 32 consecutive rows walk the stencil differences together
+// and row i takes the entries its mask keeps, so the k-th reads of the warp are consecutive
+// particles.  An entry the mask drops comes as pair(i, false): the body still runs (no branch,
+// so the unrolled loop can issue the loads of several entries together) and must add exact
+// zeros.  SELL-32 layout otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
+template <int UNROLL = 4, typename T, typename Pair>
+__device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, Pair &&pair) {
+    if (a.nsten > 0) {
+        for (int s0 = 0; s0 < a.nsten; s0 += 32) {
+            const unsigned m = __ldg(a.nmask + (int64_t)(s0 >> 5) * a.n + i);
+            const int lim = min(32, a.nsten - s0);
+            const int *off = a.soff + s0;
+#pragma unroll UNROLL
+            for (int b = 0; b < lim; b++) {
+                const bool on = (m >> b) & 1u;
+                pair(on ? i + __ldg(off + b) : i, on);
+            }
+        }
+    } else {
+        const int64_t base = a.slice_off[i >> 5] + (i & 31);
+        const int len = a.row_len[i];
+        const int *cp = a.col + base;
+#pragma unroll 4
+        for (int k = 0; k < len; k++) pair(__ldg(cp + 32 * k), true);
+    }
+}
+
+// |X_j - X_i| for the kernel weight: r2 rsqrt(r2) in FP32 (one special-function op), sqrt in FP64.
+__device__ __forceinline__ float pair_dist(float r2) { return r2 * rsqrtf(r2); }
+__device__ __forceinline__ double pair_dist(double r2) { return sqrt(r2); }
+// x / y of the viscosity term: fast division in FP32, IEEE division in FP64.
+__device__ __forceinline__ float pair_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double pair_div(double x, double y) { return x / y; }
+
+// |X_j - X_i|^2 of a pair and the Wendland C2 factor t = max(1 - r / (2h), 0) (w = t^3).
+template <typename T, int DIM> __device__ __forceinline__ T pair_r2(const T d[DIM]) {
+    T r2 = d[0] * d[0];
+    r2 = t_fma(d[1], d[1], r2);
+    if (DIM == 3) r2 = t_fma(d[DIM - 1], d[DIM - 1], r2);
+    return r2;
+}
+template <typename T> __device__ __forceinline__ T pair_t(T r2, T inv2h) {
+    return t_max(t_fma(-pair_dist(r2), inv2h, T(1)), T(0));
+}
+
+// Prefetch the SELL-32 slice of row i to L2 (no index stream in the stencil layout).
+template <typename T> __device__ __forceinline__ void prefetch_rows(const StepArgs<T> &a, int i) {
+    if (a.nsten == 0) prefetch_slice(a.col, a.slice_off, i);
+}
+
 // ---------------------------------------------------------------- pass 1a: deformation gradient
 // G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i.  Register-light so
 // that many warps keep neighbour gathers in flight.
 template <typename T, int DIM>
 __device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[DIM][DIM]) {
     const int n = a.n;
-    const int64_t base = a.slice_off[i >> 5] + (i & 31);
-    const int len = a.row_len[i];
     const V4<T> xi = a.X0V[i];
     const V4<T> ui = a.ug_cur[i];
     T B[DIM][DIM];
@@ -53,10 +102,7 @@ __device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[D
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) B[p][q] = T(0);
-    const int *cp = a.col + base;
-#pragma unroll 4
-    for (int k = 0; k < len; k++) {
-        const int j = __ldg(cp + 32 * k);
+    for_each_neighbour(a, i, [&](const int j, const bool on) {
         const V4<T> xj = ldg4(a.X0V + j);
         const V4<T> uj = ldg4(a.ug_cur + j);
         T d[DIM], du[DIM];
@@ -68,27 +114,25 @@ __device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[D
             d[DIM - 1] = xj.z - xi.z;
             du[DIM - 1] = uj.z - ui.z;
         }
-        T r2 = d[0] * d[0] + d[1] * d[1];
-        if (DIM == 3) r2 += d[DIM - 1] * d[DIM - 1];
-        const T t = t_max(T(1) - t_sqrt(r2) * a.inv2h, T(0));
+        const T t = pair_t(pair_r2<T, DIM>(d), a.inv2h);
         const T Vj = DIM == 3 ? xj.w : xj.z;
-        const T aw = t * t * t * Vj;
+        const T aw = on ? t * t * t * Vj : T(0);
 #pragma unroll
         for (int p = 0; p < DIM; p++) {
             const T c = aw * du[p];
 #pragma unroll
-            for (int q = 0; q < DIM; q++) B[p][q] += c * d[q];
+            for (int q = 0; q < DIM; q++) B[p][q] = t_fma(c, d[q], B[p][q]);
         }
-    }
+    });
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, n, i, A);
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) {
-            T s = T(0);
+            T s = B[p][0] * A[0][q];
 #pragma unroll
-            for (int r = 0; r < DIM; r++) s += B[p][r] * A[r][q];
+            for (int r = 1; r < DIM; r++) s = t_fma(B[p][r], A[r][q], s);
             Gm[p][q] = s;
         }
 }
@@ -97,13 +141,36 @@ template <typename T, int DIM, int BS>
 __global__ void __launch_bounds__(BS, 1024 / BS) k_gradient(StepArgs<T> a) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= a.n) return;
-    prefetch_slice(a.col, a.slice_off, i);
+    prefetch_rows(a, i);
     T Gm[DIM][DIM];
     dev_gradient<T, DIM>(a, i, Gm);
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) a.G[(p * DIM + q) * a.n + i] = Gm[p][q];
+}
+
+// First moment of the corrected kernel, sum_j V_j w_ij (X_j - X_i): it depends on the reference
+// configuration only, so the setup computes it once for pass 2 (same terms, same order).
+template <typename T, int DIM> __global__ void k_first_moment(StepArgs<T> a, V4<T> *S1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const V4<T> xi = a.X0V[i];
+    T s1[3] = {T(0), T(0), T(0)};
+    for_each_neighbour(a, i, [&](const int j, const bool on) {
+        const V4<T> xj = ldg4(a.X0V + j);
+        T d[DIM];
+        d[0] = xj.x - xi.x;
+        d[1] = xj.y - xi.y;
+        if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
+        const T t = pair_t(pair_r2<T, DIM>(d), a.inv2h);
+        const T w = on ? t * t * t : T(0);
+        const T Vj = DIM == 3 ? xj.w : xj.z;
+        const T aw = w * Vj;
+#pragma unroll
+        for (int p = 0; p < DIM; p++) s1[p] = t_fma(aw, d[p], s1[p]);
+    });
+    S1[i] = V4<T>{s1[0], s1[1], s1[2], T(0)};
 }
 
 // ---------------------------------------------------------------- pass 1b: stress
@@ -226,8 +293,6 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
     const int n = a.n;
     const int sp = a.spec[i];
     {
-        const int64_t base = a.slice_off[i >> 5] + (i & 31);
-        const int len = a.row_len[i];
         const V4<T> xi = a.X0V[i];
         const V4<T> ui = a.ug_cur[i];
         const V4<T> vsi = a.vs_cur[i];
@@ -236,42 +301,41 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         const T irho = T(1) / m.rho;
         const T cvis = m.beta1 * m.c0;
         T s1[DIM], s2[DIM], s3[DIM], Tl[DIM == 3 ? 6 : 3];
+        {
+            const V4<T> m1 = a.S1[i];  // sum_j V_j w d, fixed in the reference configuration
+            s1[0] = m1.x;
+            s1[1] = m1.y;
+            if (DIM == 3) s1[DIM - 1] = m1.z;
+        }
 #pragma unroll
-        for (int p = 0; p < DIM; p++) s1[p] = s2[p] = s3[p] = T(0);
+        for (int p = 0; p < DIM; p++) s2[p] = s3[p] = T(0);
 #pragma unroll
         for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
-        const int *cp = a.col + base;
-#pragma unroll 4
-        for (int k = 0; k < len; k++) {
-            const int j = __ldg(cp + 32 * k);
+        for_each_neighbour<2>(a, i, [&](const int j, const bool on) {
             const V4<T> xj = ldg4(a.X0V + j);
             T d[DIM];
             d[0] = xj.x - xi.x;
             d[1] = xj.y - xi.y;
             if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
-            T r2 = d[0] * d[0] + d[1] * d[1];
-            if (DIM == 3) r2 += d[DIM - 1] * d[DIM - 1];
-            const T t = t_max(T(1) - t_sqrt(r2) * a.inv2h, T(0));
-            const T w = t * t * t;
+            const T r2 = pair_r2<T, DIM>(d);
+            const T t = pair_t(r2, a.inv2h);
+            const T w = on ? t * t * t : T(0);
             const T Vj = DIM == 3 ? xj.w : xj.z;
             const T aw = w * Vj;
             T Qd[DIM];
             if (DIM == 3) {
                 const V4<T> q0 = ldg4(a.Qa + j), q1 = ldg4(a.Qb + j);
                 const T q2 = __ldg(a.Qc + j);
-                Qd[0] = q0.x * d[0] + q0.y * d[1] + q0.z * d[DIM - 1];
-                Qd[1] = q0.w * d[0] + q1.x * d[1] + q1.y * d[DIM - 1];
-                Qd[DIM - 1] = q1.z * d[0] + q1.w * d[1] + q2 * d[DIM - 1];
+                Qd[0] = t_fma(q0.z, d[DIM - 1], t_fma(q0.y, d[1], q0.x * d[0]));
+                Qd[1] = t_fma(q1.y, d[DIM - 1], t_fma(q1.x, d[1], q0.w * d[0]));
+                Qd[DIM - 1] = t_fma(q2, d[DIM - 1], t_fma(q1.w, d[1], q1.z * d[0]));
             } else {
                 const V4<T> q0 = ldg4(a.Qa + j);
-                Qd[0] = q0.x * d[0] + q0.y * d[1];
-                Qd[1] = q0.z * d[0] + q0.w * d[1];
+                Qd[0] = t_fma(q0.y, d[1], q0.x * d[0]);
+                Qd[1] = t_fma(q0.w, d[1], q0.z * d[0]);
             }
 #pragma unroll
-            for (int p = 0; p < DIM; p++) {
-                s1[p] += aw * d[p];
-                s2[p] += aw * Qd[p];
-            }
+            for (int p = 0; p < DIM; p++) s2[p] = t_fma(aw, Qd[p], s2[p]);
             if (VISC || frac) {
                 const V4<T> vsj = ldg4(a.vs_cur + j);
                 if (VISC) {
@@ -286,35 +350,36 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
                         dv[DIM - 1] = vsj.z - vsi.z;
                         dx[DIM - 1] = d[DIM - 1] + (uj.z - ui.z);
                     }
-                    T vx = dv[0] * dx[0] + dv[1] * dx[1];
-                    T vX = dv[0] * d[0] + dv[1] * d[1];
+                    T vx = t_fma(dv[1], dx[1], dv[0] * dx[0]);
+                    T vX = t_fma(dv[1], d[1], dv[0] * d[0]);
                     if (DIM == 3) {
-                        vx += dv[DIM - 1] * dx[DIM - 1];
-                        vX += dv[DIM - 1] * d[DIM - 1];
+                        vx = t_fma(dv[DIM - 1], dx[DIM - 1], vx);
+                        vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
                     }
-                    if (vx < T(0)) {  // pair in relative compression
-                        const T G = a.h * vX / (r2 + a.visc_eps);
-                        const T pi = (m.beta2 * G - cvis) * G * irho;
+                    if (on && vx < T(0)) {  // pair in relative compression
+                        const T G = pair_div(a.h * vX, r2 + a.visc_eps);
+                        const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
                         const T c = mj * pi * w;
 #pragma unroll
-                        for (int p = 0; p < DIM; p++) s3[p] += c * d[p];
+                        for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
                     }
                 }
                 if (frac) {
-                    const T c = (vsi.w - vsj.w) * aw / r2;
-                    Tl[0] += c * d[0] * d[0];
-                    Tl[1] += c * d[1] * d[1];
+                    const T c = on ? (vsi.w - vsj.w) * aw / r2 : T(0);
+                    const T c0 = c * d[0], c1 = c * d[1];
+                    Tl[0] = t_fma(c0, d[0], Tl[0]);
+                    Tl[1] = t_fma(c1, d[1], Tl[1]);
                     if (DIM == 3) {
-                        Tl[2] += c * d[2] * d[2];
-                        Tl[3] += c * d[0] * d[1];
-                        Tl[4] += c * d[0] * d[2];
-                        Tl[5] += c * d[1] * d[2];
+                        Tl[2] = t_fma(c * d[2], d[2], Tl[2]);
+                        Tl[3] = t_fma(c0, d[1], Tl[3]);
+                        Tl[4] = t_fma(c0, d[2], Tl[4]);
+                        Tl[5] = t_fma(c1, d[2], Tl[5]);
                     } else {
-                        Tl[2] += c * d[0] * d[1];
+                        Tl[2] = t_fma(c0, d[1], Tl[2]);
                     }
                 }
             }
-        }
+        });
         // own matrices
         T Qi[DIM][DIM];
         if (DIM == 3) {
@@ -331,12 +396,12 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         for (int p = 0; p < DIM; p++) {
             T f = s2[p];
 #pragma unroll
-            for (int q = 0; q < DIM; q++) f += Qi[p][q] * s1[q];
+            for (int q = 0; q < DIM; q++) f = t_fma(Qi[p][q], s1[q], f);
             acc[p] = f * irho;
             if (VISC) {
                 T v = T(0);
 #pragma unroll
-                for (int q = 0; q < DIM; q++) v += a.Vm[(p * DIM + q) * n + i] * s3[q];
+                for (int q = 0; q < DIM; q++) v = t_fma(a.Vm[(p * DIM + q) * n + i], s3[q], v);
                 acc[p] -= v;
             }
             acc[p] += a.grav[p];
@@ -491,7 +556,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) k_pass2(StepArgs<T> a) {
     double vmag = 0.0, amag = 0.0;
     int sp = 0;
     if (active) {
-        prefetch_slice(a.col, a.slice_off, i);
+        prefetch_rows(a, i);
         sp = a.spec[i];
         dev_pass2<T, DIM, FRAC, VISC>(a, i, vmag, amag);
     }
@@ -564,7 +629,7 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
         for (int base = blockIdx.x * BS; base < n; base += stride) {
             const int i = base + threadIdx.x;
             if (i < n) {
-                prefetch_slice(a.col, a.slice_off, i);
+                prefetch_rows(a, i);
                 T Gm[DIM][DIM];
                 dev_gradient<T, DIM>(a, i, Gm);
                 dev_stress<T, DIM, FRAC, false>(a, i, Gm);
@@ -578,7 +643,7 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
             double vmag = 0.0, amag = 0.0;
             int sp = 0;
             if (active) {
-                prefetch_slice(a.col, a.slice_off, i);
+                prefetch_rows(a, i);
                 sp = a.spec[i];
                 dev_pass2<T, DIM, FRAC, VISC>(a, i, vmag, amag);
             }

@@ -115,6 +115,10 @@ TL_HD float t_cos(float x) { return cosf(x); }
 TL_HD double t_cos(double x) { return cos(x); }
 TL_HD float t_abs(float x) { return fabsf(x); }
 TL_HD double t_abs(double x) { return fabs(x); }
+// a b + c with one rounding (the library is compiled without implicit contraction, so
+// every fused multiply-add is written out and rounds the same in every kernel)
+TL_HD float t_fma(float a, float b, float c) { return fmaf(a, b, c); }
+TL_HD double t_fma(double a, double b, double c) { return fma(a, b, c); }
 TL_HD float t_max(float a, float b) { return fmaxf(a, b); }
 TL_HD double t_max(double a, double b) { return fmax(a, b); }
 TL_HD float t_min(float a, float b) { return fminf(a, b); }

@@ -61,6 +61,11 @@ struct tlsph_ctx {
     int64_t *row_ptr = nullptr;
     int *col = nullptr, *row_len = nullptr, *sell = nullptr;
     int64_t *slice_off = nullptr;
+    int nsten = 0;                // stencil layout entries (0 = none)
+    int *soff = nullptr;          // stencil differences j - i, ascending
+    unsigned *nmask = nullptr;    // row masks over the stencil
+    int layout = TLSPH_LAYOUT_AUTO;
+    void *S1 = nullptr;  // sum_j V_j w_ij (X_j - X_i)
     void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr}, *Vm = nullptr;
     void *Qa = nullptr, *Qb = nullptr, *Qc = nullptr, *G = nullptr;
     void *Ahat = nullptr, *K = nullptr, *ep = nullptr, *H = nullptr, *sdot = nullptr;
@@ -150,6 +155,10 @@ void free_device(tlsph_ctx *c) {
     c->allocs.clear();
     c->X0d = nullptr;
     c->perm = nullptr;
+    c->S1 = nullptr;
+    c->nsten = 0;
+    c->soff = nullptr;
+    c->nmask = nullptr;
     c->Fd = c->Pd = c->psid = c->accd = nullptr;
     c->bar = nullptr;
     c->sur_W = nullptr;
@@ -247,7 +256,12 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.slice_off = c->slice_off;
     a.row_len = c->row_len;
     a.col = c->sell;
+    const bool sten = c->layout == TLSPH_LAYOUT_AUTO && c->nsten > 0;
+    a.nsten = sten ? c->nsten : 0;
+    a.soff = sten ? c->soff : nullptr;
+    a.nmask = sten ? c->nmask : nullptr;
     a.X0V = (const V4<T> *)c->X0V;
+    a.S1 = (const V4<T> *)c->S1;
     a.ug_cur = (const V4<T> *)c->ug[cur];
     a.ug_next = (V4<T> *)c->ug[nxt];
     a.vs_cur = (const V4<T> *)c->vs[cur];
@@ -295,7 +309,8 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
 }
 
 // Algorithmic HBM bytes of one step: every particle's own records read / written once,
-// neighbour gathers served on chip, neighbour indices read once per neighbour pass.
+// neighbour gathers served on chip, neighbour indices read once per neighbour pass (4 B per
+// pair, the CSR definition, whichever layout the kernels walk).
 double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
     const int d = c->p.dim;
     const double n = (double)c->n, nnz = (double)c->nnz;
@@ -304,10 +319,52 @@ double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
     double stress = n * (d * d * ts + nsym * ts + 2 + q + d * d * ts);
     if (c->has_j2) stress += n * 2 * 7 * ts;
     if (c->has_frac) stress += n * (v4 + 2 * ts);
-    double p2 = n * (4 + 8.0 / 32 + 3 * v4 + q + 2 + 4 + 2 + 2 * 8.0 * d + 2 * v4) + 4.0 * nnz;
+    double p2 = n * (4 + 8.0 / 32 + 4 * v4 + q + 2 + 4 + 2 + 2 * 8.0 * d + 2 * v4) + 4.0 * nnz;  // + first moment
     if (c->has_visc) p2 += n * d * d * ts;
     if (c->has_frac) p2 += n * (nsym * ts + 3 * ts);
     return grad + stress + p2;
+}
+
+// Stencil layout of the CSR rows (lattice inputs): the distinct pair differences j - i,
+// kept when there are at most kMaxStencil of them, and one bit mask per row.  Otherwise the
+// context keeps the SELL-32 rows only.
+tlsph_status build_stencil(tlsph_ctx *c) {
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    c->nsten = 0;
+    if (n < 1 || c->nnz < 1) return TLSPH_OK;
+    const int64_t words = 2 * kStencilSpan / 32;
+    unsigned *bitmap;
+    int *cnt;
+    DA(bitmap, words * sizeof(unsigned));
+    DA(cnt, 2 * sizeof(int));
+    CK(cudaMemsetAsync(bitmap, 0, words * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
+    k_stencil_diffs<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, bitmap, cnt);
+    CKL();
+    std::vector<unsigned> hb(words);
+    int hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hb.data(), bitmap, words * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hc[0] != 0) return TLSPH_OK;
+    std::vector<int> D;
+    for (int64_t w = 0; w < words; w++)
+        for (unsigned m = hb[w]; m; m &= m - 1) {
+            if ((int)D.size() == kMaxStencil) return TLSPH_OK;
+            D.push_back((int)(32 * w + __builtin_ctz(m) - kStencilSpan));
+        }
+    const int nw = ((int)D.size() + 31) / 32;
+    DA(c->soff, D.size() * sizeof(int));
+    DA(c->nmask, (size_t)nw * n * sizeof(unsigned));
+    CK(cudaMemcpyAsync(c->soff, D.data(), D.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_stencil_mask<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, c->soff, (int)D.size(), c->nmask,
+                                                      cnt + 1);
+    CKL();
+    CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hc[1] == 0) c->nsten = (int)D.size();
+    return TLSPH_OK;
 }
 
 template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
@@ -535,6 +592,8 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     CKL();
     k_sell_fill<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, c->slice_off, c->sell);
     CKL();
+    st = build_stencil(c);
+    if (st != TLSPH_OK) return st;
     // ---- state
     DA(c->u64, 3 * n * sizeof(double));
     CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
@@ -594,6 +653,14 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     CK(cudaMemsetAsync(c->vmax, 0, ns_ * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->amax, 0, ns_ * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->done, 0, sizeof(unsigned int), s));
+    // first moment of the corrected kernel (reference configuration)
+    DA(c->S1, n * sizeof(V4<T>));
+    {
+        const StepArgs<T> a = make_args<T>(c);
+        if (dim == 3) k_first_moment<T, 3><<<blocks_for(n), kThreads, 0, s>>>(a, (V4<T> *)c->S1);
+        else k_first_moment<T, 2><<<blocks_for(n), kThreads, 0, s>>>(a, (V4<T> *)c->S1);
+        CKL();
+    }
     int hf[kNumFlags];
     CK(cudaMemcpyAsync(hf, c->flags, sizeof hf, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1368,6 +1435,7 @@ tlsph_status tlsph_get_info(tlsph_ctx *c, tlsph_info *out) {
     out->nnz = c->built ? c->nnz : -1;
     out->max_row = c->max_row;
     out->bytes_per_step = c->bytes_per_step;
+    out->stencil = (c->layout == TLSPH_LAYOUT_AUTO) ? c->nsten : 0;
     out->noconverge = out->nonfinite = 0;
     if (c->built) {
         int hf[kNumFlags];
@@ -1408,6 +1476,12 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
     }
     if (option == TLSPH_OPT_BARRIER_TEST) {
         c->barrier_test = value != 0;
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_NEIGHBOUR_LAYOUT) {
+        if (value != TLSPH_LAYOUT_AUTO && value != TLSPH_LAYOUT_CSR) return fail(c, TLSPH_ERR_ARG, "bad layout");
+        c->layout = value;
+        drop_graph(c);
         return TLSPH_OK;
     }
     return fail(c, TLSPH_ERR_ARG, "unknown option %d", option);

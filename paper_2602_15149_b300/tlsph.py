@@ -21,7 +21,8 @@ MODEL_NH, MODEL_J2 = 2, 3
 BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "ACC": 11, "CPINV": 12,
          "STATE": 100}
-OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST = 1, 2, 3, 4, 5
+OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6
+LAYOUT_AUTO, LAYOUT_CSR = 0, 1
 MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 MODE_NAMES = {MODE_LAUNCH: "launch", MODE_GRAPH: "graph", MODE_PERSISTENT: "persistent"}
 
@@ -54,7 +55,8 @@ class Material(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("noconverge", C.c_int64),
-                ("nonfinite", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int64), ("bytes_per_step", C.c_double)]
+                ("nonfinite", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int64), ("bytes_per_step", C.c_double),
+                ("stencil", C.c_int64)]
 
 
 class Tuning(C.Structure):
