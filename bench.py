@@ -259,7 +259,7 @@ def measure_surrogate(args, shape, device, stream, plain):
     perm = torch.randperm(m, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
     x, y = x.index_select(0, perm), y.index_select(0, perm)
     ntr = int(0.95 * m)
-    net, info = surrogate.train(x[:ntr], y[:ntr], epochs=args.sur_epochs, batch=4096, lr=2e-3, device=device,
+    net, info = surrogate.train(x[:ntr], y[:ntr], epochs=args.sur_epochs, batch=2048, lr=2e-3, device=device,
                                 time_budget_s=args.sur_train_s)
     err = surrogate.stress_error(net, x[ntr:], y[ntr:], case.materials[0].sigma_y0)
     del x, y
@@ -427,8 +427,8 @@ def main():
     ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
-    ap.add_argument("--sur-epochs", type=int, default=4)
-    ap.add_argument("--sur-train-s", type=float, default=60.0, help="training time limit (s)")
+    ap.add_argument("--sur-epochs", type=int, default=10)
+    ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()

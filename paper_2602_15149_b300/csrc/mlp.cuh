@@ -19,9 +19,20 @@ constexpr int kOffW0 = 0, kOffB0 = kOffW0 + kHid * kIn, kOffW1 = kOffB0 + kHid, 
               kOffB3 = kOffW3 + kOut * kHid, kNumParams = kOffB3 + kOut;
 constexpr int kNumWeights = kHid * kIn + 2 * kHid * kHid + kOut * kHid;  // bf16 weights (no biases)
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU through the hardware tanh: sigma(z) = (1 + tanh(z / 2)) / 2, so SiLU(z) = h + h tanh(h)
+// with h = z / 2 (one special-function op; its relative error, about 2^-11, is below the bf16
+// rounding the activations get next).  Training and inference use the same functions.
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu_f(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_fast(h), h);
+}
 __device__ __forceinline__ float silu_grad_f(float z) {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
     return s * (1.0f + z * (1.0f - s));
 }
 
@@ -232,8 +243,10 @@ struct SurrogateDev {
     int scope;  // 0 every J2 particle, 1 J2 particles whose trial state yields
 };
 
-// Shared-memory layout of one block's forward pass over 128 rows.  Rows are padded (24 and
-// 136 bf16) so that the fragment loads of 8 rows x 4 words hit 32 distinct banks.
+// Shared-memory layout of one block's forward pass over 128 rows: the weights and biases, the
+// block's normalised inputs and its outputs; hidden activations stay in registers.  Rows are
+// padded (24 and 136 bf16, 48 and 272 bytes) so that the 8 row addresses of an ldmatrix
+// phase fall on distinct 16-byte bank groups.
 constexpr int kLd16 = kIn + 8, kLd128 = kHid + 8;
 struct MlpSmem {
     __nv_bfloat16 W0[kHid][kLd16];
@@ -241,9 +254,8 @@ struct MlpSmem {
     __nv_bfloat16 W2[kHid][kLd128];
     __nv_bfloat16 W3[kOut][kLd128];
     float bias[3 * kHid + kOut];
-    __nv_bfloat16 H[128][kLd128];  // activations of the block's 128 rows
-    __nv_bfloat16 X[128][kLd16];   // normalised inputs
-    float Y[128][kOut + 1];        // outputs
+    __nv_bfloat16 X[128][kLd16];  // normalised inputs
+    float Y[128][kOut + 1];       // outputs
 };
 
 __device__ __forceinline__ void mlp_load_params(MlpSmem &sm, const SurrogateDev &s) {
@@ -263,91 +275,90 @@ __device__ __forceinline__ void mlp_load_params(MlpSmem &sm, const SurrogateDev 
     for (int i = threadIdx.x; i < 3 * kHid + kOut; i += blockDim.x) sm.bias[i] = s.bias[i];
 }
 
-// One hidden layer for the warp's 16 rows [r0, r0 + 16): H[r][:] = SiLU(in[r][:] W^T + b).
-// K = 16 (input layer) or 128.  The 128 outputs are produced in two halves of 64 columns.
-template <int K, int LDIN, int LDW>
-__device__ __forceinline__ void mlp_hidden(MlpSmem &sm, const __nv_bfloat16 *in, const __nv_bfloat16 *W,
-                                           const float *bias, int r0) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float out[2][8][4];
+// Four 8 x 8 bf16 matrices from shared memory; lane l gives the address of row l % 8 of
+// matrix l / 8 and receives in r[q] the pair (row l / 4, columns 2 (l % 4), +1) of matrix q.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *p) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// B fragments of two neighbouring n8 tiles (output columns n0 .. n0 + 15) and one k16 tile
+// (input columns k0 .. k0 + 15) of W[n][k]: b[0], b[1] for columns n0 .. n0 + 7, b[2], b[3]
+// for n0 + 8 .. n0 + 15.
+__device__ __forceinline__ void load_b_pair(uint32_t b[4], const __nv_bfloat16 *W, int ldw, int n0, int k0) {
+    const int lane = threadIdx.x & 31;
+    ldmatrix_x4(b, W + (n0 + (lane & 7) + ((lane >> 4) << 3)) * ldw + k0 + ((lane >> 3) & 1) * 8);
+}
+
+// One hidden layer for a warp's 16 rows with the activations in registers: hin holds the A
+// fragments of the input (KT tiles of 16 columns), hout receives those of SiLU(in W^T + b)
+// (128 columns = 8 tiles).  The accumulator of n8 tiles 2 kk and 2 kk + 1 is, element for
+// element, the A fragment of k tile kk of the next layer.
+template <int KT>
+__device__ __forceinline__ void mlp_layer_regs(const uint32_t (&hin)[KT][4], const __nv_bfloat16 *W, int ldw,
+                                               const float *bias, uint32_t (&hout)[8][4]) {
+    const int t = threadIdx.x & 3;
+    float acc[16][4];
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
+    for (int j = 0; j < 16; j++)
 #pragma unroll
-        for (int j = 0; j < 8; j++)
+        for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 4; q++) out[half][j][q] = 0.0f;
+    for (int kk = 0; kk < KT; kk++)
 #pragma unroll
-        for (int k0 = 0; k0 < K; k0 += 16) {
-            uint32_t a[4];
-            const __nv_bfloat16 *ar0 = in + (r0 + g) * LDIN + k0 + 2 * t;
-            const __nv_bfloat16 *ar1 = in + (r0 + g + 8) * LDIN + k0 + 2 * t;
-            a[0] = *reinterpret_cast<const uint32_t *>(ar0);
-            a[1] = *reinterpret_cast<const uint32_t *>(ar1);
-            a[2] = *reinterpret_cast<const uint32_t *>(ar0 + 8);
-            a[3] = *reinterpret_cast<const uint32_t *>(ar1 + 8);
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const __nv_bfloat16 *br = W + (64 * half + 8 * j + g) * LDW + k0 + 2 * t;
-                uint32_t b[2] = {*reinterpret_cast<const uint32_t *>(br), *reinterpret_cast<const uint32_t *>(br + 8)};
-                mma_bf16_16816(out[half][j], a, b);
-            }
+        for (int jj = 0; jj < 8; jj++) {
+            uint32_t b[4];
+            load_b_pair(b, W, ldw, 16 * jj, 16 * kk);
+            mma_bf16_16816(acc[2 * jj], hin[kk], b);
+            mma_bf16_16816(acc[2 * jj + 1], hin[kk], b + 2);
         }
+#pragma unroll
+    for (int kk = 0; kk < 8; kk++) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        const float *a0 = acc[2 * kk], *a1 = acc[2 * kk + 1];
+        hout[kk][0] = pack_bf16(silu_f(a0[0] + bias[c0]), silu_f(a0[1] + bias[c0 + 1]));
+        hout[kk][1] = pack_bf16(silu_f(a0[2] + bias[c0]), silu_f(a0[3] + bias[c0 + 1]));
+        hout[kk][2] = pack_bf16(silu_f(a1[0] + bias[c1]), silu_f(a1[1] + bias[c1 + 1]));
+        hout[kk][3] = pack_bf16(silu_f(a1[2] + bias[c1]), silu_f(a1[3] + bias[c1 + 1]));
     }
-    __syncwarp();  // every read of the warp's input rows is done before they are overwritten
+}
+
+// Forward pass of rows [r0, r0 + 16) of sm.X into sm.Y by one warp.
+__device__ __forceinline__ void mlp_forward_rows(MlpSmem &sm, int r0) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t x[1][4], h1[8][4], h2[8][4];
+    ldmatrix_x4(x[0], &sm.X[r0 + (lane & 15)][(lane >> 4) * 8]);
+    mlp_layer_regs<1>(x, &sm.W0[0][0], kLd16, sm.bias, h1);
+    mlp_layer_regs<8>(h1, &sm.W1[0][0], kLd128, sm.bias + kHid, h2);
+    mlp_layer_regs<8>(h2, &sm.W2[0][0], kLd128, sm.bias + 2 * kHid, h1);
+    float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 #pragma unroll
-    for (int half = 0; half < 2; half++)
+    for (int kk = 0; kk < 8; kk++) {
+        uint32_t b[4];
+        load_b_pair(b, &sm.W3[0][0], kLd128, 0, 16 * kk);
+        mma_bf16_16816(acc[0], h1[kk], b);
+        mma_bf16_16816(acc[1], h1[kk], b + 2);
+    }
+    const float *b3 = sm.bias + 3 * kHid;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int col = 64 * half + 8 * j + 2 * t;
+    for (int j = 0; j < 2; j++)
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int row = r0 + g + 8 * h;
-                const float v0 = silu_f(out[half][j][2 * h] + bias[col]);
-                const float v1 = silu_f(out[half][j][2 * h + 1] + bias[col + 1]);
-                *reinterpret_cast<uint32_t *>(&sm.H[row][col]) = pack_bf16(v0, v1);
-            }
+        for (int h = 0; h < 2; h++) {
+            const int row = r0 + g + 8 * h, col = 8 * j + 2 * t;
+            sm.Y[row][col] = acc[j][2 * h] + b3[col];
+            sm.Y[row][col + 1] = acc[j][2 * h + 1] + b3[col + 1];
         }
-    __syncwarp();
 }
 
 // Forward pass of the block's 128 rows of sm.X into sm.Y; warp w owns rows [32 w, 32 w + 32).
 // Called by the 4 warps of a 128-thread block; every warp only touches its own rows.
 __device__ __forceinline__ void mlp_forward_block(MlpSmem &sm) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int sub = 0; sub < 2; sub++) {
-        const int r0 = 32 * w + 16 * sub;
-        mlp_hidden<kIn, kLd16, kLd16>(sm, &sm.X[0][0], &sm.W0[0][0], sm.bias, r0);
-        mlp_hidden<kHid, kLd128, kLd128>(sm, &sm.H[0][0], &sm.W1[0][0], sm.bias + kHid, r0);
-        mlp_hidden<kHid, kLd128, kLd128>(sm, &sm.H[0][0], &sm.W2[0][0], sm.bias + 2 * kHid, r0);
-        // output layer: 16 columns
-        float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-#pragma unroll
-        for (int k0 = 0; k0 < kHid; k0 += 16) {
-            uint32_t a[4];
-            const __nv_bfloat16 *ar0 = &sm.H[r0 + g][k0 + 2 * t];
-            const __nv_bfloat16 *ar1 = &sm.H[r0 + g + 8][k0 + 2 * t];
-            a[0] = *reinterpret_cast<const uint32_t *>(ar0);
-            a[1] = *reinterpret_cast<const uint32_t *>(ar1);
-            a[2] = *reinterpret_cast<const uint32_t *>(ar0 + 8);
-            a[3] = *reinterpret_cast<const uint32_t *>(ar1 + 8);
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const __nv_bfloat16 *br = &sm.W3[8 * j + g][k0 + 2 * t];
-                uint32_t b[2] = {*reinterpret_cast<const uint32_t *>(br), *reinterpret_cast<const uint32_t *>(br + 8)};
-                mma_bf16_16816(acc[j], a, b);
-            }
-        }
-        const float *b3 = sm.bias + 3 * kHid;
-#pragma unroll
-        for (int j = 0; j < 2; j++)
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int row = r0 + g + 8 * h, col = 8 * j + 2 * t;
-                sm.Y[row][col] = acc[j][2 * h] + b3[col];
-                sm.Y[row][col + 1] = acc[j][2 * h + 1] + b3[col + 1];
-            }
-        __syncwarp();
-    }
+    const int w = threadIdx.x >> 5;
+    mlp_forward_rows(sm, 32 * w);
+    mlp_forward_rows(sm, 32 * w + 16);
+    __syncwarp();
 }
 
 // Standalone forward over n rows of raw inputs (normalised / denormalised inside), 128 rows per block.

@@ -739,11 +739,11 @@ __global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsign
 // and walks tiles of 128 particles.  A J2 particle (without phase field) whose normalised
 // features lie inside the training envelope takes P and the increments of its state from the
 // network (BF16 tensor cores, FP32 accumulation); with scope 1 only particles whose trial
-// state yields do, and elastic trial states keep the exact update.  All others take the exact
-// constitutive update.  A tile in which no particle uses the network skips the forward pass.
+// state yields do.  Every other particle is marked in exact[] for k_stress_exact, which runs
+// next.  A tile in which no particle uses the network skips the forward pass.
 // counters: [0] network, [1] J2 outside the envelope, [2] elastic trial states (scope 1).
 template <int DIM, bool FRAC>
-__global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, SurrogateDev s,
+__global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, SurrogateDev s, uint8_t *exact,
                                                        unsigned long long *counters) {
     extern __shared__ __align__(16) unsigned char smraw[];
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
@@ -754,25 +754,19 @@ __global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, Surrog
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i = tile * 128 + threadIdx.x;
         const bool active = i < n;
-        float Gm[DIM][DIM];
         bool use = false;
         float xn[16];
+        M3<float> G = m3_zero<float>();
         if (active) {
             for (int p = 0; p < DIM; p++)
-                for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * n + i];
+                for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
             const MatT<float> m = a.mats[a.mid[i]];
             if (m.model == 3 && !(FRAC && m.fracture)) {
-                M3<float> G = m3_zero<float>();
-                for (int p = 0; p < DIM; p++)
-                    for (int q = 0; q < DIM; q++) G(p, q) = Gm[p][q];
                 float K6[6];
                 for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
                 const float ep = a.ep[i];
                 bool plastic = true;
-                if (s.scope == 1) {
-                    const Kin<float> kin = kinematics(G);
-                    plastic = j2_trial(kin, K6, ep, m).f > 0.0f;
-                }
+                if (s.scope == 1) plastic = j2_trial(kinematics(G), K6, ep, m).f > 0.0f;
                 if (plastic) {
                     M3<float> F = G;
                     F.a[0] += 1.0f;
@@ -793,19 +787,15 @@ __global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, Surrog
                     n_el++;
                 }
             }
+            exact[i] = use ? 0 : 1;
         }
         for (int c = 0; c < 16; c++) sm.X[threadIdx.x][c] = __float2bfloat16_rn(use ? xn[c] : 0.0f);
         if (__syncthreads_or(use)) {  // block-uniform
             mlp_forward_block(sm);
-            __syncthreads();
-        }
-        if (active) {
             if (use) {
                 float yr[16];
                 for (int c = 0; c < 16; c++) yr[c] = sm.Y[threadIdx.x][c] * s.out_std[c] + s.out_mean[c];
-                M3<float> G = m3_zero<float>(), P, db;
-                for (int p = 0; p < DIM; p++)
-                    for (int q = 0; q < DIM; q++) G(p, q) = Gm[p][q];
+                M3<float> P, db;
                 for (int q = 0; q < 9; q++) P.a[q] = yr[q];
                 db.a[0] = yr[9]; db.a[4] = yr[10]; db.a[8] = yr[11];
                 db.a[1] = db.a[3] = yr[12];
@@ -842,8 +832,6 @@ __global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, Surrog
                 a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
                 dev_write_qvm<float, DIM>(a, i, F, P, 1.0f + det_eye_plus_m1(G));
                 n_mlp++;
-            } else {
-                dev_stress<float, DIM, FRAC, false>(a, i, Gm);
             }
         }
         __syncthreads();
@@ -858,6 +846,19 @@ __global__ void __launch_bounds__(128, 1) k_stress_sur(StepArgs<float> a, Surrog
         atomicAdd(&counters[1], (unsigned long long)n_out);
         atomicAdd(&counters[2], (unsigned long long)n_el);
     }
+}
+
+// The exact constitutive update of the particles k_stress_sur left to it (exact[i] = 1).
+template <int DIM, bool FRAC, int BS>
+__global__ void __launch_bounds__(BS) k_stress_exact(StepArgs<float> a, const uint8_t *exact) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= a.n || !exact[i]) return;
+    float Gm[DIM][DIM];
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * a.n + i];
+    dev_stress<float, DIM, FRAC, false>(a, i, Gm);
 }
 
 // ---------------------------------------------------------------- diagnostics

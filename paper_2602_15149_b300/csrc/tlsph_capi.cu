@@ -87,6 +87,7 @@ struct tlsph_ctx {
     __nv_bfloat16 *sur_W = nullptr;
     float *sur_bias = nullptr, *sur_norm = nullptr;
     unsigned long long *sur_count = nullptr;  // network, outside the envelope, elastic trial
+    uint8_t *sur_exact = nullptr;             // particles left to the exact update in a step
     int sur_scope = 0;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
@@ -164,6 +165,7 @@ void free_device(tlsph_ctx *c) {
     c->sur_W = nullptr;
     c->sur_bias = c->sur_norm = nullptr;
     c->sur_count = nullptr;
+    c->sur_exact = nullptr;
     c->sur_on = false;
     c->built = false;
 }
@@ -720,11 +722,14 @@ template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
         attr_set[DIM - 2][FRAC] = true;
     }
-    int nsm = 0;
+    int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->p.device));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sizeof(MlpSmem)));
     const int64_t tiles = (c->n + 127) / 128;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, tiles));
-    kern<<<grid, 128, sizeof(MlpSmem), c->stream>>>(a, sur_dev(c), c->sur_count);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, tiles));
+    kern<<<grid, 128, sizeof(MlpSmem), c->stream>>>(a, sur_dev(c), c->sur_exact, c->sur_count);
+    CKL();
+    k_stress_exact<DIM, FRAC, kThreads><<<blocks_for(c->n), kThreads, 0, c->stream>>>(a, c->sur_exact);
     CKL();
     return TLSPH_OK;
 }
@@ -2005,6 +2010,7 @@ tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
         DA(c->sur_bias, (3 * kHid + kOut) * 4);
         DA(c->sur_norm, 96 * 4);
         DA(c->sur_count, 3 * sizeof(unsigned long long));
+        DA(c->sur_exact, c->n);
     }
     CK(cudaStreamSynchronize(m->stream));
     CK(cudaMemcpyAsync(c->sur_W, m->Wb, kNumWeights * 2, cudaMemcpyDeviceToDevice, c->stream));

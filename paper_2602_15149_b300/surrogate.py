@@ -48,7 +48,10 @@ def generate_samples(case, n_target, steps, every=20, stride_elastic=4, stride_p
 
 
 def train(x, y, epochs=10, batch=4096, lr=2e-3, lr_end=1e-5, seed=0, device=0, time_budget_s=None, log=None):
-    """Train a fresh network on (x, y) with Adam and a cosine learning-rate schedule."""
+    """Train a fresh network on (x, y) with Adam and a cosine learning-rate schedule.
+
+    With a time budget the number of epochs is cut after the first one to what fits, and the
+    schedule is stretched over the epochs that remain, so it still ends at lr_end."""
     import torch
 
     mlp = tlsph.MLP(batch=batch, device=device)
@@ -60,18 +63,22 @@ def train(x, y, epochs=10, batch=4096, lr=2e-3, lr_end=1e-5, seed=0, device=0, t
     gen = torch.Generator(device=x.device).manual_seed(seed)
     t0 = time.perf_counter()
     step, losses = 0, []
-    for ep in range(epochs):
+    ep = 0
+    while ep < epochs:
         perm = torch.randperm(n, device=x.device, generator=gen)
         xs, ys = x.index_select(0, perm), y.index_select(0, perm)
         for b in range(nb):
-            a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * step / total))
+            a = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * min(step, total) / total))
             loss = mlp.train_step(xs[b * batch:(b + 1) * batch], ys[b * batch:(b + 1) * batch], a)
             step += 1
         losses.append(loss)
+        ep += 1
+        elapsed = time.perf_counter() - t0
         if log:
-            log(f"epoch {ep}: loss {loss:.3e} ({time.perf_counter() - t0:.1f} s)")
-        if time_budget_s and time.perf_counter() - t0 > time_budget_s:
-            break
+            log(f"epoch {ep}: loss {loss:.3e} ({elapsed:.1f} s)")
+        if time_budget_s and ep == 1 and epochs > 1:
+            epochs = max(1, min(epochs, int(time_budget_s / max(elapsed, 1e-9))))
+            total = max(1, epochs * nb)
     return mlp, {"epochs": len(losses), "steps": step, "final_loss": losses[-1] if losses else None,
                  "train_s": time.perf_counter() - t0, "samples": n}
 
