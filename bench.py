@@ -173,23 +173,31 @@ def oracle_sample(seconds=15.0, shape=(32, 32, 16)):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (the method as plainly written) on the host cores.
+    Its step is one time step of a bounded sample of the workload: the same lattice recipe,
+    material and loading on a 32 x 32 x 16 block (16,384 particles), so that --steps 2000 ends
+    within a few minutes."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    res = []
-    for _ in range(args.warmup):
-        oracle_sample(seconds=1.0, shape=(16, 16, 8))
+    from tests.oracle_cases import make_oracle
+    shape = (32, 32, 16)
+    case = W.block_3d(nx=shape[0], ny=shape[1], nz=shape[2], steps=args.steps)
+    o = make_oracle(case)
+    o.step(args.warmup)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        res.append(oracle_sample(seconds=max(1.0, 60.0 / max(args.steps, 1)), shape=(32, 32, 16)))
+    o.step(args.steps)
     el = time.perf_counter() - t0
-    val = statistics.median(r["value"] for r in res)
+    val = case.n * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"block_3d_j2 {shape[0]}x{shape[1]}x{shape[2]} = {case.n} particles (same recipe as the "
+              f"128x128x64 block), {args.steps} steps after {args.warmup} warm-up steps, FP64 OpenMP")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "block_3d_j2 sample 32x32x16 of the 128x128x64 J2 block (FP64 CPU oracle)",
-                       "particles": 32 * 32 * 16},
-            "cpu_baseline": dict(res[0], value=val),
+            "config": {"workload": "block_3d_j2 128x128x64 J2 block, bounded sample 32x32x16 (FP64 CPU oracle)",
+                       "particles": case.n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -251,18 +259,18 @@ def measure_surrogate(args, shape, device, stream, plain):
     every = 20
     points = max(1, args.steps // every)
     t0 = time.perf_counter()
-    x, y = surrogate.generate_samples(case, n_target=args.sur_samples, steps=args.steps, every=every,
+    x, y, pn = surrogate.generate_samples(case, n_target=args.sur_samples, steps=args.steps, every=every,
                                       stride_elastic=16, stride_plastic=8, device=device,
                                       stream=stream.cuda_stream, per_call=2 * args.sur_samples // points)
     gen_s = time.perf_counter() - t0
     m = x.shape[0]
     perm = torch.randperm(m, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
-    x, y = x.index_select(0, perm), y.index_select(0, perm)
+    x, y, pn = x.index_select(0, perm), y.index_select(0, perm), pn.index_select(0, perm)
     ntr = int(0.95 * m)
     net, info = surrogate.train(x[:ntr], y[:ntr], epochs=args.sur_epochs, batch=2048, lr=2e-3, device=device,
                                 time_budget_s=args.sur_train_s)
-    err = surrogate.stress_error(net, x[ntr:], y[ntr:], case.materials[0].sigma_y0)
-    del x, y
+    err = surrogate.stress_error(net, x[ntr:], y[ntr:], pn[ntr:], case.materials[0].sigma_y0)
+    del x, y, pn
     torch.cuda.empty_cache()
 
     exact = tlsph.from_case(case, device=device, stream=stream.cuda_stream)

@@ -265,9 +265,11 @@ tlsph_status tlsph_autotune(tlsph_ctx *ctx, int trial_steps, tlsph_tuning *best,
  * layer l maps a row x to x W_l^T + b_l.  Rows of features (16 floats):
  *   x = (F row-major 9, b_e^tr xx yy zz xy xz yz, eps_p^n),  b_e^tr = F C_p^-1 F^T (trial elastic
  *       left Cauchy-Green tensor of Sec. 2.3.3 with F_p frozen),
- *   y = (P row-major 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map: the
- *       updated state enters as increments (zero in elastic steps, small in plastic ones), so the
- *       network's relative error does not accumulate in the plastic state.
+ *   y = (P - P^tr row-major 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map,
+ *       with the elastic predictor P^tr = tau F^-T, tau = mu dev(J^-2/3 b_e^tr) + kappa/2 (J^2 - 1) I
+ *       (the stress of the trial state, closed form in x).  Stress and state enter as plastic
+ *       corrections (zero in elastic steps, small in plastic ones), so the network's relative
+ *       error neither reaches the elastic response nor accumulates in the plastic state.
  * Parameters (37,264 floats, packed): W0 (128 x 16), b0 (128), W1 (128 x 128), b1, W2 (128 x 128),
  * b2, W3 (16 x 128), b3 (16).  Normalisation (96 floats): input mean (16), input std (16), output
  * mean (16), output std (16), and the envelope of normalised inputs: lower (16), upper (16).
@@ -305,9 +307,9 @@ tlsph_status tlsph_mlp_forward(tlsph_mlp *mlp, int64_t n, const float *x, float 
                                      states keep the exact (closed-form) update */
 /* Use the network in the J2 update of an FP32 context (NULL = exact return map only).  A J2
  * particle without phase field whose normalised features lie inside the envelope (and, with
- * TLSPH_SURROGATE_PLASTIC, whose trial state yields) takes P from the network and its state from
- * the network's increments: C_p^-1 += F^-1 (b_e^{n+1} - b_e^tr) F^-T followed by the projection
- * det C_p^-1 = 1 (eq. Fp_iso_proj), eps_p += max(0, increment).  All others keep the exact
+ * TLSPH_SURROGATE_PLASTIC, whose trial state yields) takes P = P^tr + the network's correction and
+ * its state from the network's increments: C_p^-1 += F^-1 (b_e^{n+1} - b_e^tr) F^-T followed by the
+ * projection det C_p^-1 = 1 (eq. Fp_iso_proj), eps_p += max(0, increment).  All others keep the exact
  * update.  The weights are copied; later changes to mlp need another call.  The step then runs
  * in TLSPH_MODE_LAUNCH.  TLSPH_ERR_ARG for an FP64 context or an unknown scope. */
 tlsph_status tlsph_set_surrogate(tlsph_ctx *ctx, const tlsph_mlp *mlp, int scope);
@@ -318,9 +320,10 @@ tlsph_status tlsph_surrogate_counts(tlsph_ctx *ctx, int64_t counts[3]);
 /* Return-map samples of the current state without advancing it: every J2 particle is a
  * candidate, kept with probability 1/stride_elastic (elastic step) or 1/stride_plastic (plastic
  * step) by a hash of its index and salt.  Rows go to x, y (device, cap x 16 floats each) in
- * particle order; *count (host) = rows written (at most cap). */
+ * particle order, and the Frobenius norm of the exact P of each row to pnorm (device, cap floats;
+ * may be NULL); *count (host) = rows written (at most cap). */
 tlsph_status tlsph_j2_samples(tlsph_ctx *ctx, int stride_elastic, int stride_plastic, unsigned salt, float *x,
-                              float *y, int64_t cap, int64_t *count);
+                              float *y, float *pnorm, int64_t cap, int64_t *count);
 
 /* Largest particle count accepted by tlsph_cell_sort_noalloc. */
 #define TLSPH_NOALLOC_MAX_PARTICLES 131072

@@ -232,6 +232,19 @@ template <typename T> TL_HD J2Trial<T> j2_trial(const Kin<T> &k, const T K6[6], 
     return t;
 }
 
+// Second Piola-Kirchhoff stress of the J2 model at a plastic state, from dev(D) of that state:
+// S = mu J^-2/3 (C_p^-1 - tr(A)/3 C^-1) + kappa/2 (J^2 - 1) C^-1 = mu J^-2/3 C^-1 dev(D)^T + ...
+// With the trial state (C_p^-1 of the last step) it is the elastic predictor.
+template <typename T> TL_HD M3<T> j2_stress(const Kin<T> &k, const M3<T> &dev, const MatT<T> &m) {
+    const M3<T> Siso = sym_part(mul(k.Ci, transpose(dev)));
+    const T fi = m.mu * k.Jm23;
+    const T fv = T(0.5) * m.kappa * k.Jm1 * (k.Jm1 + T(2));
+    M3<T> S;
+#pragma unroll
+    for (int q = 0; q < 9; q++) S.a[q] = fi * Siso.a[q] + fv * k.Ci.a[q];
+    return S;
+}
+
 // J2 update.  K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.  Returns 0, or 1 if the
 // bracket / iteration did not converge (the state is still updated with the last iterate).
 template <typename T>
@@ -329,12 +342,7 @@ TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6
     }
     ep_out = ep + dg;
     dgamma = dg;
-    // S = mu J^-2/3 (C_p^-1 - tr(A)/3 C^-1) + kappa/2 (J^2 - 1) C^-1 = mu J^-2/3 C^-1 dev(D)^T + ...
-    M3<T> Siso = sym_part(mul(k.Ci, transpose(dev)));
-    T fi = m.mu * k.Jm23;
-    T fv = T(0.5) * m.kappa * k.Jm1 * (k.Jm1 + T(2));
-#pragma unroll
-    for (int q = 0; q < 9; q++) S.a[q] = fi * Siso.a[q] + fv * k.Ci.a[q];
+    S = j2_stress(k, dev, m);
     return status;
 }
 

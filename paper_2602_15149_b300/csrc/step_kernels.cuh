@@ -663,9 +663,11 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
 // ---------------------------------------------------------------- learned constitutive surrogate
 // Features of a J2 material point (rows of 16): x = (F row-major 9, b_e^tr xx yy zz xy xz yz,
 // eps_p^n) with the trial elastic left Cauchy-Green tensor b_e^tr = F C_p^-1 F^T, and targets
-// y = (P 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map: the updated
-// state enters as increments, which vanish in elastic steps and stay small in plastic ones,
-// so that the network's relative error does not accumulate in the state.
+// y = (P - P^tr 9, b_e^{n+1} - b_e^tr 6, eps_p^{n+1} - eps_p^n) of the exact return map, where
+// P^tr = F S(C_p^-1 of the last step) is the elastic predictor (closed form in x: P^tr = tau F^-T,
+// tau = mu dev(J^-2/3 b_e^tr) + kappa/2 (J^2 - 1) I).  Stress and state enter as the plastic
+// corrections, which vanish in elastic steps and stay small in plastic ones, so that the
+// network's relative error neither reaches the elastic response nor accumulates in the state.
 __device__ __forceinline__ void sym_to6(const M3<float> &b, float *o) {
     o[0] = b.a[0];
     o[1] = b.a[4];
@@ -689,7 +691,7 @@ template <typename T> __device__ __forceinline__ M3<T> left_cg(const M3<T> &F, c
 // exclusive scan of the flags), in particle order.
 template <typename T, int DIM, bool WRITE>
 __global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsigned salt, int64_t *flag,
-                             const int64_t *offset, float *x, float *y, int64_t cap) {
+                             const int64_t *offset, float *x, float *y, float *pnorm, int64_t cap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int n = a.n;
@@ -720,15 +722,20 @@ __global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsign
     F.a[4] += T(1);
     F.a[8] += T(1);
     const M3<T> P = mul(F, S);
+    // elastic predictor: the stress of the trial state (C_p^-1 of the last step)
+    const M3<T> Ptr = mul(F, j2_stress(kin, j2_trial(kin, K6, ep, m).dev, m));
     const M3<T> btr = left_cg(F, K6), bnew = left_cg(F, K6o);
     float *xr = x + 16 * offset[i], *yr = y + 16 * offset[i];
     M3<float> bf, bd;
+    T pn = T(0);
     for (int q = 0; q < 9; q++) {
         xr[q] = (float)F.a[q];
-        yr[q] = (float)P.a[q];
+        yr[q] = (float)(P.a[q] - Ptr.a[q]);
         bf.a[q] = (float)btr.a[q];
         bd.a[q] = (float)(bnew.a[q] - btr.a[q]);
+        pn += P.a[q] * P.a[q];
     }
+    if (pnorm) pnorm[offset[i]] = (float)t_sqrt(pn);
     sym_to6(bf, xr + 9);
     sym_to6(bd, yr + 9);
     xr[15] = (float)ep;
@@ -737,9 +744,9 @@ __global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsign
 
 // Pass 1b with the surrogate (FP32): every block loads the network into shared memory once
 // and walks tiles of 128 particles.  A J2 particle (without phase field) whose normalised
-// features lie inside the training envelope takes P and the increments of its state from the
-// network (BF16 tensor cores, FP32 accumulation); with scope 1 only particles whose trial
-// state yields do.  Every other particle is marked in exact[] for k_stress_exact, which runs
+// features lie inside the training envelope takes the plastic corrections of P and of its
+// state from the network (BF16 tensor cores, FP32 accumulation) on top of the closed-form
+// elastic predictor; with scope 1 only particles whose trial state yields do.  Every other particle is marked in exact[] for k_stress_exact, which runs
 // next.  A tile in which no particle uses the network skips the forward pass.
 // counters: [0] network, [1] J2 outside the envelope, [2] elastic trial states (scope 1).
 template <int DIM, bool FRAC>
@@ -795,8 +802,17 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
             if (use) {
                 float yr[16];
                 for (int c = 0; c < 16; c++) yr[c] = sm.Y[threadIdx.x][c] * s.out_std[c] + s.out_mean[c];
-                M3<float> P, db;
-                for (int q = 0; q < 9; q++) P.a[q] = yr[q];
+                // P = elastic predictor + the network's plastic correction
+                const MatT<float> m = a.mats[a.mid[i]];
+                float K6[6];
+                for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+                const Kin<float> kin = kinematics(G);
+                M3<float> Fp = G;
+                Fp.a[0] += 1.0f;
+                Fp.a[4] += 1.0f;
+                Fp.a[8] += 1.0f;
+                M3<float> P = mul(Fp, j2_stress(kin, j2_trial(kin, K6, a.ep[i], m).dev, m)), db;
+                for (int q = 0; q < 9; q++) P.a[q] += yr[q];
                 db.a[0] = yr[9]; db.a[4] = yr[10]; db.a[8] = yr[11];
                 db.a[1] = db.a[3] = yr[12];
                 db.a[2] = db.a[6] = yr[13];

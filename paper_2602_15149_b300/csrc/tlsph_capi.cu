@@ -2037,7 +2037,7 @@ tlsph_status tlsph_surrogate_counts(tlsph_ctx *c, int64_t counts[3]) {
 }
 
 tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plastic, unsigned salt, float *x,
-                              float *y, int64_t cap, int64_t *count) {
+                              float *y, float *pnorm, int64_t cap, int64_t *count) {
     if (!c || !x || !y || !count || cap < 0 || stride_elastic < 1 || stride_plastic < 1) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     const int64_t n = c->n;
@@ -2054,12 +2054,12 @@ tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plast
         k_gradient<T, D, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
         k_j2_samples<T, D, false><<<nb, kThreads, 0, c->stream>>>(a, stride_elastic, stride_plastic, salt, flag,
-                                                                   nullptr, x, y, cap);
+                                                                   nullptr, x, y, pnorm, cap);
         CKL();
         tlsph_status st = scan_exclusive(c, n + 1, flag, off);
         if (st != TLSPH_OK) return st;
         k_j2_samples<T, D, true><<<nb, kThreads, 0, c->stream>>>(a, stride_elastic, stride_plastic, salt, flag, off,
-                                                                  x, y, cap);
+                                                                  x, y, pnorm, cap);
         CKL();
         return TLSPH_OK;
     };

@@ -24,7 +24,7 @@ def he_uniform(seed=0, sizes=(16, 128, 128, 128, 16)):
 
 def generate_samples(case, n_target, steps, every=20, stride_elastic=4, stride_plastic=1, device=0, stream=None,
                      precision=None, per_call=None):
-    """Run the workload with the exact return map and collect (x, y) rows every `every` steps.
+    """Run the workload with the exact return map and collect (x, y, |P|) rows every `every` steps.
 
     With `per_call`, both strides double after a call that kept more rows than that, so that the
     samples spread over the whole run instead of filling up in its first steps."""
@@ -33,18 +33,19 @@ def generate_samples(case, n_target, steps, every=20, stride_elastic=4, stride_p
     dev = torch.device("cuda", device)
     x = torch.empty((n_target, 16), dtype=torch.float32, device=dev)
     y = torch.empty((n_target, 16), dtype=torch.float32, device=dev)
+    pn = torch.empty((n_target,), dtype=torch.float32, device=dev)
     g = tlsph.from_case(case, precision=precision, device=device, stream=stream)
     n, k, salt = 0, 0, 0
     while k < steps and n < n_target:
         g.step(every)
         k += every
         salt += 1
-        got = g.j2_samples(x[n:], y[n:], stride_elastic, stride_plastic, salt)
+        got = g.j2_samples(x[n:], y[n:], stride_elastic, stride_plastic, salt, pnorm=pn[n:])
         n += got
         if per_call and got > per_call:
             stride_elastic, stride_plastic = 2 * stride_elastic, 2 * stride_plastic
     g.close()
-    return x[:n], y[:n]
+    return x[:n], y[:n], pn[:n]
 
 
 def train(x, y, epochs=10, batch=4096, lr=2e-3, lr_end=1e-5, seed=0, device=0, time_budget_s=None, log=None):
@@ -83,8 +84,10 @@ def train(x, y, epochs=10, batch=4096, lr=2e-3, lr_end=1e-5, seed=0, device=0, t
                  "train_s": time.perf_counter() - t0, "samples": n}
 
 
-def stress_error(mlp, x, y, sigma_y0):
-    """Per-sample relative stress error |P_net - P_exact|_F / max(|P_exact|_F, sigma_y0) (mean, p99, max)."""
+def stress_error(mlp, x, y, pnorm, sigma_y0):
+    """Per-sample relative stress error |P_net - P_exact|_F / max(|P_exact|_F, sigma_y0) (mean, p99,
+    max) over the rows inside the envelope.  The stress columns of y hold P - P^tr, the network's
+    as well, so their difference is P_net - P_exact."""
     import torch
 
     out = torch.empty_like(y)
@@ -92,7 +95,7 @@ def stress_error(mlp, x, y, sigma_y0):
     mlp.forward(x, out, outside)
     inside = outside == 0
     d = torch.linalg.norm(out[:, :9] - y[:, :9], dim=1)
-    ref = torch.clamp(torch.linalg.norm(y[:, :9], dim=1), min=sigma_y0)
+    ref = torch.clamp(pnorm, min=sigma_y0)
     e = (d / ref)[inside].double()
     return {"mean": float(e.mean()), "p99": float(torch.quantile(e.float(), 0.99)), "max": float(e.max()),
             "inside_fraction": float(inside.float().mean())}

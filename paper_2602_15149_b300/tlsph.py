@@ -120,7 +120,7 @@ def load_library(path: str = LIB_PATH):
         "tlsph_mlp_forward": (C.c_int, [P, C.c_int64, V, V, V]),
         "tlsph_set_surrogate": (C.c_int, [P, P, C.c_int]),
         "tlsph_surrogate_counts": (C.c_int, [P, I64]),
-        "tlsph_j2_samples": (C.c_int, [P, C.c_int, C.c_int, C.c_uint, V, V, C.c_int64, I64]),
+        "tlsph_j2_samples": (C.c_int, [P, C.c_int, C.c_int, C.c_uint, V, V, V, C.c_int64, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,12 +297,13 @@ class TLSPH:
         self._ck(self.lib.tlsph_surrogate_counts(self.ctx, c.ctypes.data_as(C.POINTER(C.c_int64))), "surrogate_counts")
         return int(c[0]), int(c[1]), int(c[2])
 
-    def j2_samples(self, x, y, stride_elastic=1, stride_plastic=1, salt=0):
-        """Return-map samples of the current state into torch CUDA float32 tensors x, y (cap x 16);
-        returns the number of rows written."""
+    def j2_samples(self, x, y, stride_elastic=1, stride_plastic=1, salt=0, pnorm=None):
+        """Return-map samples of the current state into torch CUDA float32 tensors x, y (cap x 16)
+        and optionally pnorm (cap, |P|_F of each row); returns the number of rows written."""
         cnt = np.zeros(1, np.int64)
         self._ck(self.lib.tlsph_j2_samples(self.ctx, stride_elastic, stride_plastic, salt, x.data_ptr(), y.data_ptr(),
-                                           int(x.shape[0]), cnt.ctypes.data_as(C.POINTER(C.c_int64))), "j2_samples")
+                                           None if pnorm is None else pnorm.data_ptr(), int(x.shape[0]),
+                                           cnt.ctypes.data_as(C.POINTER(C.c_int64))), "j2_samples")
         return int(cnt[0])
 
     def kernel_times(self):

@@ -69,11 +69,11 @@ def test_gradients_match_reference(torch):
 def trained(torch):
     """A network trained on return-map samples of a small J2 block (same recipe as the 1M block)."""
     case = W.block_3d(nx=24, ny=24, nz=12)
-    x, y = surrogate.generate_samples(case, n_target=400_000, steps=1200, every=10, stride_elastic=2)
+    x, y, pn = surrogate.generate_samples(case, n_target=400_000, steps=1200, every=10, stride_elastic=2)
     n = x.shape[0]
     ntr = int(0.9 * n)
     net, info = surrogate.train(x[:ntr], y[:ntr], epochs=60, batch=1024, lr=2e-3)
-    return case, net, info, (x[ntr:], y[ntr:]), (x[:ntr], y[:ntr])
+    return case, net, info, (x[ntr:], y[ntr:], pn[ntr:]), (x[:ntr], y[:ntr])
 
 
 def test_samples_are_deterministic(torch):
@@ -81,18 +81,20 @@ def test_samples_are_deterministic(torch):
     a = surrogate.generate_samples(case, n_target=20_000, steps=300, every=30, stride_elastic=1)
     b = surrogate.generate_samples(case, n_target=20_000, steps=300, every=30, stride_elastic=1)
     assert a[0].shape[0] > 1000
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
-    # elastic rows carry exactly zero state increments; plastic rows a positive eps_p increment
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    # elastic rows carry exactly zero corrections (stress and state); plastic rows a positive
+    # eps_p increment
     y = a[1].cpu().numpy()
     assert np.all(y[:, 15] >= 0.0)
-    zero = np.all(y[:, 9:16] == 0.0, axis=1)
+    zero = np.all(y == 0.0, axis=1)
     assert zero.any() and (y[:, 15] > 0.0).any()
+    assert np.all(a[2].cpu().numpy() > 0.0)
 
 
 def test_training_learns_the_return_map(trained):
-    case, net, info, (xv, yv), _ = trained
+    case, net, info, (xv, yv, pv), _ = trained
     assert info["samples"] > 50_000
-    err = surrogate.stress_error(net, xv, yv, case.materials[0].sigma_y0)
+    err = surrogate.stress_error(net, xv, yv, pv, case.materials[0].sigma_y0)
     print("held-out stress error", err, info)
     assert err["inside_fraction"] > 0.95
     assert err["mean"] <= 1e-2
