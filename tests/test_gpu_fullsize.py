@@ -1,0 +1,113 @@
+"""Parity at the full sizes of the measured workloads, in the configuration bench.py times
+(FP32 fields with FP64 displacement, kernel launches of 128 threads, stencil layout).
+
+* 3D J2 block, 128 x 128 x 64 = 1,048,576 particles: neighbour lists and cell sort bit-exact
+  against the oracle's cell search; after the benchmark's 2000 steps, F and P of every particle
+  recomputed by the oracle from the GPU's state (u, C_p^-1, eps_p), the oracle evaluating
+  eq. deformGradTLSPH and the J2 update in FP64.
+* 2D notched phase-field plate, 500 x 200 = 100,000 particles, against the oracle run step for
+  step over the full 4000 steps (compared every 500 steps), with the bounds of the phase field
+  and the irreversibility of the history functional.
+* 512 independent 2D specimens (about 6M particles): after 300 steps of the whole batch, the
+  smallest, a median and the largest specimen against the oracle run of that specimen alone.
+
+Tolerances: the FP32 bar of the scope, relative L2 1e-4 for u and the per-particle matrices, and
+1e-3 for the damage field.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_15149_b300 import tlsph, workloads as W
+from tests.oracle_cases import make_oracle
+from tests.test_gpu_batched import specimen_alone
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def fp_from_cpinv(cp):
+    """A plastic deformation gradient with F_p^-1 F_p^-T = C_p^-1: the symmetric one,
+    F_p = (C_p^-1)^(-1/2).  The J2 stress depends on F_p only through C_p^-1."""
+    lam, vec = np.linalg.eigh(cp)
+    return np.einsum("nij,nj,nkj->nik", vec, lam ** -0.5, vec)
+
+
+def test_block_1m_setup_bit_exact_and_state_parity():
+    case = W.block_3d()
+    g = tlsph.from_case(case)
+    assert g.n == 1 << 20 and g.get_info()["stencil"] > 0
+    o = make_oracle(case)
+    rp_o, col_o = o.neighbours()
+    rp_g, col_g = g.neighbours()
+    assert np.array_equal(rp_o, rp_g)
+    assert np.array_equal(col_o, col_g)
+    del col_o, col_g
+    assert np.array_equal(o.perm(), g.permutation())
+    g.step(case.steps)
+    info = g.get_info()
+    assert info["noconverge"] == 0 and info["nonfinite"] == 0
+    U, ep, cp = g.read_state("U"), g.read_state("EPSP"), g.read_state("CPINV")
+    Fg, Pg = g.read_state("F"), g.read_state("P")
+    assert ep.max() > 1e-3  # the block yields
+    o.write("U", U)
+    o.write("EPSP", ep)
+    o.write("FP", fp_from_cpinv(cp))
+    Fo, Po = o.read("F"), o.read("P")
+    eye = np.eye(3)[None]
+    err_g = rel_l2(Fg - eye, Fo - eye)
+    err_p = rel_l2(Pg, Po)
+    plastic = ep > 0
+    err_pp = rel_l2(Pg[plastic], Po[plastic])
+    print("1M block after 2000 steps: rel-L2 (F - I)", err_g, "P", err_p, "P (plastic particles)", err_pp,
+          "plastic fraction", plastic.mean())
+    assert err_g <= 1e-4 and err_p <= 1e-4 and err_pp <= 1e-4
+
+
+def test_notched_plate_full_size():
+    case = W.notched_plate()
+    assert case.n == 100_000
+    g = tlsph.from_case(case)
+    o = make_oracle(case)
+    H_prev = None
+    for k in range(case.steps // 500):
+        g.step(500)
+        o.step(500)
+        H = g.read_state("H")
+        if H_prev is not None:
+            assert np.all(H >= H_prev)  # eq. irreversibility
+        H_prev = H
+        eu = rel_l2(g.read_state("U"), o.read("U"))
+        s_g, s_o = g.read_state("S"), o.read("S")
+        es = float(np.abs(s_g - s_o).max())
+        print("notched 500 x 200, %d steps: rel-L2(u) %.3e max |ds| %.3e min s %.4f" % (500 * (k + 1), eu, es,
+                                                                                          s_o.min()))
+        assert eu <= 1e-4 and es <= 1e-3
+        assert s_g.min() >= 0.0 and s_g.max() <= 1.0
+    info = g.get_info()
+    assert info["nonfinite"] == 0
+    to, dto = o.time()
+    tg, dtg = g.time()
+    assert dtg == dto and abs(tg - to) <= 1e-12 * to
+
+
+def test_batch_512_specimens_sampled():
+    case = W.batched(nspec=512)
+    g = tlsph.from_case(case)
+    steps = 300
+    g.step(steps)
+    U = g.read_state("U")
+    sizes = np.bincount(case.specimen_id, minlength=512)
+    order = np.argsort(sizes, kind="stable")
+    for s in (int(order[0]), int(order[256]), int(order[-1])):
+        sub, idx = specimen_alone(case, s)
+        o = make_oracle(sub)
+        o.step(steps)
+        err = rel_l2(U[idx], o.read("U"))
+        to, dto = o.time()
+        tg, dtg = g.time(s)
+        print("specimen", s, "particles", sizes[s], "rel-L2(u)", err)
+        assert err <= 1e-4
+        assert dtg == dto and abs(tg - to) <= 1e-12 * to
