@@ -350,6 +350,7 @@ __global__ void k_sell_pad(int64_t total, int *sell, int v) {
 // which is the ascending column order of its CSR row: both layouts visit the same pairs in
 // the same order.  The k-th visit of 32 consecutive rows reads 32 consecutive particles.
 constexpr int kMaxStencil = 128;
+constexpr int kMaxRun = 8;  // longest run of consecutive differences the step kernels unroll
 constexpr int64_t kStencilSpan = (int64_t)1 << 22;  // |j - i| the difference bitmap covers
 
 // Set bit (d + kStencilSpan) of the bitmap for every pair difference d; *far counts pairs

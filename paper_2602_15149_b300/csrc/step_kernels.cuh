@@ -41,27 +41,42 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // Visit the neighbours j of particle i in ascending sorted index, calling pair(j, on).  Stencil
 // layout (a.nsten > 0): the warp's 32 consecutive rows walk the stencil differences together
 // and row i takes the entries its mask keeps, so the k-th reads of the warp are consecutive
-// particles.  An entry the mask drops comes as pair(i, false): the body still runs (no branch,
-// so the unrolled loop can issue the loads of several entries together) and must add exact
-// zeros.  SELL-32 layout otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
-template <int UNROLL = 4, typename T, typename Pair>
+// particles.  The differences come in runs of consecutive values (one row of a lattice
+// stencil each), so the k-th entry of a run reads at a fixed offset from the run's base.  An
+// entry the mask drops comes as pair(i + D, false), reading another particle or the zero halo
+// around the gathered arrays: the body runs without a branch (the unrolled run issues its
+// loads together) and must add exact zeros.  With SKIP, an entry that no row of the warp keeps
+// is skipped (a warp vote), which saves its loads at the faces of a block.  SELL-32 layout
+// otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
+template <int UNROLL = 4, bool SKIP = false, typename T, typename Pair>
 __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, Pair &&pair) {
     if (a.nsten > 0) {
-        for (int s0 = 0; s0 < a.nsten; s0 += 32) {
-            const unsigned m = __ldg(a.nmask + (int64_t)(s0 >> 5) * a.n + i);
-            const int lim = min(32, a.nsten - s0);
-            const int *off = a.soff + s0;
-#pragma unroll UNROLL
-            for (int b = 0; b < lim; b++) {
-                const bool on = (m >> b) & 1u;
-                pair(on ? i + __ldg(off + b) : i, on);
+        const int nw = (a.nsten + 31) >> 5;
+        unsigned mw[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) mw[q] = q < nw ? __ldg(a.nmask + (int64_t)q * a.n + i) : 0u;
+        for (int r = 0; r < a.nruns; r++) {
+            const int2 rr = __ldg(a.runs + r);
+            const int s0 = rr.y & 255, len = rr.y >> 8;
+            const int w0 = s0 >> 5;
+            const unsigned lo = w0 == 0 ? mw[0] : w0 == 1 ? mw[1] : w0 == 2 ? mw[2] : mw[3];
+            const unsigned hi = w0 == 0 ? mw[1] : w0 == 1 ? mw[2] : w0 == 2 ? mw[3] : 0u;
+            const unsigned bits = __funnelshift_r(lo, hi, s0 & 31);
+            const int io = i + rr.x;
+#pragma unroll
+            for (int k = 0; k < kMaxRun; k++) {
+                if (k < len) {
+                    const bool on = (bits >> k) & 1u;
+                    if (SKIP && !__any_sync(__activemask(), on)) continue;
+                    pair(io + k, on);
+                }
             }
         }
     } else {
         const int64_t base = a.slice_off[i >> 5] + (i & 31);
         const int len = a.row_len[i];
         const int *cp = a.col + base;
-#pragma unroll 4
+#pragma unroll UNROLL
         for (int k = 0; k < len; k++) pair(__ldg(cp + 32 * k), true);
     }
 }
@@ -174,7 +189,7 @@ template <typename T, int DIM> __global__ void k_first_moment(StepArgs<T> a, V4<
 }
 
 // ---------------------------------------------------------------- pass 1b: stress
-template <typename T, int DIM>
+template <typename T, int DIM, bool FRAC>
 __device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J);
 
 // Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and the
@@ -234,11 +249,14 @@ __device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T 
         a.psi_out[i] = psi;
         return;
     }
-    dev_write_qvm<T, DIM>(a, i, F, P, T(1) + kin.Jm1);
+    dev_write_qvm<T, DIM, FRAC>(a, i, F, P, T(1) + kin.Jm1);
 }
 
 // Per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i (in-plane block).
-template <typename T, int DIM>
+// In 3D, q22 goes to Qc, or, in a step without phase field (s is constant), to the fourth
+// component of the particle's current velocity record, so that pass 2 gathers five float4
+// records per neighbour instead of five and a float.
+template <typename T, int DIM, bool FRAC>
 __device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J) {
     const int n = a.n;
     T A[3][3];
@@ -265,7 +283,8 @@ __device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const
     if (DIM == 3) {
         a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[0][DIM - 1], Qm[1][0]};
         a.Qb[i] = V4<T>{Qm[1][1], Qm[1][DIM - 1], Qm[DIM - 1][0], Qm[DIM - 1][1]};
-        a.Qc[i] = Qm[DIM - 1][DIM - 1];
+        if (FRAC) a.Qc[i] = Qm[DIM - 1][DIM - 1];
+        else reinterpret_cast<T *>(const_cast<V4<T> *>(a.vs_cur))[4 * i + 3] = Qm[DIM - 1][DIM - 1];
     } else {
         a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[1][0], Qm[1][1]};
     }
@@ -311,7 +330,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         for (int p = 0; p < DIM; p++) s2[p] = s3[p] = T(0);
 #pragma unroll
         for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
-        for_each_neighbour<2>(a, i, [&](const int j, const bool on) {
+        for_each_neighbour<4, true>(a, i, [&](const int j, const bool on) {
             const V4<T> xj = ldg4(a.X0V + j);
             T d[DIM];
             d[0] = xj.x - xi.x;
@@ -323,9 +342,12 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             const T Vj = DIM == 3 ? xj.w : xj.z;
             const T aw = w * Vj;
             T Qd[DIM];
+            // the neighbour's velocity record (its fourth component is s, or q22 without phase field)
+            V4<T> vsj = V4<T>{T(0), T(0), T(0), T(0)};
+            if (VISC || FRAC) vsj = ldg4(a.vs_cur + j);
             if (DIM == 3) {
                 const V4<T> q0 = ldg4(a.Qa + j), q1 = ldg4(a.Qb + j);
-                const T q2 = __ldg(a.Qc + j);
+                const T q2 = FRAC ? __ldg(a.Qc + j) : (VISC ? vsj.w : __ldg(&a.vs_cur[j].w));
                 Qd[0] = t_fma(q0.z, d[DIM - 1], t_fma(q0.y, d[1], q0.x * d[0]));
                 Qd[1] = t_fma(q1.y, d[DIM - 1], t_fma(q1.x, d[1], q0.w * d[0]));
                 Qd[DIM - 1] = t_fma(q2, d[DIM - 1], t_fma(q1.w, d[1], q1.z * d[0]));
@@ -337,7 +359,6 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
 #pragma unroll
             for (int p = 0; p < DIM; p++) s2[p] = t_fma(aw, Qd[p], s2[p]);
             if (VISC || frac) {
-                const V4<T> vsj = ldg4(a.vs_cur + j);
                 if (VISC) {
                     const V4<T> uj = ldg4(a.ug_cur + j);
                     const T mj = DIM == 3 ? uj.w : xj.w;  // reference mass m0_j
@@ -386,7 +407,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             const V4<T> q0 = a.Qa[i], q1 = a.Qb[i];
             Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
             Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
-            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = a.Qc[i];
+            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = FRAC ? a.Qc[i] : vsi.w;
         } else {
             const V4<T> q0 = a.Qa[i];
             Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
@@ -438,7 +459,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             }
         }
         // phase field (eq. phasefieldddot)
-        T s_new = vsi.w;
+        T s_new = FRAC ? vsi.w : T(1);
         if (frac) {
             T A[3][3];
             load_ahat<T, DIM>(a.Ahat, n, i, A);
@@ -846,7 +867,7 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
                 a.K[4 * n + i] = Kn.a[2];
                 a.K[5 * n + i] = Kn.a[5];
                 a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
-                dev_write_qvm<float, DIM>(a, i, F, P, 1.0f + det_eye_plus_m1(G));
+                dev_write_qvm<float, DIM, FRAC>(a, i, F, P, 1.0f + det_eye_plus_m1(G));
                 n_mlp++;
             }
         }

@@ -63,6 +63,9 @@ struct tlsph_ctx {
     int64_t *slice_off = nullptr;
     int nsten = 0;                // stencil layout entries (0 = none)
     int *soff = nullptr;          // stencil differences j - i, ascending
+    int2 *runs = nullptr;         // runs of consecutive differences
+    int nruns = 0;
+    int64_t halo = 0;             // zero elements before and after each gathered array (stencil layout)
     unsigned *nmask = nullptr;    // row masks over the stencil
     int layout = TLSPH_LAYOUT_AUTO;
     void *S1 = nullptr;  // sum_j V_j w_ij (X_j - X_i)
@@ -158,6 +161,9 @@ void free_device(tlsph_ctx *c) {
     c->perm = nullptr;
     c->S1 = nullptr;
     c->nsten = 0;
+    c->nruns = 0;
+    c->halo = 0;
+    c->runs = nullptr;
     c->soff = nullptr;
     c->nmask = nullptr;
     c->Fd = c->Pd = c->psid = c->accd = nullptr;
@@ -260,6 +266,8 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.col = c->sell;
     const bool sten = c->layout == TLSPH_LAYOUT_AUTO && c->nsten > 0;
     a.nsten = sten ? c->nsten : 0;
+    a.nruns = sten ? c->nruns : 0;
+    a.runs = sten ? c->runs : nullptr;
     a.soff = sten ? c->soff : nullptr;
     a.nmask = sten ? c->nmask : nullptr;
     a.X0V = (const V4<T> *)c->X0V;
@@ -365,7 +373,43 @@ tlsph_status build_stencil(tlsph_ctx *c) {
     CKL();
     CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (hc[1] == 0) c->nsten = (int)D.size();
+    if (hc[1] != 0) return TLSPH_OK;
+    // runs of consecutive differences (at most kMaxRun long)
+    std::vector<int2> runs;
+    int64_t halo = 0;
+    for (size_t a = 0; a < D.size();) {
+        size_t e = a + 1;
+        while (e < D.size() && D[e] == D[e - 1] + 1 && (int)(e - a) < kMaxRun) e++;
+        runs.push_back(make_int2(D[a], (int)a | ((int)(e - a) << 8)));
+        a = e;
+    }
+    for (int d : D) halo = std::max<int64_t>(halo, std::abs((int64_t)d));
+    DA(c->runs, runs.size() * sizeof(int2));
+    CK(cudaMemcpyAsync(c->runs, runs.data(), runs.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    c->nruns = (int)runs.size();
+    c->halo = halo;
+    c->nsten = (int)D.size();
+    return TLSPH_OK;
+}
+
+// Move a gathered array of n elements into a zero-filled allocation with c->halo elements
+// before and after it (the stencil runs read every particle i + D, in range or not).
+tlsph_status add_halo(tlsph_ctx *c, void *&ptr, size_t elem, int64_t n) {
+    const int64_t H = c->halo;
+    void *raw = nullptr;
+    DA(raw, (size_t)(n + 2 * H) * elem);
+    CK(cudaMemsetAsync(raw, 0, (size_t)(n + 2 * H) * elem, c->stream));
+    void *np = (char *)raw + (size_t)H * elem;
+    if (ptr) {
+        CK(cudaMemcpyAsync(np, ptr, (size_t)n * elem, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        auto it = std::find(c->allocs.begin(), c->allocs.end(), ptr);
+        if (it != c->allocs.end()) {
+            cudaFree(*it);
+            c->allocs.erase(it);
+        }
+    }
+    ptr = np;
     return TLSPH_OK;
 }
 
@@ -596,12 +640,28 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     CKL();
     st = build_stencil(c);
     if (st != TLSPH_OK) return st;
+    if (c->nsten > 0) {  // zero halo around the gathered arrays
+        st = add_halo(c, c->X0V, sizeof(V4<T>), n);
+        for (int q = 0; q < 2 && st == TLSPH_OK; q++) {
+            st = add_halo(c, c->vs[q], sizeof(V4<T>), n);
+            if (st == TLSPH_OK) st = add_halo(c, c->ug[q], sizeof(V4<T>), n);
+        }
+        if (st != TLSPH_OK) return st;
+    }
     // ---- state
     DA(c->u64, 3 * n * sizeof(double));
     CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
-    DA(c->Qa, n * sizeof(V4<T>));
-    DA(c->Qb, (dim == 3 ? n : 1) * sizeof(V4<T>));
-    DA(c->Qc, (dim == 3 ? n : 1) * sizeof(T));
+    if (c->nsten > 0) {
+        c->Qa = c->Qb = c->Qc = nullptr;
+        st = add_halo(c, c->Qa, sizeof(V4<T>), n);
+        if (st == TLSPH_OK) st = add_halo(c, c->Qb, sizeof(V4<T>), dim == 3 ? n : 1);
+        if (st == TLSPH_OK) st = add_halo(c, c->Qc, sizeof(T), dim == 3 ? n : 1);
+        if (st != TLSPH_OK) return st;
+    } else {
+        DA(c->Qa, n * sizeof(V4<T>));
+        DA(c->Qb, (dim == 3 ? n : 1) * sizeof(V4<T>));
+        DA(c->Qc, (dim == 3 ? n : 1) * sizeof(T));
+    }
     CK(cudaMemsetAsync(c->Qa, 0, n * sizeof(V4<T>), s));
     DA(c->G, dim * dim * n * sizeof(T));
     DA(c->Vm, dim * dim * n * sizeof(T));
