@@ -46,9 +46,10 @@ FALLBACK_BF16_TFLOPS = 1400.0
 MLP_FLOP_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16)  # 73,728
 
 # DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel
-# sources it was taken on; reported as null once the kernels change.
-NCU_TRAFFIC = {"sources": None, "pass2": None, "gradient": None, "stress": None}
+# of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
+# profiles/dram_traffic__block_3d_j2_128x128x64.md), keyed by the hash of the kernel sources it
+# was taken on; reported as null once the kernels change.
+NCU_TRAFFIC = {"sources": "76c6ecc9e7a17569", "pass2": 236611840.0, "gradient": 92325888.0, "stress": 144994560.0}
 
 
 def source_hash() -> str:
@@ -153,6 +154,34 @@ def dist_env():
     return ws, rank, local
 
 
+def shard_specimens(nspec, rank, ws):
+    """The specimens rank takes in an N-rank run of the batched form: every ws-th, from rank on
+    (specimens are ordered by size, so the shares balance).  No data crosses ranks."""
+    return list(range(rank, nspec, ws))
+
+
+def max_over_ranks(x, device=None):
+    """The largest x of all ranks (x itself when the run has one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, device=None):
+    """The sum of x over all ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def oracle_sample(seconds=15.0, shape=(32, 32, 16)):
     """The FP64 oracle as it stands on a bounded sample of the workload (same lattice recipe,
     material and loading, smaller block): particle-steps/s on the host cores."""
@@ -209,7 +238,9 @@ def measure_batched(args, device, stream):
     import torch
     from paper_2602_15149_b300 import tlsph
 
-    case = W.batched(nspec=args.batch_specimens, steps=args.steps)
+    ws, rank, _ = dist_env()
+    full = W.batched(nspec=args.batch_specimens, steps=args.steps)
+    case = W.subset(full, shard_specimens(args.batch_specimens, rank, ws)) if ws > 1 else full
     t0 = time.perf_counter()
     g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
@@ -218,19 +249,23 @@ def measure_batched(args, device, stream):
     steps = max(10, min(args.steps, 1000))
     dev = torch.device("cuda", device)
     torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     g.step_async(steps)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     st = g.sync(check=False)
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    particles = int(sum_over_ranks(case.n, dev))
     info = g.get_info()
     g.close()
-    return {"workload": f"batched_2d {args.batch_specimens} specimens, {case.n} particles, "
-                        f"log-uniform 500-50k each, NH/J2, own clocks", "particles": case.n,
+    return {"workload": f"batched_2d {args.batch_specimens} specimens, {particles} particles, "
+                        f"log-uniform 500-50k each, NH/J2, own clocks", "particles": particles,
             "specimens": args.batch_specimens, "steps": steps, "ms_per_step": ms / steps,
-            "value": case.n * steps / (ms * 1e-3), "unit": UNIT, "tuned": best, "candidates": allt,
+            "value": particles * steps / (ms * 1e-3), "unit": UNIT, "tuned": best, "candidates": allt,
+            "sharding": f"specimens by rank ({ws} ranks, no collective on the data path)",
             "setup_s": setup_s, "status": int(st), "mean_neighbours": info["nnz"] / case.n}
 
 
@@ -348,10 +383,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     launches = g.get_info()["kernel_launches"] - l0
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     value = ws * n * args.steps / (ms * 1e-3)
 
     # per-kernel durations (CUDA events around each launch on the same stream)
@@ -382,10 +414,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     g2.close()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     h2d = n * (8 * 3 + 8 + 4 + 8 * 3) + sum(n for _ in case.bcs)
     d2h = u.nbytes + 8 * 4 * args.steps
 

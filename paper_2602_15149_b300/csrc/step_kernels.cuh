@@ -46,11 +46,24 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // entry the mask drops comes as pair(i + D, false), reading another particle or the zero halo
 // around the gathered arrays: the body runs without a branch (the unrolled run issues its
 // loads together) and must add exact zeros.  With SKIP, an entry that no row of the warp keeps
-// is skipped (a warp vote), which saves its loads at the faces of a block.  SELL-32 layout
-// otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
-template <int UNROLL = 4, bool SKIP = false, typename T, typename Pair>
+// is skipped (a warp vote), which saves its loads at the faces of a block.  Without RUNS the
+// entries are walked one by one (UNROLL at a time across runs, each reading its difference).
+// SELL-32 layout otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
+template <int UNROLL = 4, bool SKIP = false, bool RUNS = true, typename T, typename Pair>
 __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, Pair &&pair) {
-    if (a.nsten > 0) {
+    if (!RUNS && a.nsten > 0) {
+        for (int s0 = 0; s0 < a.nsten; s0 += 32) {
+            const unsigned m = __ldg(a.nmask + (int64_t)(s0 >> 5) * a.n + i);
+            const int lim = min(32, a.nsten - s0);
+            const int *off = a.soff + s0;
+#pragma unroll UNROLL
+            for (int b = 0; b < lim; b++) {
+                const bool on = (m >> b) & 1u;
+                if (SKIP && !__any_sync(__activemask(), on)) continue;
+                pair(i + __ldg(off + b), on);
+            }
+        }
+    } else if (a.nsten > 0) {
         const int nw = (a.nsten + 31) >> 5;
         unsigned mw[4];
 #pragma unroll
@@ -117,7 +130,7 @@ __device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[D
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) B[p][q] = T(0);
-    for_each_neighbour(a, i, [&](const int j, const bool on) {
+    for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
         const V4<T> xj = ldg4(a.X0V + j);
         const V4<T> uj = ldg4(a.ug_cur + j);
         T d[DIM], du[DIM];
@@ -330,7 +343,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         for (int p = 0; p < DIM; p++) s2[p] = s3[p] = T(0);
 #pragma unroll
         for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
-        for_each_neighbour<4, true>(a, i, [&](const int j, const bool on) {
+        for_each_neighbour<4>(a, i, [&](const int j, const bool on) {
             const V4<T> xj = ldg4(a.X0V + j);
             T d[DIM];
             d[0] = xj.x - xi.x;

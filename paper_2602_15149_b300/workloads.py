@@ -26,6 +26,7 @@ c = sqrt((lambda + 2 mu)/rho) (the step the solvers take in their
 """
 from __future__ import annotations
 
+import copy
 import math
 from dataclasses import dataclass, field
 
@@ -216,3 +217,26 @@ def batched(nspec=512, n_min=500, n_max=50000, dp=1e-3, seed=0, steps=1000, prec
                                       (rate * nrm[0], rate * nrm[1], 0.0), ramp=100 * dt))
         off += X.shape[0]
     return case
+
+
+def subset(case: Case, specimens) -> Case:
+    """The given specimens of a batched case as a case of their own (specimens renumbered
+    0 .. k-1 in the given order's sorted order; materials, boundary conditions and loads kept).
+    A rank of a multi-GPU run takes its share of the specimens this way."""
+    keep = np.sort(np.asarray(list(specimens), dtype=np.int64))
+    sel = np.isin(case.specimen_id, keep)
+    idx = np.nonzero(sel)[0]
+    renum = np.full(int(case.specimen_id.max()) + 1, -1, np.int64)
+    renum[keep] = np.arange(keep.size)
+    sub = copy.copy(case)
+    sub.X0 = case.X0[idx].copy()
+    sub.vol = case.vol[idx].copy()
+    sub.v0 = case.v0[idx].copy()
+    sub.material_id = case.material_id[idx].copy()
+    sub.specimen_id = renum[case.specimen_id[idx]].astype(np.int32)
+    sub.bcs = [BC(b.mask[idx], b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area) for b in case.bcs]
+    loads = getattr(case, "specimen_loads", [])
+    sub.specimen_loads = [BC(loads[s].mask[idx], loads[s].kind, loads[s].comp_mask, loads[s].value,
+                             ramp=loads[s].ramp) for s in keep] if loads else []
+    return sub
+
