@@ -314,10 +314,15 @@ def measure_surrogate(args, shape, device, stream, plain):
     exact.close()
     out = {"workload": f"block_3d_j2 {'x'.join(map(str, shape))}, same as the plain step",
            "samples": m, "train_samples": ntr, "sample_gen_s": gen_s, "training": info, "stress_error": err,
-           "network": "16-128-128-128-16 SiLU, bf16 weights, fp32 accumulation (mma.sync m16n8k16)"}
-    for name, scope in (("all", tlsph.SURROGATE_ALL), ("plastic", tlsph.SURROGATE_PLASTIC)):
+           "network": "16-128-128-128-16 SiLU, bf16 weights, fp32 accumulation (tcgen05.mma with TMEM "
+                      "accumulators; mma.sync m16n8k16 for comparison)"}
+    for name, scope, path in (("all", tlsph.SURROGATE_ALL, tlsph.TENSOR_TCGEN05),
+                              ("plastic", tlsph.SURROGATE_PLASTIC, tlsph.TENSOR_TCGEN05),
+                              ("all_mma_sync", tlsph.SURROGATE_ALL, tlsph.TENSOR_MMA_SYNC)):
         g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+        net.set_tensor_path(path)
         g.set_surrogate(net, scope)
+        net.set_tensor_path(tlsph.TENSOR_TCGEN05)
         g.step(args.warmup)
         ms, st = timed_steps(g, args.steps - args.warmup, stream, dev)
         steps_t = args.steps - args.warmup
@@ -331,7 +336,8 @@ def measure_surrogate(args, shape, device, stream, plain):
         mlp_rows = used / max(args.steps, 1)  # network rows per launch (warm-up + timed steps)
         tflops = MLP_FLOP_PER_ROW * mlp_rows / (stress_ms * 1e-3) / 1e12
         peak, src = bf16_peak()
-        out[name] = {"ms_per_step": ms / steps_t, "value": n * steps_t / (ms * 1e-3), "unit": UNIT,
+        out[name] = {"tensor_path": "tcgen05" if path == tlsph.TENSOR_TCGEN05 else "mma.sync",
+                     "ms_per_step": ms / steps_t, "value": n * steps_t / (ms * 1e-3), "unit": UNIT,
                      "vs_plain": (n * steps_t / (ms * 1e-3)) / plain["value"],
                      "status": st, "rows_network": used, "rows_outside_envelope": outside,
                      "rows_elastic_exact": elastic,

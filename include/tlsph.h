@@ -299,8 +299,18 @@ tlsph_status tlsph_mlp_train_step(tlsph_mlp *mlp, const float *x, const float *y
  * parameters) and *loss (host) may each be NULL. */
 tlsph_status tlsph_mlp_gradients(tlsph_mlp *mlp, const float *x, const float *y, float *grads, float *loss);
 /* y = network(x) for n raw rows (denormalised outputs); outside[r] (may be NULL) = 1 when row r
- * lies outside the envelope. */
+ * lies outside the envelope.  TLSPH_ERR_TIMEOUT if a wait on the tensor cores ran out. */
 tlsph_status tlsph_mlp_forward(tlsph_mlp *mlp, int64_t n, const float *x, float *y, int32_t *outside);
+/* Tensor-core path of the inference kernels (tlsph_mlp_forward and the surrogate pass of a context
+ * that tlsph_set_surrogate gives this network):
+ *  TLSPH_TENSOR_TCGEN05 (default): tcgen05.mma, M = 128 x N = 128 (16 for the output layer) x K = 16,
+ *    operands in shared memory, FP32 accumulators in tensor memory, one CTA of 128 threads per tile
+ *    of 128 rows;
+ *  TLSPH_TENSOR_MMA_SYNC: warp-level mma.sync.m16n8k16, activations in registers.
+ * Both take BF16 operands and accumulate in FP32; they differ only in summation order. */
+#define TLSPH_TENSOR_MMA_SYNC 0
+#define TLSPH_TENSOR_TCGEN05 1
+tlsph_status tlsph_mlp_set_tensor_path(tlsph_mlp *mlp, int path);
 /* Scope of the surrogate in the J2 update. */
 #define TLSPH_SURROGATE_ALL 0     /* every J2 particle inside the envelope takes the network */
 #define TLSPH_SURROGATE_PLASTIC 1 /* only those whose trial state yields (f > 0); elastic trial

@@ -18,6 +18,7 @@
 #pragma once
 #include "common.cuh"
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace tl {
 
@@ -776,12 +777,111 @@ __global__ void k_j2_samples(StepArgs<T> a, int stride_el, int stride_pl, unsign
     yr[15] = (float)(epo - ep);
 }
 
-// Pass 1b with the surrogate (FP32): every block loads the network into shared memory once
-// and walks tiles of 128 particles.  A J2 particle (without phase field) whose normalised
-// features lie inside the training envelope takes the plastic corrections of P and of its
-// state from the network (BF16 tensor cores, FP32 accumulation) on top of the closed-form
-// elastic predictor; with scope 1 only particles whose trial state yields do.  Every other particle is marked in exact[] for k_stress_exact, which runs
-// next.  A tile in which no particle uses the network skips the forward pass.
+// Features of the surrogate for particle i (FP32): xn = normalised (F, b_e^tr, eps_p) when i is a
+// J2 particle without phase field that the network serves (inside the envelope and, with scope 1,
+// with a yielding trial state); returns whether it does.  Counts the J2 particles it leaves to the
+// exact update (n_out: outside the envelope, n_el: elastic trial state under scope 1).
+template <int DIM, bool FRAC>
+__device__ __forceinline__ bool sur_features(const StepArgs<float> &a, const SurrogateDev &s, int i, const M3<float> &G,
+                                             float xn[16], int &n_out, int &n_el) {
+    const int n = a.n;
+    const MatT<float> m = a.mats[a.mid[i]];
+    if (m.model != 3 || (FRAC && m.fracture)) return false;
+    float K6[6];
+    for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+    const float ep = a.ep[i];
+    if (s.scope == 1 && !(j2_trial(kinematics(G), K6, ep, m).f > 0.0f)) {
+        n_el++;
+        return false;
+    }
+    M3<float> F = G;
+    F.a[0] += 1.0f;
+    F.a[4] += 1.0f;
+    F.a[8] += 1.0f;
+    const M3<float> btr = left_cg(F, K6);
+    float xr[16];
+    for (int q = 0; q < 9; q++) xr[q] = F.a[q];
+    sym_to6(btr, xr + 9);
+    xr[15] = ep;
+    bool use = s.enabled != 0;
+    for (int c = 0; c < 16; c++) {
+        xn[c] = (xr[c] - s.in_mean[c]) / s.in_std[c];
+        use = use && xn[c] >= s.env_lo[c] && xn[c] <= s.env_hi[c];
+    }
+    if (!use) n_out++;
+    return use;
+}
+
+// Apply the network's outputs yn (normalised) to particle i: P = elastic predictor + correction,
+// C_p^-1 += F^-1 db F^-T with det C_p^-1 = 1 (eq. Fp_iso_proj), eps_p += max(0, increment), and
+// the pass-2 matrices.
+template <int DIM, bool FRAC>
+__device__ __forceinline__ void sur_apply(const StepArgs<float> &a, const SurrogateDev &s, int i, const M3<float> &G,
+                                          const float yn[16]) {
+    const int n = a.n;
+    float yr[16];
+    for (int c = 0; c < 16; c++) yr[c] = yn[c] * s.out_std[c] + s.out_mean[c];
+    const MatT<float> m = a.mats[a.mid[i]];
+    float K6[6];
+    for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
+    const Kin<float> kin = kinematics(G);
+    M3<float> F = G;
+    F.a[0] += 1.0f;
+    F.a[4] += 1.0f;
+    F.a[8] += 1.0f;
+    M3<float> P = mul(F, j2_stress(kin, j2_trial(kin, K6, a.ep[i], m).dev, m)), db;
+    for (int q = 0; q < 9; q++) P.a[q] += yr[q];
+    db.a[0] = yr[9]; db.a[4] = yr[10]; db.a[8] = yr[11];
+    db.a[1] = db.a[3] = yr[12];
+    db.a[2] = db.a[6] = yr[13];
+    db.a[5] = db.a[7] = yr[14];
+    if (DIM == 2) {  // plane strain: keep the in-plane block structure
+        P.a[2] = P.a[5] = P.a[6] = P.a[7] = 0.0f;
+        db.a[2] = db.a[6] = db.a[5] = db.a[7] = 0.0f;
+    }
+    // b_e^{n+1} = b_e^tr + db with b_e^tr = F C_p^-1 F^T, so C_p^-1 grows by F^-1 db F^-T (added to
+    // C_p^-1 - I directly: no cancellation), then det C_p^-1 = 1 as in eq. Fp_iso_proj
+    M3<float> Fi;
+    inverse(F, Fi);
+    const M3<float> dK = sym_part(mul(mul(Fi, db), transpose(Fi)));
+    M3<float> Kn;
+    Kn.a[0] = K6[0]; Kn.a[4] = K6[1]; Kn.a[8] = K6[2];
+    Kn.a[1] = Kn.a[3] = K6[3];
+    Kn.a[2] = Kn.a[6] = K6[4];
+    Kn.a[5] = Kn.a[7] = K6[5];
+    for (int q = 0; q < 9; q++) Kn.a[q] += dK.a[q];
+    const float fm1 = expm1f(-log1pf(det_eye_plus_m1(Kn)) / 3.0f);
+    for (int q = 0; q < 9; q++) Kn.a[q] = Kn.a[q] * (1.0f + fm1);
+    a.K[0 * n + i] = Kn.a[0] + fm1;
+    a.K[1 * n + i] = Kn.a[4] + fm1;
+    a.K[2 * n + i] = Kn.a[8] + fm1;
+    a.K[3 * n + i] = Kn.a[1];
+    a.K[4 * n + i] = Kn.a[2];
+    a.K[5 * n + i] = Kn.a[5];
+    a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
+    dev_write_qvm<float, DIM, FRAC>(a, i, F, P, 1.0f + kin.Jm1);
+}
+
+__device__ __forceinline__ void sur_count(unsigned long long *counters, int n_mlp, int n_out, int n_el) {
+    for (int o = 16; o > 0; o >>= 1) {
+        n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
+        n_out += __shfl_xor_sync(0xffffffffu, n_out, o);
+        n_el += __shfl_xor_sync(0xffffffffu, n_el, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&counters[0], (unsigned long long)n_mlp);
+        atomicAdd(&counters[1], (unsigned long long)n_out);
+        atomicAdd(&counters[2], (unsigned long long)n_el);
+    }
+}
+
+// Pass 1b with the surrogate (FP32), warp-level tensor cores: every block loads the network into
+// shared memory once and walks tiles of 128 particles.  A J2 particle (without phase field) whose
+// normalised features lie inside the training envelope takes the plastic corrections of P and of
+// its state from the network (BF16 mma.sync, FP32 accumulation) on top of the closed-form
+// elastic predictor; with scope 1 only particles whose trial state yields do.  Every other
+// particle is marked in exact[] for k_stress_exact, which runs next.  A tile in which no
+// particle uses the network skips the forward pass.
 // counters: [0] network, [1] J2 outside the envelope, [2] elastic trial states (scope 1).
 template <int DIM, bool FRAC>
 __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, SurrogateDev s, uint8_t *exact,
@@ -801,101 +901,67 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
         if (active) {
             for (int p = 0; p < DIM; p++)
                 for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
-            const MatT<float> m = a.mats[a.mid[i]];
-            if (m.model == 3 && !(FRAC && m.fracture)) {
-                float K6[6];
-                for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
-                const float ep = a.ep[i];
-                bool plastic = true;
-                if (s.scope == 1) plastic = j2_trial(kinematics(G), K6, ep, m).f > 0.0f;
-                if (plastic) {
-                    M3<float> F = G;
-                    F.a[0] += 1.0f;
-                    F.a[4] += 1.0f;
-                    F.a[8] += 1.0f;
-                    const M3<float> btr = left_cg(F, K6);
-                    float xr[16];
-                    for (int q = 0; q < 9; q++) xr[q] = F.a[q];
-                    sym_to6(btr, xr + 9);
-                    xr[15] = ep;
-                    use = s.enabled != 0;
-                    for (int c = 0; c < 16; c++) {
-                        xn[c] = (xr[c] - s.in_mean[c]) / s.in_std[c];
-                        use = use && xn[c] >= s.env_lo[c] && xn[c] <= s.env_hi[c];
-                    }
-                    n_out += use ? 0 : 1;
-                } else {
-                    n_el++;
-                }
-            }
+            use = sur_features<DIM, FRAC>(a, s, i, G, xn, n_out, n_el);
             exact[i] = use ? 0 : 1;
         }
         for (int c = 0; c < 16; c++) sm.X[threadIdx.x][c] = __float2bfloat16_rn(use ? xn[c] : 0.0f);
         if (__syncthreads_or(use)) {  // block-uniform
             mlp_forward_block(sm);
             if (use) {
-                float yr[16];
-                for (int c = 0; c < 16; c++) yr[c] = sm.Y[threadIdx.x][c] * s.out_std[c] + s.out_mean[c];
-                // P = elastic predictor + the network's plastic correction
-                const MatT<float> m = a.mats[a.mid[i]];
-                float K6[6];
-                for (int q = 0; q < 6; q++) K6[q] = a.K[q * n + i];
-                const Kin<float> kin = kinematics(G);
-                M3<float> Fp = G;
-                Fp.a[0] += 1.0f;
-                Fp.a[4] += 1.0f;
-                Fp.a[8] += 1.0f;
-                M3<float> P = mul(Fp, j2_stress(kin, j2_trial(kin, K6, a.ep[i], m).dev, m)), db;
-                for (int q = 0; q < 9; q++) P.a[q] += yr[q];
-                db.a[0] = yr[9]; db.a[4] = yr[10]; db.a[8] = yr[11];
-                db.a[1] = db.a[3] = yr[12];
-                db.a[2] = db.a[6] = yr[13];
-                db.a[5] = db.a[7] = yr[14];
-                if (DIM == 2) {  // plane strain: keep the in-plane block structure
-                    P.a[2] = P.a[5] = P.a[6] = P.a[7] = 0.0f;
-                    db.a[2] = db.a[6] = db.a[5] = db.a[7] = 0.0f;
-                }
-                M3<float> F = G;
-                F.a[0] += 1.0f;
-                F.a[4] += 1.0f;
-                F.a[8] += 1.0f;
-                // b_e^{n+1} = b_e^tr + db with b_e^tr = F C_p^-1 F^T, so C_p^-1 grows by F^-1 db F^-T
-                // (added to C_p^-1 - I directly: no cancellation), then det C_p^-1 = 1 as in
-                // eq. Fp_iso_proj
-                M3<float> Fi;
-                inverse(F, Fi);
-                const M3<float> dK = sym_part(mul(mul(Fi, db), transpose(Fi)));
-                M3<float> Kn;
-                Kn.a[0] = a.K[0 * n + i]; Kn.a[4] = a.K[1 * n + i]; Kn.a[8] = a.K[2 * n + i];
-                Kn.a[1] = Kn.a[3] = a.K[3 * n + i];
-                Kn.a[2] = Kn.a[6] = a.K[4 * n + i];
-                Kn.a[5] = Kn.a[7] = a.K[5 * n + i];
-                for (int q = 0; q < 9; q++) Kn.a[q] += dK.a[q];
-                const float fm1 = expm1f(-log1pf(det_eye_plus_m1(Kn)) / 3.0f);
-                for (int q = 0; q < 9; q++) Kn.a[q] = Kn.a[q] * (1.0f + fm1);
-                a.K[0 * n + i] = Kn.a[0] + fm1;
-                a.K[1 * n + i] = Kn.a[4] + fm1;
-                a.K[2 * n + i] = Kn.a[8] + fm1;
-                a.K[3 * n + i] = Kn.a[1];
-                a.K[4 * n + i] = Kn.a[2];
-                a.K[5 * n + i] = Kn.a[5];
-                a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
-                dev_write_qvm<float, DIM, FRAC>(a, i, F, P, 1.0f + det_eye_plus_m1(G));
+                sur_apply<DIM, FRAC>(a, s, i, G, sm.Y[threadIdx.x]);
                 n_mlp++;
             }
         }
         __syncthreads();
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
-        n_out += __shfl_xor_sync(0xffffffffu, n_out, o);
-        n_el += __shfl_xor_sync(0xffffffffu, n_el, o);
+    sur_count(counters, n_mlp, n_out, n_el);
+}
+
+// The same pass on the 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM; see
+// mlp_tc.cuh): CTAs of 4 groups x 128 threads, each group persistent over tiles of 128
+// particles.  A wait on the tensor cores that runs out sets kFlagTimeout and ends the group's
+// work (its remaining particles keep their old state).
+template <int DIM, bool FRAC>
+__global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<float> a, SurrogateDev s,
+                                                                     uint8_t *exact, unsigned long long *counters) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    MlpTcSmem &sm = *reinterpret_cast<MlpTcSmem *>(smraw);
+    mlp_tc_setup(sm, s);
+    const int g = threadIdx.x >> 7, r = threadIdx.x & 127;
+    unsigned phase = 0;
+    bool pending = false;
+    const int n = a.n, ntiles = (n + 127) / 128;
+    int n_mlp = 0, n_out = 0, n_el = 0;
+    for (int tile = blockIdx.x * kTcGroups + g; tile < ntiles; tile += gridDim.x * kTcGroups) {
+        const int i = tile * 128 + r;
+        const bool active = i < n;
+        bool use = false;
+        float xn[16];
+        M3<float> G = m3_zero<float>();
+        if (active) {
+            for (int p = 0; p < DIM; p++)
+                for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
+            use = sur_features<DIM, FRAC>(a, s, i, G, xn, n_out, n_el);
+            exact[i] = use ? 0 : 1;
+        }
+        if (!use)
+            for (int c = 0; c < 16; c++) xn[c] = 0.0f;
+        mlp_tc_put_row(sm, g, r, xn);
+        if (group_or(g, use)) {  // group-uniform
+            float yn[16];
+            if (!mlp_tc_tile(sm, g, r, phase, yn)) {
+                if (r == 0) atomicAdd(&a.flags[kFlagTimeout], 1);
+                pending = true;
+                break;
+            }
+            if (use) {
+                sur_apply<DIM, FRAC>(a, s, i, G, yn);
+                n_mlp++;
+            }
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&counters[0], (unsigned long long)n_mlp);
-        atomicAdd(&counters[1], (unsigned long long)n_out);
-        atomicAdd(&counters[2], (unsigned long long)n_el);
-    }
+    mlp_tc_finish(sm, g, phase, pending);
+    sur_count(counters, n_mlp, n_out, n_el);
 }
 
 // The exact constitutive update of the particles k_stress_sur left to it (exact[i] = 1).

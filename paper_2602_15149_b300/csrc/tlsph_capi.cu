@@ -91,6 +91,7 @@ struct tlsph_ctx {
     float *sur_bias = nullptr, *sur_norm = nullptr;
     unsigned long long *sur_count = nullptr;  // network, outside the envelope, elastic trial
     uint8_t *sur_exact = nullptr;             // particles left to the exact update in a step
+    int sur_tensor = TLSPH_TENSOR_TCGEN05;    // tensor path of the network pass
     int sur_scope = 0;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
@@ -776,18 +777,21 @@ SurrogateDev sur_dev(const tlsph_ctx *c) {
 }
 
 template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const StepArgs<float> &a) {
-    auto kern = k_stress_sur<DIM, FRAC>;
-    static bool attr_set[2][2] = {{false, false}, {false, false}};
-    if (!attr_set[DIM - 2][FRAC]) {
-        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-        attr_set[DIM - 2][FRAC] = true;
+    const bool tc = c->sur_tensor == TLSPH_TENSOR_TCGEN05;
+    auto kern = tc ? k_stress_sur_tc<DIM, FRAC> : k_stress_sur<DIM, FRAC>;
+    const size_t smem = tc ? sizeof(MlpTcSmem) : sizeof(MlpSmem);
+    static bool attr_set[2][2][2] = {};
+    if (!attr_set[tc][DIM - 2][FRAC]) {
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[tc][DIM - 2][FRAC] = true;
     }
+    const int threads = tc ? 128 * kTcGroups : 128;
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->p.device));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sizeof(MlpSmem)));
-    const int64_t tiles = (c->n + 127) / 128;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, tiles));
-    kern<<<grid, 128, sizeof(MlpSmem), c->stream>>>(a, sur_dev(c), c->sur_exact, c->sur_count);
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const int64_t ctas = (c->n + threads - 1) / threads;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, ctas));
+    kern<<<grid, threads, smem, c->stream>>>(a, sur_dev(c), c->sur_exact, c->sur_count);
     CKL();
     k_stress_exact<DIM, FRAC, kThreads><<<blocks_for(c->n), kThreads, 0, c->stream>>>(a, c->sur_exact);
     CKL();
@@ -1741,6 +1745,8 @@ struct tlsph_mlp {
     float *Yn, *Z0, *Z1, *Z2, *out, *dout, *dA, *dZf, *loss;
     double *stat_d;
     float *stat_f;
+    int *tc_flag;           // tensor-core waits that ran out in the last forward
+    int tensor_path = TLSPH_TENSOR_TCGEN05;
     int64_t t = 0;
 };
 
@@ -1871,7 +1877,7 @@ tlsph_status tlsph_mlp_create(int device, void *cuda_stream, int batch, tlsph_ml
     MAX(m->doutb, B * kOut * 2) MAX(m->doutT, B * kOut * 2)
     MAX(m->Yn, B * kOut * 4) MAX(m->Z0, B * kHid * 4) MAX(m->Z1, B * kHid * 4) MAX(m->Z2, B * kHid * 4)
     MAX(m->out, B * kOut * 4) MAX(m->dout, B * kOut * 4) MAX(m->dA, B * kHid * 4) MAX(m->dZf, B * kHid * 4)
-    MAX(m->loss, 4) MAX(m->stat_d, 64 * 8) MAX(m->stat_f, 64 * 4)
+    MAX(m->loss, 4) MAX(m->stat_d, 64 * 8) MAX(m->stat_f, 64 * 4) MAX(m->tc_flag, 4)
 #undef MAX
     if (st != TLSPH_OK) {
         tlsph_mlp_destroy(m);
@@ -2044,6 +2050,27 @@ tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y
     d.env_lo = m->norm + 64;
     d.env_hi = m->norm + 80;
     d.enabled = 1;
+    if (m->tensor_path == TLSPH_TENSOR_TCGEN05) {
+        static bool attr_tc = false;
+        if (!attr_tc) {
+            MK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(MlpTcSmem)));
+            attr_tc = true;
+        }
+        int nsm = 0, per_sm = 0;
+        MK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+        MK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_forward_tc, 128 * kTcGroups, sizeof(MlpTcSmem)));
+        const int64_t ctas = (n + 128 * kTcGroups - 1) / (128 * kTcGroups);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, ctas));
+        MK(cudaMemsetAsync(m->tc_flag, 0, sizeof(int), m->stream));
+        k_mlp_forward_tc<<<grid, 128 * kTcGroups, sizeof(MlpTcSmem), m->stream>>>(n, x, y, d, outside, m->tc_flag);
+        MK(cudaGetLastError());
+        int h = 0;
+        MK(cudaMemcpyAsync(&h, m->tc_flag, sizeof h, cudaMemcpyDeviceToHost, m->stream));
+        MK(cudaStreamSynchronize(m->stream));
+        if (h) return mfail(m, TLSPH_ERR_TIMEOUT, "a tensor-core wait ran out");
+        return TLSPH_OK;
+    }
     static bool attr = false;
     if (!attr) {
         MK(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
@@ -2052,6 +2079,13 @@ tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y
     k_mlp_forward<<<(unsigned)((n + 127) / 128), 128, sizeof(MlpSmem), m->stream>>>(n, x, y, d, outside);
     MK(cudaGetLastError());
     MK(cudaStreamSynchronize(m->stream));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_mlp_set_tensor_path(tlsph_mlp *m, int path) {
+    if (!m) return TLSPH_ERR_ARG;
+    if (path != TLSPH_TENSOR_MMA_SYNC && path != TLSPH_TENSOR_TCGEN05) return mfail(m, TLSPH_ERR_ARG, "unknown tensor path");
+    m->tensor_path = path;
     return TLSPH_OK;
 }
 
@@ -2080,6 +2114,7 @@ tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
     CK(cudaStreamSynchronize(c->stream));
     c->sur_on = true;
     c->sur_scope = scope;
+    c->sur_tensor = m->tensor_path;
     c->mode = TLSPH_MODE_LAUNCH;
     drop_graph(c);
     return TLSPH_OK;

@@ -35,9 +35,11 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_mlp_destroy", "tlsph_mlp_last_error", "tlsph_mlp_set_params", "tlsph_mlp_get_params",
            "tlsph_mlp_set_normalization", "tlsph_mlp_get_normalization", "tlsph_mlp_fit_normalization",
            "tlsph_mlp_train_step", "tlsph_mlp_gradients", "tlsph_mlp_forward", "tlsph_set_surrogate",
-           "tlsph_surrogate_counts", "tlsph_j2_samples"]
+           "tlsph_surrogate_counts", "tlsph_j2_samples",
+           "tlsph_mlp_set_tensor_path"]
 MLP_NUM_PARAMS = 37264
 SURROGATE_ALL, SURROGATE_PLASTIC = 0, 1
+TENSOR_MMA_SYNC, TENSOR_TCGEN05 = 0, 1
 NOALLOC_MAX_PARTICLES = 131072
 
 
@@ -121,6 +123,7 @@ def load_library(path: str = LIB_PATH):
         "tlsph_set_surrogate": (C.c_int, [P, P, C.c_int]),
         "tlsph_surrogate_counts": (C.c_int, [P, I64]),
         "tlsph_j2_samples": (C.c_int, [P, C.c_int, C.c_int, C.c_uint, V, V, V, C.c_int64, I64]),
+        "tlsph_mlp_set_tensor_path": (C.c_int, [P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -347,6 +350,10 @@ class MLP:
         a = np.zeros(MLP_NUM_PARAMS, np.float32)
         self._ck(self.lib.tlsph_mlp_get_params(self.h, a.ctypes.data), "get_params")
         return a
+
+    def set_tensor_path(self, path):
+        """TENSOR_TCGEN05 (default) or TENSOR_MMA_SYNC for the inference kernels."""
+        self._ck(self.lib.tlsph_mlp_set_tensor_path(self.h, int(path)), "set_tensor_path")
 
     def set_normalization(self, norm):
         a = np.ascontiguousarray(norm, np.float32).reshape(96)

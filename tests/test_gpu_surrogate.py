@@ -31,10 +31,12 @@ def torch():
     return t
 
 
-def test_forward_matches_reference(torch):
+@pytest.mark.parametrize("path", [tlsph.TENSOR_TCGEN05, tlsph.TENSOR_MMA_SYNC])
+def test_forward_matches_reference(torch, path):
     params = ref.init_params(seed=3)
     params = [(bf16_round(W).astype(np.float64), b) for W, b in params]
     net = tlsph.MLP(batch=256)
+    net.set_tensor_path(path)
     net.set_params(tlsph.pack_params(params))
     net.set_normalization(identity_norm())
     x = np.random.default_rng(0).normal(size=(300, 16)).astype(np.float32)
@@ -44,6 +46,25 @@ def test_forward_matches_reference(torch):
     out_ref, _ = ref.forward(params, bf16_round(x).astype(np.float64))
     err = np.linalg.norm(yd.cpu().numpy() - out_ref) / np.linalg.norm(out_ref)
     assert err < 1e-2, err
+
+
+def test_tensor_paths_agree(torch):
+    """tcgen05 (TMEM accumulators) and mma.sync give the same network output up to summation
+    order, on a ragged row count that spans many tiles."""
+    params = ref.init_params(seed=9)
+    net = tlsph.MLP(batch=256)
+    net.set_params(tlsph.pack_params(params))
+    net.set_normalization(identity_norm())
+    x = torch.from_numpy(np.random.default_rng(4).normal(size=(100_003, 16)).astype(np.float32)).cuda()
+    outs = []
+    for path in (tlsph.TENSOR_TCGEN05, tlsph.TENSOR_MMA_SYNC):
+        net.set_tensor_path(path)
+        y = torch.empty_like(x)
+        net.forward(x, y)
+        outs.append(y.cpu().numpy())
+    err = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
+    print("tcgen05 vs mma.sync: rel-L2", err, "bit-identical", np.array_equal(outs[0], outs[1]))
+    assert np.all(np.isfinite(outs[0])) and err < 2e-3, err
 
 
 def test_gradients_match_reference(torch):
@@ -116,22 +137,26 @@ def test_fallback_outside_envelope_is_the_exact_step(torch):
     assert used == 0 and fallback == 120 * case.n and elastic == 0
 
 
-@pytest.mark.parametrize("scope", [tlsph.SURROGATE_ALL, tlsph.SURROGATE_PLASTIC])
-def test_surrogate_step_tracks_exact_step(trained, scope):
+@pytest.mark.parametrize("scope,path", [(tlsph.SURROGATE_ALL, tlsph.TENSOR_TCGEN05),
+                                        (tlsph.SURROGATE_PLASTIC, tlsph.TENSOR_TCGEN05),
+                                        (tlsph.SURROGATE_ALL, tlsph.TENSOR_MMA_SYNC)])
+def test_surrogate_step_tracks_exact_step(trained, scope, path):
     """400 steps with the network in the J2 update stay within 1% (rel-L2 of u) of the exact run.
     The held-out stress error is ~0.5%; the state enters as increments, so the error does not
     random-walk in the state."""
     case, net, _, _, _ = trained
     exact = tlsph.from_case(case)
     sur = tlsph.from_case(case)
+    net.set_tensor_path(path)
     sur.set_surrogate(net, scope)
+    net.set_tensor_path(tlsph.TENSOR_TCGEN05)
     exact.step(400)
     sur.step(400)
     used, outside, elastic = sur.surrogate_counts()
     ue, us = exact.read_state("U"), sur.read_state("U")
     err = float(np.linalg.norm(us - ue) / np.linalg.norm(ue))
     ep_e, ep_s = exact.read_state("EPSP"), sur.read_state("EPSP")
-    print("scope", scope, "surrogate vs exact: rel-L2(u)", err, "max |d eps_p|", np.abs(ep_s - ep_e).max(),
+    print("scope", scope, "path", path, "surrogate vs exact: rel-L2(u)", err, "max |d eps_p|", np.abs(ep_s - ep_e).max(),
           "rows by network", used, "outside", outside, "elastic", elastic)
     assert used + outside + elastic == 400 * case.n
     if scope == tlsph.SURROGATE_ALL:
