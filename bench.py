@@ -44,6 +44,11 @@ SHAPE = (128, 128, 64)
 FALLBACK_HBM_GBS = 6400.0
 FALLBACK_BF16_TFLOPS = 1400.0
 MLP_FLOP_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16)  # 73,728
+# FP32 operations per neighbour pair of the 3D J2 step with viscosity, counted from the loop bodies
+# (an FMA counts 2; rsqrt 1): k_gradient 38; k_pass2 54, plus 15 for a pair in relative compression
+# (taken as half of the pairs).  Peak: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz.
+FLOP_PER_PAIR = {"gradient": 38.0, "pass2": 54.0 + 0.5 * 15.0}
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 # DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
 # of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
@@ -444,6 +449,13 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
                      "kernel_ms": kms, "kernel_bytes": kb,
                      "step_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},
+        "alu": {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                "flop_per_pair": FLOP_PER_PAIR,
+                "kernel": {k: (FLOP_PER_PAIR[k] * nnz / (kms[k] * 1e-3) / 1e12) for k in FLOP_PER_PAIR},
+                "kernel_frac": {k: (FLOP_PER_PAIR[k] * nnz / (kms[k] * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
+                                for k in FLOP_PER_PAIR},
+                "step": sum(FLOP_PER_PAIR.values()) * nnz / (ms / args.steps * 1e-3) / 1e12},
         "clocks": clk.summary(),
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps},
