@@ -65,7 +65,8 @@ template <typename T> struct StepArgs {
     const unsigned *nmask;  // stencil layout: row masks, ceil(nsten / 32) arrays of n
     const int *soff;       // stencil differences j - i, ascending
     const int2 *runs;      // runs of consecutive differences: (first difference, first entry | length << 8)
-    int nsten, nruns;      // stencil entries (0 = SELL-32 rows) and runs
+    int nsten, nruns;      // stencil entries (0 = SELL-32 rows) and runs (the most of any table)
+    int sten_groups;       // stencil tables: 1, or one per specimen (kMaxStencil entries each)
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
     const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) (reference configuration)
     const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, m0 in 3D)

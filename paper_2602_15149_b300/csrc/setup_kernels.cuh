@@ -345,43 +345,50 @@ __global__ void k_sell_pad(int64_t total, int *sell, int v) {
 // ---------------------------------------------------------------- stencil layout
 // On a lattice in lattice order (one particle per fine cell, cells filling a box) the index
 // difference j - i of a neighbour pair takes few distinct values: the lattice offsets within
-// the support.  D = the sorted distinct differences; when |D| <= kMaxStencil every row is a
-// bit mask over D (bit s set iff (i, i + D[s]) is a pair).  A row visits D in ascending order,
-// which is the ascending column order of its CSR row: both layouts visit the same pairs in
-// the same order.  The k-th visit of 32 consecutive rows reads 32 consecutive particles.
+// the support.  Per group of rows (a specimen: its own box, so its own row pitch), D = the sorted
+// distinct differences; when every group has at most kMaxStencil of them, every row is a bit
+// mask over its group's D (bit s set iff (i, i + D[s]) is a pair).  A row visits D in ascending
+// order, which is the ascending column order of its CSR row: both layouts visit the same pairs in
+// the same order.  The k-th visit of 32 consecutive rows of a group reads 32 consecutive particles.
 constexpr int kMaxStencil = 128;
 constexpr int kMaxRun = 8;  // longest run of consecutive differences the step kernels unroll
-constexpr int64_t kStencilSpan = (int64_t)1 << 22;  // |j - i| the difference bitmap covers
 
-// Set bit (d + kStencilSpan) of the bitmap for every pair difference d; *far counts pairs
-// beyond the span.  The bit is read first so that repeated differences cost no atomic.
-__global__ void k_stencil_diffs(int64_t n, const int64_t *row_ptr, const int *col, unsigned *bitmap, int *far) {
+// Set bit (d + span) of group grp[i]'s bitmap (words_per_group words each) for every pair
+// difference d of row i; *far counts pairs beyond +-span.  The bit is read first so that repeated
+// differences cost no atomic.
+__global__ void k_stencil_diffs(int64_t n, const int64_t *row_ptr, const int *col, const int *grp, int64_t span,
+                                int64_t words_per_group, unsigned *bitmap, int *far) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    unsigned *bm = bitmap + (grp ? (int64_t)grp[i] : 0) * words_per_group;
     for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
         const int64_t d = (int64_t)col[k] - i;
-        if (d < -kStencilSpan || d >= kStencilSpan) {
+        if (d < -span || d >= span) {
             atomicAdd(far, 1);
             continue;
         }
-        const uint64_t b = (uint64_t)(d + kStencilSpan);
+        const uint64_t b = (uint64_t)(d + span);
         const unsigned bit = 1u << (b & 31);
-        if (!(((volatile unsigned *)bitmap)[b >> 5] & bit)) atomicOr(&bitmap[b >> 5], bit);
+        if (!(((volatile unsigned *)bm)[b >> 5] & bit)) atomicOr(&bm[b >> 5], bit);
     }
 }
 
-// Row masks over D (ascending, nsten entries): words w = 0 .. ceil(nsten / 32) - 1 at
-// mask[w n + i].  A difference missing from D or a row out of ascending order counts in *bad.
-__global__ void k_stencil_mask(int64_t n, const int64_t *row_ptr, const int *col, const int *D, int nsten,
-                               unsigned *mask, int *bad) {
+// Row masks over the row's group's D (D: kMaxStencil entries per group, nsten[g] used): words
+// w = 0 .. nw - 1 at mask[w n + i].  A difference missing from D or a row out of ascending order
+// counts in *bad.
+__global__ void k_stencil_mask(int64_t n, const int64_t *row_ptr, const int *col, const int *grp, const int *D,
+                               const int *nsten_g, int nw, unsigned *mask, int *bad) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int g = grp ? grp[i] : 0;
+    const int *Dg = D + (int64_t)g * kMaxStencil;
+    const int nsten = nsten_g[g];
     unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     int s = 0;
     for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
         const int64_t d = (int64_t)col[k] - i;
-        while (s < nsten && (int64_t)D[s] < d) s++;
-        if (s == nsten || (int64_t)D[s] != d) {
+        while (s < nsten && (int64_t)Dg[s] < d) s++;
+        if (s == nsten || (int64_t)Dg[s] != d) {
             atomicAdd(bad, 1);
             return;
         }
@@ -394,7 +401,6 @@ __global__ void k_stencil_mask(int64_t n, const int64_t *row_ptr, const int *col
         }
         s++;  // strictly ascending rows: the next pair lies further on
     }
-    const int nw = (nsten + 31) / 32;
     mask[i] = m0;
     if (nw > 1) mask[n + i] = m1;
     if (nw > 2) mask[2 * n + i] = m2;

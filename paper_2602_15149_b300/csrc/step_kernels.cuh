@@ -42,7 +42,8 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // Visit the neighbours j of particle i in ascending sorted index, calling pair(j, on).  Stencil
 // layout (a.nsten > 0): the warp's 32 consecutive rows walk the stencil differences together
 // and row i takes the entries its mask keeps, so the k-th reads of the warp are consecutive
-// particles.  The differences come in runs of consecutive values (one row of a lattice
+// particles (one table per specimen when each specimen has its own row pitch; a warp that
+// spans two specimens reads two tables).  The differences come in runs of consecutive values (one row of a lattice
 // stencil each), so the k-th entry of a run reads at a fixed offset from the run's base.  An
 // entry the mask drops comes as pair(i + D, false), reading another particle or the zero halo
 // around the gathered arrays: the body runs without a branch (the unrolled run issues its
@@ -52,11 +53,13 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // SELL-32 layout otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
 template <int UNROLL = 4, bool SKIP = false, bool RUNS = true, typename T, typename Pair>
 __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, Pair &&pair) {
+    // the row's stencil table: its specimen's, when each specimen has its own
+    const int tab = a.nsten > 0 && a.sten_groups > 1 ? a.spec[i] * kMaxStencil : 0;
     if (!RUNS && a.nsten > 0) {
         for (int s0 = 0; s0 < a.nsten; s0 += 32) {
             const unsigned m = __ldg(a.nmask + (int64_t)(s0 >> 5) * a.n + i);
             const int lim = min(32, a.nsten - s0);
-            const int *off = a.soff + s0;
+            const int *off = a.soff + tab + s0;
 #pragma unroll UNROLL
             for (int b = 0; b < lim; b++) {
                 const bool on = (m >> b) & 1u;
@@ -70,7 +73,7 @@ __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, 
 #pragma unroll
         for (int q = 0; q < 4; q++) mw[q] = q < nw ? __ldg(a.nmask + (int64_t)q * a.n + i) : 0u;
         for (int r = 0; r < a.nruns; r++) {
-            const int2 rr = __ldg(a.runs + r);
+            const int2 rr = __ldg(a.runs + tab + r);
             const int s0 = rr.y & 255, len = rr.y >> 8;
             const int w0 = s0 >> 5;
             const unsigned lo = w0 == 0 ? mw[0] : w0 == 1 ? mw[1] : w0 == 2 ? mw[2] : mw[3];

@@ -65,6 +65,7 @@ struct tlsph_ctx {
     int *soff = nullptr;          // stencil differences j - i, ascending
     int2 *runs = nullptr;         // runs of consecutive differences
     int nruns = 0;
+    int sten_groups = 1;          // stencil tables (one per specimen)
     int64_t halo = 0;             // zero elements before and after each gathered array (stencil layout)
     unsigned *nmask = nullptr;    // row masks over the stencil
     int layout = TLSPH_LAYOUT_AUTO;
@@ -163,6 +164,7 @@ void free_device(tlsph_ctx *c) {
     c->S1 = nullptr;
     c->nsten = 0;
     c->nruns = 0;
+    c->sten_groups = 1;
     c->halo = 0;
     c->runs = nullptr;
     c->soff = nullptr;
@@ -268,6 +270,7 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     const bool sten = c->layout == TLSPH_LAYOUT_AUTO && c->nsten > 0;
     a.nsten = sten ? c->nsten : 0;
     a.nruns = sten ? c->nruns : 0;
+    a.sten_groups = c->sten_groups;
     a.runs = sten ? c->runs : nullptr;
     a.soff = sten ? c->soff : nullptr;
     a.nmask = sten ? c->nmask : nullptr;
@@ -336,60 +339,83 @@ double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
     return grad + stress + p2;
 }
 
-// Stencil layout of the CSR rows (lattice inputs): the distinct pair differences j - i,
-// kept when there are at most kMaxStencil of them, and one bit mask per row.  Otherwise the
-// context keeps the SELL-32 rows only.
+// Stencil layout of the CSR rows (lattice inputs), one table per specimen: the distinct pair
+// differences j - i of the specimen's rows, kept when no specimen has more than kMaxStencil of
+// them, and one bit mask per row.  Otherwise the context keeps the SELL-32 rows only.
 tlsph_status build_stencil(tlsph_ctx *c) {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
     c->nsten = 0;
     if (n < 1 || c->nnz < 1) return TLSPH_OK;
-    const int64_t words = 2 * kStencilSpan / 32;
+    const int G = std::max(c->nspec, 1);
+    // difference bitmaps: 2^25 bits in all, 2^14 .. 2^23 per specimen
+    int64_t bits = (int64_t)1 << 23;
+    while (bits > ((int64_t)1 << 14) && bits * G > ((int64_t)1 << 25)) bits >>= 1;
+    const int64_t span = bits / 2, wpg = bits / 32;
     unsigned *bitmap;
     int *cnt;
-    DA(bitmap, words * sizeof(unsigned));
+    DA(bitmap, (size_t)G * wpg * sizeof(unsigned));
     DA(cnt, 2 * sizeof(int));
-    CK(cudaMemsetAsync(bitmap, 0, words * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(bitmap, 0, (size_t)G * wpg * sizeof(unsigned), s));
     CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
-    k_stencil_diffs<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, bitmap, cnt);
+    const int *grp = G > 1 ? c->spec : nullptr;
+    k_stencil_diffs<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, grp, span, wpg, bitmap, cnt);
     CKL();
-    std::vector<unsigned> hb(words);
+    std::vector<unsigned> hb((size_t)G * wpg);
     int hc[2] = {0, 0};
-    CK(cudaMemcpyAsync(hb.data(), bitmap, words * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hb.data(), bitmap, hb.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hc[0] != 0) return TLSPH_OK;
-    std::vector<int> D;
-    for (int64_t w = 0; w < words; w++)
-        for (unsigned m = hb[w]; m; m &= m - 1) {
-            if ((int)D.size() == kMaxStencil) return TLSPH_OK;
-            D.push_back((int)(32 * w + __builtin_ctz(m) - kStencilSpan));
-        }
-    const int nw = ((int)D.size() + 31) / 32;
+    std::vector<int> D((size_t)G * kMaxStencil, 0), nst(G, 0);
+    int nmax = 0;
+    int64_t halo = 0;
+    for (int g = 0; g < G; g++) {
+        const unsigned *bm = hb.data() + (size_t)g * wpg;
+        for (int64_t w = 0; w < wpg; w++)
+            for (unsigned m = bm[w]; m; m &= m - 1) {
+                if (nst[g] == kMaxStencil) return TLSPH_OK;
+                const int d = (int)(32 * w + __builtin_ctz(m) - span);
+                D[(size_t)g * kMaxStencil + nst[g]++] = d;
+                halo = std::max<int64_t>(halo, std::abs((int64_t)d));
+            }
+        nmax = std::max(nmax, nst[g]);
+    }
+    if (nmax == 0) return TLSPH_OK;
+    const int nw = (nmax + 31) / 32;
+    int *nst_d;
     DA(c->soff, D.size() * sizeof(int));
+    DA(nst_d, G * sizeof(int));
     DA(c->nmask, (size_t)nw * n * sizeof(unsigned));
     CK(cudaMemcpyAsync(c->soff, D.data(), D.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    k_stencil_mask<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, c->soff, (int)D.size(), c->nmask,
+    CK(cudaMemcpyAsync(nst_d, nst.data(), G * sizeof(int), cudaMemcpyHostToDevice, s));
+    k_stencil_mask<<<blocks_for(n), kThreads, 0, s>>>(n, c->row_ptr, c->col, grp, c->soff, nst_d, nw, c->nmask,
                                                       cnt + 1);
     CKL();
     CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hc[1] != 0) return TLSPH_OK;
-    // runs of consecutive differences (at most kMaxRun long)
-    std::vector<int2> runs;
-    int64_t halo = 0;
-    for (size_t a = 0; a < D.size();) {
-        size_t e = a + 1;
-        while (e < D.size() && D[e] == D[e - 1] + 1 && (int)(e - a) < kMaxRun) e++;
-        runs.push_back(make_int2(D[a], (int)a | ((int)(e - a) << 8)));
-        a = e;
+    // runs of consecutive differences (at most kMaxRun long), kMaxStencil slots per specimen; unused
+    // slots have length 0
+    std::vector<int2> runs((size_t)G * kMaxStencil, make_int2(0, 0));
+    int rmax = 0;
+    for (int g = 0; g < G; g++) {
+        const int *Dg = D.data() + (size_t)g * kMaxStencil;
+        int r = 0;
+        for (int a = 0; a < nst[g];) {
+            int e = a + 1;
+            while (e < nst[g] && Dg[e] == Dg[e - 1] + 1 && e - a < kMaxRun) e++;
+            runs[(size_t)g * kMaxStencil + r++] = make_int2(Dg[a], a | ((e - a) << 8));
+            a = e;
+        }
+        rmax = std::max(rmax, r);
     }
-    for (int d : D) halo = std::max<int64_t>(halo, std::abs((int64_t)d));
     DA(c->runs, runs.size() * sizeof(int2));
     CK(cudaMemcpyAsync(c->runs, runs.data(), runs.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-    c->nruns = (int)runs.size();
+    c->nruns = rmax;
     c->halo = halo;
-    c->nsten = (int)D.size();
+    c->sten_groups = G;
+    c->nsten = nmax;
     return TLSPH_OK;
 }
 

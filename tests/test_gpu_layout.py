@@ -1,6 +1,6 @@
-"""Neighbour layouts: the stencil layout (lattice inputs) and the SELL-32 rows visit the same
-pairs in the same order, so whole steps agree bit for bit; inputs whose pair differences take
-more than 128 values keep the SELL-32 rows."""
+"""Neighbour layouts: the stencil layout (lattice inputs; one table per specimen in a batch) and
+the SELL-32 rows visit the same pairs in the same order, so whole steps agree bit for bit; inputs
+whose pair differences take more than 128 values keep the SELL-32 rows."""
 import numpy as np
 import pytest
 
@@ -43,10 +43,13 @@ def test_stencil_size_of_the_lattices():
     assert 92 <= n3 <= 122 and 24 <= n2 <= 28, (n3, n2)
 
 
-def test_batched_specimens_bit_identical():
-    # a few small specimens: the union of their lattice offsets may still fit the stencil
-    case = W.batched(nspec=6, n_min=200, n_max=1500, seed=3)
+@pytest.mark.parametrize("nspec", [6, 40])
+def test_batched_specimens_bit_identical(nspec):
+    # each specimen is a lattice with its own row pitch: one stencil table per specimen (2D: the
+    # 24 offsets inside the support, plus the 4 at its edge when rounding brings them in)
+    case = W.batched(nspec=nspec, n_min=200, n_max=1500, seed=3)
     auto = tlsph.from_case(case)
+    assert 24 <= auto.get_info()["stencil"] <= 28
     csr = tlsph.from_case(case)
     csr.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, tlsph.LAYOUT_CSR)
     auto.step(100)
