@@ -587,7 +587,7 @@ template <typename T> __device__ __forceinline__ void dev_finalize(const StepArg
 }
 
 template <typename T, int DIM, bool FRAC, bool VISC, int BS>
-__global__ void __launch_bounds__(BS, 1024 / BS) k_pass2(StepArgs<T> a) {
+__global__ void __launch_bounds__(BS, 896 / BS) k_pass2(StepArgs<T> a) {
     __shared__ bool s_last;
     const int i = blockIdx.x * BS + threadIdx.x;
     const bool active = i < a.n;
