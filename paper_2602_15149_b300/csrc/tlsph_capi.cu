@@ -120,6 +120,24 @@ tlsph_status fail(tlsph_ctx *c, tlsph_status st, const char *fmt, ...) {
     return st;
 }
 
+// Makes the context's device current for the duration of a call and restores the caller's.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (dev < 0) return;
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) cudaGetLastError();
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 #define CK(call)                                                                                     \
     do {                                                                                             \
         cudaError_t e_ = (call);                                                                     \
@@ -806,11 +824,8 @@ template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const
     const bool tc = c->sur_tensor == TLSPH_TENSOR_TCGEN05;
     auto kern = tc ? k_stress_sur_tc<DIM, FRAC> : k_stress_sur<DIM, FRAC>;
     const size_t smem = tc ? sizeof(MlpTcSmem) : sizeof(MlpSmem);
-    static bool attr_set[2][2][2] = {};
-    if (!attr_set[tc][DIM - 2][FRAC]) {
-        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[tc][DIM - 2][FRAC] = true;
-    }
+    // per launch: the attribute belongs to the current device, and setting it costs no device work
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int threads = tc ? 128 * kTcGroups : 128;
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->p.device));
@@ -1371,6 +1386,7 @@ tlsph_status tlsph_add_notch(tlsph_ctx *c, const double quad[12]) {
 }
 
 tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (c->n <= 0 || c->mats.empty()) return fail(c, TLSPH_ERR_STATE, "no particles");
     cudaSetDevice(c->p.device);
@@ -1380,6 +1396,7 @@ tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
 }
 
 tlsph_status tlsph_step_async(tlsph_ctx *c, int64_t nsteps) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before step");
     if (nsteps < 0) return fail(c, TLSPH_ERR_ARG, "negative step count");
@@ -1387,6 +1404,7 @@ tlsph_status tlsph_step_async(tlsph_ctx *c, int64_t nsteps) {
 }
 
 tlsph_status tlsph_sync(tlsph_ctx *c) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     return check_flags(c);
@@ -1406,6 +1424,7 @@ int64_t tlsph_field_bytes(const tlsph_ctx *c, int field) {
 }
 
 tlsph_status tlsph_read_state(tlsph_ctx *c, int field, void *dst, size_t bytes, int dst_is_device) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before read_state");
     int64_t need = tlsph_field_bytes(c, field);
@@ -1439,6 +1458,7 @@ tlsph_status tlsph_read_state(tlsph_ctx *c, int field, void *dst, size_t bytes, 
 }
 
 tlsph_status tlsph_write_state(tlsph_ctx *c, int field, const void *src, size_t bytes, int src_is_device) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before write_state");
     int64_t need = tlsph_field_bytes(c, field);
@@ -1468,12 +1488,14 @@ tlsph_status tlsph_write_state(tlsph_ctx *c, int field, const void *src, size_t 
 }
 
 tlsph_status tlsph_energies(tlsph_ctx *c, double out[6]) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !out) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     return c->p.precision == TLSPH_FP64 ? energies_impl<double>(c, out) : energies_impl<float>(c, out);
 }
 
 tlsph_status tlsph_time(tlsph_ctx *c, int specimen, double *t, double *dt) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !t || !dt) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     if (specimen < 0 || specimen >= c->nspec) return fail(c, TLSPH_ERR_ARG, "specimen out of range");
@@ -1486,6 +1508,7 @@ tlsph_status tlsph_time(tlsph_ctx *c, int specimen, double *t, double *dt) {
 int64_t tlsph_nnz(const tlsph_ctx *c) { return (c && c->built) ? c->nnz : -1; }
 
 tlsph_status tlsph_neighbours(tlsph_ctx *c, int64_t *row_ptr, int32_t *col, int64_t cap) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !row_ptr || !col) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     if (cap < c->nnz) return fail(c, TLSPH_ERR_ARG, "cap < nnz (%lld)", (long long)c->nnz);
@@ -1514,6 +1537,7 @@ tlsph_status tlsph_neighbours(tlsph_ctx *c, int64_t *row_ptr, int32_t *col, int6
 }
 
 tlsph_status tlsph_permutation(tlsph_ctx *c, int64_t *perm) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !perm) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     std::vector<int> p(c->n);
@@ -1524,6 +1548,7 @@ tlsph_status tlsph_permutation(tlsph_ctx *c, int64_t *perm) {
 }
 
 tlsph_status tlsph_get_info(tlsph_ctx *c, tlsph_info *out) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !out) return TLSPH_ERR_ARG;
     out->steps = c->steps;
     out->kernel_launches = c->launches;
@@ -1543,6 +1568,7 @@ tlsph_status tlsph_get_info(tlsph_ctx *c, tlsph_info *out) {
 }
 
 tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (option == TLSPH_OPT_KERNEL_TIMING) {
         if (c->timing && !value) {
@@ -1583,6 +1609,7 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
 }
 
 tlsph_status tlsph_autotune(tlsph_ctx *c, int trial_steps, tlsph_tuning *best, tlsph_tuning *all) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before autotune");
     if (trial_steps < 1) return fail(c, TLSPH_ERR_ARG, "trial_steps must be >= 1");
@@ -1591,6 +1618,7 @@ tlsph_status tlsph_autotune(tlsph_ctx *c, int trial_steps, tlsph_tuning *best, t
 }
 
 tlsph_status tlsph_kernel_times(tlsph_ctx *c, double ms[3], int64_t count[3]) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !ms || !count) return TLSPH_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream));
     collect_timing(c);
@@ -1942,6 +1970,7 @@ void tlsph_mlp_destroy(tlsph_mlp *m) {
 const char *tlsph_mlp_last_error(const tlsph_mlp *m) { return m ? m->err.c_str() : "null network"; }
 
 tlsph_status tlsph_mlp_set_params(tlsph_mlp *m, const float *params) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !params) return TLSPH_ERR_ARG;
     MK(cudaMemcpyAsync(m->P, params, kNumParams * 4, cudaMemcpyHostToDevice, m->stream));
     MK(cudaMemsetAsync(m->m, 0, kNumParams * 4, m->stream));
@@ -1954,6 +1983,7 @@ tlsph_status tlsph_mlp_set_params(tlsph_mlp *m, const float *params) {
 }
 
 tlsph_status tlsph_mlp_get_params(tlsph_mlp *m, float *params) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !params) return TLSPH_ERR_ARG;
     MK(cudaMemcpyAsync(params, m->P, kNumParams * 4, cudaMemcpyDeviceToHost, m->stream));
     MK(cudaStreamSynchronize(m->stream));
@@ -1961,6 +1991,7 @@ tlsph_status tlsph_mlp_get_params(tlsph_mlp *m, float *params) {
 }
 
 tlsph_status tlsph_mlp_set_normalization(tlsph_mlp *m, const float norm[96]) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !norm) return TLSPH_ERR_ARG;
     for (int c = 0; c < 16; c++)
         if (!(norm[16 + c] > 0.0f) || !(norm[48 + c] > 0.0f)) return mfail(m, TLSPH_ERR_ARG, "std must be > 0");
@@ -1970,6 +2001,7 @@ tlsph_status tlsph_mlp_set_normalization(tlsph_mlp *m, const float norm[96]) {
 }
 
 tlsph_status tlsph_mlp_get_normalization(tlsph_mlp *m, float norm[96]) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !norm) return TLSPH_ERR_ARG;
     MK(cudaMemcpyAsync(norm, m->norm, 96 * 4, cudaMemcpyDeviceToHost, m->stream));
     MK(cudaStreamSynchronize(m->stream));
@@ -1977,6 +2009,7 @@ tlsph_status tlsph_mlp_get_normalization(tlsph_mlp *m, float norm[96]) {
 }
 
 tlsph_status tlsph_mlp_fit_normalization(tlsph_mlp *m, int64_t n, const float *x, const float *y, float margin) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !x || !y || n < 2 || !(margin >= 0.0f)) return TLSPH_ERR_ARG;
     cudaStream_t s = m->stream;
     float st_h[6][16];
@@ -2037,6 +2070,7 @@ tlsph_status tlsph_mlp_fit_normalization(tlsph_mlp *m, int64_t n, const float *x
 }
 
 tlsph_status tlsph_mlp_gradients(tlsph_mlp *m, const float *x, const float *y, float *grads, float *loss) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !x || !y) return TLSPH_ERR_ARG;
     tlsph_status st = mlp_fwd_bwd(m, x, y);
     if (st != TLSPH_OK) return st;
@@ -2047,6 +2081,7 @@ tlsph_status tlsph_mlp_gradients(tlsph_mlp *m, const float *x, const float *y, f
 }
 
 tlsph_status tlsph_mlp_train_step(tlsph_mlp *m, const float *x, const float *y, float lr, float *loss) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !x || !y || !(lr > 0.0f)) return TLSPH_ERR_ARG;
     tlsph_status st = mlp_fwd_bwd(m, x, y);
     if (st != TLSPH_OK) return st;
@@ -2065,6 +2100,7 @@ tlsph_status tlsph_mlp_train_step(tlsph_mlp *m, const float *x, const float *y, 
 }
 
 tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y, int32_t *outside) {
+    DeviceScope ds_(m ? m->device : -1);
     if (!m || !x || !y || n < 1) return TLSPH_ERR_ARG;
     SurrogateDev d{};
     d.W = m->Wb;
@@ -2077,12 +2113,7 @@ tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y
     d.env_hi = m->norm + 80;
     d.enabled = 1;
     if (m->tensor_path == TLSPH_TENSOR_TCGEN05) {
-        static bool attr_tc = false;
-        if (!attr_tc) {
-            MK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(MlpTcSmem)));
-            attr_tc = true;
-        }
+        MK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpTcSmem)));
         int nsm = 0, per_sm = 0;
         MK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
         MK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_forward_tc, 128 * kTcGroups, sizeof(MlpTcSmem)));
@@ -2097,11 +2128,7 @@ tlsph_status tlsph_mlp_forward(tlsph_mlp *m, int64_t n, const float *x, float *y
         if (h) return mfail(m, TLSPH_ERR_TIMEOUT, "a tensor-core wait ran out");
         return TLSPH_OK;
     }
-    static bool attr = false;
-    if (!attr) {
-        MK(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
-        attr = true;
-    }
+    MK(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)));
     k_mlp_forward<<<(unsigned)((n + 127) / 128), 128, sizeof(MlpSmem), m->stream>>>(n, x, y, d, outside);
     MK(cudaGetLastError());
     MK(cudaStreamSynchronize(m->stream));
@@ -2116,6 +2143,7 @@ tlsph_status tlsph_mlp_set_tensor_path(tlsph_mlp *m, int path) {
 }
 
 tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before set_surrogate");
     if (!m) {
@@ -2147,6 +2175,7 @@ tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
 }
 
 tlsph_status tlsph_surrogate_counts(tlsph_ctx *c, int64_t counts[3]) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !counts) return TLSPH_ERR_ARG;
     unsigned long long h[3] = {0, 0, 0};
     if (c->sur_count) {
@@ -2159,6 +2188,7 @@ tlsph_status tlsph_surrogate_counts(tlsph_ctx *c, int64_t counts[3]) {
 
 tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plastic, unsigned salt, float *x,
                               float *y, float *pnorm, int64_t cap, int64_t *count) {
+    DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !x || !y || !count || cap < 0 || stride_elastic < 1 || stride_plastic < 1) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "not built");
     const int64_t n = c->n;
