@@ -19,17 +19,12 @@ constexpr int kOffW0 = 0, kOffB0 = kOffW0 + kHid * kIn, kOffW1 = kOffB0 + kHid, 
               kOffB3 = kOffW3 + kOut * kHid, kNumParams = kOffB3 + kOut;
 constexpr int kNumWeights = kHid * kIn + 2 * kHid * kHid + kOut * kHid;  // bf16 weights (no biases)
 
-// SiLU through the hardware tanh: sigma(z) = (1 + tanh(z / 2)) / 2, so SiLU(z) = h + h tanh(h)
-// with h = z / 2 (one special-function op; its relative error, about 2^-11, is below the bf16
-// rounding the activations get next).  Training and inference use the same functions.
+// Derivative of SiLU for the backward pass (FP32, through the hardware tanh:
+// sigma(z) = (1 + tanh(z / 2)) / 2, SiLU'(z) = sigma (1 + z (1 - sigma))).
 __device__ __forceinline__ float tanh_fast(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-__device__ __forceinline__ float silu_f(float z) {
-    const float h = 0.5f * z;
-    return fmaf(h, tanh_fast(h), h);
 }
 __device__ __forceinline__ float silu_grad_f(float z) {
     const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
@@ -47,6 +42,19 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// The activations of a hidden layer as the next layer reads them: SiLU of the two pre-activations
+// (lo, hi) in packed bf16 arithmetic, SiLU(z) = h + h tanh(h) with h = z / 2: one conversion, one
+// multiply, one tanh and one fused multiply-add (single rounding) for two values.  Training and
+// both inference paths use this same function.
+__device__ __forceinline__ uint32_t silu_bf16x2(float lo, float hi) {
+    uint32_t x, h, t, y;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(x) : "f"(hi), "f"(lo));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(x), "r"(0x3F003F00u));  // (0.5, 0.5)
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(y) : "r"(h), "r"(t), "r"(h));
+    return y;
 }
 
 // ------------------------------------------------------------------ generic GEMM (training)
@@ -100,7 +108,7 @@ __global__ void k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *A, const _
             C[(size_t)row * N + col] = v0;
             C[(size_t)row * N + col + 1] = v1;
             if (EPI == 1) {
-                *reinterpret_cast<uint32_t *>(Aout + (size_t)row * N + col) = pack_bf16(silu_f(v0), silu_f(v1));
+                *reinterpret_cast<uint32_t *>(Aout + (size_t)row * N + col) = silu_bf16x2(v0, v1);
             } else if (EPI == 2) {
                 *reinterpret_cast<uint32_t *>(Aout + (size_t)row * N + col) = pack_bf16(v0, v1);
             }
@@ -318,10 +326,10 @@ __device__ __forceinline__ void mlp_layer_regs(const uint32_t (&hin)[KT][4], con
     for (int kk = 0; kk < 8; kk++) {
         const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
         const float *a0 = acc[2 * kk], *a1 = acc[2 * kk + 1];
-        hout[kk][0] = pack_bf16(silu_f(a0[0] + bias[c0]), silu_f(a0[1] + bias[c0 + 1]));
-        hout[kk][1] = pack_bf16(silu_f(a0[2] + bias[c0]), silu_f(a0[3] + bias[c0 + 1]));
-        hout[kk][2] = pack_bf16(silu_f(a1[0] + bias[c1]), silu_f(a1[1] + bias[c1 + 1]));
-        hout[kk][3] = pack_bf16(silu_f(a1[2] + bias[c1]), silu_f(a1[3] + bias[c1 + 1]));
+        hout[kk][0] = silu_bf16x2(a0[0] + bias[c0], a0[1] + bias[c0 + 1]);
+        hout[kk][1] = silu_bf16x2(a0[2] + bias[c0], a0[3] + bias[c0 + 1]);
+        hout[kk][2] = silu_bf16x2(a1[0] + bias[c1], a1[1] + bias[c1 + 1]);
+        hout[kk][3] = silu_bf16x2(a1[2] + bias[c1], a1[3] + bias[c1 + 1]);
     }
 }
 

@@ -202,8 +202,8 @@ __device__ __forceinline__ bool mlp_tc_tile(MlpTcSmem &sm, int g, int r, unsigne
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         const int c = c0 + 8 * q8 + 2 * q;
-                        p[q] = pack_bf16(silu_f(__uint_as_float(v[8 * q8 + 2 * q]) + b[c]),
-                                         silu_f(__uint_as_float(v[8 * q8 + 2 * q + 1]) + b[c + 1]));
+                        p[q] = silu_bf16x2(__uint_as_float(v[8 * q8 + 2 * q]) + b[c],
+                                           __uint_as_float(v[8 * q8 + 2 * q + 1]) + b[c + 1]);
                     }
                     *reinterpret_cast<uint4 *>(gr.H + ((c0 >> 3) + q8) * 2048 + r * 16) = make_uint4(p[0], p[1], p[2], p[3]);
                 }

@@ -274,12 +274,19 @@ __device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T 
 // component of the particle's current velocity record, so that pass 2 gathers five float4
 // records per neighbour instead of five and a float.
 template <typename T, int DIM, bool FRAC>
+__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J);
+template <typename T, int DIM, bool FRAC>
 __device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J) {
+    M3<T> Fi;
+    inverse(F, Fi);
+    dev_write_qvm_fi<T, DIM, FRAC>(a, i, Fi, P, J);
+}
+// The same, given F^-1.
+template <typename T, int DIM, bool FRAC>
+__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J) {
     const int n = a.n;
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, n, i, A);
-    M3<T> Fi;
-    inverse(F, Fi);
     T Qm[DIM][DIM], Vm[DIM][DIM];
     bool ok = true;
 #pragma unroll
@@ -808,7 +815,7 @@ __device__ __forceinline__ bool sur_features(const StepArgs<float> &a, const Sur
     xr[15] = ep;
     bool use = s.enabled != 0;
     for (int c = 0; c < 16; c++) {
-        xn[c] = (xr[c] - s.in_mean[c]) / s.in_std[c];
+        xn[c] = __fdividef(xr[c] - s.in_mean[c], s.in_std[c]);
         use = use && xn[c] >= s.env_lo[c] && xn[c] <= s.env_hi[c];
     }
     if (!use) n_out++;
@@ -862,7 +869,7 @@ __device__ __forceinline__ void sur_apply(const StepArgs<float> &a, const Surrog
     a.K[4 * n + i] = Kn.a[2];
     a.K[5 * n + i] = Kn.a[5];
     a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
-    dev_write_qvm<float, DIM, FRAC>(a, i, F, P, 1.0f + kin.Jm1);
+    dev_write_qvm_fi<float, DIM, FRAC>(a, i, Fi, P, 1.0f + kin.Jm1);
 }
 
 __device__ __forceinline__ void sur_count(unsigned long long *counters, int n_mlp, int n_out, int n_el) {
