@@ -1,6 +1,6 @@
 """FP64 CPU oracle of the TLSPH solid step (arXiv 2602.15149).
 
-TEST INFRASTRUCTURE ONLY.  This package is the parity judge for the CUDA
+TEST INFRASTRUCTURE ONLY.  This package is the parity reference for the CUDA
 library and the timed CPU baseline; only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg
 may import it.  It shares no code with the CUDA path
