@@ -27,7 +27,7 @@ FIELDS = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, 
 class _Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("h", C.c_double), ("support", C.c_double), ("cfl", C.c_double),
                 ("dt_mode", C.c_int), ("fixed_dt", C.c_double), ("gravity", C.c_double * 3),
-                ("visc_literal", C.c_int), ("lap_uncorrected", C.c_int)]
+                ("visc_literal", C.c_int), ("lap_uncorrected", C.c_int), ("integrator", C.c_int)]
 
 
 class _Material(C.Structure):
@@ -121,10 +121,10 @@ class Oracle:
 
     def __init__(self, dim: int, h: float, cfl: float = 0.3, dt_mode: int = DT_CFL_STATIC,
                  fixed_dt: float = 0.0, gravity=(0.0, 0.0, 0.0), support: float = 2.0,
-                 visc_literal: bool = False, lap_uncorrected: bool = False):
+                 visc_literal: bool = False, lap_uncorrected: bool = False, integrator: int = 1):
         self.lib = load_oracle()
         p = _Params(dim, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity), int(visc_literal),
-                    int(lap_uncorrected))
+                    int(lap_uncorrected), int(integrator))
         self.ctx = self.lib.orc_create(C.byref(p))
         if not self.ctx:
             raise ValueError("invalid oracle parameters")

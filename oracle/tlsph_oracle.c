@@ -2,7 +2,7 @@
  * FP64 CPU oracle for the total-Lagrangian SPH (TLSPH) solid step of
  * "SoliDualSPHysics" (arXiv 2602.15149).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the parity judge for the CUDA
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity reference for the CUDA
  * library and the timed CPU baseline.  Only tests/, __graft_entry__.smoke()
  * and bench.py's CPU-baseline leg may load it.  It shares no code, header
  * or constant with the CUDA path.
@@ -18,8 +18,9 @@
  *     eq. MomentumEqTLSPH, eq. artViscCoef),
  *   - hyperbolic phase field (Sec. 2.2, eq. phasefieldddot, SPH Laplacian
  *     eq. phasefieldLapLacian),
- *   - Algorithm 1 time update with velocity / force boundary conditions
- *     (Sec. 2.5, Sec. 3.3.2), and the time-step bound eq. dt_criterion.
+ *   - Algorithm 1 (symplectic Euler) or Algorithm 2 (leapfrog) time update
+ *     with velocity / force boundary conditions (Sec. 2.5, Sec. 3.3.2), and
+ *     the time-step bound eq. dt_criterion.
  *
  * Readings of the paper where it is silent or inconsistent are marked
  * "reading:" below.  Compile with -ffp-contract=off so that no fused
@@ -62,6 +63,7 @@ typedef struct {
     double gravity[3];  /* body force per unit mass f_0 */
     int visc_literal;   /* 0: Pv = -J pi F^-T (dissipative reading), 1: literal +J pi F^-1 */
     int lap_uncorrected;/* 0: Laplacian uses the corrected gradient, 1: raw kernel gradient */
+    int integrator;     /* 1 (or 0): Algorithm 1, symplectic Euler; 2: Algorithm 2, leapfrog */
 } orc_params;
 
 typedef struct {
@@ -403,7 +405,9 @@ static double j2_energy(const double *F, const double *Fp, const orc_material *m
 static void *xcalloc(size_t n, size_t sz) { return n ? calloc(n, sz) : calloc(1, sz); }
 
 orc_ctx *orc_create(const orc_params *p) {
-    if (!p || (p->dim != 2 && p->dim != 3) || !(p->h > 0.0) || !(p->support > 0.0)) return NULL;
+    if (!p || (p->dim != 2 && p->dim != 3) || !(p->h > 0.0) || !(p->support > 0.0) || p->integrator < 0 ||
+        p->integrator > 2)
+        return NULL;
     orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
     c->p = *p;
     return c;
@@ -888,9 +892,39 @@ static int one_step(orc_ctx *c) {
             c->dt[s] = c->p.cfl * (dtv < dta ? dtv : dta);
         }
     }
+    /* Algorithm 2, predictor: the forces of this step act at the half level,
+     *   u_{n+1/2} = u_n + dt/2 v_n,  v_{n+1/2} = v_n + dt/2 a_{n-1/2},  s_{n+1/2} = s_n + dt/2 sdot_n;
+     * reading: velocity BCs hold at t_{n+1/2} for v_{n+1/2} (which enters the viscosity), and
+     * s_{n+1/2} is kept in [0, 1].  v_n is kept for the corrector. */
+    const int leap = c->p.integrator == 2;
+    double *vn_save = NULL;
+    if (leap) {
+        vn_save = (double *)malloc(sizeof(double) * 3 * n);
+        memcpy(vn_save, c->v, sizeof(double) * 3 * n);
+        for (int64_t i = 0; i < n; i++) {
+            int sp = c->spec[i];
+            double dt = c->dt[sp], th = c->t[sp] + 0.5 * dt;
+            for (int k = 0; k < d; k++) {
+                c->u[3 * i + k] = c->u[3 * i + k] + 0.5 * dt * vn_save[3 * i + k];
+                c->v[3 * i + k] = vn_save[3 * i + k] + 0.5 * dt * c->acc[3 * i + k];
+            }
+            for (int b = 0; b < c->nbc; b++) {
+                const orc_bc *bc = &c->bc[b];
+                if (bc->kind != ORC_BC_VEL || !bc->mask[i]) continue;
+                double f = bc_factor(bc, th);
+                if (f < 0.0) continue;
+                for (int k = 0; k < d; k++)
+                    if (bc->comp_mask & (1 << k)) c->v[3 * i + k] = f * bc->value[k];
+            }
+            if (is_fracture(c, i)) {
+                double sh = c->s[i] + 0.5 * dt * c->sdot[i];
+                c->s[i] = sh < 0.0 ? 0.0 : (sh > 1.0 ? 1.0 : sh);
+            }
+        }
+    }
     double *Fpn = (double *)malloc(sizeof(double) * 9 * n);
     double *epn = (double *)malloc(sizeof(double) * n);
-    /* Step 2: F and stress for every particle (from u_n, s_n) */
+    /* Step 2: F and stress for every particle (from u_n, s_n; Algorithm 2: the half level) */
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; i++) {
         deformation_gradient(c, c->u, i, &c->F[9 * i]);
@@ -960,8 +994,9 @@ static int one_step(orc_ctx *c) {
         }
         for (int k = 0; k < d; k++) a[k] += c->p.gravity[k];
         double mass = rho_i * c->vol[i];
-        double t_n = c->t[c->spec[i]];
-        for (int b = 0; b < c->nbc; b++) { /* force BCs at t_n (Algorithm 1, step 3) */
+        /* force BCs at the time of the forces: t_n (Algorithm 1), t_{n+1/2} (Algorithm 2) */
+        double t_n = c->t[c->spec[i]] + (leap ? 0.5 * c->dt[c->spec[i]] : 0.0);
+        for (int b = 0; b < c->nbc; b++) {
             const orc_bc *bc = &c->bc[b];
             if (bc->kind == ORC_BC_VEL || !bc->mask[i]) continue;
             double f = bc_factor(bc, t_n);
@@ -1002,7 +1037,9 @@ static int one_step(orc_ctx *c) {
         int sp = c->spec[i];
         double dt = c->dt[sp], t1 = c->t[sp] + dt;
         double vn[3];
-        for (int k = 0; k < 3; k++) vn[k] = c->v[3 * i + k] + (k < d ? dt * c->acc[3 * i + k] : 0.0);
+        /* v_{n+1} = v_n + dt a (Algorithm 1: a_n; Algorithm 2: a_{n+1/2}, from the saved v_n) */
+        const double *vold = leap ? &vn_save[3 * i] : &c->v[3 * i];
+        for (int k = 0; k < 3; k++) vn[k] = vold[k] + (k < d ? dt * c->acc[3 * i + k] : 0.0);
         for (int b = 0; b < c->nbc; b++) { /* velocity BCs at t_{n+1} */
             const orc_bc *bc = &c->bc[b];
             if (bc->kind != ORC_BC_VEL || !bc->mask[i]) continue;
@@ -1012,9 +1049,11 @@ static int one_step(orc_ctx *c) {
                 if (bc->comp_mask & (1 << k)) vn[k] = f * bc->value[k];
         }
         double vv = 0.0, aa = 0.0;
+        /* u_{n+1} = u_n + dt v_{n+1} (Algorithm 1); u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2) */
+        const double du = leap ? 0.5 * dt : dt;
         for (int k = 0; k < d; k++) {
             c->v[3 * i + k] = vn[k];
-            c->u[3 * i + k] = c->u[3 * i + k] + dt * vn[k];
+            c->u[3 * i + k] = c->u[3 * i + k] + du * vn[k];
             vv += vn[k] * vn[k];
             aa += c->acc[3 * i + k] * c->acc[3 * i + k];
         }
@@ -1028,7 +1067,8 @@ static int one_step(orc_ctx *c) {
                          (1.0 + dt * c->pf_g[i] + dt * dt * c->pf_k[i]);
             c->sdd[i] = (sd1 - c->sdot[i]) / dt;
             c->sdot[i] = sd1;
-            double sn = c->s[i] + dt * c->sdot[i];
+            /* s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1); s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2) */
+            double sn = c->s[i] + du * c->sdot[i];
             c->s[i] = sn < 0.0 ? 0.0 : (sn > 1.0 ? 1.0 : sn); /* reading: s kept in [0, 1] */
         }
         memcpy(&c->Fp[9 * i], &Fpn[9 * i], 9 * sizeof(double));
@@ -1039,6 +1079,7 @@ static int one_step(orc_ctx *c) {
     c->step++;
     free(Fpn);
     free(epn);
+    free(vn_save);
     return nonfinite ? ORC_ERR_NONFINITE : ORC_OK;
 }
 

@@ -88,6 +88,7 @@ class Case:
     steps: int = 1000
     precision: str = "fp32"     # "fp64" or "fp32" (fp32 fields, fp64 displacement)
     gravity: tuple = (0.0, 0.0, 0.0)
+    integrator: int = 1         # 1: Algorithm 1 (symplectic Euler), 2: Algorithm 2 (leapfrog)
 
     @property
     def n(self) -> int:
