@@ -287,6 +287,25 @@ def timed_steps(g, steps, stream, dev):
     return e0.elapsed_time(e1), int(st)
 
 
+def measure_leapfrog(args, shape, device, stream, plain):
+    """Algorithm 2 (leapfrog: predictor, forces at the half level, corrector) on the same block, against
+    the plain Algorithm 1 step."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    dev = torch.device("cuda", device)
+    case = W.block_3d(*shape, steps=args.steps)
+    case.integrator = tlsph.INTEGRATOR_LEAPFROG
+    g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    g.step(args.warmup)
+    ms, st = timed_steps(g, args.steps, stream, dev)
+    g.close()
+    value = case.n * args.steps / (ms * 1e-3)
+    return {"workload": "block_3d_j2, Algorithm 2 (leapfrog)", "ms_per_step": ms / args.steps, "value": value,
+            "unit": UNIT, "vs_algorithm_1": value / plain["value"], "status": st,
+            "kernels_per_step": 4}
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -432,6 +451,7 @@ def run_ours(args):
 
     batched = measure_batched(args, local, stream) if not args.no_batched else None
     sur = measure_surrogate(args, shape, local, stream, plain) if not args.no_surrogate else None
+    leapfrog = measure_leapfrog(args, shape, local, stream, plain)
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -463,6 +483,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "batched": batched,
         "surrogate": sur,
+        "leapfrog": leapfrog,
         "status": int(st),
         "cpu_baseline": cpu,
     }

@@ -93,10 +93,21 @@ enum {
     TLSPH_FIELD_STATE = 100 /* opaque checkpoint blob of the whole evolving state (read/write, see tlsph_field_bytes) */
 };
 
+/* Time integration (Sec. 2.5).
+ *  TLSPH_INTEGRATOR_EULER (Algorithm 1, symplectic Euler): forces from u_n, v_{n+1} = v_n + dt a_n,
+ *    u_{n+1} = u_n + dt v_{n+1};
+ *  TLSPH_INTEGRATOR_LEAPFROG (Algorithm 2): predictor u_{n+1/2} = u_n + dt/2 v_n,
+ *    v_{n+1/2} = v_n + dt/2 a_{n-1/2} (velocity BCs at t_{n+1/2}), s_{n+1/2} = s_n + dt/2 sdot_n; forces,
+ *    viscosity and force BCs at the half level; corrector v_{n+1} = v_n + dt a_{n+1/2},
+ *    u_{n+1} = u_{n+1/2} + dt/2 v_{n+1}, s_{n+1} = s_{n+1/2} + dt/2 sdot_{n+1}.  The acceleration of the
+ *    last step is part of the state (TLSPH_FIELD_ACC, checkpoints).  Not with TLSPH_MODE_PERSISTENT. */
+#define TLSPH_INTEGRATOR_EULER 1
+#define TLSPH_INTEGRATOR_LEAPFROG 2
+
 typedef struct {
     int dim;            /* 2 (plane strain, x-y plane) or 3 */
     int precision;      /* TLSPH_FP64 or TLSPH_FP32_U64 */
-    int integrator;     /* 1 = Algorithm 1 (the only one supported) */
+    int integrator;     /* TLSPH_INTEGRATOR_*: 1 = Algorithm 1 (0 means 1), 2 = Algorithm 2 */
     double h;           /* smoothing length (Wendland C2, support R = support * h) */
     double support;     /* 2.0 for Wendland C2 */
     double cfl;         /* C_CFL */

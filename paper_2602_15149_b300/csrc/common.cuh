@@ -98,6 +98,11 @@ template <typename T> struct StepArgs {
     double hd, cfl, fixed_dt;
     T h, inv2h, visc_eps;
     T grav[3];
+    // Algorithm 2 (leapfrog): the step reads the half level through ug_cur / vs_cur, takes v_n from
+    // v_own and writes v_{n+1}, u_{n+1} in place through vs_next / ug_next; acc_out keeps a_{n+1/2}
+    int leap;
+    const V4<T> *v_own;
+    V4<T> *ug_half, *vs_half;  // predictor output
     // diagnostics (may be null)
     T *Fout, *Pout, *psi_out, *acc_out;
 };

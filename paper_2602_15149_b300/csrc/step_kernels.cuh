@@ -451,7 +451,8 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             }
             acc[p] += a.grav[p];
         }
-        const double t_n = a.t[sp], dt = a.dt[sp], t_1 = t_n + dt;
+        // forces act at t_n (Algorithm 1) or t_{n+1/2} (Algorithm 2); velocity BCs hold at t_{n+1}
+        const double dt = a.dt[sp], t_1 = a.t[sp] + dt, t_n = a.t[sp] + (a.leap ? 0.5 * dt : 0.0);
         const int g = a.bcgrp[i];
         const T mass = DIM == 3 ? m.rho * xi.w : xi.w;
         double vset[3];
@@ -504,10 +505,13 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             const T dts = (T)dt;
             const T sd_new = (sd + dts * r) / (T(1) + dts * gam + dts * dts * kk);
             a.sdot[i] = sd_new;
-            s_new = t_min(T(1), t_max(T(0), si + (T)dt * sd_new));
+            // s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1), s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2)
+            s_new = t_min(T(1), t_max(T(0), si + (T)(a.leap ? 0.5 * dt : dt) * sd_new));
         }
-        // Algorithm 1 update
-        T vn[3] = {vsi.x, vsi.y, vsi.z};
+        // update: v_{n+1} = v_n + dt a; u_{n+1} = u_n + dt v_{n+1} (Algorithm 1) or
+        // u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2, u64 holding u_{n+1/2})
+        const V4<T> vo = a.leap ? a.v_own[i] : vsi;
+        T vn[3] = {vo.x, vo.y, vo.z};
         const T dtT = (T)dt;
 #pragma unroll
         for (int p = 0; p < DIM; p++) {
@@ -517,7 +521,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         double un[3];
 #pragma unroll
         for (int p = 0; p < DIM; p++) {
-            un[p] = a.u64[p * n + i] + dt * (double)vn[p];
+            un[p] = a.u64[p * n + i] + (a.leap ? 0.5 * dt : dt) * (double)vn[p];
             a.u64[p * n + i] = un[p];
         }
         a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), DIM == 3 ? mass : T(0)};
@@ -535,6 +539,50 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
         amag = (double)t_sqrt(aa);
         if (!(isfinite(vmag) && isfinite(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
     }
+}
+
+// Velocity boundary conditions of particle i at time t: the constrained components of v take the
+// prescribed values.
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_velocity_bcs(const StepArgs<T> &a, int i, double t, T v[3]) {
+    const int g = a.bcgrp[i];
+    if (!g) return;
+    for (int b = 0; b < kMaxBcPerParticle; b++) {
+        const int id = a.grp_bcs[4 * g + b];
+        if (id < 0) break;
+        const BCDev bc = a.bcs[id];
+        if (bc.kind != 0) continue;
+        const double f = bc_factor(bc, t);
+        if (f < 0.0) continue;
+        for (int p = 0; p < DIM; p++)
+            if (bc.comp_mask & (1 << p)) v[p] = (T)(f * bc.value[p]);
+    }
+}
+
+// Algorithm 2, predictor: u_{n+1/2} = u_n + dt/2 v_n (FP64 accumulator and its FP32 copy),
+// v_{n+1/2} = v_n + dt/2 a_{n-1/2} with the velocity BCs at t_{n+1/2}, s_{n+1/2} = s_n + dt/2 sdot_n
+// (kept in [0, 1]).  The half level goes to ug_half / vs_half, which the step's other kernels read.
+template <typename T, int DIM, bool FRAC, int BS>
+__global__ void __launch_bounds__(BS) k_predict(StepArgs<T> a) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= a.n) return;
+    const int n = a.n;
+    const int sp = a.spec[i];
+    const double dt = a.dt[sp], th = a.t[sp] + 0.5 * dt;
+    const V4<T> v = a.v_own[i];
+    const T vv[3] = {v.x, v.y, v.z};
+    T uf[3] = {T(0), T(0), T(0)}, vh[3] = {v.x, v.y, v.z};
+    for (int p = 0; p < DIM; p++) {
+        const double uh = a.u64[p * n + i] + 0.5 * dt * (double)vv[p];
+        a.u64[p * n + i] = uh;
+        uf[p] = (T)uh;
+        vh[p] = vv[p] + (T)(0.5 * dt) * a.acc_out[p * n + i];
+    }
+    dev_velocity_bcs<T, DIM>(a, i, th, vh);
+    T sh = v.w;
+    if (FRAC && a.mats[a.mid[i]].fracture) sh = t_min(T(1), t_max(T(0), v.w + (T)(0.5 * dt) * a.sdot[i]));
+    a.ug_half[i] = V4<T>{uf[0], uf[1], DIM == 3 ? uf[DIM - 1] : T(0), DIM == 3 ? a.ug_next[i].w : T(0)};
+    a.vs_half[i] = V4<T>{vh[0], vh[1], DIM == 3 ? vh[DIM - 1] : T(0), sh};
 }
 
 // Per-specimen maxima of |v_{n+1}| and |a_n| of one block (one atomic per block when the

@@ -52,6 +52,7 @@ struct tlsph_ctx {
     int max_row = 0;
     int64_t nslice = 0, sell_total = 0;
     bool has_j2 = false, has_frac = false, has_visc = false;
+    bool leap = false;  // Algorithm 2 (leapfrog) instead of Algorithm 1
     bool record_acc = false;
     double bytes_per_step = 0.0;
     // device memory
@@ -337,6 +338,26 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.Pout = (T *)c->Pd;
     a.psi_out = (T *)c->psid;
     a.acc_out = c->record_acc ? (T *)c->accd : nullptr;
+    return a;
+}
+
+// Arguments of the step kernels.  Algorithm 1 ping-pongs the displacement and velocity records
+// (read cur, write next).  Algorithm 2 keeps them in place: the predictor writes the half level to
+// the other buffers, the forces read it from there, and pass 2 writes v_{n+1}, u_{n+1} in place.
+template <typename T> StepArgs<T> make_step_args(tlsph_ctx *c) {
+    StepArgs<T> a = make_args<T>(c);
+    if (c->leap) {
+        const int cur = c->parity, nxt = c->parity ^ 1;
+        a.leap = 1;
+        a.v_own = (const V4<T> *)c->vs[cur];
+        a.ug_half = (V4<T> *)c->ug[nxt];
+        a.vs_half = (V4<T> *)c->vs[nxt];
+        a.ug_cur = (const V4<T> *)c->ug[nxt];
+        a.vs_cur = (const V4<T> *)c->vs[nxt];
+        a.ug_next = (V4<T> *)c->ug[cur];
+        a.vs_next = (V4<T> *)c->vs[cur];
+        a.acc_out = (T *)c->accd;
+    }
     return a;
 }
 
@@ -844,7 +865,7 @@ template <typename T, int DIM, bool FRAC, int BS>
 tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
     const unsigned nb = blocks_for(c->n, BS);
     for (int64_t k = 0; k < nsteps; k++) {
-        StepArgs<T> a = make_args<T>(c);
+        StepArgs<T> a = make_step_args<T>(c);
         int ev[3] = {-1, -1, -1};
         if (timing && c->ev_next + 6 > 4096) {
             cudaStreamSynchronize(c->stream);
@@ -862,6 +883,10 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
             c->ev_pending.push_back({cat, ev[cat]});
         };
         start(1);
+        if (c->leap) {  // Algorithm 2, predictor (timed with the deformation gradient)
+            k_predict<T, DIM, FRAC, BS><<<nb, BS, 0, c->stream>>>(a);
+            CKL();
+        }
         k_gradient<T, DIM, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
         stop(1);
@@ -884,7 +909,7 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
         else k_pass2<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
         stop(0);
-        c->parity ^= 1;
+        if (!c->leap) c->parity ^= 1;
         c->steps++;
     }
     return TLSPH_OK;
@@ -963,6 +988,7 @@ tlsph_status step_mode(tlsph_ctx *c, int64_t nsteps) {
     if (c->mode == TLSPH_MODE_GRAPH && !c->timing) return step_graph<T, DIM, FRAC, BS>(c, nsteps);
     if (c->mode == TLSPH_MODE_PERSISTENT) {
         if (BS == 64) return fail(c, TLSPH_ERR_ARG, "the persistent mode needs a block of 128 or 256");
+        if (c->leap) return fail(c, TLSPH_ERR_ARG, "the persistent mode runs Algorithm 1 only");
         return c->has_visc ? step_persistent_v<T, DIM, FRAC, true, (BS < 128 ? 128 : BS)>(c, nsteps)
                            : step_persistent_v<T, DIM, FRAC, false, (BS < 128 ? 128 : BS)>(c, nsteps);
     }
@@ -1048,7 +1074,8 @@ int field_comps(const tlsph_ctx *c, int field) {
 
 size_t state_bytes(const tlsph_ctx *c) {
     const size_t ts = c->p.precision == TLSPH_FP64 ? 8 : 4, n = (size_t)c->n;
-    return 64 + n * (3 * 8 + 2 * 4 * ts + ts * (1 + 1 + 6 + 1)) + (size_t)c->nspec * 2 * 8;
+    return 64 + n * (3 * 8 + 2 * 4 * ts + ts * (1 + 1 + 6 + 1)) + (size_t)c->nspec * 2 * 8 +
+           (c->leap ? (size_t)c->p.dim * n * ts : 0);
 }
 
 template <typename T> tlsph_status read_impl(tlsph_ctx *c, int field, double *dst /* device, caller order */) {
@@ -1115,7 +1142,8 @@ template <typename T> tlsph_status state_io(tlsph_ctx *c, char *blob /* host */,
                     {c->vs[c->parity], n * sizeof(V4<T>)}, {c->sdot, n * ts},
                     {c->H, n * ts},               {c->K, 6 * n * ts},
                     {c->ep, n * ts},              {c->t, (size_t)c->nspec * 8},
-                    {c->dt, (size_t)c->nspec * 8}};
+                    {c->dt, (size_t)c->nspec * 8},
+                    {c->accd, c->leap ? (size_t)c->p.dim * n * ts : 0}};  // a_{n-1/2} of Algorithm 2
     int64_t hdr[8] = {0x54534c50485354LL, (int64_t)n, c->p.precision, c->nspec, c->steps, c->p.dim, 0, 0};
     cudaStream_t s = c->stream;
     if (save) {
@@ -1168,6 +1196,7 @@ struct Snap {
 template <typename T> std::vector<Snap> snap_parts(tlsph_ctx *c) {
     const size_t n = (size_t)c->n, ns = (size_t)c->nspec, ts = sizeof(T);
     return {{c->u64, 3 * n * 8},       {c->ug[c->parity], n * sizeof(V4<T>)}, {c->vs[c->parity], n * sizeof(V4<T>)},
+            {c->accd, c->leap ? (size_t)c->p.dim * n * ts : 0},
             {c->sdot, n * ts},         {c->H, n * ts},                         {c->K, 6 * n * ts},
             {c->ep, n * ts},           {c->t, ns * 8},                         {c->dt, ns * 8},
             {c->vmax, ns * 8},         {c->amax, ns * 8},                      {c->last_v, ns * 8},
@@ -1264,7 +1293,7 @@ tlsph_status tlsph_create(const tlsph_params *params, tlsph_ctx **out) {
     *out = nullptr;
     if (!params || (params->dim != 2 && params->dim != 3) || !(params->h > 0.0) || !(params->support > 0.0) ||
         (params->precision != TLSPH_FP64 && params->precision != TLSPH_FP32_U64) ||
-        (params->integrator != 0 && params->integrator != 1) || params->dt_mode < 0 || params->dt_mode > 2 ||
+        params->integrator < 0 || params->integrator > 2 || params->dt_mode < 0 || params->dt_mode > 2 ||
         (params->dt_mode == TLSPH_DT_FIXED && !(params->fixed_dt > 0.0)) ||
         (params->dt_mode != TLSPH_DT_FIXED && !(params->cfl > 0.0)))
         return TLSPH_ERR_ARG;
@@ -1276,6 +1305,7 @@ tlsph_status tlsph_create(const tlsph_params *params, tlsph_ctx **out) {
     if (cudaSetDevice(params->device) != cudaSuccess) return TLSPH_ERR_CUDA;
     tlsph_ctx *c = new tlsph_ctx();
     c->p = *params;
+    c->leap = params->integrator == TLSPH_INTEGRATOR_LEAPFROG;
     if (params->cuda_stream) {
         c->stream = (cudaStream_t)params->cuda_stream;
     } else {

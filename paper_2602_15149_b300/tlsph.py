@@ -24,6 +24,7 @@ FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "
 OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6
 LAYOUT_AUTO, LAYOUT_CSR = 0, 1
 MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
+INTEGRATOR_EULER, INTEGRATOR_LEAPFROG = 1, 2
 MODE_NAMES = {MODE_LAUNCH: "launch", MODE_GRAPH: "graph", MODE_PERSISTENT: "persistent"}
 
 # every entry point declared in include/tlsph.h
@@ -141,9 +142,9 @@ class TLSPH:
     """One TLSPH context on a CUDA device (methods carry the C-ABI names without the prefix)."""
 
     def __init__(self, dim, h, precision=FP32_U64, cfl=0.3, dt_mode=DT_CFL_STATIC, fixed_dt=0.0,
-                 gravity=(0.0, 0.0, 0.0), support=2.0, device=0, stream=None):
+                 gravity=(0.0, 0.0, 0.0), support=2.0, device=0, stream=None, integrator=INTEGRATOR_EULER):
         self.lib = load_library()
-        p = Params(dim, precision, 1, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity),
+        p = Params(dim, precision, integrator, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity),
                    stream, device)
         ctx = C.c_void_p()
         st = self.lib.tlsph_create(C.byref(p), C.byref(ctx))
@@ -416,7 +417,7 @@ def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
     """Create a context from a :class:`workloads.Case` (marshalling only)."""
     prec = precision if precision is not None else (FP64 if case.precision == "fp64" else FP32_U64)
     t = TLSPH(case.dim, case.h, prec, case.cfl, case.dt_mode, case.fixed_dt, case.gravity, device=device,
-              stream=stream)
+              stream=stream, integrator=getattr(case, "integrator", INTEGRATOR_EULER))
     t.set_materials(case.materials)
     t.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
     for b in list(case.bcs) + list(getattr(case, "specimen_loads", [])):
