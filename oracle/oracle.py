@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tlsph_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_tlsph.so")
 
-MODEL_NH, MODEL_J2 = 2, 3
+MODEL_SVK, MODEL_NH, MODEL_J2 = 1, 2, 3
 BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
 FIELDS = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "FP": 9,
@@ -102,6 +102,9 @@ def load_oracle():
     lib.orc_sound_speed.restype = C.c_double
     lib.orc_sound_speed.argtypes = [C.POINTER(_Material)]
     lib.orc_nh_stress.argtypes = [D, C.c_double, C.POINTER(_Material), D, D, D]
+    lib.orc_svk_stress.argtypes = [D, C.c_double, C.POINTER(_Material), D, D, D]
+    lib.orc_sym_eig3.argtypes = [D, D, D]
+    lib.orc_sym_eig3.restype = None
     lib.orc_j2_update.argtypes = [D, D, C.c_double, C.POINTER(_Material), D, D, D, D, C.POINTER(C.c_int)]
     _lib = lib
     return lib
@@ -247,6 +250,28 @@ def nh_stress(F, s, mat: OracleMaterial):
     if st != 0:
         raise ValueError("nh_stress: invalid F")
     return S.reshape(3, 3), pp.value, pm.value
+
+
+def svk_stress(F, s, mat: OracleMaterial):
+    """St. Venant-Kirchhoff stress with the spectral split: (S, psi_plus, psi_minus)."""
+    lib = load_oracle()
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(9)
+    S = np.zeros(9)
+    pp, pm = C.c_double(), C.c_double()
+    m = mat.c_struct()
+    st = lib.orc_svk_stress(_dp(F), s, C.byref(m), _dp(S), C.byref(pp), C.byref(pm))
+    if st != 0:
+        raise ValueError("svk_stress: invalid F")
+    return S.reshape(3, 3), pp.value, pm.value
+
+
+def sym_eig3(A):
+    """Jacobi eigen-decomposition of a symmetric 3x3 matrix: (eigenvalues, Q with the eigenvectors as columns)."""
+    lib = load_oracle()
+    A = np.ascontiguousarray(A, dtype=np.float64).reshape(9)
+    w, Q = np.zeros(3), np.zeros(9)
+    lib.orc_sym_eig3(_dp(A), _dp(w), _dp(Q))
+    return w, Q.reshape(3, 3)
 
 
 def j2_update(F, Fp, ep, mat: OracleMaterial):

@@ -38,6 +38,7 @@
 #define ORC_ERR_NONFINITE -5
 #define ORC_ERR_STATE -8
 
+#define ORC_MODEL_SVK 1
 #define ORC_MODEL_NH 2
 #define ORC_MODEL_J2 3
 
@@ -67,7 +68,7 @@ typedef struct {
 } orc_params;
 
 typedef struct {
-    int model;          /* ORC_MODEL_NH or ORC_MODEL_J2 */
+    int model;          /* ORC_MODEL_SVK, ORC_MODEL_NH or ORC_MODEL_J2 */
     double rho, E, nu;
     double sigma_y0, H_hard;
     double beta1, beta2;
@@ -261,6 +262,91 @@ int orc_nh_stress(const double *F, double s, const orc_material *m, double *S, d
 }
 
 /* ------------------------------------------------------------------ */
+/* Symmetric eigen-decomposition by cyclic Jacobi rotations (FP64):    */
+/* A = Q diag(w) Q^T, eigenvectors as the columns of Q (row-major).    */
+/* ------------------------------------------------------------------ */
+void orc_sym_eig3(const double *A, double *w, double *Q) {
+    double a[9];
+    memcpy(a, A, sizeof a);
+    a[1] = a[3] = 0.5 * (A[1] + A[3]);
+    a[2] = a[6] = 0.5 * (A[2] + A[6]);
+    a[5] = a[7] = 0.5 * (A[5] + A[7]);
+    m_eye(Q);
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+        double dia = a[0] * a[0] + a[4] * a[4] + a[8] * a[8];
+        if (off == 0.0 || off <= 1e-40 * dia) break;
+        static const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int r = 0; r < 3; r++) {
+            int p = P[r][0], q = P[r][1];
+            double apq = a[3 * p + q];
+            if (apq == 0.0) continue;
+            /* the rotation J(p, q, theta) that zeroes a_pq: tan(2 theta) = 2 a_pq / (a_qq - a_pp) */
+            double theta = (a[3 * q + q] - a[3 * p + p]) / (2.0 * apq);
+            double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+            double J[9];
+            m_eye(J);
+            J[3 * p + p] = cs;
+            J[3 * q + q] = cs;
+            J[3 * p + q] = sn;
+            J[3 * q + p] = -sn;
+            double Jt[9], tmp[9];
+            m_tr(J, Jt);
+            m_mul(Jt, a, tmp);
+            m_mul(tmp, J, a); /* a <- J^T a J */
+            a[3 * p + q] = a[3 * q + p] = 0.0;
+            m_mul(Q, J, tmp); /* Q <- Q J */
+            memcpy(Q, tmp, sizeof tmp);
+        }
+    }
+    for (int k = 0; k < 3; k++) w[k] = a[4 * k];
+}
+
+/* ------------------------------------------------------------------ */
+/* St. Venant-Kirchhoff stress with the spectral split of the          */
+/* Green-Lagrange strain (Sec. 2.3.1, eq. elasEnergyP, elasEnergyN,    */
+/* GLstratinP, GLstratinN, 2PK_SVK1, 2PK_SVK2):                         */
+/*   E = (F^T F - I) / 2 = Q diag(lambda_a) Q^T,                        */
+/*   E+- = Q diag({lambda_a}+-) Q^T,                                     */
+/*   psi+- = lambda/2 {tr E}+-^2 + mu tr(E+- E+-),                       */
+/*   S+- = lambda {tr E}+- I + 2 mu E+-,   S = s^2 S+ + S-.              */
+/* ------------------------------------------------------------------ */
+int orc_svk_stress(const double *F, double s, const orc_material *m, double *S, double *psi_plus,
+                   double *psi_minus) {
+    double lam, mu, kap;
+    lame(m, &lam, &mu, &kap);
+    double Ft[9], C[9], E[9], w[3], Q[9];
+    m_tr(F, Ft);
+    m_mul(Ft, F, C);
+    for (int k = 0; k < 9; k++) E[k] = 0.5 * (C[k] - (k % 4 == 0 ? 1.0 : 0.0));
+    orc_sym_eig3(E, w, Q);
+    double Ep[9] = {0}, Em[9] = {0};
+    double sp2 = 0.0, sm2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double lp = w[a] > 0.0 ? w[a] : 0.0, lm = w[a] < 0.0 ? w[a] : 0.0;
+        sp2 += lp * lp;
+        sm2 += lm * lm;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double qq = Q[3 * i + a] * Q[3 * j + a];
+                Ep[3 * i + j] += lp * qq;
+                Em[3 * i + j] += lm * qq;
+            }
+    }
+    double trE = m_trace(E);
+    double trp = trE > 0.0 ? trE : 0.0, trm = trE < 0.0 ? trE : 0.0;
+    *psi_plus = 0.5 * lam * trp * trp + mu * sp2;
+    *psi_minus = 0.5 * lam * trm * trm + mu * sm2;
+    double s2 = s * s;
+    for (int k = 0; k < 9; k++) {
+        double id = (k % 4 == 0) ? 1.0 : 0.0;
+        S[k] = s2 * (lam * trp * id + 2.0 * mu * Ep[k]) + (lam * trm * id + 2.0 * mu * Em[k]);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Finite-strain J2 plasticity, F_p stored (Sec. 2.3.3).               */
 /* ------------------------------------------------------------------ */
 static double j2_sigma_eq(const double *Ce, double J, double mu) {
@@ -433,7 +519,7 @@ int orc_set_materials(orc_ctx *c, int n, const orc_material *m) {
     if (!c || n <= 0 || !m) return ORC_ERR_ARG;
     for (int i = 0; i < n; i++) {
         if (!(m[i].E > 0.0) || !(m[i].nu > -1.0 && m[i].nu < 0.5) || !(m[i].rho > 0.0)) return ORC_ERR_ARG;
-        if (m[i].model != ORC_MODEL_NH && m[i].model != ORC_MODEL_J2) return ORC_ERR_ARG;
+        if (m[i].model != ORC_MODEL_SVK && m[i].model != ORC_MODEL_NH && m[i].model != ORC_MODEL_J2) return ORC_ERR_ARG;
     }
     free(c->mat);
     c->mat = (orc_material *)malloc(sizeof(orc_material) * n);
@@ -845,10 +931,11 @@ static void constitutive(orc_ctx *c, int64_t i, const double *F, int commit, dou
     const orc_material *m = &c->mat[c->mid[i]];
     double S[9];
     c->status[i] = 0;
-    if (m->model == ORC_MODEL_NH) {
+    if (m->model == ORC_MODEL_NH || m->model == ORC_MODEL_SVK) {
         double s = is_fracture(c, i) ? c->s[i] : 1.0; /* degradation with s_n (Algorithm 1) */
         double pp, pm;
-        if (orc_nh_stress(F, s, m, S, &pp, &pm) != 0) {
+        int st = m->model == ORC_MODEL_NH ? orc_nh_stress(F, s, m, S, &pp, &pm) : orc_svk_stress(F, s, m, S, &pp, &pm);
+        if (st != 0) {
             for (int k = 0; k < 9; k++) P[k] = NAN;
             c->status[i] = 2;
             return;

@@ -8,15 +8,17 @@ Recipes (the paper's own workloads use CAD geometry that is not available, so
 these lattices stand in for them at the same scale):
 
 * ``plate_2d``      -- 2D plane-strain elastic plate, square lattice
-  X = ((i + 1/2) dp, (j + 1/2) dp), no jitter; neo-Hookean; left edge clamped,
+  X = ((i + 1/2) dp, (j + 1/2) dp), no jitter; neo-Hookean (or St. Venant-
+  Kirchhoff); left edge clamped,
   right edge pulled in x at ``v_pull`` with a linear ramp over ``ramp_steps``
   steps (100 x 20 particles, dp = 1 mm is the full case).
 * ``block_3d``      -- 3D block, lattice jittered by U(-jitter dp, +jitter dp)
   per axis from ``numpy.random.default_rng(seed)``; J2 plasticity; bottom face
   fixed, top face pressed down at ``v_press`` (128 x 128 x 64 is the full case).
 * ``notched_plate`` -- 2D plate 0.1 x 0.04 m with an edge notch of length
-  0.05 m at mid-height, phase-field fracture, +-1 MPa traction on the top and
-  bottom rows (500 x 200 particles is the full case).
+  0.05 m at mid-height, phase-field fracture of a neo-Hookean (or St. Venant-
+  Kirchhoff) solid, +-1 MPa traction on the top and bottom rows (500 x 200
+  particles is the full case).
 * ``batched``       -- many independent 2D specimens of log-uniform size with
   random materials and loading (512 specimens is the full case).
 
@@ -35,7 +37,8 @@ import numpy as np
 
 REF_WAVE_SPEED = 5856.0  # m/s, sets ramp durations (see the module docstring)
 
-MODEL_NH, MODEL_J2 = 2, 3
+MODEL_SVK, MODEL_NH, MODEL_J2 = 1, 2, 3
+_MODELS = {"svk": MODEL_SVK, "nh": MODEL_NH}
 BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
 
@@ -109,18 +112,19 @@ def lattice(shape, dp, jitter=0.0, seed=0, origin=None):
 
 
 def plate_2d(nx=100, ny=20, dp=1e-3, v_pull=1.0, ramp_steps=100, steps=1000, precision="fp64",
-             beta1=1.0, beta2=0.0):
-    """2D plane-strain Neo-Hookean plate, left edge clamped, right edge pulled (ramped)."""
+             beta1=1.0, beta2=0.0, model="nh"):
+    """2D plane-strain hyperelastic plate (``model`` "nh" or "svk"), left edge clamped, right edge
+    pulled (ramped)."""
     X, idx = lattice((nx, ny), dp)
     n = X.shape[0]
-    mat = Material(model=MODEL_NH, rho=7850.0, E=200e9, nu=0.3, beta1=beta1, beta2=beta2)
+    mat = Material(model=_MODELS[model], rho=7850.0, E=200e9, nu=0.3, beta1=beta1, beta2=beta2)
     h = 1.5 * dp
     dt = 0.3 * h / REF_WAVE_SPEED
     left = (idx[:, 0] == 0).astype(np.uint8)
     right = (idx[:, 0] == nx - 1).astype(np.uint8)
     bcs = [BC(left, BC_VEL, 0b11, (0.0, 0.0, 0.0)),
            BC(right, BC_VEL, 0b01, (v_pull, 0.0, 0.0), ramp=ramp_steps * dt)]
-    return Case("plate_2d_nh", 2, dp, h, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
+    return Case("plate_2d_" + model, 2, dp, h, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
                 np.zeros((n, 2)), np.zeros(n, np.int32), None, bcs, [], steps, precision)
 
 
@@ -139,14 +143,15 @@ def block_3d(nx=128, ny=128, nz=64, dp=1e-3, jitter=0.01, seed=2602, v_press=5.0
 
 
 def notched_plate(nx=500, ny=200, width=0.1, height=0.04, notch_len=0.05, traction=1e6, steps=4000,
-                  precision="fp32", s_lim=0.1, beta1=0.2):
-    """2D phase-field plate with an edge notch at mid-height, pulled by +-traction on top/bottom rows."""
+                  precision="fp32", s_lim=0.1, beta1=0.2, model="nh"):
+    """2D phase-field plate with an edge notch at mid-height, pulled by +-traction on top/bottom rows
+    (``model`` "nh" or "svk" for the degraded hyperelastic law)."""
     dp = width / nx
     assert abs(dp * ny - height) < 1e-12 * height
     X, idx = lattice((nx, ny), dp)
     n = X.shape[0]
-    mat = Material(model=MODEL_NH, rho=2450.0, E=32e9, nu=0.2, beta1=beta1, fracture=1, Gc=3.0, eps0=2.0 * dp,
-                   s_lim=s_lim)
+    mat = Material(model=_MODELS[model], rho=2450.0, E=32e9, nu=0.2, beta1=beta1, fracture=1, Gc=3.0,
+                   eps0=2.0 * dp, s_lim=s_lim)
     top = (idx[:, 1] == ny - 1).astype(np.uint8)
     bot = (idx[:, 1] == 0).astype(np.uint8)
     area = dp * 1.0  # unit thickness
@@ -154,7 +159,7 @@ def notched_plate(nx=500, ny=200, width=0.1, height=0.04, notch_len=0.05, tracti
            BC(bot, BC_TRACTION, 0b10, (0.0, -traction, 0.0), area=area)]
     y0 = 0.5 * height
     notch = [(0.0, y0, 0.0), (notch_len, y0, 0.0), (notch_len, y0, 1.0), (0.0, y0, 1.0)]
-    return Case("notched_plate_pf", 2, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
+    return Case("notched_plate_pf" if model == "nh" else "notched_plate_pf_" + model, 2, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
                 np.zeros((n, 2)), np.zeros(n, np.int32), None, bcs, [np.array(notch, dtype=np.float64)], steps,
                 precision)
 

@@ -627,3 +627,127 @@ def test_energy_error_orders_of_the_two_integrators():
     assert 1.6 < r1 < 2.8, r1
     assert 3.3 < r2 < 5.0, r2
     assert w2 < 5e-3  # and it stays bounded over 1000 steps
+
+
+# ---------------------------------------------------------------- St. Venant-Kirchhoff, spectral split
+SVK = O.OracleMaterial(model=O.MODEL_SVK, rho=2450.0, E=32e9, nu=0.2, beta1=0.0, fracture=1, Gc=3.0,
+                       eps0=4e-4)
+
+
+def _svk_lame():
+    return lame(SVK.E, SVK.nu)
+
+
+def _F_of_E(E):
+    """The symmetric F with F^T F = I + 2 E."""
+    w, Q = np.linalg.eigh(np.eye(3) + 2.0 * E)
+    return Q @ np.diag(np.sqrt(w)) @ Q.T
+
+
+def test_jacobi_eigensolver_matches_lapack():
+    rng = np.random.default_rng(5)
+    mats = [rng.normal(size=(3, 3)) for _ in range(20)]
+    mats = [0.5 * (A + A.T) for A in mats]
+    mats += [np.diag([1.0, 1.0, -2.0]), np.zeros((3, 3)), np.eye(3) * 3e-4, np.diag([2.0, 2.0, 5.0])]
+    R = rand_rotation(rng)
+    mats.append(R @ np.diag([1e-3, 1e-3, -4e-4]) @ R.T)  # a repeated eigenvalue in a rotated frame
+    for A in mats:
+        w, Q = O.sym_eig3(A)
+        scale = max(np.abs(A).max(), 1e-300)
+        assert np.allclose(np.sort(w), np.linalg.eigvalsh(A), rtol=0, atol=1e-13 * scale)
+        assert np.allclose(Q.T @ Q, np.eye(3), atol=1e-13)
+        assert np.allclose(Q @ np.diag(w) @ Q.T, A, atol=1e-13 * scale)
+
+
+def test_svk_without_degradation_is_the_textbook_law():
+    """s = 1: S = lambda tr(E) I + 2 mu E and psi+ + psi- = lambda/2 (tr E)^2 + mu tr(E^2)."""
+    lam, mu = _svk_lame()
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        B = rng.normal(scale=3e-3, size=(3, 3))
+        E = 0.5 * (B + B.T)
+        S, pp, pm = O.svk_stress(_F_of_E(E), 1.0, SVK)
+        ref = lam * np.trace(E) * np.eye(3) + 2 * mu * E
+        # E = (F^T F - I) / 2 is formed from F with about 1e-16 absolute error
+        assert np.abs(S - ref).max() <= 1e-11 * np.abs(ref).max()
+        psi = 0.5 * lam * np.trace(E) ** 2 + mu * np.trace(E @ E)
+        assert abs(pp + pm - psi) <= 1e-10 * psi
+
+
+def test_svk_tension_degrades_and_compression_does_not():
+    lam, mu = _svk_lame()
+    R = rand_rotation(np.random.default_rng(7))
+    Et = R @ np.diag([2e-3, 1e-3, 5e-4]) @ R.T
+    S_full = lam * np.trace(Et) * np.eye(3) + 2 * mu * Et
+    S, pp, pm = O.svk_stress(_F_of_E(Et), 0.3, SVK)
+    assert pm == 0.0 and np.allclose(S, 0.09 * S_full, rtol=1e-10, atol=1e-6)
+    Ec = -Et
+    S_full = lam * np.trace(Ec) * np.eye(3) + 2 * mu * Ec
+    S, pp, pm = O.svk_stress(_F_of_E(Ec), 0.3, SVK)
+    assert pp == 0.0 and np.allclose(S, S_full, rtol=1e-10, atol=1e-6)
+
+
+@pytest.mark.parametrize("s", [1.0, 0.0])
+def test_svk_split_stresses_are_energy_derivatives(s):
+    """S+ = d psi+ / dE (s = 1 gives S+ + S-; s = 0 gives S-): central differences in E of a
+    mixed-sign strain."""
+    rng = np.random.default_rng(8)
+    R = rand_rotation(rng)
+    E = R @ np.diag([1.5e-3, -7e-4, 3e-4]) @ R.T
+    S, _, _ = O.svk_stress(_F_of_E(E), s, SVK)
+
+    def psi(Ek):
+        _, pp, pm = O.svk_stress(_F_of_E(Ek), s, SVK)
+        return s * s * pp + pm
+
+    h = 1e-8
+    for (i, j) in [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]:  # symmetric perturbations
+        dE = np.zeros((3, 3))
+        dE[i, j] = dE[j, i] = h
+        d = (psi(E + dE) - psi(E - dE)) / (2 * h)
+        expect = S[i, j] * (1 if i == j else 2)
+        assert abs(d - expect) <= 1e-5 * np.abs(S).max(), (i, j, d, expect)
+
+
+def test_svk_frame_indifference():
+    rng = np.random.default_rng(9)
+    for _ in range(5):
+        F = np.eye(3) + rng.normal(scale=2e-3, size=(3, 3))
+        Q = rand_rotation(rng)
+        S1, pp1, pm1 = O.svk_stress(F, 0.6, SVK)
+        S2, pp2, pm2 = O.svk_stress(Q @ F, 0.6, SVK)
+        # S is invariant (P = F S rotates with F); psi+- are invariant up to the rounding of Q F
+        assert np.abs(S1 - S2).max() <= 1e-10 * np.abs(S1).max()
+        assert abs(pp1 - pp2) <= 1e-10 * (pp1 + pm1) and abs(pm1 - pm2) <= 1e-10 * (pp1 + pm1)
+
+
+def test_svk_free_body_conserves_energy():
+    """Step level: with the St. Venant-Kirchhoff law and no viscosity the scheme's energy (whose strain part
+    is the law's own psi) stays within 1e-6 of its start, so S is the derivative of the psi it reports."""
+    case = _free_body(0.0)
+    case.materials[0].model = O.MODEL_SVK
+    o = make_oracle(case)
+    E0 = _staggered_energy(o, case)
+    worst = 0.0
+    for _ in range(10):
+        o.step(49)
+        worst = max(worst, abs(_staggered_energy(o, case) - E0) / E0)
+    assert worst < 1e-6
+
+
+def test_svk_notched_plate_history_and_damage():
+    """The degraded St. Venant-Kirchhoff plate: H never decreases, s stays in [0, 1] and the notch tip
+    loses stiffness first."""
+    case = W.notched_plate(nx=50, ny=20, steps=300, model="svk")
+    o = make_oracle(case)
+    Hprev = o.read("H")
+    for _ in range(6):
+        o.step(50)
+        Hn = o.read("H")
+        assert np.all(Hn >= Hprev)
+        Hprev = Hn
+        s = o.read("S")
+        assert s.min() >= 0.0 and s.max() <= 1.0
+    tip = np.argmax(Hprev)
+    X = case.X0
+    assert abs(X[tip, 0] - 0.05) < 4 * case.dp and abs(X[tip, 1] - 0.02) < 4 * case.dp
