@@ -306,6 +306,27 @@ def measure_leapfrog(args, shape, device, stream, plain):
             "kernels_per_step": 4}
 
 
+def measure_phase_field(args, device, stream):
+    """Phase-field fracture on the full notched plate (500 x 200, FP32) with the two degraded
+    hyperelastic laws: the neo-Hookean J-split and the St. Venant-Kirchhoff spectral split."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    dev = torch.device("cuda", device)
+    out = {}
+    for model in ("nh", "svk"):
+        case = W.notched_plate(model=model, steps=args.steps)
+        g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+        g.step(args.warmup)
+        ms, st = timed_steps(g, args.steps, stream, dev)
+        g.close()
+        out[model] = {"ms_per_step": ms / args.steps, "value": case.n * args.steps / (ms * 1e-3), "status": st}
+    out["workload"] = "notched_plate 500x200 phase field, FP32"
+    out["unit"] = UNIT
+    out["svk_vs_nh"] = out["svk"]["value"] / out["nh"]["value"]
+    return out
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -452,6 +473,7 @@ def run_ours(args):
     batched = measure_batched(args, local, stream) if not args.no_batched else None
     sur = measure_surrogate(args, shape, local, stream, plain) if not args.no_surrogate else None
     leapfrog = measure_leapfrog(args, shape, local, stream, plain)
+    phase_field = measure_phase_field(args, local, stream)
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -484,6 +506,7 @@ def run_ours(args):
         "batched": batched,
         "surrogate": sur,
         "leapfrog": leapfrog,
+        "phase_field": phase_field,
         "status": int(st),
         "cpu_baseline": cpu,
     }

@@ -68,8 +68,13 @@ enum {
     TLSPH_DT_ADAPTIVE = 1,   /* C min(h / (c + |v|max), sqrt(h / |a|max)) from the previous step, per specimen */
     TLSPH_DT_CFL_STATIC = 2  /* C h / c per specimen (c = max sound speed of its materials) */
 };
-/* constitutive models (Sec. 3.3 <constitmodel>) */
-enum { TLSPH_MODEL_NH = 2, TLSPH_MODEL_J2 = 3 };
+/* constitutive models (Sec. 3.3 <constitmodel>):
+ *   SVK  St. Venant-Kirchhoff, S = s^2 S+ + S- with the spectral split of the Green-Lagrange strain
+ *        (Sec. 2.3.1, eq. GLstratinP, GLstratinN, 2PK_SVK1, 2PK_SVK2); the history takes psi+ of
+ *        eq. elasEnergyP;
+ *   NH   compressible neo-Hookean with the J-split of the degradation (Sec. 2.3.2);
+ *   J2   finite-strain J2 plasticity with isotropic hardening (Sec. 2.3.3), no fracture. */
+enum { TLSPH_MODEL_SVK = 1, TLSPH_MODEL_NH = 2, TLSPH_MODEL_J2 = 3 };
 /* boundary-condition kinds (Sec. 3.3.2 <bcvel>, <bcforce type=1|2|3>) */
 enum {
     TLSPH_BC_VEL = 0,        /* masked velocity components are set to value * ramp(t_{n+1}) */
@@ -119,7 +124,7 @@ typedef struct {
 } tlsph_params;
 
 typedef struct {
-    int model;          /* TLSPH_MODEL_NH or TLSPH_MODEL_J2 */
+    int model;          /* TLSPH_MODEL_SVK, TLSPH_MODEL_NH or TLSPH_MODEL_J2 */
     double rho, E, nu;  /* reference density, Young's modulus, Poisson's ratio */
     double sigma_y0;    /* J2: initial yield stress */
     double H_hard;      /* J2: linear hardening modulus */

@@ -1,9 +1,12 @@
 // Constitutive updates of the TLSPH step (device code).
 //
-// Both models take the displacement gradient G = F - I (so that small
+// The models take the displacement gradient G = F - I (so that small
 // strains keep their relative precision in FP32) and return the second
 // Piola-Kirchhoff stress S.
 //
+//  * St. Venant-Kirchhoff with the spectral split of the Green-Lagrange strain
+//    (Sec. 2.3.1): S = s^2 S+ + S-, S+- = lambda {tr E}+- I + 2 mu E+-, where E+-
+//    keep the positive / negative eigenvalues of E.
 //  * Neo-Hookean with the J-split of the phase-field degradation (Sec. 2.3.2):
 //      S = s^2 (Svol + Siso)       J >= 1
 //      S = Svol + s^2 Siso         J <  1
@@ -25,9 +28,10 @@
 namespace tl {
 
 template <typename T> struct MatT {
-    int model;      // 2 NH, 3 J2
+    int model;      // 1 SVK, 2 NH, 3 J2
     int fracture;   // phase field on
     T rho, mu, kappa, sy0, Hh, beta1, beta2, c0, Gc, eps0, s_lim, mass_scale;
+    T lam;          // Lame's first parameter
 };
 
 // x + x^2/2 - log(1 + x) (= (J^2 - 1)/2 - ln J with x = J - 1), series near 0
@@ -138,6 +142,165 @@ template <typename T> TL_HD void eig_traceless(const M3<T> &B, T q2, T e[3]) {
     e[0] = two_sp * t_cos(phi);
     e[1] = two_sp * t_cos(phi + T(2.0943951023931953));
     e[2] = -e[0] - e[1];
+}
+
+// Positive part of the symmetric 2x2 matrix [[a, b], [b, d]] with eigenvalues p1 >= p2: all of
+// it when p2 >= 0, nothing when p1 <= 0, else p1 (A - p2 I) / (p1 - p2) (the spectral projector
+// onto the p1 eigenvector, scaled by p1).
+template <typename T> TL_HD void pos_part2(T a, T b, T d, T &pa, T &pb, T &pd, T &p1, T &p2) {
+    const T m = T(0.5) * (a + d), h = T(0.5) * (a - d);
+    const T r = t_sqrt(h * h + b * b);
+    p1 = m + r;
+    p2 = m - r;
+    if (p2 >= T(0)) {
+        pa = a;
+        pb = b;
+        pd = d;
+    } else if (p1 <= T(0)) {
+        pa = pb = pd = T(0);
+    } else {  // p1 > 0 > p2, so r > 0
+        const T f = p1 / (T(2) * r);
+        pa = f * (a - p2);
+        pb = f * b;
+        pd = f * (d - p2);
+    }
+}
+
+// Spectral split of a symmetric strain (eq. GLstratinP): Ep = Q diag({lambda_a}+) Q^T and the
+// eigenvalues l[3].  In 2D (plane strain) E has the in-plane block and E33 = 0.  In 3D the
+// deviator, scaled to unit largest entry, gives by the trigonometric form its eigenvalue
+// farthest from the other two; that one is accurate and separated from the others by at
+// least half the spectral range, so its eigenvector n, the largest cross product of two rows
+// of (dev E - e I), is accurate too.  The other two eigenvalues are those of the 2x2 block of E
+// in the plane orthogonal to n, found in closed form, so near-equal eigenvalues (which the
+// trigonometric form resolves only to sqrt(eps)) keep full accuracy.
+template <typename T, int DIM> TL_HD void strain_split(const M3<T> &E, M3<T> &Ep, T l[3]) {
+    if (DIM == 2) {
+        T pa, pb, pd;
+        pos_part2(E.a[0], E.a[1], E.a[4], pa, pb, pd, l[0], l[1]);
+        l[2] = T(0);
+        Ep = m3_zero<T>();
+        Ep.a[0] = pa;
+        Ep.a[1] = Ep.a[3] = pb;
+        Ep.a[4] = pd;
+        return;
+    }
+    const T t = trace(E) / T(3);
+    M3<T> B = E;
+    B.a[0] -= t;
+    B.a[4] -= t;
+    B.a[8] -= t;
+    T sc = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) sc = t_max(sc, t_abs(B.a[q]));
+    if (!(sc > T(0))) {  // isotropic
+        l[0] = l[1] = l[2] = t;
+        Ep = t > T(0) ? E : m3_zero<T>();
+        return;
+    }
+    const T isc = T(1) / sc;
+#pragma unroll
+    for (int q = 0; q < 9; q++) B.a[q] *= isc;
+    T e[3];
+    eig_traceless(B, trace_mul(B, B), e);  // e[0] largest, e[1] smallest, e[2] between
+    const T ei = (e[0] - e[2] >= e[2] - e[1]) ? e[0] : e[1];
+    // eigenvector of ei: null vector of M = B - ei I from the largest cross product of two rows
+    T r[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) r[i][j] = B.a[3 * i + j] - (i == j ? ei : T(0));
+    T n[3] = {T(0), T(0), T(0)}, best = T(-1);
+#pragma unroll
+    for (int pr = 0; pr < 3; pr++) {
+        const int i = pr == 2 ? 1 : 0, j = pr == 0 ? 1 : 2;
+        const T c0 = r[i][1] * r[j][2] - r[i][2] * r[j][1];
+        const T c1 = r[i][2] * r[j][0] - r[i][0] * r[j][2];
+        const T c2 = r[i][0] * r[j][1] - r[i][1] * r[j][0];
+        const T nn = c0 * c0 + c1 * c1 + c2 * c2;
+        if (nn > best) {
+            best = nn;
+            n[0] = c0;
+            n[1] = c1;
+            n[2] = c2;
+        }
+    }
+    T inv = T(1) / t_sqrt(best);
+    n[0] *= inv;
+    n[1] *= inv;
+    n[2] *= inv;
+    // orthonormal u, v spanning the plane orthogonal to n: u = e_k x n for the axis k least aligned with n
+    T u[3];
+    const T a0 = t_abs(n[0]), a1 = t_abs(n[1]), a2 = t_abs(n[2]);
+    if (a0 <= a1 && a0 <= a2) {
+        u[0] = T(0), u[1] = -n[2], u[2] = n[1];
+    } else if (a1 <= a2) {
+        u[0] = n[2], u[1] = T(0), u[2] = -n[0];
+    } else {
+        u[0] = -n[1], u[1] = n[0], u[2] = T(0);
+    }
+    inv = T(1) / t_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    u[0] *= inv;
+    u[1] *= inv;
+    u[2] *= inv;
+    const T v[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+    // the 2x2 block of B in (u, v)
+    T Bu[3], Bv[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        Bu[i] = B.a[3 * i] * u[0] + B.a[3 * i + 1] * u[1] + B.a[3 * i + 2] * u[2];
+        Bv[i] = B.a[3 * i] * v[0] + B.a[3 * i + 1] * v[1] + B.a[3 * i + 2] * v[2];
+    }
+    const T buu = u[0] * Bu[0] + u[1] * Bu[1] + u[2] * Bu[2];
+    const T buv = v[0] * Bu[0] + v[1] * Bu[1] + v[2] * Bu[2];
+    const T bvv = v[0] * Bv[0] + v[1] * Bv[1] + v[2] * Bv[2];
+    T pa, pb, pd;
+    pos_part2(sc * buu + t, sc * buv, sc * bvv + t, pa, pb, pd, l[1], l[2]);
+    l[0] = sc * ei + t;
+    const T lo = t_min(l[0], l[2]), hi = t_max(l[0], l[1]);
+    if (lo >= T(0)) {
+        Ep = E;
+        return;
+    }
+    if (hi <= T(0)) {
+        Ep = m3_zero<T>();
+        return;
+    }
+    const T li = t_max(l[0], T(0));
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            Ep.a[3 * i + j] = li * n[i] * n[j] + pa * u[i] * u[j] + pb * (u[i] * v[j] + v[i] * u[j]) + pd * v[i] * v[j];
+}
+
+// St. Venant-Kirchhoff stress with the spectral split (eq. elasEnergyP, elasEnergyN, 2PK_SVK1,
+// 2PK_SVK2): S = s^2 (lambda {tr E}+ I + 2 mu E+) + lambda {tr E}- I + 2 mu E-, E = (C - I) / 2.
+template <typename T, int DIM>
+TL_HD void svk_stress(const Kin<T> &k, T s, const MatT<T> &m, M3<T> &S, T &psi_plus, T &psi_minus) {
+    M3<T> E;
+#pragma unroll
+    for (int q = 0; q < 9; q++) E.a[q] = T(0.5) * k.E2.a[q];
+    M3<T> Ep;
+    T l[3];
+    strain_split<T, DIM>(E, Ep, l);
+    const T tr = trace(E);
+    const T trp = t_max(tr, T(0)), trm = t_min(tr, T(0));
+    T sp2 = T(0), sm2 = T(0);
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const T lp = t_max(l[q], T(0)), lm = t_min(l[q], T(0));
+        sp2 += lp * lp;
+        sm2 += lm * lm;
+    }
+    psi_plus = T(0.5) * m.lam * trp * trp + m.mu * sp2;
+    psi_minus = T(0.5) * m.lam * trm * trm + m.mu * sm2;
+    const T s2 = s * s, mu2 = T(2) * m.mu;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const T id = (q % 4 == 0) ? T(1) : T(0);
+        S.a[q] = s2 * (m.lam * trp * id + mu2 * Ep.a[q]) + (m.lam * trm * id + mu2 * (E.a[q] - Ep.a[q]));
+    }
 }
 
 // exp(X) - I by scaling and squaring of a Taylor series (order 6 in FP32, 12 in FP64).

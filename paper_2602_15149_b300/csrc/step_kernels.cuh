@@ -247,7 +247,8 @@ __device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T 
         }
     } else {
         T pp, pm;
-        nh_stress(kin, s, m, S, pp, pm);
+        if (m.model == 1) svk_stress<T, DIM>(kin, s, m, S, pp, pm);
+        else nh_stress(kin, s, m, S, pp, pm);
         psi = s * s * pp + pm;
         if (!DIAG && frac && pp > a.H[i]) a.H[i] = pp;  // eq. irreversibility
     }

@@ -567,6 +567,7 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         d.eps0 = (T)m.eps0;
         d.s_lim = (T)m.s_lim;
         d.mass_scale = T(1);
+        d.lam = (T)lam;
     }
     std::vector<char> used(c->mats.size(), 0);
     for (int64_t pi = 0; pi < n; pi++) used[c->midh[pi]] = 1;
@@ -1337,7 +1338,7 @@ tlsph_status tlsph_set_materials(tlsph_ctx *c, int n, const tlsph_material *m) {
     for (int i = 0; i < n; i++) {
         if (!(m[i].E > 0.0) || !(m[i].nu > -1.0 && m[i].nu < 0.5) || !(m[i].rho > 0.0))
             return fail(c, TLSPH_ERR_ARG, "material %d: need E > 0, -1 < nu < 0.5, rho > 0", i);
-        if (m[i].model != TLSPH_MODEL_NH && m[i].model != TLSPH_MODEL_J2)
+        if (m[i].model != TLSPH_MODEL_SVK && m[i].model != TLSPH_MODEL_NH && m[i].model != TLSPH_MODEL_J2)
             return fail(c, TLSPH_ERR_ARG, "material %d: unknown model %d", i, m[i].model);
         if (m[i].model == TLSPH_MODEL_J2 && !(m[i].sigma_y0 > 0.0))
             return fail(c, TLSPH_ERR_ARG, "material %d: J2 needs sigma_y0 > 0", i);

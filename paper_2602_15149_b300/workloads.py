@@ -19,6 +19,10 @@ these lattices stand in for them at the same scale):
   0.05 m at mid-height, phase-field fracture of a neo-Hookean (or St. Venant-
   Kirchhoff) solid, +-1 MPa traction on the top and bottom rows (500 x 200
   particles is the full case).
+* ``crack_branching`` -- the paper's dynamic crack-branching benchmark (Sec. 4,
+  crack branching): the notched plate in plane strain at dx = 0.0625 mm
+  (1600 x 640 = 1,024,000 particles), St. Venant-Kirchhoff, eps0 = 2 dx,
+  s_l = 0.05, C_CFL = 0.2, beta1 = 0.2, constant 1 MPa traction, run to 80-120 us.
 * ``batched``       -- many independent 2D specimens of log-uniform size with
   random materials and loading (512 specimens is the full case).
 
@@ -162,6 +166,17 @@ def notched_plate(nx=500, ny=200, width=0.1, height=0.04, notch_len=0.05, tracti
     return Case("notched_plate_pf" if model == "nh" else "notched_plate_pf_" + model, 2, dp, 1.5 * dp, 0.3, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dp * dp),
                 np.zeros((n, 2)), np.zeros(n, np.int32), None, bcs, [np.array(notch, dtype=np.float64)], steps,
                 precision)
+
+
+def crack_branching(nx=1600, ny=640, t_end=80e-6, precision="fp32"):
+    """The paper's crack-branching case: the 100 x 40 mm notched plate with the degraded SVK law,
+    its soft-particle limit (0.05) and Courant number (0.2).  ``steps`` is only a size hint (t_end
+    over 0.2 h / REF_WAVE_SPEED); runs of this case stop on the simulated time instead."""
+    case = notched_plate(nx=nx, ny=ny, traction=1e6, precision=precision, s_lim=0.05, beta1=0.2, model="svk")
+    case.name = "crack_branching_svk"
+    case.cfl = 0.2
+    case.steps = int(math.ceil(t_end / (0.2 * case.h / REF_WAVE_SPEED)))
+    return case
 
 
 def batched(nspec=512, n_min=500, n_max=50000, dp=1e-3, seed=0, steps=1000, precision="fp32"):

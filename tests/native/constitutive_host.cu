@@ -10,6 +10,7 @@ template <typename T> static MatT<T> mat(double E, double nu, double sy0, double
     m.model = 3;
     m.mu = (T)mu;
     m.kappa = (T)(lam + 2.0 * mu / 3.0);
+    m.lam = (T)lam;
     m.sy0 = (T)sy0;
     m.Hh = (T)Hh;
     return m;
@@ -47,7 +48,31 @@ static void nh(const double *G, double sphase, double E, double nu, double *S, d
     *pm = b;
 }
 
+template <typename T, int DIM>
+static void svk(const double *G, double sphase, double E, double nu, double *S, double *pp, double *pm) {
+    M3<T> g;
+    for (int q = 0; q < 9; q++) g.a[q] = (T)G[q];
+    MatT<T> m = mat<T>(E, nu, 0.0, 0.0);
+    m.model = 1;
+    Kin<T> kin = kinematics(g);
+    M3<T> s;
+    T a, b;
+    svk_stress<T, DIM>(kin, (T)sphase, m, s, a, b);
+    for (int q = 0; q < 9; q++) S[q] = s.a[q];
+    *pp = a;
+    *pm = b;
+}
+
 extern "C" {
+void hc_svk(int prec, int dim, const double *G, double s, double E, double nu, double *S, double *pp, double *pm) {
+    if (prec == 64) {
+        if (dim == 3) svk<double, 3>(G, s, E, nu, S, pp, pm);
+        else svk<double, 2>(G, s, E, nu, S, pp, pm);
+    } else {
+        if (dim == 3) svk<float, 3>(G, s, E, nu, S, pp, pm);
+        else svk<float, 2>(G, s, E, nu, S, pp, pm);
+    }
+}
 int hc_j2_d(const double *G, const double *K6, double ep, double E, double nu, double sy0, double Hh, double *K6o,
             double *epo, double *S, double *dg) {
     return j2<double>(G, K6, ep, E, nu, sy0, Hh, K6o, epo, S, dg);

@@ -1,7 +1,7 @@
 """The library's constitutive device code, compiled for the host, against the FP64 oracle.
 
 tests/native/constitutive_host.cu includes csrc/constitutive.cuh unchanged and is built
-with nvcc as host code, so the GPU's NH and J2 (C_p^-1 form) arithmetic is checked on
+with nvcc as host code, so the GPU's SVK (spectral split), NH and J2 (C_p^-1 form) arithmetic is checked on
 the CPU in both FP64 and FP32, without a GPU.
 """
 import ctypes as C
@@ -12,7 +12,8 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from tests.test_oracle_pins import STEEL_J2, STEEL_NH, _plastic_state, _trial_F
+from tests.test_oracle_pins import (STEEL_J2, STEEL_NH, SVK, _F_of_E, _plastic_state, _trial_F, lame,
+                                     rand_rotation)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "native", "constitutive_host.cu")
@@ -32,6 +33,7 @@ def hc():
         f.argtypes = [D, D, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, D, D, D, D]
     for f in (lib.hc_nh_d, lib.hc_nh_f):
         f.argtypes = [D, C.c_double, C.c_double, C.c_double, D, D, D]
+    lib.hc_svk.argtypes = [C.c_int, C.c_int, D, C.c_double, C.c_double, C.c_double, D, D, D]
     return lib
 
 
@@ -104,3 +106,52 @@ def test_nh_matches_oracle(hc, prec, tol):
             floor = 1e-15 * STEEL_NH.E
             assert abs(pp.value - ppo) <= 50 * tol * abs(ppo) + floor
             assert abs(pm.value - pmo) <= 50 * tol * abs(pmo) + floor
+
+
+# ---------------------------------------------------------------- St. Venant-Kirchhoff split
+def _svk(hc, prec, dim, F, s):
+    G = np.ascontiguousarray(F - np.eye(3)).ravel()
+    S = np.zeros(9)
+    pp, pm = C.c_double(), C.c_double()
+    hc.hc_svk(prec, dim, _p(G), s, SVK.E, SVK.nu, _p(S), C.byref(pp), C.byref(pm))
+    return S.reshape(3, 3), pp.value, pm.value
+
+
+def _svk_strains(rng, dim):
+    """Strains whose spectra the split finds hardest: repeated, near-equal straddling zero, isotropic,
+    single-signed, and generic, in random frames (in-plane frames in 2D)."""
+    spectra = [(1e-3, -2e-4, -2e-4), (-1e-3, 2e-4, 2e-4), (1e-3, 1e-9, -1e-9), (1e-3, -1e-9, -1e-9),
+               (3e-4, 3e-4, 3e-4), (-3e-4, -3e-4, -3e-4), (1e-3, 5e-4, 2e-4), (-1e-3, -5e-4, -2e-4),
+               (1e-3, 0.0, 0.0), (2e-3, -1e-3, 3e-7), (1e-3, 1e-3 * (1 + 1e-7), -4e-4), (0.0, 0.0, 0.0)]
+    spectra += [tuple(rng.normal(scale=1e-3, size=3)) for _ in range(40)]
+    out = []
+    for lam in spectra:
+        if dim == 2:
+            R = np.eye(3)
+            th = rng.uniform(0, np.pi)
+            R[:2, :2] = [[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]]
+            E = R @ np.diag([lam[0], lam[1], 0.0]) @ R.T
+        else:
+            R = rand_rotation(rng)
+            E = R @ np.diag(lam) @ R.T
+        out.append(E)
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec,tol", [(64, 2e-12), (32, 2e-6)])
+def test_svk_split_matches_oracle(hc, dim, prec, tol):
+    """Stress and both energies of the device split against the oracle's Jacobi split, for degraded and
+    intact particles, relative to the stress scale of the strain (FP32 is bounded by the rounding of E
+    itself, about eps |E|)."""
+    rng = np.random.default_rng(11 + dim)
+    lam, mu = lame(SVK.E, SVK.nu)
+    for E in _svk_strains(rng, dim):
+        F = _F_of_E(E)
+        for s in (1.0, 0.4, 0.0):
+            So, ppo, pmo = O.svk_stress(F, s, SVK)
+            Sd, ppd, pmd = _svk(hc, prec, dim, F, s)
+            scale = max((lam + 2 * mu) * np.abs(E).max(), 1.0)
+            assert np.abs(Sd - So).max() <= tol * scale, (E, s, Sd, So)
+            escale = max((lam + 2 * mu) * np.abs(E).max() ** 2, 1e-30)
+            assert abs(ppd - ppo) <= tol * escale and abs(pmd - pmo) <= tol * escale
