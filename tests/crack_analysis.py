@@ -41,16 +41,28 @@ def runs(col):
 def branched_columns(cracked, j0, gap):
     """Columns whose cracked cells form a run wholly above the notch plane and one wholly below it,
     each at least ``gap`` rows from it (the two branches, with intact material between them).
-    Returns {column: (centre row above, centre row below)}."""
+    Returns {column: (centre row of the lowest run above, centre row of the highest run below)}."""
+    ny = cracked.shape[0]
+    pad = np.zeros((1, cracked.shape[1]), bool)
+    prev = np.vstack([pad, cracked[:-1]])
+    nxt = np.vstack([cracked[1:], pad])
+    starts = cracked & ~prev
+    ends = cracked & ~nxt
+    R = np.arange(ny)[:, None]
+    j_up = int(math.ceil(j0 + gap))
+    j_lo = int(math.floor(j0 - gap))
+    up_c = starts & (R >= j_up)
+    lo_c = ends & (R <= j_lo)
+    has = up_c.any(axis=0) & lo_c.any(axis=0)
     out = {}
-    for i in range(cracked.shape[1]):
-        rs = runs(cracked[:, i])
-        up = [r for r in rs if r[0] >= j0 + gap]
-        lo = [r for r in rs if r[1] <= j0 - gap]
-        if up and lo:
-            u = min(up, key=lambda r: r[0])
-            d = max(lo, key=lambda r: r[1])
-            out[i] = (0.5 * (u[0] + u[1]), 0.5 * (d[0] + d[1]))
+    if not has.any():
+        return out
+    up_first = np.argmax(up_c, axis=0)
+    up_end = np.argmax(ends & (R >= up_first[None, :]), axis=0)
+    lo_last = ny - 1 - np.argmax(lo_c[::-1], axis=0)
+    lo_start = ny - 1 - np.argmax((starts & (R <= lo_last[None, :]))[::-1], axis=0)
+    for i in np.nonzero(has)[0]:
+        out[int(i)] = (0.5 * (up_first[i] + up_end[i]), 0.5 * (lo_start[i] + lo_last[i]))
     return out
 
 

@@ -58,3 +58,22 @@ def test_asymmetric_pattern_is_reported():
     g = tr.geometry()
     assert g["asymmetry"] > 0.3
     assert g["angle_lo_deg"] - g["angle_up_deg"] > 12.0
+
+
+def test_vectorised_branch_detection_equals_column_scan():
+    """branched_columns against a plain per-column scan of the runs, on random patterns."""
+    from tests.crack_analysis import branched_columns
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        ny, nx = rng.integers(10, 40), rng.integers(1, 20)
+        c = rng.random((ny, nx)) < rng.uniform(0.05, 0.6)
+        j0, gap = rng.uniform(2, ny - 3), int(rng.integers(0, 4))
+        ref = {}
+        for i in range(nx):
+            rs = runs(c[:, i])
+            up = [r for r in rs if r[0] >= j0 + gap]
+            lo = [r for r in rs if r[1] <= j0 - gap]
+            if up and lo:
+                u, d = min(up, key=lambda r: r[0]), max(lo, key=lambda r: r[1])
+                ref[i] = (0.5 * (u[0] + u[1]), 0.5 * (d[0] + d[1]))
+        assert branched_columns(c, j0, gap) == ref
