@@ -327,6 +327,44 @@ def measure_phase_field(args, device, stream):
     return out
 
 
+def measure_crack_branching(args, device, stream):
+    """The paper's crack-branching case at its published size (1600 x 640 = 1,024,000 particles, SVK,
+    phase field) run to 80 us: throughput of the stepping (CUDA events around each 1 us chunk; the
+    read-back of s between chunks is not timed) and the crack's milestones against the printed values."""
+    import torch
+    from paper_2602_15149_b300 import crack, tlsph
+
+    dev = torch.device("cuda", device)
+    case = W.crack_branching(t_end=80e-6)
+    g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    g.step(1)
+    t, dt = g.time()
+    per = max(1, int(round(1e-6 / dt)))
+    split = crack.CrackTracker(case.X0, case.dp, 0.02, 0.05, threshold=0.25, branch_gap_rows=1)
+    sustained = crack.CrackTracker(case.X0, case.dp, 0.02, 0.05, threshold=0.25, branch_gap_rows=4)
+    ms, steps, st = 0.0, 1, 0
+    while t < 80e-6:
+        m, st1 = timed_steps(g, per, stream, dev)
+        ms += m
+        steps += per
+        st |= st1
+        t, dt = g.time()
+        sv = g.read_state("S")
+        split.add(t, sv)
+        sustained.add(t, sv)
+    g.close()
+    geo = sustained.geometry()
+    us = lambda x: None if x is None else x * 1e6
+    return {"workload": "crack_branching 1600x640 SVK phase field (the paper's case), to 80 us, FP32",
+            "particles": case.n, "steps": steps, "ms_per_step": ms / (steps - 1),
+            "value": case.n * (steps - 1) / (ms * 1e-3), "unit": UNIT, "status": st,
+            "t_initiation_us": us(split.t_init), "t_first_split_us": us(split.t_branch),
+            "t_sustained_branches_us": us(sustained.t_branch),
+            "branch_x_mm": None if geo["branch_x"] is None else geo["branch_x"] * 1e3,
+            "divergence_angle_deg": geo["angle_deg"], "asymmetry": geo["asymmetry"],
+            "paper": {"t_initiation_us": 14.0, "t_branching_us": 35.0, "divergence_angle_deg": 60.0}}
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -474,6 +512,7 @@ def run_ours(args):
     sur = measure_surrogate(args, shape, local, stream, plain) if not args.no_surrogate else None
     leapfrog = measure_leapfrog(args, shape, local, stream, plain)
     phase_field = measure_phase_field(args, local, stream)
+    crack_b = measure_crack_branching(args, local, stream) if not args.no_crack else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -507,6 +546,7 @@ def run_ours(args):
         "surrogate": sur,
         "leapfrog": leapfrog,
         "phase_field": phase_field,
+        "crack_branching": crack_b,
         "status": int(st),
         "cpu_baseline": cpu,
     }
@@ -526,6 +566,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
     ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching case")
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
     ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")

@@ -106,6 +106,8 @@ def load_oracle():
     lib.orc_sym_eig3.argtypes = [D, D, D]
     lib.orc_sym_eig3.restype = None
     lib.orc_j2_update.argtypes = [D, D, C.c_double, C.POINTER(_Material), D, D, D, D, C.POINTER(C.c_int)]
+    lib.orc_set_bc_values.argtypes = [C.c_void_p, C.c_int, C.c_int, D, C.POINTER(C.c_uint8)]
+    lib.orc_prepare_step.argtypes = [C.c_void_p]
     _lib = lib
     return lib
 
@@ -124,7 +126,8 @@ class Oracle:
 
     def __init__(self, dim: int, h: float, cfl: float = 0.3, dt_mode: int = DT_CFL_STATIC,
                  fixed_dt: float = 0.0, gravity=(0.0, 0.0, 0.0), support: float = 2.0,
-                 visc_literal: bool = False, lap_uncorrected: bool = False, integrator: int = 1):
+                 visc_literal: bool = False, lap_uncorrected: bool = False, integrator: int = 1,
+                 dx: float | None = None):
         self.lib = load_oracle()
         p = _Params(dim, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity), int(visc_literal),
                     int(lap_uncorrected), int(integrator))
@@ -133,6 +136,10 @@ class Oracle:
             raise ValueError("invalid oracle parameters")
         self.dim = dim
         self.n = 0
+        self.dx = h / 1.5 if dx is None else dx  # the expression variable dx (particle spacing)
+        self.integrator = integrator
+        self._exbcs = []
+        self._nbc = 0
 
     def __del__(self):
         if getattr(self, "ctx", None):
@@ -159,6 +166,8 @@ class Oracle:
                                              None if sid is None else sid.ctypes.data_as(C.POINTER(C.c_int32))),
                "create_particles")
         self.n = n
+        self._X0 = X0.copy()
+        self._spec = np.zeros(n, np.int64) if sid is None else sid.astype(np.int64)
 
     def add_bc(self, mask, kind, comp_mask, value, t_start=0.0, t_end=-1.0, ramp=0.0, area=0.0):
         m = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -166,6 +175,57 @@ class Oracle:
         val[:len(value)] = value
         _check(self.lib.orc_add_bc(self.ctx, m.ctypes.data_as(C.POINTER(C.c_uint8)), kind, comp_mask, _dp(val),
                                    t_start, t_end, ramp, area), "add_bc")
+        self._nbc += 1
+        return self._nbc - 1
+
+    def add_bc_expr(self, mask, kind, comp_mask, exprs, t_start=0.0, t_end=-1.0, area=0.0):
+        """A condition whose component k takes the value of exprs[k] (an oracle.expr.Expression) per particle
+        and per step; skipped values leave the component alone.  Velocity values are evaluated at the time
+        the step prescribes them (t_{n+1}; Algorithm 2 also t_{n+1/2} for the predictor), force values at
+        the time of the forces, all with the displacement at the start of the step."""
+        b = self.add_bc(mask, kind, comp_mask, (0.0, 0.0, 0.0), t_start, t_end, 0.0, area)
+        self._exbcs.append((b, kind, comp_mask, list(exprs) + [None] * (3 - len(exprs))))
+        return b
+
+    def variables(self, t_offset=0.0):
+        """The built-in expression variables of every particle at t_n + t_offset * dt (state at t_n)."""
+        from oracle.expr import particle_variables
+        nspec = int(self._spec.max()) + 1 if self.n else 1
+        ts = np.array([self.time(s) for s in range(nspec)])
+        t, dt = ts[self._spec, 0], ts[self._spec, 1]
+        return particle_variables(self._X0, self.read("U"), t + t_offset * dt, dt, self.dx)
+
+    def apply_expr(self, field: str, exprs, t_offset=0.0):
+        """Set the components of a state field ("U" or "V") to expressions evaluated now (None or a skipped
+        value leaves a component as it is)."""
+        vars_ = self.variables(t_offset)
+        cur = self.read(field).copy()
+        for k, e in enumerate(list(exprs)[:self.dim]):
+            if e is None:
+                continue
+            val, skip = e.evaluate(**vars_)
+            cur[~skip, k] = val[~skip]
+        self.write(field, cur)
+
+    def _set_expr_values(self):
+        _check(self.lib.orc_prepare_step(self.ctx), "prepare_step")
+        leap = self.integrator == 2
+        for b, kind, cm, exprs in self._exbcs:
+            if kind == 0:
+                phases = [(0, 1.0)] + ([(1, 0.5)] if leap else [])
+            else:
+                phases = [(0, 0.5 if leap else 0.0)]
+            for phase, off in phases:
+                vars_ = self.variables(off)
+                val = np.zeros((self.n, 3))
+                skip = np.ones((self.n, 3), np.uint8)
+                for k in range(3):
+                    if (cm >> k) & 1 and exprs[k] is not None:
+                        v, sk = exprs[k].evaluate(**vars_)
+                        val[:, k] = v
+                        skip[:, k] = sk
+                _check(self.lib.orc_set_bc_values(self.ctx, b, phase, _dp(val), skip.ctypes.data_as(
+                    C.POINTER(C.c_uint8))), "set_bc_values")
 
     def add_notch(self, quad):
         q = np.ascontiguousarray(quad, dtype=np.float64).reshape(12)
@@ -190,7 +250,12 @@ class Oracle:
         return p
 
     def step(self, nsteps: int = 1):
-        _check(self.lib.orc_step(self.ctx, nsteps), "step")
+        if not self._exbcs:
+            _check(self.lib.orc_step(self.ctx, nsteps), "step")
+            return
+        for _ in range(nsteps):  # expressions are evaluated before every step
+            self._set_expr_values()
+            _check(self.lib.orc_step(self.ctx, 1), "step")
 
     def read(self, field: str):
         per = {"U": self.dim, "V": self.dim, "X": self.dim, "ACC": self.dim, "P": 9, "F": 9, "FP": 9, "L": 9,

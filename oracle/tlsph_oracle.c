@@ -82,6 +82,10 @@ typedef struct {
     double t_start, t_end, ramp, area;
     uint8_t *mask;
     int64_t count;
+    /* user-defined expressions (Sec. 3.3): per-particle prescribed values (n x 3) and skip flags set
+     * before each step by the caller; [0] for the step's value, [1] for the leapfrog predictor */
+    double *exval[2];
+    uint8_t *exskip[2];
 } orc_bc;
 
 typedef struct orc_ctx {
@@ -504,7 +508,13 @@ static void free_particles(orc_ctx *c) {
     free(c->sdd); free(c->lap); free(c->pf_b); free(c->pf_k); free(c->pf_g); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
     free(c->P); free(c->L); free(c->status); free(c->row_ptr); free(c->col); free(c->perm);
     free(c->t); free(c->dt); free(c->vmax); free(c->amax); free(c->cmax);
-    for (int b = 0; b < c->nbc; b++) free(c->bc[b].mask);
+    for (int b = 0; b < c->nbc; b++) {
+        free(c->bc[b].mask);
+        for (int ph = 0; ph < 2; ph++) {
+            free(c->bc[b].exval[ph]);
+            free(c->bc[b].exskip[ph]);
+        }
+    }
     c->nbc = 0;
 }
 
@@ -589,6 +599,7 @@ int orc_add_bc(orc_ctx *c, const uint8_t *mask, int kind, int comp_mask, const d
                double t_end, double ramp, double area) {
     if (!c || !mask || !value || c->n <= 0 || c->nbc >= ORC_MAX_BC || kind < 0 || kind > 3) return ORC_ERR_ARG;
     orc_bc *b = &c->bc[c->nbc];
+    memset(b, 0, sizeof *b);
     b->kind = kind;
     b->comp_mask = comp_mask;
     memcpy(b->value, value, 3 * sizeof(double));
@@ -601,6 +612,20 @@ int orc_add_bc(orc_ctx *c, const uint8_t *mask, int kind, int comp_mask, const d
     b->count = 0;
     for (int64_t i = 0; i < c->n; i++) b->count += mask[i] ? 1 : 0;
     c->nbc++;
+    return ORC_OK;
+}
+
+/* Per-particle values of a boundary condition given by expressions (caller order, n x 3, and a skip
+ * flag per value); phase 0 is used by the step's update, phase 1 by the Algorithm 2 predictor. */
+int orc_set_bc_values(orc_ctx *c, int b, int phase, const double *val, const uint8_t *skip) {
+    if (!c || b < 0 || b >= c->nbc || phase < 0 || phase > 1 || !val || !skip) return ORC_ERR_ARG;
+    orc_bc *bc = &c->bc[b];
+    if (!bc->exval[phase]) {
+        bc->exval[phase] = (double *)malloc(sizeof(double) * 3 * c->n);
+        bc->exskip[phase] = (uint8_t *)malloc(3 * c->n);
+    }
+    memcpy(bc->exval[phase], val, sizeof(double) * 3 * c->n);
+    memcpy(bc->exskip[phase], skip, 3 * c->n);
     return ORC_OK;
 }
 
@@ -962,11 +987,21 @@ static double bc_factor(const orc_bc *b, double t) {
     return 1.0;
 }
 
-/* One step of Algorithm 1 for all particles. */
-static int one_step(orc_ctx *c) {
-    int64_t n = c->n;
-    int d = c->p.dim;
-    /* step sizes per specimen (eq. dt_criterion) */
+/* The value a condition prescribes for component k of particle i (factor f = bc_factor >= 0): the
+ * ramped constant, or the expression's value; returns 0 when the expression skips it. */
+static int bc_value(const orc_bc *b, int phase, int64_t i, int k, double f, double *out) {
+    if (b->exval[0]) {
+        const int ph = b->exval[phase] ? phase : 0;
+        if (b->exskip[ph][3 * i + k]) return 0;
+        *out = b->exval[ph][3 * i + k];
+        return 1;
+    }
+    *out = f * b->value[k];
+    return 1;
+}
+
+/* Step sizes per specimen (eq. dt_criterion), from the state the next step starts from. */
+static void step_sizes(orc_ctx *c) {
     for (int s = 0; s < c->nspec; s++) {
         double h = c->p.h;
         if (c->p.dt_mode == ORC_DT_FIXED) {
@@ -979,6 +1014,21 @@ static int one_step(orc_ctx *c) {
             c->dt[s] = c->p.cfl * (dtv < dta ? dtv : dta);
         }
     }
+}
+
+/* Sets the step sizes of the next step (orc_time then reports them), so that a caller can evaluate
+ * time-dependent expressions for it. */
+int orc_prepare_step(orc_ctx *c) {
+    if (!c || !c->built) return ORC_ERR_STATE;
+    step_sizes(c);
+    return ORC_OK;
+}
+
+/* One step of Algorithm 1 (or 2) for all particles. */
+static int one_step(orc_ctx *c) {
+    int64_t n = c->n;
+    int d = c->p.dim;
+    step_sizes(c);
     /* Algorithm 2, predictor: the forces of this step act at the half level,
      *   u_{n+1/2} = u_n + dt/2 v_n,  v_{n+1/2} = v_n + dt/2 a_{n-1/2},  s_{n+1/2} = s_n + dt/2 sdot_n;
      * reading: velocity BCs hold at t_{n+1/2} for v_{n+1/2} (which enters the viscosity), and
@@ -1000,8 +1050,10 @@ static int one_step(orc_ctx *c) {
                 if (bc->kind != ORC_BC_VEL || !bc->mask[i]) continue;
                 double f = bc_factor(bc, th);
                 if (f < 0.0) continue;
-                for (int k = 0; k < d; k++)
-                    if (bc->comp_mask & (1 << k)) c->v[3 * i + k] = f * bc->value[k];
+                for (int k = 0; k < d; k++) {
+                    double val;
+                    if ((bc->comp_mask & (1 << k)) && bc_value(bc, 1, i, k, f, &val)) c->v[3 * i + k] = val;
+                }
             }
             if (is_fracture(c, i)) {
                 double sh = c->s[i] + 0.5 * dt * c->sdot[i];
@@ -1089,8 +1141,8 @@ static int one_step(orc_ctx *c) {
             double f = bc_factor(bc, t_n);
             if (f < 0.0) continue;
             for (int k = 0; k < d; k++) {
-                if (!(bc->comp_mask & (1 << k))) continue;
-                double val = f * bc->value[k];
+                double val;
+                if (!(bc->comp_mask & (1 << k)) || !bc_value(bc, 0, i, k, f, &val)) continue;
                 if (bc->kind == ORC_BC_TRACTION) a[k] += val * bc->area / mass;
                 else if (bc->kind == ORC_BC_ACCEL) a[k] += val;
                 else a[k] += val / ((double)bc->count * mass);
@@ -1132,8 +1184,10 @@ static int one_step(orc_ctx *c) {
             if (bc->kind != ORC_BC_VEL || !bc->mask[i]) continue;
             double f = bc_factor(bc, t1);
             if (f < 0.0) continue;
-            for (int k = 0; k < d; k++)
-                if (bc->comp_mask & (1 << k)) vn[k] = f * bc->value[k];
+            for (int k = 0; k < d; k++) {
+                double val;
+                if ((bc->comp_mask & (1 << k)) && bc_value(bc, 0, i, k, f, &val)) vn[k] = val;
+            }
         }
         double vv = 0.0, aa = 0.0;
         /* u_{n+1} = u_n + dt v_{n+1} (Algorithm 1); u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2) */

@@ -1,4 +1,4 @@
-"""Crack geometry of the notched plate from its phase field (test infrastructure).
+"""Crack geometry of the notched plate from its phase field (post-processing of read-back state).
 
 The plate is a regular lattice X = ((i + 1/2) dp, (j + 1/2) dp), so the phase field s maps to an
 (ny, nx) image.  A cell is cracked when s < threshold.  From a sequence of images this extracts what
@@ -67,7 +67,12 @@ def branched_columns(cracked, j0, gap):
 
 
 class CrackTracker:
-    """Feed (t, s) snapshots of the notched plate; read the crack's milestones."""
+    """Feed (t, s) snapshots of the notched plate; read the crack's milestones.
+
+    ``t_init``: first snapshot with a cracked cell ahead of the notch tip.  ``t_branch``: first snapshot
+    in which some column ahead of the tip holds cracked runs on both sides of the notch plane, each at
+    least ``branch_gap_rows`` rows from it.  With one row this is the first split of the crack band;
+    with a few rows, sustained branches."""
 
     def __init__(self, X0, dp, y0, notch_len, threshold=0.25, branch_gap_rows=4):
         self.X0, self.dp, self.thr = X0, dp, threshold

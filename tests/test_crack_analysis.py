@@ -4,7 +4,7 @@ import math
 import numpy as np
 
 from paper_2602_15149_b300 import workloads as W
-from tests.crack_analysis import CrackTracker, image, runs
+from paper_2602_15149_b300.crack import CrackTracker, image, runs
 
 
 def _y_crack(case, x_b, half_angle_deg, x_end, width, tilt_lo=0.0):
@@ -62,7 +62,7 @@ def test_asymmetric_pattern_is_reported():
 
 def test_vectorised_branch_detection_equals_column_scan():
     """branched_columns against a plain per-column scan of the runs, on random patterns."""
-    from tests.crack_analysis import branched_columns
+    from paper_2602_15149_b300.crack import branched_columns
     rng = np.random.default_rng(0)
     for _ in range(200):
         ny, nx = rng.integers(10, 40), rng.integers(1, 20)
