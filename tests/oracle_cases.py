@@ -12,6 +12,7 @@ def oracle_material(m: W.Material) -> OracleMaterial:
 
 def make_oracle(case: W.Case, build=True, method=None, **kw) -> Oracle:
     kw.setdefault("integrator", getattr(case, "integrator", 1))
+    kw.setdefault("dx", case.dp)
     o = Oracle(case.dim, case.h, cfl=case.cfl, dt_mode=case.dt_mode, fixed_dt=case.fixed_dt,
                gravity=case.gravity, **kw)
     o.set_materials([oracle_material(m) for m in case.materials])

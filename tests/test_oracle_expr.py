@@ -216,3 +216,91 @@ def test_cantilever_expression_is_the_first_mode():
     d2_mid = (v([0.1 - h])[0] - 2 * v([0.1])[0] + v([0.1 + h])[0]) / h ** 2
     assert abs(d2) < 0.02 * abs(d2_mid)
     assert e.evaluate(x0=np.array([0.1]), t=1e-6)[1].all()  # after t = 0 the body is free
+
+
+# ---- expressions as boundary conditions in the oracle's step ------------------------------------------
+from paper_2602_15149_b300 import workloads as W  # noqa: E402
+from tests.oracle_cases import make_oracle  # noqa: E402
+
+
+def _plate(integrator=1, pull_ramp=False):
+    case = W.plate_2d(nx=30, ny=8, beta1=0.2)
+    if not pull_ramp:
+        case.bcs[1].ramp = 0.0
+    case.integrator = integrator
+    return case
+
+
+def _run(case, steps, exbcs=(), drop=()):
+    bcs = [b for k, b in enumerate(case.bcs) if k not in drop]
+    c = W.Case(**{**case.__dict__, "bcs": bcs})
+    o = make_oracle(c)
+    for mask, kind, cm, exprs in exbcs:
+        o.add_bc_expr(mask, kind, cm, exprs)
+    o.step(steps)
+    return o
+
+
+def test_constant_expressions_equal_constant_conditions():
+    """The clamp and the pull written as expressions give bit-identical runs (Algorithms 1 and 2)."""
+    for integ in (1, 2):
+        case = _plate(integ)
+        ref = _run(case, 150).read("U")
+        left, right = case.bcs[0].mask, case.bcs[1].mask
+        zero = Expression("0")
+        pull = Expression(repr(case.bcs[1].value[0]))
+        got = _run(case, 150, [(left, 0, 0b11, [zero, zero]), (right, 0, 0b01, [pull])], drop=(0, 1)).read("U")
+        assert np.array_equal(got, ref)
+        # the clamp as one expression over every particle, skipping all but the left column
+        clamp = Expression("if(x0 < dx, 0, skip)")
+        everyone = np.ones(case.n, np.uint8)
+        got = _run(case, 150, [(everyone, 0, 0b11, [clamp, clamp])], drop=(0,)).read("U")
+        assert np.array_equal(got, ref)
+
+
+def test_skipped_condition_does_nothing():
+    case = _plate()
+    ref = _run(case, 100).read("U")
+    got = _run(case, 100, [(np.ones(case.n, np.uint8), 0, 0b11, [Expression("skip"), Expression("Skip")])]).read("U")
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_time_dependent_velocity_integrates_exactly(integrator):
+    """v_x = A sin(w t) on the right edge.  Algorithm 1 prescribes v_{n+1} at t_{n+1}, so u_N = sum_k dt v(t_k),
+    k = 1..N; Algorithm 2 adds dt/2 (v_n + v_{n+1}) with v_0 = 0 (the trapezoid rule)."""
+    case = _plate(integrator)
+    A, w, N = 0.3, 2e5, 120
+    o = _run(case, N, [(case.bcs[1].mask, 0, 0b01, [Expression(f"{A}*sin({w}*t)")])], drop=(1,))
+    _, dt = o.time()
+    tk = dt * np.arange(N + 1)
+    v = A * np.sin(w * tk)
+    want = dt * v[1:].sum() if integrator == 1 else 0.5 * dt * (v[:-1] + v[1:]).sum()
+    ux = o.read("U")[case.bcs[1].mask.astype(bool), 0]
+    assert np.allclose(ux, want, rtol=1e-12, atol=0)
+    assert abs(want) > 1e-9
+
+
+def test_traction_expression_equals_constant_traction():
+    case = W.notched_plate(nx=40, ny=16, steps=100)
+    ref = _run(case, 100).read("U")
+    top, bot = case.bcs[0], case.bcs[1]
+    o = make_oracle(W.Case(**{**case.__dict__, "bcs": []}))
+    o.add_bc_expr(top.mask, top.kind, top.comp_mask, [None, Expression(repr(top.value[1]))], area=top.area)
+    o.add_bc_expr(bot.mask, bot.kind, bot.comp_mask, [None, Expression(repr(bot.value[1]))], area=bot.area)
+    o.step(100)
+    assert np.array_equal(o.read("U"), ref)
+
+
+def test_initial_velocity_from_the_cantilever_expression():
+    """apply_expr sets v at t = 0 from the paper's expression; the clamped part (x0 <= 0) gets 0."""
+    X, _ = W.lattice((44, 4), 5e-3, origin=(-0.02, 0.0))
+    case = W.Case("beam", 2, 5e-3, 7.5e-3, 0.3, W.DT_CFL_STATIC, 0.0, [W.Material(model=W.MODEL_SVK)], X,
+                  np.full(X.shape[0], 25e-6), np.zeros_like(X), np.zeros(X.shape[0], np.int32), None)
+    o = make_oracle(case)
+    e = Expression(CANTILEVER_EXPR, CANTILEVER_LOCALS)
+    o.apply_expr("V", [None, e])
+    v = o.read("V")
+    want, _ = e.evaluate(x0=X[:, 0], t=0.0)
+    assert np.array_equal(v[:, 1], want) and np.all(v[:, 0] == 0.0)
+    assert np.all(v[X[:, 0] <= 0.0, 1] == 0.0) and v[:, 1].max() > 0.5
