@@ -121,6 +121,7 @@ typedef struct {
     double gravity[3];  /* body force per unit mass */
     void *cuda_stream;  /* cudaStream_t to enqueue on; NULL = a stream the context creates */
     int device;         /* CUDA device ordinal */
+    double dx;          /* particle spacing, the expression variable dx; 0 = h / 1.5 */
 } tlsph_params;
 
 typedef struct {
@@ -173,6 +174,46 @@ tlsph_status tlsph_create_particles(tlsph_ctx *ctx, int64_t n, const double *X0,
  * particle for TLSPH_BC_TRACTION.  At most 4 conditions may cover one particle. */
 tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int comp_mask, const double value[3],
                           double t_start, double t_end, double ramp, double area);
+
+/* ---- User-defined expressions (Sec. 3.3, user-defined expressions; the tables of built-in variables,
+ * functions and operators).
+ * Variables: x0 y0 z0 (reference position), x y z (current position), ux uy uz (displacement), t, dt,
+ * dx (params.dx).  Operators, lowest precedence first: or, and, < > <= >= == !=, + -, * /, ^ (right-
+ * associative); unary minus binds looser than ^ (-2^2 = -4).  Functions: sin cos tan cot sinh cosh tanh
+ * coth sqrt abs log (base 10) ln pow(x, y) and if(c, a, b) (only the taken branch is evaluated).
+ * Comparisons and and/or give 1 or 0; a value is true when it is not 0.  The keyword skip (or Skip)
+ * makes a value "skipped": an operation on a skipped operand, and an if() with a skipped condition,
+ * give a skipped result, and a skipped result leaves the quantity it would set unchanged.  Locals:
+ * "name = expression; ..." evaluated in order before the expression.  Arithmetic is IEEE double.
+ * Expressions are compiled on the host to a bytecode that the device interprets per particle. */
+
+/* Checks an expression (and its locals, may be NULL) without a context or a GPU: TLSPH_OK, or
+ * TLSPH_ERR_ARG with the first error (and its position) written to msg (msg_len bytes, may be 0). */
+tlsph_status tlsph_expr_check(const char *locals, const char *expr, char *msg, size_t msg_len);
+
+/* Compiles an expression for this context; *id receives its index (0, 1, ...) for the calls below.
+ * TLSPH_ERR_ARG (message in tlsph_last_error) when it does not parse.  At most 4096 per context. */
+tlsph_status tlsph_expr_compile(tlsph_ctx *ctx, const char *locals, const char *expr, int *id);
+
+/* A boundary condition (Sec. 3.3.2) of the given kind whose masked components take, per particle and per
+ * step, the value of expression expr_id[k] (every component in comp_mask needs one; a skipped value
+ * leaves that component of that particle free in that step).  The expressions see the state at the
+ * start of the step; the time t is the one the step applies the condition at: t_{n+1} for velocities
+ * (and t_{n+1/2} for the Algorithm 2 predictor), the time of the forces (t_n, Algorithm 2: t_{n+1/2})
+ * for forces.  The condition is active for t_start <= t <= t_end (t_end < 0: no end); there is no ramp.
+ * Like tlsph_add_bc, it must come before tlsph_build_ref_neighbours.  Not with TLSPH_MODE_PERSISTENT. */
+tlsph_status tlsph_add_bc_expr(tlsph_ctx *ctx, const uint8_t *mask, int kind, int comp_mask, const int expr_id[3],
+                               double t_start, double t_end, double area);
+
+/* Sets components of a state field, TLSPH_FIELD_U or TLSPH_FIELD_V, of every particle to expressions
+ * evaluated now on the device (t = the current time, dt = the coming step); expr_id[k] < 0, or a skipped
+ * value, leaves component k as it is.  Initial conditions are set this way after
+ * tlsph_build_ref_neighbours. */
+tlsph_status tlsph_apply_expr(tlsph_ctx *ctx, int field, const int expr_id[3]);
+
+/* Evaluates expression id on the device for n rows of variables (host memory, row-major, 12 per row in the
+ * order x0 y0 z0 x y z ux uy uz t dt dx); writes n values to out and n skip flags (0/1) to skip (host). */
+tlsph_status tlsph_expr_eval(tlsph_ctx *ctx, int id, int64_t n, const double *vars, double *out, uint8_t *skip);
 
 /* Pre-existing notch (Sec. 3.3.1): quad[12] = p1..p4 (x, y, z).  3D: the
  * planar convex quad p1..p4; 2D: the segment p1-p2 (x, y).  A reference bond

@@ -196,8 +196,9 @@ class Oracle:
         return particle_variables(self._X0, self.read("U"), t + t_offset * dt, dt, self.dx)
 
     def apply_expr(self, field: str, exprs, t_offset=0.0):
-        """Set the components of a state field ("U" or "V") to expressions evaluated now (None or a skipped
-        value leaves a component as it is)."""
+        """Set the components of a state field ("U" or "V") to expressions evaluated now (t = the current time,
+        dt = the coming step; None or a skipped value leaves a component as it is)."""
+        _check(self.lib.orc_prepare_step(self.ctx), "prepare_step")
         vars_ = self.variables(t_offset)
         cur = self.read(field).copy()
         for k, e in enumerate(list(exprs)[:self.dim]):

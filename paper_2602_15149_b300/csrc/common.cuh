@@ -40,6 +40,8 @@ struct BCDev {
     int kind, comp_mask;
     double value[3];
     double t_start, t_end, ramp, area, inv_count;
+    int expr[3];  // per component: index of a user-defined expression giving the value, or -1 (Sec. 3.3)
+    int pad;
 };
 constexpr int kMaxBcPerParticle = 4;
 
@@ -103,6 +105,13 @@ template <typename T> struct StepArgs {
     int leap;
     const V4<T> *v_own;
     V4<T> *ug_half, *vs_half;  // predictor output
+    // values of conditions given by expressions (Sec. 3.3), evaluated at the start of the step for the
+    // particles in the expression list: expos[i] = list position p or -1; exval[(2 p + phase) * 12 +
+    // 3 slot + k] and bit 3 slot + k of exskip[2 p + phase] (slot = the condition's place in the
+    // particle's group, phase 1 = the Algorithm 2 predictor)
+    const int *expos;
+    const double *exval;
+    const uint16_t *exskip;
     // diagnostics (may be null)
     T *Fout, *Pout, *psi_out, *acc_out;
 };

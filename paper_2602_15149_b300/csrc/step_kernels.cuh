@@ -17,10 +17,27 @@
 // specimen clocks (eq. dt_criterion).
 #pragma once
 #include "common.cuh"
+#include "expr_eval.cuh"
 #include "mlp.cuh"
 #include "mlp_tc.cuh"
 
 namespace tl {
+
+// Value a boundary condition prescribes for component k of particle i (slot = the condition's place in
+// the particle's group, f = its ramp factor at the time in question, >= 0): the ramped constant, or
+// the value its expression took at the start of the step.  False when the expression skips it.
+template <typename T>
+__device__ __forceinline__ bool dev_bc_value(const StepArgs<T> &a, const BCDev &bc, int i, int slot, int phase,
+                                             int k, double f, double &val) {
+    if (bc.expr[k] >= 0) {
+        const int q = 2 * a.expos[i] + phase;
+        if ((a.exskip[q] >> (3 * slot + k)) & 1u) return false;
+        val = a.exval[q * 12 + 3 * slot + k];
+        return true;
+    }
+    val = f * bc.value[k];
+    return true;
+}
 
 template <typename T, int DIM> __device__ __forceinline__ void load_ahat(const T *Ahat, int n, int i, T A[3][3]) {
     if (DIM == 3) {
@@ -466,17 +483,19 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
                 if (bc.kind == 0) {  // velocity: value at t_{n+1}
                     const double f = bc_factor(bc, t_1);
                     if (f < 0.0) continue;
-                    for (int p = 0; p < DIM; p++)
-                        if (bc.comp_mask & (1 << p)) {
-                            vset[p] = f * bc.value[p];
+                    for (int p = 0; p < DIM; p++) {
+                        double val;
+                        if ((bc.comp_mask & (1 << p)) && dev_bc_value(a, bc, i, b, 0, p, f, val)) {
+                            vset[p] = val;
                             vmask |= 1 << p;
                         }
+                    }
                 } else {  // forces at t_n
                     const double f = bc_factor(bc, t_n);
                     if (f < 0.0) continue;
                     for (int p = 0; p < DIM; p++) {
-                        if (!(bc.comp_mask & (1 << p))) continue;
-                        const double val = f * bc.value[p];
+                        double val;
+                        if (!(bc.comp_mask & (1 << p)) || !dev_bc_value(a, bc, i, b, 0, p, f, val)) continue;
                         if (bc.kind == 1) acc[p] += (T)(val * bc.area / (double)mass);
                         else if (bc.kind == 2) acc[p] += (T)val;
                         else acc[p] += (T)(val * bc.inv_count / (double)mass);
@@ -543,9 +562,9 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
 }
 
 // Velocity boundary conditions of particle i at time t: the constrained components of v take the
-// prescribed values.
+// prescribed values (expression values of the given phase).
 template <typename T, int DIM>
-__device__ __forceinline__ void dev_velocity_bcs(const StepArgs<T> &a, int i, double t, T v[3]) {
+__device__ __forceinline__ void dev_velocity_bcs(const StepArgs<T> &a, int i, double t, T v[3], int phase) {
     const int g = a.bcgrp[i];
     if (!g) return;
     for (int b = 0; b < kMaxBcPerParticle; b++) {
@@ -555,8 +574,10 @@ __device__ __forceinline__ void dev_velocity_bcs(const StepArgs<T> &a, int i, do
         if (bc.kind != 0) continue;
         const double f = bc_factor(bc, t);
         if (f < 0.0) continue;
-        for (int p = 0; p < DIM; p++)
-            if (bc.comp_mask & (1 << p)) v[p] = (T)(f * bc.value[p]);
+        for (int p = 0; p < DIM; p++) {
+            double val;
+            if ((bc.comp_mask & (1 << p)) && dev_bc_value(a, bc, i, b, phase, p, f, val)) v[p] = (T)val;
+        }
     }
 }
 
@@ -579,7 +600,7 @@ __global__ void __launch_bounds__(BS) k_predict(StepArgs<T> a) {
         uf[p] = (T)uh;
         vh[p] = vv[p] + (T)(0.5 * dt) * a.acc_out[p * n + i];
     }
-    dev_velocity_bcs<T, DIM>(a, i, th, vh);
+    dev_velocity_bcs<T, DIM>(a, i, th, vh, 1);
     T sh = v.w;
     if (FRAC && a.mats[a.mid[i]].fracture) sh = t_min(T(1), t_max(T(0), v.w + (T)(0.5 * dt) * a.sdot[i]));
     a.ug_half[i] = V4<T>{uf[0], uf[1], DIM == 3 ? uf[DIM - 1] : T(0), DIM == 3 ? a.ug_next[i].w : T(0)};
@@ -1175,6 +1196,109 @@ __global__ void k_rows_caller(int64_t n, const int64_t *row_ptr, const int *col,
             y--;
         }
         col_out[o + y + 1] = v;
+    }
+}
+
+// ---- user-defined expressions (Sec. 3.3)
+
+// Built-in variables of particle i at time t: x0 y0 z0 x y z ux uy uz t dt dx (FP64 reference positions
+// and displacement).
+template <typename T, int DIM>
+__device__ __forceinline__ void ex_vars(const StepArgs<T> &a, const double *X0d, int i, double t, double dt,
+                                        double dx, double v[kExVars]) {
+    const int n = a.n;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const double x0 = q < DIM ? X0d[q * n + i] : 0.0;
+        const double u = q < DIM ? a.u64[q * n + i] : 0.0;
+        v[q] = x0;
+        v[3 + q] = x0 + u;
+        v[6 + q] = u;
+    }
+    v[9] = t;
+    v[10] = dt;
+    v[11] = dx;
+}
+
+// Evaluates the expressions of the boundary conditions of the listed particles for the coming step,
+// with the state at its start: velocity values at t_{n+1} (and, for Algorithm 2, at t_{n+1/2} for the
+// predictor, phase 1), force values at the time of the forces.  One thread per listed particle.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_expr_bcs(StepArgs<T> a, const int *exlist, int m, const double *X0d,
+                                                  const ExInstr *code, const double *K, const ExProg *progs,
+                                                  double dx, double *exval, uint16_t *exskip) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const int i = exlist[p];
+    const int g = a.bcgrp[i];
+    const int sp = a.spec[i];
+    const double t = a.t[sp], dt = a.dt[sp];
+    double v[kExVars];
+    ex_vars<T, DIM>(a, X0d, i, t, dt, dx, v);
+    uint32_t skip0 = 0, skip1 = 0;
+    for (int b = 0; b < kMaxBcPerParticle && g; b++) {
+        const int id = a.grp_bcs[4 * g + b];
+        if (id < 0) break;
+        const BCDev bc = a.bcs[id];
+        for (int k = 0; k < DIM; k++) {
+            const int e = bc.expr[k];
+            if (e < 0 || !(bc.comp_mask & (1 << k))) continue;
+            const ExProg pr = progs[e];
+            const int nph = (bc.kind == 0 && a.leap) ? 2 : 1;
+            for (int ph = 0; ph < nph; ph++) {
+                double off;
+                if (bc.kind == 0) off = ph == 0 ? dt : 0.5 * dt;
+                else off = a.leap ? 0.5 * dt : 0.0;
+                v[9] = t + off;
+                bool sk;
+                const double val = ex_run(code + pr.code, pr.ncode, K + pr.consts, v, sk);
+                exval[(2 * p + ph) * 12 + 3 * b + k] = val;
+                if (sk) (ph == 0 ? skip0 : skip1) |= 1u << (3 * b + k);
+            }
+        }
+    }
+    exskip[2 * p] = (uint16_t)skip0;
+    exskip[2 * p + 1] = (uint16_t)skip1;
+}
+
+// Sets components of the displacement (field 0) or velocity (field 1) of every particle to expressions
+// evaluated now (time t_n of its specimen); a skipped value or a component without an expression (-1)
+// is left alone.  The FP32 copy of the displacement follows.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_expr_field(StepArgs<T> a, const double *X0d, const ExInstr *code,
+                                                    const double *K, const ExProg *progs, int3 ids, double dx,
+                                                    int field, V4<T> *ug, V4<T> *vs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int n = a.n;
+    const int sp = a.spec[i];
+    double v[kExVars];
+    ex_vars<T, DIM>(a, X0d, i, a.t[sp], a.dt[sp], dx, v);
+    const int id[3] = {ids.x, ids.y, ids.z};
+    double val[3];
+    bool set[3] = {false, false, false};
+    for (int k = 0; k < DIM; k++) {
+        if (id[k] < 0) continue;
+        const ExProg pr = progs[id[k]];
+        bool sk;
+        val[k] = ex_run(code + pr.code, pr.ncode, K + pr.consts, v, sk);
+        set[k] = !sk;
+    }
+    if (field == 0) {
+        V4<T> r = ug[i];
+        T *rc = &r.x;
+        for (int k = 0; k < DIM; k++)
+            if (set[k]) {
+                a.u64[k * n + i] = val[k];
+                rc[k] = (T)val[k];
+            }
+        ug[i] = r;
+    } else {
+        V4<T> r = vs[i];
+        T *rc = &r.x;
+        for (int k = 0; k < DIM; k++)
+            if (set[k]) rc[k] = (T)val[k];
+        vs[i] = r;
     }
 }
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/tlsph.h"
+#include "expr_compile.h"
 #include "setup_kernels.cuh"
 #include "step_kernels.cuh"
 
@@ -29,6 +30,7 @@ struct BCHost {
     double t_start, t_end, ramp, area;
     std::vector<int64_t> ids;  // the masked particles (kept as a list: a batch has one condition per specimen)
     int64_t count;
+    int expr[3] = {-1, -1, -1};  // user-defined expressions giving the components (Sec. 3.3)
 };
 
 }  // namespace
@@ -95,8 +97,20 @@ struct tlsph_ctx {
     uint8_t *sur_exact = nullptr;             // particles left to the exact update in a step
     int sur_tensor = TLSPH_TENSOR_TCGEN05;    // tensor path of the network pass
     int sur_scope = 0;
+    // user-defined expressions (Sec. 3.3): compiled programs, their device tables (uploaded when the set
+    // changes), and the particles whose boundary conditions use them (sorted order) with their values
+    std::vector<ExProgram> exprogs;
+    bool ex_dirty = false;
+    ExInstr *excode = nullptr;
+    double *exK = nullptr;
+    ExProg *exprog = nullptr;
+    int nexlist = 0;
+    int *exlist = nullptr, *expos = nullptr;
+    double *exval = nullptr;
+    uint16_t *exskip = nullptr;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
+    int64_t graph_launches = 0;  // kernels in the captured two-step graph
     cudaGraphExec_t gexec = nullptr;
     unsigned int *bar = nullptr;
     bool barrier_test = false;
@@ -174,10 +188,24 @@ void drop_graph(tlsph_ctx *c) {
     c->gexec = nullptr;
 }
 
+void free_ex_tables(tlsph_ctx *c) {
+    cudaFree(c->excode);
+    cudaFree(c->exK);
+    cudaFree(c->exprog);
+    c->excode = nullptr;
+    c->exK = nullptr;
+    c->exprog = nullptr;
+    c->ex_dirty = !c->exprogs.empty();
+}
+
 void free_device(tlsph_ctx *c) {
     drop_graph(c);
     for (void *q : c->allocs) cudaFree(q);
     c->allocs.clear();
+    c->nexlist = 0;
+    c->exlist = c->expos = nullptr;
+    c->exval = nullptr;
+    c->exskip = nullptr;
     c->X0d = nullptr;
     c->perm = nullptr;
     c->S1 = nullptr;
@@ -338,8 +366,45 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.Pout = (T *)c->Pd;
     a.psi_out = (T *)c->psid;
     a.acc_out = c->record_acc ? (T *)c->accd : nullptr;
+    a.expos = c->expos;
+    a.exval = c->exval;
+    a.exskip = c->exskip;
     return a;
 }
+
+// Uploads the compiled expressions (code, constants, offsets) when the set has changed.
+tlsph_status ex_sync(tlsph_ctx *c) {
+    if (!c->ex_dirty) return TLSPH_OK;
+    drop_graph(c);  // a captured step refers to the old tables
+    free_ex_tables(c);
+    std::vector<ExInstr> code;
+    std::vector<double> K;
+    std::vector<ExProg> progs;
+    for (const ExProgram &p : c->exprogs) {
+        progs.push_back(ExProg{(int)code.size(), (int)p.code.size(), (int)K.size(), 0});
+        code.insert(code.end(), p.code.begin(), p.code.end());
+        K.insert(K.end(), p.consts.begin(), p.consts.end());
+    }
+    K.push_back(0.0);
+    const size_t bc = code.size() * sizeof(ExInstr), bk = K.size() * sizeof(double), bp = progs.size() * sizeof(ExProg);
+    if (cudaMalloc(&c->excode, bc) != cudaSuccess || cudaMalloc(&c->exK, bk) != cudaSuccess ||
+        cudaMalloc(&c->exprog, bp) != cudaSuccess) {
+        cudaGetLastError();
+        free_ex_tables(c);
+        return fail(c, TLSPH_ERR_OOM, "expression tables");
+    }
+    // synchronous copies: the host vectors end with this call
+    if (cudaMemcpy(c->excode, code.data(), bc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->exK, K.data(), bk, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->exprog, progs.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TLSPH_ERR_CUDA, "expression tables upload");
+    }
+    c->ex_dirty = false;
+    return TLSPH_OK;
+}
+
+double ex_dx(const tlsph_ctx *c) { return c->p.dx > 0.0 ? c->p.dx : c->p.h / 1.5; }
 
 // Arguments of the step kernels.  Algorithm 1 ping-pongs the displacement and velocity records
 // (read cur, write next).  Algorithm 2 keeps them in place: the predictor writes the half level to
@@ -542,7 +607,11 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         d.ramp = h.ramp;
         d.area = h.area;
         d.inv_count = h.count > 0 ? 1.0 / (double)h.count : 0.0;
+        for (int q = 0; q < 3; q++) d.expr[q] = h.expr[q];
+        d.pad = 0;
     }
+    for (size_t b = c->bcs.size(); b < bch.size(); b++)
+        for (int q = 0; q < 3; q++) bch[b].expr[q] = -1;
     DA(c->bcdev, bch.size() * sizeof(BCDev));
     CK(cudaMemcpyAsync(c->bcdev, bch.data(), bch.size() * sizeof(BCDev), cudaMemcpyHostToDevice, s));
     // ---- materials
@@ -655,6 +724,38 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
                                                       (const MatT<T> *)c->matsdev, c->mid, (V4<T> *)c->X0V);
     CKL();
     CK(cudaMemcpyAsync(c->vs[1], c->vs[0], n * sizeof(V4<T>), cudaMemcpyDeviceToDevice, s));
+    // ---- particles whose boundary conditions use expressions (sorted order), and their value slots
+    {
+        std::vector<uint8_t> has_ex(n, 0);
+        for (const BCHost &b : c->bcs)
+            if (b.expr[0] >= 0 || b.expr[1] >= 0 || b.expr[2] >= 0)
+                for (int64_t pi : b.ids) has_ex[pi] = 1;
+        int64_t m = 0;
+        for (int64_t pi = 0; pi < n; pi++) m += has_ex[pi];
+        if (m > 0) {
+            if (m > INT32_MAX / 24) return fail(c, TLSPH_ERR_ARG, "too many particles with expression conditions");
+            std::vector<int> permh(n), list, pos(n, -1);
+            CK(cudaMemcpyAsync(permh.data(), c->perm, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int64_t k = 0; k < n; k++)
+                if (has_ex[permh[k]]) {
+                    pos[k] = (int)list.size();
+                    list.push_back((int)k);
+                }
+            c->nexlist = (int)m;
+            DA(c->exlist, m * sizeof(int));
+            DA(c->expos, n * sizeof(int));
+            DA(c->exval, m * 24 * sizeof(double));
+            DA(c->exskip, m * 2 * sizeof(uint16_t));
+            CK(cudaMemcpyAsync(c->exlist, list.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(c->expos, pos.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+            CK(cudaMemsetAsync(c->exval, 0, m * 24 * sizeof(double), s));
+            CK(cudaMemsetAsync(c->exskip, 0xff, m * 2 * sizeof(uint16_t), s));
+            CK(cudaStreamSynchronize(s));  // the host vectors end with this block
+            tlsph_status st = ex_sync(c);
+            if (st != TLSPH_OK) return st;
+        }
+    }
     // ---- neighbours (count, scan, fill)
     DA(c->row_len, n * sizeof(int));
     DA(c->row_ptr, (n + 1) * sizeof(int64_t));
@@ -884,6 +985,11 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
             c->ev_pending.push_back({cat, ev[cat]});
         };
         start(1);
+        if (c->nexlist > 0) {  // boundary values given by expressions, from the state at the step's start
+            k_expr_bcs<T, DIM><<<blocks_for(c->nexlist, 128), 128, 0, c->stream>>>(
+                a, c->exlist, c->nexlist, c->X0d, c->excode, c->exK, c->exprog, ex_dx(c), c->exval, c->exskip);
+            CKL();
+        }
         if (c->leap) {  // Algorithm 2, predictor (timed with the deformation gradient)
             k_predict<T, DIM, FRAC, BS><<<nb, BS, 0, c->stream>>>(a);
             CKL();
@@ -931,6 +1037,7 @@ tlsph_status step_graph(tlsph_ctx *c, int64_t nsteps) {
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         tlsph_status st = step_launches<T, DIM, FRAC, BS>(c, 2, false);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->graph_launches = c->launches - launches;
         c->parity = par;
         c->steps = steps;
         c->launches = launches;
@@ -945,7 +1052,7 @@ tlsph_status step_graph(tlsph_ctx *c, int64_t nsteps) {
     }
     for (; nsteps >= 2; nsteps -= 2) {
         CK(cudaGraphLaunch(c->gexec, c->stream));
-        c->launches += 6;
+        c->launches += c->graph_launches;
         c->steps += 2;
     }
     if (nsteps) return step_launches<T, DIM, FRAC, BS>(c, nsteps, false);
@@ -990,6 +1097,8 @@ tlsph_status step_mode(tlsph_ctx *c, int64_t nsteps) {
     if (c->mode == TLSPH_MODE_PERSISTENT) {
         if (BS == 64) return fail(c, TLSPH_ERR_ARG, "the persistent mode needs a block of 128 or 256");
         if (c->leap) return fail(c, TLSPH_ERR_ARG, "the persistent mode runs Algorithm 1 only");
+        if (c->nexlist > 0)
+            return fail(c, TLSPH_ERR_ARG, "the persistent mode takes no boundary conditions given by expressions");
         return c->has_visc ? step_persistent_v<T, DIM, FRAC, true, (BS < 128 ? 128 : BS)>(c, nsteps)
                            : step_persistent_v<T, DIM, FRAC, false, (BS < 128 ? 128 : BS)>(c, nsteps);
     }
@@ -1284,6 +1393,23 @@ tlsph_status autotune_impl(tlsph_ctx *c, int trial, tlsph_tuning *best, tlsph_tu
     return TLSPH_OK;
 }
 
+template <typename T> tlsph_status apply_expr_impl(tlsph_ctx *c, int field, const int ids[3]) {
+    tlsph_status st = ex_sync(c);
+    if (st != TLSPH_OK) return st;
+    StepArgs<T> a = make_args<T>(c);
+    const int3 id3 = make_int3(ids[0], ids[1], ids[2]);
+    const int f = field == TLSPH_FIELD_U ? 0 : 1;
+    V4<T> *ug = (V4<T> *)c->ug[c->parity], *vs = (V4<T> *)c->vs[c->parity];
+    const unsigned nb = blocks_for(c->n, 128);
+    if (c->p.dim == 3)
+        k_expr_field<T, 3><<<nb, 128, 0, c->stream>>>(a, c->X0d, c->excode, c->exK, c->exprog, id3, ex_dx(c), f, ug, vs);
+    else
+        k_expr_field<T, 2><<<nb, 128, 0, c->stream>>>(a, c->X0d, c->excode, c->exK, c->exprog, id3, ex_dx(c), f, ug, vs);
+    CKL();
+    CK(cudaStreamSynchronize(c->stream));
+    return TLSPH_OK;
+}
+
 }  // namespace
 
 // ===================================================================== C-ABI
@@ -1325,6 +1451,7 @@ void tlsph_destroy(tlsph_ctx *c) {
     cudaSetDevice(c->p.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_device(c);
+    free_ex_tables(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1416,6 +1543,100 @@ tlsph_status tlsph_add_notch(tlsph_ctx *c, const double quad[12]) {
     return TLSPH_OK;
 }
 
+tlsph_status tlsph_expr_check(const char *locals, const char *expr, char *msg, size_t msg_len) {
+    if (!expr) return TLSPH_ERR_ARG;
+    ExCompiler comp;
+    ExProgram prog;
+    std::string err;
+    const bool ok = comp.compile(locals ? locals : "", expr, prog, err);
+    if (msg && msg_len) snprintf(msg, msg_len, "%s", ok ? "" : err.c_str());
+    return ok ? TLSPH_OK : TLSPH_ERR_ARG;
+}
+
+tlsph_status tlsph_expr_compile(tlsph_ctx *c, const char *locals, const char *expr, int *id) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!expr || !id) return fail(c, TLSPH_ERR_ARG, "expr_compile: null expression or id");
+    if (c->exprogs.size() >= 4096) return fail(c, TLSPH_ERR_ARG, "too many expressions");
+    ExCompiler comp;
+    ExProgram prog;
+    std::string err;
+    if (!comp.compile(locals ? locals : "", expr, prog, err)) return fail(c, TLSPH_ERR_ARG, "expression: %s", err.c_str());
+    c->exprogs.push_back(std::move(prog));
+    c->ex_dirty = true;
+    *id = (int)c->exprogs.size() - 1;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_add_bc_expr(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_mask, const int expr_id[3],
+                               double t_start, double t_end, double area) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!expr_id) return fail(c, TLSPH_ERR_ARG, "add_bc_expr: null expression ids");
+    const int dim = c->p.dim;
+    if (comp_mask <= 0 || comp_mask >= (1 << dim)) return fail(c, TLSPH_ERR_ARG, "add_bc_expr: bad component mask");
+    for (int q = 0; q < dim; q++)
+        if ((comp_mask >> q) & 1)
+            if (expr_id[q] < 0 || expr_id[q] >= (int)c->exprogs.size())
+                return fail(c, TLSPH_ERR_ARG, "add_bc_expr: component %d has no compiled expression", q);
+    const double zero[3] = {0.0, 0.0, 0.0};
+    tlsph_status st = tlsph_add_bc(c, mask, kind, comp_mask, zero, t_start, t_end, 0.0, area);
+    if (st != TLSPH_OK) return st;
+    for (int q = 0; q < 3; q++) c->bcs.back().expr[q] = (q < dim && ((comp_mask >> q) & 1)) ? expr_id[q] : -1;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_apply_expr(tlsph_ctx *c, int field, const int expr_id[3]) {
+    DeviceScope ds_(c ? c->p.device : -1);
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before apply_expr");
+    if (!expr_id || (field != TLSPH_FIELD_U && field != TLSPH_FIELD_V))
+        return fail(c, TLSPH_ERR_ARG, "apply_expr: field must be U or V");
+    int ids[3] = {-1, -1, -1};
+    for (int q = 0; q < c->p.dim; q++) {
+        if (expr_id[q] >= (int)c->exprogs.size()) return fail(c, TLSPH_ERR_ARG, "apply_expr: unknown expression");
+        ids[q] = expr_id[q] < 0 ? -1 : expr_id[q];
+    }
+    return c->p.precision == TLSPH_FP64 ? apply_expr_impl<double>(c, field, ids) : apply_expr_impl<float>(c, field, ids);
+}
+
+tlsph_status tlsph_expr_eval(tlsph_ctx *c, int id, int64_t n, const double *vars, double *out, uint8_t *skip) {
+    DeviceScope ds_(c ? c->p.device : -1);
+    if (!c) return TLSPH_ERR_ARG;
+    if (id < 0 || id >= (int)c->exprogs.size()) return fail(c, TLSPH_ERR_ARG, "expr_eval: unknown expression");
+    if (n < 0 || (n > 0 && (!vars || !out || !skip))) return fail(c, TLSPH_ERR_ARG, "expr_eval: bad buffers");
+    if (n == 0) return TLSPH_OK;
+    tlsph_status st = ex_sync(c);
+    if (st != TLSPH_OK) return st;
+    double *dv = nullptr, *dout = nullptr;
+    uint8_t *dsk = nullptr;
+    if (cudaMalloc(&dv, n * kExVars * sizeof(double)) != cudaSuccess || cudaMalloc(&dout, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dsk, n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dv);
+        cudaFree(dout);
+        cudaFree(dsk);
+        return fail(c, TLSPH_ERR_OOM, "expr_eval buffers");
+    }
+    ExProg pr{0, (int)c->exprogs[id].code.size(), 0, 0};
+    for (int q = 0; q < id; q++) {
+        pr.code += (int)c->exprogs[q].code.size();
+        pr.consts += (int)c->exprogs[q].consts.size();
+    }
+    cudaMemcpyAsync(dv, vars, n * kExVars * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    k_expr_rows<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(c->excode, c->exK, pr, n, dv, dout, dsk);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        c->launches++;
+        cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(skip, dsk, n, cudaMemcpyDeviceToHost, c->stream);
+        e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(dv);
+    cudaFree(dout);
+    cudaFree(dsk);
+    if (e != cudaSuccess) return fail(c, TLSPH_ERR_CUDA, "expr_eval: %s", cudaGetErrorString(e));
+    return TLSPH_OK;
+}
+
 tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
     DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
@@ -1431,6 +1652,10 @@ tlsph_status tlsph_step_async(tlsph_ctx *c, int64_t nsteps) {
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before step");
     if (nsteps < 0) return fail(c, TLSPH_ERR_ARG, "negative step count");
+    if (c->nexlist > 0 && c->ex_dirty) {
+        tlsph_status st = ex_sync(c);
+        if (st != TLSPH_OK) return st;
+    }
     return c->p.precision == TLSPH_FP64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
 }
 

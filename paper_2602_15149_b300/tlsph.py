@@ -37,7 +37,8 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_mlp_set_normalization", "tlsph_mlp_get_normalization", "tlsph_mlp_fit_normalization",
            "tlsph_mlp_train_step", "tlsph_mlp_gradients", "tlsph_mlp_forward", "tlsph_set_surrogate",
            "tlsph_surrogate_counts", "tlsph_j2_samples",
-           "tlsph_mlp_set_tensor_path"]
+           "tlsph_mlp_set_tensor_path", "tlsph_expr_check", "tlsph_expr_compile", "tlsph_add_bc_expr",
+           "tlsph_apply_expr", "tlsph_expr_eval"]
 MLP_NUM_PARAMS = 37264
 SURROGATE_ALL, SURROGATE_PLASTIC = 0, 1
 TENSOR_MMA_SYNC, TENSOR_TCGEN05 = 0, 1
@@ -47,7 +48,7 @@ NOALLOC_MAX_PARTICLES = 131072
 class Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("precision", C.c_int), ("integrator", C.c_int), ("h", C.c_double),
                 ("support", C.c_double), ("cfl", C.c_double), ("dt_mode", C.c_int), ("fixed_dt", C.c_double),
-                ("gravity", C.c_double * 3), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+                ("gravity", C.c_double * 3), ("cuda_stream", C.c_void_p), ("device", C.c_int), ("dx", C.c_double)]
 
 
 class Material(C.Structure):
@@ -93,6 +94,12 @@ def load_library(path: str = LIB_PATH):
         "tlsph_create_particles": (C.c_int, [P, C.c_int64, D, D, D, I32, I32]),
         "tlsph_add_bc": (C.c_int, [P, U8, C.c_int, C.c_int, D, C.c_double, C.c_double, C.c_double, C.c_double]),
         "tlsph_add_notch": (C.c_int, [P, D]),
+        "tlsph_expr_check": (C.c_int, [C.c_char_p, C.c_char_p, C.c_char_p, C.c_size_t]),
+        "tlsph_expr_compile": (C.c_int, [P, C.c_char_p, C.c_char_p, C.POINTER(C.c_int)]),
+        "tlsph_add_bc_expr": (C.c_int, [P, U8, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_double, C.c_double,
+                                        C.c_double]),
+        "tlsph_apply_expr": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
+        "tlsph_expr_eval": (C.c_int, [P, C.c_int, C.c_int64, D, D, U8]),
         "tlsph_build_ref_neighbours": (C.c_int, [P]),
         "tlsph_step": (C.c_int, [P, C.c_int64]),
         "tlsph_step_async": (C.c_int, [P, C.c_int64]),
@@ -142,10 +149,10 @@ class TLSPH:
     """One TLSPH context on a CUDA device (methods carry the C-ABI names without the prefix)."""
 
     def __init__(self, dim, h, precision=FP32_U64, cfl=0.3, dt_mode=DT_CFL_STATIC, fixed_dt=0.0,
-                 gravity=(0.0, 0.0, 0.0), support=2.0, device=0, stream=None, integrator=INTEGRATOR_EULER):
+                 gravity=(0.0, 0.0, 0.0), support=2.0, device=0, stream=None, integrator=INTEGRATOR_EULER, dx=0.0):
         self.lib = load_library()
         p = Params(dim, precision, integrator, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity),
-                   stream, device)
+                   stream, device, dx)
         ctx = C.c_void_p()
         st = self.lib.tlsph_create(C.byref(p), C.byref(ctx))
         if st != OK:
@@ -199,6 +206,34 @@ class TLSPH:
     def add_notch(self, quad):
         q = np.ascontiguousarray(quad, np.float64).reshape(12)
         self._ck(self.lib.tlsph_add_notch(self.ctx, _d(q)), "add_notch")
+
+    def expr_compile(self, expr, locals_=""):
+        """Compile a user-defined expression; returns its id."""
+        i = C.c_int()
+        self._ck(self.lib.tlsph_expr_compile(self.ctx, locals_.encode(), expr.encode(), C.byref(i)), "expr_compile")
+        return i.value
+
+    def add_bc_expr(self, mask, kind, comp_mask, expr_ids, t_start=0.0, t_end=-1.0, area=0.0):
+        """A boundary condition whose components take the values of compiled expressions (ids, -1 for none)."""
+        m = np.ascontiguousarray(mask, np.uint8)
+        ids = (C.c_int * 3)(*(list(expr_ids) + [-1] * (3 - len(expr_ids))))
+        self._ck(self.lib.tlsph_add_bc_expr(self.ctx, m.ctypes.data_as(C.POINTER(C.c_uint8)), kind, comp_mask, ids,
+                                            t_start, t_end, area), "add_bc_expr")
+
+    def apply_expr(self, field, expr_ids):
+        """Set the components of field "U" or "V" from compiled expressions evaluated now (ids, -1 for none)."""
+        ids = (C.c_int * 3)(*(list(expr_ids) + [-1] * (3 - len(expr_ids))))
+        self._ck(self.lib.tlsph_apply_expr(self.ctx, FIELD[field], ids), "apply_expr")
+
+    def expr_eval(self, expr_id, variables):
+        """Evaluate a compiled expression on the device for rows of the 12 built-in variables (n x 12, order
+        x0 y0 z0 x y z ux uy uz t dt dx); returns (values, skip)."""
+        v = np.ascontiguousarray(variables, np.float64).reshape(-1, 12)
+        out = np.zeros(v.shape[0])
+        skip = np.zeros(v.shape[0], np.uint8)
+        self._ck(self.lib.tlsph_expr_eval(self.ctx, expr_id, v.shape[0], _d(v), _d(out),
+                                          skip.ctypes.data_as(C.POINTER(C.c_uint8))), "expr_eval")
+        return out, skip.astype(bool)
 
     def build_ref_neighbours(self):
         self._ck(self.lib.tlsph_build_ref_neighbours(self.ctx), "build_ref_neighbours")
@@ -413,17 +448,32 @@ def cell_sort_noalloc(X0, perm, h, support=2.0, specimen_id=None, device=0, stre
                                        None if specimen_id is None else specimen_id.data_ptr(), perm.data_ptr())
 
 
+def expr_check(expr, locals_=""):
+    """Check an expression without a context or a GPU: None when it compiles, else the error message."""
+    lib = load_library()
+    buf = C.create_string_buffer(512)
+    st = lib.tlsph_expr_check(locals_.encode(), expr.encode(), buf, 512)
+    return None if st == OK else buf.value.decode()
+
+
 def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
     """Create a context from a :class:`workloads.Case` (marshalling only)."""
     prec = precision if precision is not None else (FP64 if case.precision == "fp64" else FP32_U64)
     t = TLSPH(case.dim, case.h, prec, case.cfl, case.dt_mode, case.fixed_dt, case.gravity, device=device,
-              stream=stream, integrator=getattr(case, "integrator", INTEGRATOR_EULER))
+              stream=stream, integrator=getattr(case, "integrator", INTEGRATOR_EULER), dx=case.dp)
     t.set_materials(case.materials)
     t.create_particles(case.X0, case.vol, case.v0, case.material_id, case.specimen_id)
     for b in list(case.bcs) + list(getattr(case, "specimen_loads", [])):
         t.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
     for q in case.notches:
         t.add_notch(q)
+    for b in getattr(case, "expr_bcs", []):
+        ids = [-1 if e is None else t.expr_compile(e[0], e[1]) for e in b.exprs]
+        t.add_bc_expr(b.mask, b.kind, b.comp_mask, ids, b.t_start, b.t_end, b.area)
     if build:
         t.build_ref_neighbours()
+        for fld, exprs in getattr(case, "expr_ics", []):
+            t.apply_expr(fld, [-1 if e is None else t.expr_compile(e[0], e[1]) for e in exprs])
+    elif getattr(case, "expr_ics", []):
+        raise ValueError("initial fields given by expressions need build=True")
     return t

@@ -23,6 +23,11 @@ these lattices stand in for them at the same scale):
   crack branching): the notched plate in plane strain at dx = 0.0625 mm
   (1600 x 640 = 1,024,000 particles), St. Venant-Kirchhoff, eps0 = 2 dx,
   s_l = 0.05, C_CFL = 0.2, beta1 = 0.2, constant 1 MPa traction, run to 80-120 us.
+* ``cantilever_beam`` -- the paper's freely oscillating cantilever (Sec. 4,
+  free oscillation of a cantilever beam): a 0.2 x 0.02 m plane-strain SVK beam
+  (mu = 0.715 MPa, kappa = 3.25 MPa, rho = 1000) whose columns with x0 <= 0
+  (1.5 mm) are held by expression conditions, started with the first-mode
+  velocity profile of eq. freeoscivel through an expression initial field.
 * ``batched``       -- many independent 2D specimens of log-uniform size with
   random materials and loading (512 specimens is the full case).
 
@@ -76,6 +81,18 @@ class BC:
 
 
 @dataclass
+class ExprBC:
+    """A boundary condition whose components are user-defined expressions: (text, locals) or None each."""
+    mask: np.ndarray
+    kind: int
+    comp_mask: int
+    exprs: list
+    t_start: float = 0.0
+    t_end: float = -1.0
+    area: float = 0.0
+
+
+@dataclass
 class Case:
     name: str
     dim: int
@@ -96,6 +113,8 @@ class Case:
     precision: str = "fp32"     # "fp64" or "fp32" (fp32 fields, fp64 displacement)
     gravity: tuple = (0.0, 0.0, 0.0)
     integrator: int = 1         # 1: Algorithm 1 (symplectic Euler), 2: Algorithm 2 (leapfrog)
+    expr_bcs: list = field(default_factory=list)  # ExprBC
+    expr_ics: list = field(default_factory=list)  # (field "U" or "V", [(text, locals) or None per component])
 
     @property
     def n(self) -> int:
@@ -176,6 +195,35 @@ def crack_branching(nx=1600, ny=640, t_end=80e-6, precision="fp32"):
     case.name = "crack_branching_svk"
     case.cfl = 0.2
     case.steps = int(math.ceil(t_end / (0.2 * case.h / REF_WAVE_SPEED)))
+    return case
+
+
+# The first bending mode as an initial velocity (eq. freeoscivel): v(X1) = 0.01 c_s f(X1) / f(L0) with
+# f(x) = [cos kL + cosh kL][cosh kx - cos kx] + [sin kL - sinh kL][sinh kx - sin kx], k L0 = 1.875, and the
+# clamp at X1 <= 0.  Written as the expression language's (text, locals); c_s = 57 m/s as the paper states.
+CANTILEVER_MODE_LOCALS = ("L = 0.2; k = 1.875 / L; A = 0.01 * 57.0; c1 = cos(k*L) + cosh(k*L); "
+                          "s1 = sin(k*L) - sinh(k*L); fL = c1*(cosh(k*L) - cos(k*L)) + s1*(sinh(k*L) - sin(k*L))")
+CANTILEVER_MODE = "if(x0 <= 0, 0, A * (c1*(cosh(k*x0) - cos(k*x0)) + s1*(sinh(k*x0) - sin(k*x0))) / fL)"
+CANTILEVER_CLAMP = "if(x0 <= 0, 0, skip)"
+
+
+def cantilever_beam(dx=0.5e-3, L0=0.2, H0=0.02, clamp=1.5e-3, steps=20000, precision="fp64"):
+    """The paper's 2D cantilever (x along the beam, y transverse): lattice from x = -clamp to L0, the columns
+    with x0 <= 0 held at zero velocity by expression conditions, the first-mode transverse velocity as an
+    expression initial field.  SVK with mu = 0.715 MPa, kappa = 3.25 MPa (E = 9 kappa mu / (3 kappa + mu),
+    nu = (3 kappa - 2 mu) / (2 (3 kappa + mu)) written out below), rho = 1000, artificial viscosity
+    (0.015, 0.01), Courant number 0.2."""
+    nx, ny = int(round((L0 + clamp) / dx)), int(round(H0 / dx))
+    X, _ = lattice((nx, ny), dx, origin=(-clamp, 0.0))
+    n = X.shape[0]
+    mat = Material(model=MODEL_SVK, rho=1000.0, E=1998447.2049689442, nu=0.39751552795031053, beta1=0.015,
+                   beta2=0.01)
+    case = Case("cantilever_beam_svk", 2, dx, 1.5 * dx, 0.2, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dx * dx),
+                np.zeros((n, 2)), np.zeros(n, np.int32), None, [], [], steps, precision)
+    mode = (CANTILEVER_MODE, CANTILEVER_MODE_LOCALS)
+    clampx = (CANTILEVER_CLAMP, "")
+    case.expr_bcs = [ExprBC(np.ones(n, np.uint8), BC_VEL, 0b11, [clampx, clampx])]
+    case.expr_ics = [("V", [None, mode])]
     return case
 
 

@@ -1,6 +1,7 @@
 """Drive the FP64 oracle from a workload Case (test helper; imports only oracle/ and workloads)."""
 import numpy as np
 
+from oracle.expr import Expression
 from oracle.oracle import Oracle, OracleMaterial
 from paper_2602_15149_b300 import workloads as W
 
@@ -21,6 +22,11 @@ def make_oracle(case: W.Case, build=True, method=None, **kw) -> Oracle:
         o.add_bc(b.mask, b.kind, b.comp_mask, b.value, b.t_start, b.t_end, b.ramp, b.area)
     for q in case.notches:
         o.add_notch(q)
+    for b in getattr(case, "expr_bcs", []):
+        o.add_bc_expr(b.mask, b.kind, b.comp_mask, [None if e is None else Expression(e[0], e[1]) for e in b.exprs],
+                      b.t_start, b.t_end, b.area)
     if build:
         o.build_ref_neighbours(method)
+        for fld, exprs in getattr(case, "expr_ics", []):
+            o.apply_expr(fld, [None if e is None else Expression(e[0], e[1]) for e in exprs])
     return o

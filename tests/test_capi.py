@@ -55,3 +55,29 @@ def test_library_targets_sm103a():
     cmd = build.nvcc_command()
     assert "arch=compute_103a,code=sm_103a" in " ".join(cmd)
     assert os.path.exists(build.LIB)
+
+
+def test_expr_check_accepts_what_the_oracle_parses():
+    """The library's expression compiler (no GPU needed) accepts and rejects the same texts as the oracle's
+    parser: the paper's examples, error cases, and random expressions of the full grammar."""
+    import numpy as np
+    from oracle.expr import Expression, ExprError
+    from paper_2602_15149_b300 import tlsph
+    from tests.test_oracle_expr import CANTILEVER_EXPR, CANTILEVER_LOCALS, _gen, _paper
+    cases = [(CANTILEVER_EXPR, CANTILEVER_LOCALS), ("if(x0 < 0, 0, skip)", ""), ("a*b", "a = 2; b = a + x0"),
+             ("2^-1", ""), ("-2^2", ""), ("1 or 0 and 0", ""), ("1+", ""), ("(1+2", ""), ("foo(1)", ""),
+             ("sin(1,2)", ""), ("pow(1)", ""), ("x0 y0", ""), ("1 $ 2", ""), ("q + 1", ""), ("if(1,2)", ""),
+             ("and", ""), ("1", "sin = 1"), ("1", "x0 = 2"), ("1", "a b = 1"), ("1", "a"), ("", ""), ("1e", ""),
+             ("1.5.3", ""), (".5e-3*dx", "")]
+    rng = np.random.default_rng(3)
+    cases += [(_paper(_gen(rng, 5)), "") for _ in range(300)]
+    for src, loc in cases:
+        try:
+            Expression(src, loc)
+            want_ok = True
+        except ExprError:
+            want_ok = False
+        msg = tlsph.expr_check(src, loc)
+        assert (msg is None) == want_ok, (src, loc, msg)
+        if msg is not None:
+            assert msg

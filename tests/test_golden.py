@@ -36,3 +36,19 @@ def test_crack_branching_case_is_the_published_one():
     assert m.beta1 == ref["beta1"] and m.model == W.MODEL_SVK and m.fracture == 1
     assert (m.E, m.nu, m.rho, m.Gc) == (v("crack_branching_E_Pa"), v("crack_branching_nu"), v("crack_branching_rho"),
                                         v("crack_branching_Gc"))
+
+
+def test_cantilever_case_is_the_published_one():
+    ref = GOLD["cantilever_beam"]
+    c = W.cantilever_beam(dx=0.5e-3)
+    m = c.materials[0]
+    mu = m.E / (2 * (1 + m.nu))
+    kappa = m.E / (3 * (1 - 2 * m.nu))
+    assert abs(mu - ref["mu_Pa"]) < 1e-6 * ref["mu_Pa"] and abs(kappa - ref["kappa_Pa"]) < 1e-6 * ref["kappa_Pa"]
+    assert m.rho == ref["rho"] and (m.beta1, m.beta2) == (ref["beta1"], ref["beta2"]) and c.cfl == ref["cfl"]
+    assert m.model == W.MODEL_SVK and c.dp == ref["dx_m"][0]
+    assert abs(c.X0[:, 0].min() - (-ref["clamp_m"] + c.dp / 2)) < 1e-12
+    assert abs(c.X0[:, 0].max() - (ref["L0_m"] - c.dp / 2)) < 1e-12
+    assert abs(c.X0[:, 1].max() - (ref["H0_m"] - c.dp / 2)) < 1e-12
+    for text in (W.CANTILEVER_MODE_LOCALS,):
+        assert f"{ref['kw_L0']}" in text and f"{ref['v_factor']} * {ref['c_s']}" in text
