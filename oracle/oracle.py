@@ -107,6 +107,11 @@ def load_oracle():
     lib.orc_sym_eig3.restype = None
     lib.orc_j2_update.argtypes = [D, D, C.c_double, C.POINTER(_Material), D, D, D, D, C.POINTER(C.c_int)]
     lib.orc_set_bc_values.argtypes = [C.c_void_p, C.c_int, C.c_int, D, C.POINTER(C.c_uint8)]
+    lib.orc_set_contact.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, D]
+    lib.orc_contact_energy.argtypes = [C.c_void_p]
+    lib.orc_contact_energy.restype = C.c_double
+    lib.orc_contact_force.argtypes = [C.c_int, C.c_double, C.c_double, D, D, D, D, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_double, C.c_double, D]
     lib.orc_prepare_step.argtypes = [C.c_void_p]
     _lib = lib
     return lib
@@ -186,6 +191,17 @@ class Oracle:
         b = self.add_bc(mask, kind, comp_mask, (0.0, 0.0, 0.0), t_start, t_end, 0.0, area)
         self._exbcs.append((b, kind, comp_mask, list(exprs) + [None] * (3 - len(exprs))))
         return b
+
+    def set_contact(self, contcoeff, restitution, dc=None):
+        """Contact between bodies (the specimens), reading of Sec. 3.3 <contcoeff>/<restcoef>: a linear
+        spring-dashpot normal force between particles of different specimens closer than dc (default the
+        particle spacing dx); the specimens then share one clock."""
+        r = np.ascontiguousarray(restitution, dtype=np.float64)
+        _check(self.lib.orc_set_contact(self.ctx, contcoeff, self.dx if dc is None else dc, r.size, _dp(r)),
+               "set_contact")
+
+    def contact_energy(self):
+        return float(self.lib.orc_contact_energy(self.ctx))
 
     def variables(self, t_offset=0.0):
         """The built-in expression variables of every particle at t_n + t_offset * dt (state at t_n)."""
@@ -329,6 +345,20 @@ def svk_stress(F, s, mat: OracleMaterial):
     if st != 0:
         raise ValueError("svk_stress: invalid F")
     return S.reshape(3, 3), pp.value, pm.value
+
+
+def contact_force(dim, dc, contcoeff, xi, xj, vi, vj, mi, mj, mat_i: OracleMaterial, mat_j: OracleMaterial,
+                  e_i, e_j):
+    """Contact force on particle i from particle j (zero out of contact)."""
+    lib = load_oracle()
+    a = [np.zeros(3) for _ in range(4)]
+    for dst, src in zip(a, (xi, xj, vi, vj)):
+        dst[:len(src)] = src
+    F = np.zeros(3)
+    ci = (1 - mat_i.nu ** 2) / mat_i.E
+    cj = (1 - mat_j.nu ** 2) / mat_j.E
+    lib.orc_contact_force(dim, dc, contcoeff, *[_dp(x) for x in a], mi, mj, ci, cj, e_i, e_j, _dp(F))
+    return F[:dim]
 
 
 def sym_eig3(A):

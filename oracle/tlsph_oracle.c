@@ -112,6 +112,12 @@ typedef struct orc_ctx {
     int64_t step;
     int64_t noconv;
     int built;
+    /* contact between bodies (the specimens): on/off, potential multiplier, contact distance,
+     * restitution per specimen, contact accelerations of the current step */
+    int contact;
+    double kc, dc;
+    double *rest;
+    double *accc;
 } orc_ctx;
 
 /* ------------------------------------------------------------------ */
@@ -504,6 +510,7 @@ orc_ctx *orc_create(const orc_params *p) {
 }
 
 static void free_particles(orc_ctx *c) {
+    free(c->rest); free(c->accc);
     free(c->X0); free(c->vol); free(c->u); free(c->v); free(c->acc); free(c->s); free(c->sdot);
     free(c->sdd); free(c->lap); free(c->pf_b); free(c->pf_k); free(c->pf_g); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
     free(c->P); free(c->L); free(c->status); free(c->row_ptr); free(c->col); free(c->perm);
@@ -879,6 +886,11 @@ int orc_build_neighbours(orc_ctx *c, int method) {
         double cs = orc_sound_speed(&c->mat[c->mid[i]]);
         if (cs > c->cmax[c->spec[i]]) c->cmax[c->spec[i]] = cs;
     }
+    if (c->contact) { /* bodies in contact share one clock: the largest sound speed of all */
+        double cm = 0.0;
+        for (int s = 0; s < c->nspec; s++) cm = c->cmax[s] > cm ? c->cmax[s] : cm;
+        for (int s = 0; s < c->nspec; s++) c->cmax[s] = cm;
+    }
     for (int s = 0; s < c->nspec; s++) {
         c->t[s] = 0.0;
         c->vmax[s] = 0.0;
@@ -987,6 +999,111 @@ static double bc_factor(const orc_bc *b, double t) {
     return 1.0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Contact between bodies (Algorithm 1 step 1, Algorithm 2 step 2;     */
+/* <contcoeff>, <restcoef> of Sec. 3.3).  The paper takes its contact  */
+/* model from its host framework without stating it; reading: a linear */
+/* spring-dashpot normal force between particles of different bodies   */
+/* closer than the contact distance dc (the particle spacing):          */
+/*   delta = dc - r, n = (x_i - x_j) / r, k = kc E* dc^(dim - 2),        */
+/*   1/E* = (1 - nu_i^2)/E_i + (1 - nu_j^2)/E_j,                          */
+/*   m* = m_i m_j / (m_i + m_j), e = (e_i + e_j) / 2,                     */
+/*   zeta = -ln e / sqrt(pi^2 + ln^2 e), c = 2 zeta sqrt(k m*),           */
+/*   F_i = (k delta - c (v_i - v_j).n) n,                                 */
+/* for which a head-on pair leaves with relative speed e times the one  */
+/* it came with (the damped oscillator's half period).                  */
+/* ------------------------------------------------------------------ */
+int orc_contact_force(int dim, double dc, double kc, const double *xi, const double *xj, const double *vi,
+                      const double *vj, double mi, double mj, double cinv_i, double cinv_j, double ei, double ej,
+                      double *F) {
+    double d[3] = {0, 0, 0}, r2 = 0.0;
+    F[0] = F[1] = F[2] = 0.0;
+    for (int k = 0; k < dim; k++) {
+        d[k] = xi[k] - xj[k];
+        r2 += d[k] * d[k];
+    }
+    if (!(r2 < dc * dc) || r2 == 0.0) return 0;
+    double r = sqrt(r2);
+    double kn = kc * pow(dc, dim - 2) / (cinv_i + cinv_j);
+    double ms = mi * mj / (mi + mj);
+    double e = 0.5 * (ei + ej);
+    double zeta = 0.0;
+    if (e < 1.0) {
+        double le = log(e);
+        zeta = -le / sqrt(M_PI * M_PI + le * le);
+    }
+    double cd = 2.0 * zeta * sqrt(kn * ms);
+    double vn = 0.0;
+    for (int k = 0; k < dim; k++) vn += (vi[k] - vj[k]) * d[k] / r;
+    double f = kn * (dc - r) - cd * vn;
+    for (int k = 0; k < dim; k++) F[k] = f * d[k] / r;
+    return 1;
+}
+
+static double mat_cinv(const orc_material *m) { return (1.0 - m->nu * m->nu) / m->E; }
+
+/* Contact accelerations of all particles from the current u and v (all pairs of different bodies). */
+static void contact_accel(orc_ctx *c) {
+    const int64_t n = c->n;
+    const int d = c->p.dim;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        double xi[3], a[3] = {0, 0, 0};
+        for (int k = 0; k < 3; k++) xi[k] = c->X0[3 * i + k] + c->u[3 * i + k];
+        const orc_material *mi = &c->mat[c->mid[i]];
+        const double massi = mi->rho * c->vol[i];
+        for (int64_t j = 0; j < n; j++) {
+            if (c->spec[j] == c->spec[i]) continue;
+            double xj[3], F[3];
+            for (int k = 0; k < 3; k++) xj[k] = c->X0[3 * j + k] + c->u[3 * j + k];
+            const orc_material *mj = &c->mat[c->mid[j]];
+            if (orc_contact_force(d, c->dc, c->kc, xi, xj, &c->v[3 * i], &c->v[3 * j], massi, mj->rho * c->vol[j],
+                                  mat_cinv(mi), mat_cinv(mj), c->rest[c->spec[i]], c->rest[c->spec[j]], F))
+                for (int k = 0; k < d; k++) a[k] += F[k] / massi;
+        }
+        for (int k = 0; k < 3; k++) c->accc[3 * i + k] = a[k];
+    }
+}
+
+/* Bodies = the specimens: contact acts between particles of different specimens, which then share one
+ * clock.  kc = <contcoeff>, dc = contact distance, rest[nspec] = <restcoef> per body. */
+int orc_set_contact(orc_ctx *c, double kc, double dc, int nspec, const double *rest) {
+    if (!c || c->n <= 0 || nspec != c->nspec || !rest || !(kc > 0.0) || !(dc > 0.0)) return ORC_ERR_ARG;
+    if (c->p.dt_mode == ORC_DT_ADAPTIVE) return ORC_ERR_ARG;
+    for (int s = 0; s < nspec; s++)
+        if (!(rest[s] > 0.0 && rest[s] <= 1.0)) return ORC_ERR_ARG;
+    free(c->rest);
+    c->rest = (double *)malloc(sizeof(double) * nspec);
+    memcpy(c->rest, rest, sizeof(double) * nspec);
+    free(c->accc);
+    c->accc = (double *)calloc(3 * c->n, sizeof(double));
+    c->kc = kc;
+    c->dc = dc;
+    c->contact = 1;
+    c->built = 0;
+    return ORC_OK;
+}
+
+/* Contact potential of the current state: sum over pairs of 1/2 k delta^2. */
+double orc_contact_energy(const orc_ctx *c) {
+    if (!c || !c->contact) return 0.0;
+    double E = 0.0;
+    for (int64_t i = 0; i < c->n; i++)
+        for (int64_t j = i + 1; j < c->n; j++) {
+            if (c->spec[j] == c->spec[i]) continue;
+            double r2 = 0.0;
+            for (int k = 0; k < c->p.dim; k++) {
+                double dd = c->X0[3 * i + k] + c->u[3 * i + k] - c->X0[3 * j + k] - c->u[3 * j + k];
+                r2 += dd * dd;
+            }
+            if (!(r2 < c->dc * c->dc)) continue;
+            double kn = c->kc * pow(c->dc, c->p.dim - 2) / (mat_cinv(&c->mat[c->mid[i]]) + mat_cinv(&c->mat[c->mid[j]]));
+            double dl = c->dc - sqrt(r2);
+            E += 0.5 * kn * dl * dl;
+        }
+    return E;
+}
+
 /* The value a condition prescribes for component k of particle i (factor f = bc_factor >= 0): the
  * ramped constant, or the expression's value; returns 0 when the expression skips it. */
 static int bc_value(const orc_bc *b, int phase, int64_t i, int k, double f, double *out) {
@@ -1061,6 +1178,8 @@ static int one_step(orc_ctx *c) {
             }
         }
     }
+    /* contact between bodies (Algorithm 1 step 1; Algorithm 2 step 2, at the half level) */
+    if (c->contact) contact_accel(c);
     double *Fpn = (double *)malloc(sizeof(double) * 9 * n);
     double *epn = (double *)malloc(sizeof(double) * n);
     /* Step 2: F and stress for every particle (from u_n, s_n; Algorithm 2: the half level) */
@@ -1131,7 +1250,7 @@ static int one_step(orc_ctx *c) {
                 lap += 2.0 * (c->s[i] - c->s[j]) * c->vol[j] * rg / (r * r);
             }
         }
-        for (int k = 0; k < d; k++) a[k] += c->p.gravity[k];
+        for (int k = 0; k < d; k++) a[k] += c->p.gravity[k] + (c->contact ? c->accc[3 * i + k] : 0.0);
         double mass = rho_i * c->vol[i];
         /* force BCs at the time of the forces: t_n (Algorithm 1), t_{n+1/2} (Algorithm 2) */
         double t_n = c->t[c->spec[i]] + (leap ? 0.5 * c->dt[c->spec[i]] : 0.0);

@@ -28,6 +28,10 @@ these lattices stand in for them at the same scale):
   (mu = 0.715 MPa, kappa = 3.25 MPa, rho = 1000) whose columns with x0 <= 0
   (1.5 mm) are held by expression conditions, started with the first-mode
   velocity profile of eq. freeoscivel through an expression initial field.
+* ``flyer_plate``   -- the paper's flyer-plate impact (Sec. 4): two 1 x 1 m
+  plane-strain J2 steel plates 0.05 m apart (100 x 100 particles each at
+  dx = 0.01 m) closing at +-200 m/s, contact between the two bodies
+  (contcoeff 5, restitution 0.95), Courant number 0.01.
 * ``batched``       -- many independent 2D specimens of log-uniform size with
   random materials and loading (512 specimens is the full case).
 
@@ -115,6 +119,7 @@ class Case:
     integrator: int = 1         # 1: Algorithm 1 (symplectic Euler), 2: Algorithm 2 (leapfrog)
     expr_bcs: list = field(default_factory=list)  # ExprBC
     expr_ics: list = field(default_factory=list)  # (field "U" or "V", [(text, locals) or None per component])
+    contact: dict | None = None  # {"contcoeff": kc, "restitution": [e per specimen]}: bodies = specimens
 
     @property
     def n(self) -> int:
@@ -224,6 +229,27 @@ def cantilever_beam(dx=0.5e-3, L0=0.2, H0=0.02, clamp=1.5e-3, steps=20000, preci
     clampx = (CANTILEVER_CLAMP, "")
     case.expr_bcs = [ExprBC(np.ones(n, np.uint8), BC_VEL, 0b11, [clampx, clampx])]
     case.expr_ics = [("V", [None, mode])]
+    return case
+
+
+def flyer_plate(n=100, dx=0.01, gap=0.05, v=200.0, steps=20000, precision="fp32", contcoeff=5.0, restitution=0.95,
+                model="j2"):
+    """Two identical square plates (specimens 0 and 1 = the two bodies) moving towards each other along y;
+    the lower one at +v, the upper one at -v.  J2 steel as the paper's case (rho 7870, E 200 GPa, nu 0.29,
+    sigma_y0 400 MPa, H 100 MPa, artificial viscosity 0.05), or "nh" for the same elastic constants."""
+    lo, _ = lattice((n, n), dx)
+    hi, _ = lattice((n, n), dx, origin=(0.0, n * dx + gap))
+    X = np.vstack([lo, hi])
+    m = n * n
+    spec = np.concatenate([np.zeros(m, np.int32), np.ones(m, np.int32)])
+    v0 = np.zeros((2 * m, 2))
+    v0[:m, 1] = v
+    v0[m:, 1] = -v
+    mat = Material(model=MODEL_J2 if model == "j2" else MODEL_NH, rho=7870.0, E=200e9, nu=0.29,
+                   sigma_y0=400e6 if model == "j2" else 0.0, H_hard=100e6 if model == "j2" else 0.0, beta1=0.05)
+    case = Case("flyer_plate_" + model, 2, dx, 1.5 * dx, 0.01, DT_CFL_STATIC, 0.0, [mat], X, np.full(2 * m, dx * dx), v0,
+                np.zeros(2 * m, np.int32), spec, [], [], steps, precision)
+    case.contact = {"contcoeff": contcoeff, "restitution": [restitution, restitution]}
     return case
 
 
