@@ -365,6 +365,36 @@ def measure_crack_branching(args, device, stream):
             "paper": {"t_initiation_us": 14.0, "t_branching_us": 35.0, "divergence_angle_deg": 60.0}}
 
 
+def measure_flyer_plate(args, device, stream):
+    """The paper's flyer-plate impact (two 100 x 100 J2 plates, contact between the bodies) run to 300 us in
+    FP32: throughput of the stepping (CUDA events around each chunk) and when plasticity starts."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    dev = torch.device("cuda", device)
+    case = W.flyer_plate()
+    g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    g.set_option(tlsph.OPT_MODE, tlsph.MODE_GRAPH)
+    g.step(args.warmup)
+    ms, steps, st, t, t_plastic = 0.0, 0, 0, 0.0, None
+    l0 = g.get_info()["kernel_launches"]
+    while t < 300e-6:
+        m, st1 = timed_steps(g, 200, stream, dev)
+        ms += m
+        steps += 200
+        st |= st1
+        t, _ = g.time()
+        if t_plastic is None and g.read_state("EPSP").max() > 0.0:
+            t_plastic = t
+    launches = g.get_info()["kernel_launches"] - l0
+    g.close()
+    return {"workload": "flyer_plate 2 x 100x100 J2 plates at +-200 m/s, contact, to 300 us, FP32",
+            "particles": case.n, "steps": steps, "ms_per_step": ms / steps, "value": case.n * steps / (ms * 1e-3),
+            "unit": UNIT, "status": st, "kernels_per_step": launches / steps,
+            "t_first_plastic_us": None if t_plastic is None else t_plastic * 1e6,
+            "t_contact_expected_us": 125.0}
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -513,6 +543,7 @@ def run_ours(args):
     leapfrog = measure_leapfrog(args, shape, local, stream, plain)
     phase_field = measure_phase_field(args, local, stream)
     crack_b = measure_crack_branching(args, local, stream) if not args.no_crack else None
+    flyer = measure_flyer_plate(args, local, stream) if not args.no_crack else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -547,6 +578,7 @@ def run_ours(args):
         "leapfrog": leapfrog,
         "phase_field": phase_field,
         "crack_branching": crack_b,
+        "flyer_plate": flyer,
         "status": int(st),
         "cpu_baseline": cpu,
     }
@@ -566,7 +598,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
     ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching case")
+    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching and flyer-plate cases")
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
     ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")

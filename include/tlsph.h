@@ -175,6 +175,19 @@ tlsph_status tlsph_create_particles(tlsph_ctx *ctx, int64_t n, const double *X0,
 tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int comp_mask, const double value[3],
                           double t_start, double t_end, double ramp, double area);
 
+/* Contact between bodies (Algorithm 1 step 1, Algorithm 2 step 2; <contcoeff> and <restcoef> of Sec. 3.3).
+ * The bodies are the specimens of the context (specimen_id of tlsph_create_particles); with contact on they
+ * share one clock (the largest sound speed of all, TLSPH_DT_FIXED or TLSPH_DT_CFL_STATIC only) and
+ * particles of different bodies closer than the contact distance dc = params.dx push each other.  The paper
+ * does not state its contact law; the one built is a linear spring-dashpot normal force,
+ *   F_i = (k delta - 2 zeta sqrt(k m*) (v_i - v_j).n) n,  delta = dc - r,  n = (x_i - x_j)/r,
+ *   k = contcoeff E* dc^(dim-2),  1/E* = (1 - nu_i^2)/E_i + (1 - nu_j^2)/E_j,  m* = m_i m_j/(m_i + m_j),
+ *   zeta = -ln e / sqrt(pi^2 + ln^2 e),  e = (e_i + e_j)/2 (restitution[body], in (0, 1]),
+ * under which a head-on pair separates with e times its approach speed; no friction.  Pairs are found
+ * every step in the current configuration (FP64 positions).  Must come after tlsph_create_particles and
+ * before tlsph_build_ref_neighbours; nbodies = the number of specimens.  Not with TLSPH_MODE_PERSISTENT. */
+tlsph_status tlsph_set_contact(tlsph_ctx *ctx, double contcoeff, int nbodies, const double *restitution);
+
 /* ---- User-defined expressions (Sec. 3.3, user-defined expressions; the tables of built-in variables,
  * functions and operators).
  * Variables: x0 y0 z0 (reference position), x y z (current position), ux uy uz (displacement), t, dt,

@@ -112,6 +112,8 @@ template <typename T> struct StepArgs {
     const int *expos;
     const double *exval;
     const uint16_t *exskip;
+    // contact accelerations between bodies of the step (null without contact), dim arrays of n
+    const T *accc;
     // diagnostics (may be null)
     T *Fout, *Pout, *psi_out, *acc_out;
 };

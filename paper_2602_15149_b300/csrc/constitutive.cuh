@@ -32,6 +32,7 @@ template <typename T> struct MatT {
     int fracture;   // phase field on
     T rho, mu, kappa, sy0, Hh, beta1, beta2, c0, Gc, eps0, s_lim, mass_scale;
     T lam;          // Lame's first parameter
+    T cinv;         // (1 - nu^2) / E, the material's share of the contact modulus 1/E*
 };
 
 // x + x^2/2 - log(1 + x) (= (J^2 - 1)/2 - ln J with x = J - 1), series near 0

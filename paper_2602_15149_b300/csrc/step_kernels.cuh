@@ -468,6 +468,7 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
                 acc[p] -= v;
             }
             acc[p] += a.grav[p];
+            if (a.accc) acc[p] += a.accc[p * n + i];
         }
         // forces act at t_n (Algorithm 1) or t_{n+1/2} (Algorithm 2); velocity BCs hold at t_{n+1}
         const double dt = a.dt[sp], t_1 = a.t[sp] + dt, t_n = a.t[sp] + (a.leap ? 0.5 * dt : 0.0);

@@ -14,6 +14,7 @@
 
 #include "../../include/tlsph.h"
 #include "expr_compile.h"
+#include "contact.cuh"
 #include "setup_kernels.cuh"
 #include "step_kernels.cuh"
 
@@ -108,6 +109,15 @@ struct tlsph_ctx {
     int *exlist = nullptr, *expos = nullptr;
     double *exval = nullptr;
     uint16_t *exskip = nullptr;
+    // contact between bodies (the specimens): potential multiplier, contact distance, restitution per
+    // body, spatial-hash tables and the contact accelerations of the step
+    bool contact = false;
+    double kc = 0.0;
+    std::vector<double> resth;
+    double *rest = nullptr;
+    int tsize = 0;
+    int *hcount = nullptr, *hstart = nullptr, *hbucket = nullptr, *hslot = nullptr, *hlist = nullptr, *hbsum = nullptr;
+    void *accc = nullptr;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
     int64_t graph_launches = 0;  // kernels in the captured two-step graph
@@ -202,6 +212,9 @@ void free_device(tlsph_ctx *c) {
     drop_graph(c);
     for (void *q : c->allocs) cudaFree(q);
     c->allocs.clear();
+    c->rest = nullptr;
+    c->hcount = c->hstart = c->hbucket = c->hslot = c->hlist = c->hbsum = nullptr;
+    c->accc = nullptr;
     c->nexlist = 0;
     c->exlist = c->expos = nullptr;
     c->exval = nullptr;
@@ -369,6 +382,7 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.expos = c->expos;
     a.exval = c->exval;
     a.exskip = c->exskip;
+    a.accc = c->contact ? (const T *)c->accc : nullptr;
     return a;
 }
 
@@ -637,6 +651,7 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         d.s_lim = (T)m.s_lim;
         d.mass_scale = T(1);
         d.lam = (T)lam;
+        d.cinv = (T)((1.0 - m.nu * m.nu) / m.E);
     }
     std::vector<char> used(c->mats.size(), 0);
     for (int64_t pi = 0; pi < n; pi++) used[c->midh[pi]] = 1;
@@ -859,6 +874,11 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         vv = sqrt(vv);
         if (vv > vm0[sp]) vm0[sp] = vv;
     }
+    if (c->contact) {  // bodies in contact share one clock: the largest sound speed of all
+        double m = 0.0;
+        for (int sp = 0; sp < ns_; sp++) m = std::max(m, cm[sp]);
+        for (int sp = 0; sp < ns_; sp++) cm[sp] = m;
+    }
     for (int sp = 0; sp < ns_; sp++) {
         const double h = c->p.h;
         if (c->p.dt_mode == TLSPH_DT_FIXED) dt0[sp] = c->p.fixed_dt;
@@ -883,6 +903,23 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     CK(cudaMemsetAsync(c->vmax, 0, ns_ * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->amax, 0, ns_ * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->done, 0, sizeof(unsigned int), s));
+    // contact tables (spatial hash of 2n or more buckets, a power of two)
+    if (c->contact) {
+        int ts = 1024;
+        while (ts < 2 * n) ts <<= 1;
+        if (ts > kHashScanBlock * kHashScanBlock * 4) return fail(c, TLSPH_ERR_ARG, "too many particles for contact");
+        c->tsize = ts;
+        DA(c->rest, ns_ * sizeof(double));
+        DA(c->hcount, ts * sizeof(int));
+        DA(c->hstart, ts * sizeof(int));
+        DA(c->hbsum, (ts / kHashScanBlock + 1) * sizeof(int));
+        DA(c->hbucket, n * sizeof(int));
+        DA(c->hslot, n * sizeof(int));
+        DA(c->hlist, n * sizeof(int));
+        DA(c->accc, dim * n * sizeof(T));
+        CK(cudaMemcpyAsync(c->rest, c->resth.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(c->accc, 0, dim * n * sizeof(T), s));
+    }
     // first moment of the corrected kernel (reference configuration)
     DA(c->S1, n * sizeof(V4<T>));
     {
@@ -962,6 +999,31 @@ template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const
     return TLSPH_OK;
 }
 
+// ---- contact accelerations between bodies: hash the current positions, list, sort, sum the pair forces
+template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const StepArgs<T> &a) {
+    const int n = (int)c->n, ts = c->tsize;
+    const double dc = ex_dx(c);
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->hcount, 0, ts * sizeof(int), s));
+    k_contact_count<T><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, DIM, dc, ts, c->hcount, c->hbucket, c->hslot);
+    CKL();
+    const int nb = (ts + kHashScanBlock - 1) / kHashScanBlock;
+    k_hscan_blocks<<<nb, kHashScanBlock, 0, s>>>(ts, c->hcount, c->hstart, c->hbsum);
+    CKL();
+    k_hscan_sums<<<1, kHashScanBlock, 0, s>>>(nb, c->hbsum);
+    CKL();
+    k_hscan_add<<<nb, kHashScanBlock, 0, s>>>(ts, c->hstart, c->hbsum);
+    CKL();
+    k_contact_fill<<<blocks_for(n, 128), 128, 0, s>>>(n, c->hbucket, c->hslot, c->hstart, c->hlist);
+    CKL();
+    k_contact_sort<<<blocks_for(ts, 128), 128, 0, s>>>(ts, c->hcount, c->hstart, c->hlist);
+    CKL();
+    k_contact<T, DIM><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, dc, c->kc, c->rest, ts, c->hcount, c->hstart,
+                                                         c->hlist, (T *)c->accc);
+    CKL();
+    return TLSPH_OK;
+}
+
 // ---- one step as three kernel launches (gradient, stress, force-and-damage)
 template <typename T, int DIM, bool FRAC, int BS>
 tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
@@ -993,6 +1055,10 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
         if (c->leap) {  // Algorithm 2, predictor (timed with the deformation gradient)
             k_predict<T, DIM, FRAC, BS><<<nb, BS, 0, c->stream>>>(a);
             CKL();
+        }
+        if (c->contact) {  // contact between bodies at the level of the forces
+            tlsph_status st = contact_launches<T, DIM>(c, a);
+            if (st != TLSPH_OK) return st;
         }
         k_gradient<T, DIM, BS><<<nb, BS, 0, c->stream>>>(a);
         CKL();
@@ -1099,6 +1165,7 @@ tlsph_status step_mode(tlsph_ctx *c, int64_t nsteps) {
         if (c->leap) return fail(c, TLSPH_ERR_ARG, "the persistent mode runs Algorithm 1 only");
         if (c->nexlist > 0)
             return fail(c, TLSPH_ERR_ARG, "the persistent mode takes no boundary conditions given by expressions");
+        if (c->contact) return fail(c, TLSPH_ERR_ARG, "the persistent mode takes no contact between bodies");
         return c->has_visc ? step_persistent_v<T, DIM, FRAC, true, (BS < 128 ? 128 : BS)>(c, nsteps)
                            : step_persistent_v<T, DIM, FRAC, false, (BS < 128 ? 128 : BS)>(c, nsteps);
     }
@@ -1634,6 +1701,23 @@ tlsph_status tlsph_expr_eval(tlsph_ctx *c, int id, int64_t n, const double *vars
     cudaFree(dout);
     cudaFree(dsk);
     if (e != cudaSuccess) return fail(c, TLSPH_ERR_CUDA, "expr_eval: %s", cudaGetErrorString(e));
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_set_contact(tlsph_ctx *c, double contcoeff, int nbodies, const double *restitution) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (c->n <= 0) return fail(c, TLSPH_ERR_STATE, "create_particles must come before set_contact");
+    if (!(contcoeff > 0.0) || nbodies != c->nspec || !restitution)
+        return fail(c, TLSPH_ERR_ARG, "set_contact: need contcoeff > 0 and one restitution per specimen (%d)", c->nspec);
+    if (c->p.dt_mode == TLSPH_DT_ADAPTIVE)
+        return fail(c, TLSPH_ERR_ARG, "set_contact: bodies in contact share one clock; use a fixed or static step");
+    for (int b = 0; b < nbodies; b++)
+        if (!(restitution[b] > 0.0 && restitution[b] <= 1.0))
+            return fail(c, TLSPH_ERR_ARG, "set_contact: restitution of body %d must be in (0, 1]", b);
+    c->contact = true;
+    c->kc = contcoeff;
+    c->resth.assign(restitution, restitution + nbodies);
+    c->built = false;
     return TLSPH_OK;
 }
 

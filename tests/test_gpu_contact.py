@@ -1,0 +1,93 @@
+"""Contact between bodies (reading of Sec. 3.3 <contcoeff>, <restcoef>) on the sm_103a path against the
+FP64 oracle, through the C-ABI, and the paper's flyer-plate impact (Sec. 4) at its published size.
+
+Parity: two touching 8 x 8 plates colliding (FP64 within 1e-8 of the largest displacement, FP32 within
+1e-4), both integrators; momentum conserved to rounding; launch and graph modes bit-identical.
+Flyer plate: what the paper states about its run (the figures carry no numbers) -- plasticity starts at
+the contact interface, the impact is symmetric about the mid-plane, and the plates spread laterally.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_15149_b300 import tlsph, workloads as W
+from tests.oracle_cases import make_oracle
+from tests.test_oracle_contact import _plates
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+@pytest.mark.parametrize("precision,tol", [(tlsph.FP64, 1e-8), (tlsph.FP32_U64, 1e-4)])
+def test_colliding_plates_match_oracle(integrator, precision, tol):
+    case = _plates(0.8, v=2.0)
+    case.integrator = integrator
+    o = make_oracle(case)
+    g = tlsph.from_case(case, precision=precision)
+    for _ in range(3):  # approach, impact, rebound
+        o.step(100)
+        g.step(100)
+        u_o = o.read("U")
+        assert np.abs(g.read_state("U") - u_o).max() <= tol * np.abs(u_o).max()
+        v_o = o.read("V")
+        assert np.abs(g.read_state("V") - v_o).max() <= tol * np.abs(v_o).max()
+
+
+def test_momentum_and_modes():
+    case = _plates(0.8, v=2.0)
+    m = case.materials[0].rho * case.vol
+    out = []
+    for mode in (tlsph.MODE_LAUNCH, tlsph.MODE_GRAPH):
+        g = tlsph.from_case(case, precision=tlsph.FP64)
+        g.set_option(tlsph.OPT_MODE, mode)
+        p0 = (m[:, None] * g.read_state("V")).sum(axis=0)
+        for _ in range(3):
+            g.step(100)
+            p = (m[:, None] * g.read_state("V")).sum(axis=0)
+            assert np.abs(p - p0).max() <= 1e-12 * (m * 2.0).sum()
+        out.append(g.read_state("U"))
+    assert np.array_equal(out[0], out[1])
+    g = tlsph.from_case(case, precision=tlsph.FP64)
+    g.set_option(tlsph.OPT_MODE, tlsph.MODE_PERSISTENT)
+    with pytest.raises(tlsph.TLSPHError):
+        g.step(2)
+
+
+def test_contact_needs_a_shared_clock():
+    case = _plates(0.8)
+    case.dt_mode = W.DT_ADAPTIVE
+    with pytest.raises(tlsph.TLSPHError):
+        tlsph.from_case(case, precision=tlsph.FP64)
+
+
+def test_flyer_plate_as_published():
+    """Two 100 x 100 J2 plates at +-200 m/s (FP32), run to 300 us: impact at about 125 us (0.05 m closed at
+    400 m/s), plastic strain first at the contact rows, a symmetric state, lateral spreading at the
+    interface, momentum still zero."""
+    case = W.flyer_plate()
+    g = tlsph.from_case(case)
+    g.set_option(tlsph.OPT_MODE, tlsph.MODE_GRAPH)
+    n = 100
+    m = n * n
+    X = case.X0
+    t, first_plastic, ep = 0.0, None, None
+    while t < 300e-6:
+        g.step(200)
+        t, _ = g.time()
+        ep = g.read_state("EPSP")
+        if first_plastic is None and ep.max() > 0.0:
+            first_plastic = (t, np.nonzero(ep > 0.5 * ep.max())[0])
+    assert first_plastic is not None and 110e-6 < first_plastic[0] < 160e-6
+    rows = np.rint(X[first_plastic[1], 1] / case.dp - 0.5).astype(int)
+    assert np.all((rows >= n - 3) & (rows < n + 3 + 5))  # the rows at the interface (the gap is 5 rows)
+    u = g.read_state("U")
+    lo, hi = u[:m].reshape(n, n, 2), u[m:].reshape(n, n, 2)[::-1]
+    scale = np.abs(u).max()
+    assert np.abs(hi[..., 0] - lo[..., 0]).max() <= 1e-3 * scale
+    assert np.abs(hi[..., 1] + lo[..., 1]).max() <= 1e-3 * scale
+    # the interface rows widen (barrelling): the outer columns move outwards
+    assert u[:m].reshape(n, n, 2)[n - 1, n - 1, 0] > 0 and u[:m].reshape(n, n, 2)[n - 1, 0, 0] < 0
+    v = g.read_state("V")
+    rho = case.materials[0].rho
+    p = (rho * case.vol[:, None] * v).sum(axis=0)
+    assert np.abs(p).max() <= 1e-4 * rho * case.vol.sum() * 200.0
+    assert g.get_info()["nonfinite"] == 0
