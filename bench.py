@@ -55,7 +55,7 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
 # profiles/dram_traffic__block_3d_j2_128x128x64.md), keyed by the hash of the kernel sources it
 # was taken on; reported as null once the kernels change.
-NCU_TRAFFIC = {"sources": "76c6ecc9e7a17569", "pass2": 236611840.0, "gradient": 92325888.0, "stress": 144994560.0}
+NCU_TRAFFIC = {"sources": "9fea0b2411f1233c", "pass2": 235111936.0, "gradient": 92255744.0, "stress": 145042944.0}
 
 
 def source_hash() -> str:
@@ -441,6 +441,7 @@ def measure_surrogate(args, shape, device, stream, plain):
         ms, st = timed_steps(g, args.steps - args.warmup, stream, dev)
         steps_t = args.steps - args.warmup
         used, outside, elastic = g.surrogate_counts()
+        noconv = g.get_info()["noconverge"]
         us, eps = g.read_state("U"), g.read_state("EPSP")
         g.set_option(tlsph.OPT_KERNEL_TIMING, 1)
         g.step(min(args.steps, 100))
@@ -453,7 +454,7 @@ def measure_surrogate(args, shape, device, stream, plain):
         out[name] = {"tensor_path": "tcgen05" if path == tlsph.TENSOR_TCGEN05 else "mma.sync",
                      "ms_per_step": ms / steps_t, "value": n * steps_t / (ms * 1e-3), "unit": UNIT,
                      "vs_plain": (n * steps_t / (ms * 1e-3)) / plain["value"],
-                     "status": st, "rows_network": used, "rows_outside_envelope": outside,
+                     "status": st, "noconverge": noconv, "rows_network": used, "rows_outside_envelope": outside,
                      "rows_elastic_exact": elastic,
                      "network_fraction": used / max(used + outside + elastic, 1),
                      "stress_kernel_ms": stress_ms, "plain_stress_kernel_ms": plain["stress_ms"],
