@@ -91,3 +91,29 @@ def test_flyer_plate_as_published():
     p = (rho * case.vol[:, None] * v).sum(axis=0)
     assert np.abs(p).max() <= 1e-4 * rho * case.vol.sum() * 200.0
     assert g.get_info()["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision,tol", [(tlsph.FP64, 1e-8), (tlsph.FP32_U64, 1e-4)])
+def test_colliding_blocks_3d_match_oracle(precision, tol):
+    """Two 5 x 4 x 5 NH blocks stacked along y, touching, closing at 4 m/s (the 3D contact stiffness carries
+    the spacing: k = contcoeff E* dc)."""
+    n = (5, 4, 5)
+    lo, _ = W.lattice(n, 1e-3)
+    hi, _ = W.lattice(n, 1e-3, origin=(0.0, n[1] * 1e-3, 0.0))
+    X = np.vstack([lo, hi])
+    m = lo.shape[0]
+    v0 = np.zeros_like(X)
+    v0[:m, 1], v0[m:, 1] = 2.0, -2.0
+    spec = np.repeat(np.array([0, 1], np.int32), m)
+    mat = W.Material(model=W.MODEL_NH, rho=7870.0, E=200e9, nu=0.29, beta1=0.05)
+    case = W.Case("blocks_3d_contact", 3, 1e-3, 1.5e-3, 0.05, W.DT_CFL_STATIC, 0.0, [mat], X, np.full(2 * m, 1e-9),
+                  v0, np.zeros(2 * m, np.int32), spec, [], [], 300, "fp64")
+    case.contact = {"contcoeff": 5.0, "restitution": [0.9, 0.7]}
+    o = make_oracle(case)
+    g = tlsph.from_case(case, precision=precision)
+    for _ in range(3):
+        o.step(100)
+        g.step(100)
+        u_o = o.read("U")
+        assert np.abs(g.read_state("U") - u_o).max() <= tol * np.abs(u_o).max()
+    assert o.contact_energy() >= 0.0

@@ -196,3 +196,24 @@ def test_initial_velocity_from_expression(precision):
     assert np.allclose(v[:, 1], want, rtol=tol, atol=tol * 0.57) and np.all(v[:, 0] == 0.0)
     g.apply_expr("U", [g.expr_compile("1e-4*x0"), -1])
     assert np.allclose(g.read_state("U")[:, 0], 1e-4 * X[:, 0], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_expression_conditions_3d_match_oracle(integrator):
+    """A 3D NH block: the bottom face held by an expression over every particle, the top face pulled with a
+    time- and position-dependent velocity in z and x."""
+    case = W.block_3d(nx=7, ny=6, nz=5, jitter=0.05, seed=4, precision="fp64", beta1=0.2)
+    case.materials = [W.Material(model=W.MODEL_NH, rho=7850.0, E=200e9, nu=0.3, beta1=0.2)]
+    case.integrator = integrator
+    top = case.bcs[1].mask
+    dz = case.dp
+    ex = [(np.ones(case.n, np.uint8), 0, 0b111, [("if(z0 < dx, 0, skip)", "")] * 3, 0.0),
+          (top, 0, 0b101, [("0.2*sin(w*t)*y0/0.006", "w = 3e5"), None, ("-2*min1", "w = 3e5; min1 = 1 - cos(w*t)")],
+           0.0)]
+    g = _gpu_with(case, ex, drop=(0, 1))
+    o = _oracle_with(case, ex, drop=(0, 1))
+    g.step(200)
+    o.step(200)
+    u_o = o.read("U")
+    assert np.abs(g.read_state("U") - u_o).max() <= 1e-8 * np.abs(u_o).max()
+    assert np.abs(u_o[case.X0[:, 2] < dz]).max() == 0.0
