@@ -395,6 +395,35 @@ def measure_flyer_plate(args, device, stream):
             "t_contact_expected_us": 125.0}
 
 
+def measure_taylor_bar(args, device, stream):
+    """The paper's 3D Taylor bar (J2, wall and start given by expressions) at dx = 0.4 mm to 80 us in FP32:
+    stepping throughput (CUDA events) and the final energy split and shape."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    dev = torch.device("cuda", device)
+    case = W.taylor_bar(dx=0.4e-3)
+    g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+    g.set_option(tlsph.OPT_MODE, tlsph.MODE_GRAPH)
+    KE0 = g.energies()["KE"]
+    ms, steps, st, t = 0.0, 0, 0, 0.0
+    while t < 80e-6:
+        m, st1 = timed_steps(g, 1000, stream, dev)
+        ms += m
+        steps += 1000
+        st |= st1
+        t, _ = g.time()
+    e = g.energies()
+    x = case.X0 + g.read_state("U")
+    base = x[case.X0[:, 2] < case.dp]
+    g.close()
+    return {"workload": "taylor_bar dx 0.4 mm J2 cylinder at -227 m/s onto a wall, to 80 us, FP32",
+            "particles": case.n, "steps": steps, "ms_per_step": ms / steps, "value": case.n * steps / (ms * 1e-3),
+            "unit": UNIT, "status": st, "KE_final": e["KE"] / KE0, "PW_final": e["PW"] / KE0,
+            "energy_retained": (e["KE"] + e["SE"] + e["PW"]) / KE0, "length_mm": float(x[:, 2].max() + case.dp / 2) * 1e3,
+            "base_radius_mm": float(np.sqrt(base[:, 0] ** 2 + base[:, 1] ** 2).max() + case.dp / 2) * 1e3}
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -545,6 +574,7 @@ def run_ours(args):
     phase_field = measure_phase_field(args, local, stream)
     crack_b = measure_crack_branching(args, local, stream) if not args.no_crack else None
     flyer = measure_flyer_plate(args, local, stream) if not args.no_crack else None
+    taylor = measure_taylor_bar(args, local, stream) if not args.no_crack else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -580,6 +610,7 @@ def run_ours(args):
         "phase_field": phase_field,
         "crack_branching": crack_b,
         "flyer_plate": flyer,
+        "taylor_bar": taylor,
         "status": int(st),
         "cpu_baseline": cpu,
     }
@@ -599,7 +630,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
     ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching and flyer-plate cases")
+    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching, flyer-plate and Taylor-bar cases")
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
     ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")

@@ -32,6 +32,10 @@ these lattices stand in for them at the same scale):
   plane-strain J2 steel plates 0.05 m apart (100 x 100 particles each at
   dx = 0.01 m) closing at +-200 m/s, contact between the two bodies
   (contcoeff 5, restitution 0.95), Courant number 0.01.
+* ``taylor_bar``    -- the paper's 3D Taylor impact (Sec. 4): a copper-like J2
+  cylinder (L0 = 32.4 mm, R0 = 3.2 mm; the lattice cells whose centres lie in
+  the cylinder) moving at -227 m/s onto a rigid wall at z = 0, the wall and
+  the start given by expressions, Courant number 0.02.
 * ``batched``       -- many independent 2D specimens of log-uniform size with
   random materials and loading (512 specimens is the full case).
 
@@ -250,6 +254,24 @@ def flyer_plate(n=100, dx=0.01, gap=0.05, v=200.0, steps=20000, precision="fp32"
     case = Case("flyer_plate_" + model, 2, dx, 1.5 * dx, 0.01, DT_CFL_STATIC, 0.0, [mat], X, np.full(2 * m, dx * dx), v0,
                 np.zeros(2 * m, np.int32), spec, [], [], steps, precision)
     case.contact = {"contcoeff": contcoeff, "restitution": [restitution, restitution]}
+    return case
+
+
+def taylor_bar(dx=0.4e-3, L0=32.4e-3, R0=3.2e-3, v=227.0, steps=40000, precision="fp32"):
+    """The paper's Taylor bar: lattice cells of the box [-R0, R0]^2 x [0, L0] whose centres lie within R0 of the
+    axis.  A particle whose current z is below 3/4 dx (the layer on the wall) has no axial velocity; every other
+    particle starts at -v along z.  J2 with rho 8930, E 117 GPa, nu 0.35, sigma_y0 400 MPa, H 100 MPa,
+    artificial viscosity 0.05."""
+    nxy, nz = int(math.ceil(2 * R0 / dx)), int(round(L0 / dx))
+    X, _ = lattice((nxy, nxy, nz), dx, origin=(-nxy * dx / 2, -nxy * dx / 2, 0.0))
+    X = np.ascontiguousarray(X[X[:, 0] ** 2 + X[:, 1] ** 2 <= R0 ** 2])
+    n = X.shape[0]
+    mat = Material(model=MODEL_J2, rho=8930.0, E=117e9, nu=0.35, sigma_y0=400e6, H_hard=100e6, beta1=0.05)
+    case = Case("taylor_bar_j2", 3, dx, 1.5 * dx, 0.02, DT_CFL_STATIC, 0.0, [mat], X, np.full(n, dx ** 3),
+                np.zeros((n, 3)), np.zeros(n, np.int32), None, [], [], steps, precision)
+    wall = ("if(z < 0.75*dx, 0, skip)", "")
+    case.expr_bcs = [ExprBC(np.ones(n, np.uint8), BC_VEL, 0b100, [None, None, wall])]
+    case.expr_ics = [("V", [None, None, ("if(z < 0.75*dx, 0, -v0)", f"v0 = {v!r}")])]
     return case
 
 

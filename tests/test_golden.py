@@ -2,6 +2,8 @@
 import json
 import os
 
+import numpy as np
+
 from paper_2602_15149_b300 import workloads as W
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
@@ -52,3 +54,21 @@ def test_cantilever_case_is_the_published_one():
     assert abs(c.X0[:, 1].max() - (ref["H0_m"] - c.dp / 2)) < 1e-12
     for text in (W.CANTILEVER_MODE_LOCALS,):
         assert f"{ref['kw_L0']}" in text and f"{ref['v_factor']} * {ref['c_s']}" in text
+
+
+def test_taylor_bar_case_is_the_published_one():
+    ref = GOLD["taylor_bar"]
+    c = W.taylor_bar(dx=ref["dx_m"][2])
+    m = c.materials[0]
+    assert (m.rho, m.E, m.nu, m.sigma_y0, m.H_hard, m.beta1) == (ref["rho"], ref["E_Pa"], ref["nu"], ref["sigma_y0_Pa"],
+                                                                 ref["H_Pa"], ref["beta1"])
+    assert m.model == W.MODEL_J2 and c.cfl == ref["cfl"]
+    r = np.sqrt(c.X0[:, 0] ** 2 + c.X0[:, 1] ** 2)
+    assert r.max() <= ref["R0_m"] and c.X0[:, 2].max() < ref["L0_m"] < c.X0[:, 2].max() + c.dp
+    assert str(abs(ref["v_m_s"])) in c.expr_ics[0][1][2][1]
+    # the particle set's kinetic energy is within 12% of each printed initial energy (the paper fills the
+    # cylinder with its own generator; the represented volume differs by resolution)
+    for dx, e_ref in zip(ref["dx_m"][1:], ref["initial_energy_J"][1:]):
+        cc = W.taylor_bar(dx=dx)
+        ke = 0.5 * ref["rho"] * cc.vol.sum() * ref["v_m_s"] ** 2
+        assert abs(ke - e_ref) <= 0.12 * e_ref, (dx, ke, e_ref)
