@@ -393,6 +393,17 @@ tlsph_status tlsph_mlp_set_tensor_path(tlsph_mlp *mlp, int path);
  * update.  The weights are copied; later changes to mlp need another call.  The step then runs
  * in TLSPH_MODE_LAUNCH.  TLSPH_ERR_ARG for an FP64 context or an unknown scope. */
 tlsph_status tlsph_set_surrogate(tlsph_ctx *ctx, const tlsph_mlp *mlp, int scope);
+
+/* Network files (16-128-128-128-16 layout): "TLSPHMLP", uint32 version 1, uint32 parameter count,
+ * uint32 96, the FP32 master parameters (tlsph_mlp_get_params order) and the 96-float normalisation
+ * table, little-endian.  save writes them; load replaces a network's parameters and normalisation
+ * (TLSPH_ERR_ARG with a message for a missing or foreign file). */
+tlsph_status tlsph_mlp_save(tlsph_mlp *mlp, const char *path);
+tlsph_status tlsph_mlp_load(tlsph_mlp *mlp, const char *path);
+
+/* Reads a network file and attaches it to the context as tlsph_set_surrogate(ctx, net, scope) does (the
+ * context keeps its own copy; no network object stays alive). */
+tlsph_status tlsph_load_surrogate(tlsph_ctx *ctx, const char *path, int scope);
 /* Cumulative since tlsph_set_surrogate: counts[0] particle updates served by the network,
  * counts[1] J2 updates that fell outside the envelope (exact return map), counts[2] elastic
  * trial states kept exact under TLSPH_SURROGATE_PLASTIC. */

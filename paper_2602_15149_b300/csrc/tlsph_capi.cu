@@ -2514,6 +2514,59 @@ tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
     return TLSPH_OK;
 }
 
+// Network file: 8-byte magic "TLSPHMLP", uint32 version (1), uint32 parameter count, uint32 normalisation
+// count (96), then the FP32 master parameters and the normalisation table, little-endian.
+tlsph_status tlsph_mlp_save(tlsph_mlp *m, const char *path) {
+    if (!m || !path) return TLSPH_ERR_ARG;
+    std::vector<float> P(kNumParams), N(96);
+    tlsph_status st = tlsph_mlp_get_params(m, P.data());
+    if (st != TLSPH_OK) return st;
+    st = tlsph_mlp_get_normalization(m, N.data());
+    if (st != TLSPH_OK) return st;
+    FILE *f = fopen(path, "wb");
+    if (!f) return mfail(m, TLSPH_ERR_ARG, "cannot open the file for writing");
+    const uint32_t hdr[3] = {1u, (uint32_t)kNumParams, 96u};
+    bool ok = fwrite("TLSPHMLP", 1, 8, f) == 8 && fwrite(hdr, 4, 3, f) == 3 &&
+              fwrite(P.data(), 4, P.size(), f) == P.size() && fwrite(N.data(), 4, N.size(), f) == N.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? TLSPH_OK : mfail(m, TLSPH_ERR_ARG, "writing the network file failed");
+}
+
+tlsph_status tlsph_mlp_load(tlsph_mlp *m, const char *path) {
+    if (!m || !path) return TLSPH_ERR_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return mfail(m, TLSPH_ERR_ARG, "cannot open the network file");
+    char magic[8];
+    uint32_t hdr[3];
+    std::vector<float> P(kNumParams), N(96);
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TLSPHMLP", 8) == 0 && fread(hdr, 4, 3, f) == 3 &&
+              hdr[0] == 1u && hdr[1] == (uint32_t)kNumParams && hdr[2] == 96u &&
+              fread(P.data(), 4, P.size(), f) == P.size() && fread(N.data(), 4, N.size(), f) == N.size();
+    fclose(f);
+    if (!ok) return mfail(m, TLSPH_ERR_ARG, "not a network file of this layout (16-128-128-128-16)");
+    tlsph_status st = tlsph_mlp_set_params(m, P.data());
+    if (st != TLSPH_OK) return st;
+    return tlsph_mlp_set_normalization(m, N.data());
+}
+
+tlsph_status tlsph_load_surrogate(tlsph_ctx *c, const char *path, int scope) {
+    DeviceScope ds_(c ? c->p.device : -1);
+    if (!c) return TLSPH_ERR_ARG;
+    if (!path) return fail(c, TLSPH_ERR_ARG, "load_surrogate: null path");
+    tlsph_mlp *m = nullptr;
+    tlsph_status st = tlsph_mlp_create(c->p.device, c->stream, 256, &m);
+    if (st != TLSPH_OK) return fail(c, st, "load_surrogate: cannot create the network");
+    st = tlsph_mlp_load(m, path);
+    if (st != TLSPH_OK) {
+        fail(c, st, "load_surrogate: %s", m->err.c_str());
+        tlsph_mlp_destroy(m);
+        return st;
+    }
+    st = tlsph_set_surrogate(c, m, scope);
+    tlsph_mlp_destroy(m);
+    return st;
+}
+
 tlsph_status tlsph_surrogate_counts(tlsph_ctx *c, int64_t counts[3]) {
     DeviceScope ds_(c ? c->p.device : -1);
     if (!c || !counts) return TLSPH_ERR_ARG;

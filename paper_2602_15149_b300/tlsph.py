@@ -38,7 +38,8 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_mlp_train_step", "tlsph_mlp_gradients", "tlsph_mlp_forward", "tlsph_set_surrogate",
            "tlsph_surrogate_counts", "tlsph_j2_samples",
            "tlsph_mlp_set_tensor_path", "tlsph_expr_check", "tlsph_expr_compile", "tlsph_add_bc_expr",
-           "tlsph_apply_expr", "tlsph_expr_eval", "tlsph_set_contact"]
+           "tlsph_apply_expr", "tlsph_expr_eval", "tlsph_set_contact", "tlsph_mlp_save", "tlsph_mlp_load",
+           "tlsph_load_surrogate"]
 MLP_NUM_PARAMS = 37264
 SURROGATE_ALL, SURROGATE_PLASTIC = 0, 1
 TENSOR_MMA_SYNC, TENSOR_TCGEN05 = 0, 1
@@ -101,6 +102,9 @@ def load_library(path: str = LIB_PATH):
         "tlsph_apply_expr": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
         "tlsph_expr_eval": (C.c_int, [P, C.c_int, C.c_int64, D, D, U8]),
         "tlsph_set_contact": (C.c_int, [P, C.c_double, C.c_int, D]),
+        "tlsph_mlp_save": (C.c_int, [P, C.c_char_p]),
+        "tlsph_mlp_load": (C.c_int, [P, C.c_char_p]),
+        "tlsph_load_surrogate": (C.c_int, [P, C.c_char_p, C.c_int]),
         "tlsph_build_ref_neighbours": (C.c_int, [P]),
         "tlsph_step": (C.c_int, [P, C.c_int64]),
         "tlsph_step_async": (C.c_int, [P, C.c_int64]),
@@ -336,6 +340,11 @@ class TLSPH:
         scope = SURROGATE_ALL if scope is None else scope
         self._ck(self.lib.tlsph_set_surrogate(self.ctx, None if mlp is None else mlp.h, scope), "set_surrogate")
 
+    def load_surrogate(self, path, scope=None):
+        """Attach the network stored in a file written by MLP.save."""
+        scope = SURROGATE_ALL if scope is None else scope
+        self._ck(self.lib.tlsph_load_surrogate(self.ctx, os.fsencode(path), scope), "load_surrogate")
+
     def surrogate_counts(self):
         """(network, outside the envelope, elastic trial kept exact), cumulative."""
         c = np.zeros(3, np.int64)
@@ -392,6 +401,14 @@ class MLP:
         a = np.zeros(MLP_NUM_PARAMS, np.float32)
         self._ck(self.lib.tlsph_mlp_get_params(self.h, a.ctypes.data), "get_params")
         return a
+
+    def save(self, path):
+        """Write the parameters and normalisation to a network file."""
+        self._ck(self.lib.tlsph_mlp_save(self.h, os.fsencode(path)), "save")
+
+    def load(self, path):
+        """Replace the parameters and normalisation from a network file."""
+        self._ck(self.lib.tlsph_mlp_load(self.h, os.fsencode(path)), "load")
 
     def set_tensor_path(self, path):
         """TENSOR_TCGEN05 (default) or TENSOR_MMA_SYNC for the inference kernels."""

@@ -164,3 +164,31 @@ def test_surrogate_step_tracks_exact_step(trained, scope, path):
     else:
         assert used > 0 and elastic > 0
     assert err < 1e-2
+
+
+def test_network_file_round_trip_and_load_surrogate(trained, tmp_path):
+    """A trained network written to a file and read back gives bit-identical outputs, and a context that
+    loads the file steps bit-identically to one given the network object; a foreign file is refused."""
+    import torch as t
+    case, net, _, _, _ = trained
+    path = tmp_path / "net.tlsphmlp"
+    net.save(str(path))
+    other = tlsph.MLP(batch=256)
+    other.load(str(path))
+    x = t.from_numpy(np.random.default_rng(3).normal(size=(300, 16)).astype(np.float32)).cuda()
+    y1, y2 = t.empty((300, 16), device="cuda"), t.empty((300, 16), device="cuda")
+    net.forward(x, y1)
+    other.forward(x, y2)
+    assert t.equal(y1, y2)
+    a, b = tlsph.from_case(case), tlsph.from_case(case)
+    a.set_surrogate(net, tlsph.SURROGATE_ALL)
+    b.load_surrogate(str(path), tlsph.SURROGATE_ALL)
+    a.step(50)
+    b.step(50)
+    assert np.array_equal(a.read_state("U"), b.read_state("U"))
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a network")
+    with pytest.raises(tlsph.TLSPHError):
+        b.load_surrogate(str(bad))
+    with pytest.raises(tlsph.TLSPHError):
+        other.load(str(tmp_path / "missing.bin"))
