@@ -55,12 +55,13 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
 # profiles/dram_traffic__block_3d_j2_128x128x64.md), keyed by the hash of the kernel sources it
 # was taken on; reported as null once the kernels change.
-NCU_TRAFFIC = {"sources": "9fea0b2411f1233c", "pass2": 235111936.0, "gradient": 92255744.0, "stress": 145042944.0}
+NCU_TRAFFIC = {"sources": "142748e3d3c6f1ec", "pass2": 235111936.0, "gradient": 92255744.0, "stress": 145042944.0}
 
 
 def source_hash() -> str:
+    """Hash of the device code (every kernel is defined in the csrc/*.cuh headers)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2602_15149_b300", "csrc", "*"))):
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2602_15149_b300", "csrc", "*.cuh"))):
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
@@ -424,6 +425,45 @@ def measure_taylor_bar(args, device, stream):
             "base_radius_mm": float(np.sqrt(base[:, 0] ** 2 + base[:, 1] ** 2).max() + case.dp / 2) * 1e3}
 
 
+def measure_model_variants(args, shape, device, stream):
+    """The paper's performance study varies only the material law at 1M particles (SVK, NH, both with phase
+    field, J2).  The same five variants of the block (same lattice, loading and step count), each timed on
+    its own context, and the block at three sizes with SVK (the paper's size study)."""
+    import torch
+    from paper_2602_15149_b300 import tlsph
+
+    dev = torch.device("cuda", device)
+    steps = max(20, min(args.steps, 300))
+    variants = {"A1_svk": (W.MODEL_SVK, 0), "A2_nh": (W.MODEL_NH, 0), "B1_svk_fracture": (W.MODEL_SVK, 1),
+                "B2_nh_fracture": (W.MODEL_NH, 1), "C_j2": (W.MODEL_J2, 0)}
+    out = {}
+    for name, (model, frac) in variants.items():
+        case = W.block_3d(*shape, steps=steps)
+        m = case.materials[0]
+        if model != W.MODEL_J2:
+            case.materials = [W.Material(model=model, rho=m.rho, E=m.E, nu=m.nu, beta1=m.beta1, fracture=frac,
+                                         Gc=2.0e4 if frac else 0.0, eps0=2.0 * case.dp if frac else 0.0)]
+        g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+        g.step(args.warmup)
+        ms, st = timed_steps(g, steps, stream, dev)
+        g.close()
+        out[name] = {"ms_per_step": ms / steps, "value": case.n * steps / (ms * 1e-3), "status": st}
+    t = [v["ms_per_step"] for v in out.values()]
+    sizes = {}
+    for sh in ((64, 64, 64), (128, 128, 64), (192, 192, 96)):
+        case = W.block_3d(*sh, steps=steps)
+        m = case.materials[0]
+        case.materials = [W.Material(model=W.MODEL_SVK, rho=m.rho, E=m.E, nu=m.nu, beta1=m.beta1)]
+        g = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
+        g.step(args.warmup)
+        ms, st = timed_steps(g, steps, stream, dev)
+        g.close()
+        sizes[case.n] = {"ms_per_step": ms / steps, "value": case.n * steps / (ms * 1e-3), "status": st}
+    return {"workload": f"block_3d {'x'.join(map(str, shape))} with the five material variants, {steps} steps each",
+            "unit": UNIT, "variants": out, "spread": (max(t) - min(t)) / min(t),
+            "size_scaling_svk": sizes}
+
+
 def measure_surrogate(args, shape, device, stream, plain):
     """The learned form on the same 1M J2 block: return-map samples from an exact run, training on
     the GPU, then the block stepped with the network in the J2 update (both scopes), against the
@@ -575,6 +615,7 @@ def run_ours(args):
     crack_b = measure_crack_branching(args, local, stream) if not args.no_crack else None
     flyer = measure_flyer_plate(args, local, stream) if not args.no_crack else None
     taylor = measure_taylor_bar(args, local, stream) if not args.no_crack else None
+    variants = measure_model_variants(args, shape, local, stream) if not args.no_crack else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -611,6 +652,7 @@ def run_ours(args):
         "crack_branching": crack_b,
         "flyer_plate": flyer,
         "taylor_bar": taylor,
+        "model_variants": variants,
         "status": int(st),
         "cpu_baseline": cpu,
     }
