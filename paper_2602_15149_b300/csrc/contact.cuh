@@ -35,9 +35,10 @@ __device__ __forceinline__ int cell_hash(const int64_t c[3], int tsize) {
     return (int)(h & (uint64_t)(tsize - 1));
 }
 
+// Each particle's cell (kept for the pair search) and its place in its bucket.
 template <typename T>
 __global__ void __launch_bounds__(128) k_contact_count(StepArgs<T> a, const double *X0d, int dim, double dc, int tsize,
-                                                       int *hcount, int *hbucket, int *hslot) {
+                                                       int *hcount, int *hbucket, int *hslot, int4 *hcell) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     double x[3];
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(128) k_contact_count(StepArgs<T> a, const doub
     contact_cell(X0d, a.u64, a.n, i, dim, dc, x, c);
     const int b = cell_hash(c, tsize);
     hbucket[i] = b;
+    hcell[i] = make_int4((int)c[0], (int)c[1], (int)c[2], 0);
     hslot[i] = atomicAdd(&hcount[b], 1);
 }
 
@@ -122,13 +124,15 @@ __global__ void k_contact_sort(int tsize, const int *hcount, const int *hstart, 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0d, double dc, double kc,
                                                  const double *rest, int tsize, const int *hcount,
-                                                 const int *hstart, const int *hlist, T *accc) {
+                                                 const int *hstart, const int *hlist, const int4 *hcell, T *accc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int n = a.n;
     double xi[3];
-    int64_t ci[3];
-    contact_cell(X0d, a.u64, n, i, DIM, dc, xi, ci);
+#pragma unroll
+    for (int k = 0; k < 3; k++) xi[k] = k < DIM ? X0d[k * n + i] + a.u64[k * n + i] : 0.0;
+    const int4 own = hcell[i];  // the cells the particles were filed under
+    const int64_t ci[3] = {own.x, own.y, own.z};
     const int si = a.spec[i];
     const MatT<T> mi = a.mats[a.mid[i]];
     const V4<T> Xi = a.X0V[i];
@@ -146,10 +150,11 @@ __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0
                 for (int q = beg; q < end; q++) {
                     const int j = hlist[q];
                     if (a.spec[j] == si) continue;
+                    const int4 cj = hcell[j];
+                    if (cj.x != cc[0] || cj.y != cc[1] || cj.z != cc[2]) continue;  // another cell, same bucket
                     double xj[3];
-                    int64_t cj[3];
-                    contact_cell(X0d, a.u64, n, j, DIM, dc, xj, cj);
-                    if (cj[0] != cc[0] || cj[1] != cc[1] || cj[2] != cc[2]) continue;  // another cell, same bucket
+#pragma unroll
+                    for (int k = 0; k < 3; k++) xj[k] = k < DIM ? X0d[k * n + j] + a.u64[k * n + j] : 0.0;
                     double d[3], r2 = 0.0;
 #pragma unroll
                     for (int k = 0; k < 3; k++) {

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(BS) k_stress(StepArgs<T> a) {
 
 // ---------------------------------------------------------------- pass 2
 template <typename T, int DIM, bool FRAC, bool VISC>
-__device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &vmag, double &amag) {
+__device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
     const int n = a.n;
     const int sp = a.spec[i];
     {
@@ -556,9 +556,9 @@ __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, double &v
             vv += vn[p] * vn[p];
             aa += acc[p] * acc[p];
         }
-        vmag = (double)t_sqrt(vv);
-        amag = (double)t_sqrt(aa);
-        if (!(isfinite(vmag) && isfinite(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
+        vmag = t_sqrt(vv);
+        amag = t_sqrt(aa);
+        if (!(finite_t(vmag) && finite_t(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
     }
 }
 
@@ -611,18 +611,28 @@ __global__ void __launch_bounds__(BS) k_predict(StepArgs<T> a) {
 // Per-specimen maxima of |v_{n+1}| and |a_n| of one block (one atomic per block when the
 // block holds a single specimen).
 template <typename T, int BS>
-__device__ __forceinline__ void dev_block_maxima(const StepArgs<T> &a, bool active, int sp, double vmag,
-                                                 double amag) {
+__device__ __forceinline__ void dev_block_maxima(const StepArgs<T> &a, bool active, int sp, T vmag, T amag) {
     __shared__ int s_sp;
     __shared__ double s_v[BS / 32], s_a[BS / 32];
     if (threadIdx.x == 0) s_sp = sp;
     __syncthreads();
     const bool uniform = __syncthreads_and(!active || sp == s_sp);
     if (uniform) {
-        double v = vmag, ac = amag;
-        for (int o = 16; o > 0; o >>= 1) {
-            v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-            ac = fmax(ac, __shfl_xor_sync(0xffffffffu, ac, o));
+        double v, ac;
+        if constexpr (sizeof(T) == 4) {
+            // non-negative floats order like their bit patterns; one integer reduction per warp each (a NaN
+            // counts as 0, as fmax drops it).  The maxima equal those of the same values in double.
+            const unsigned vb = __reduce_max_sync(0xffffffffu, isnan(vmag) ? 0u : __float_as_uint((float)vmag));
+            const unsigned ab = __reduce_max_sync(0xffffffffu, isnan(amag) ? 0u : __float_as_uint((float)amag));
+            v = (double)__uint_as_float(vb);
+            ac = (double)__uint_as_float(ab);
+        } else {
+            v = (double)vmag;
+            ac = (double)amag;
+            for (int o = 16; o > 0; o >>= 1) {
+                v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+                ac = fmax(ac, __shfl_xor_sync(0xffffffffu, ac, o));
+            }
         }
         if ((threadIdx.x & 31) == 0) {
             s_v[threadIdx.x >> 5] = v;
@@ -638,8 +648,8 @@ __device__ __forceinline__ void dev_block_maxima(const StepArgs<T> &a, bool acti
             atomicMax(&a.amax_bits[s_sp], (unsigned long long)__double_as_longlong(ac));
         }
     } else if (active) {
-        atomicMax(&a.vmax_bits[sp], (unsigned long long)__double_as_longlong(vmag));
-        atomicMax(&a.amax_bits[sp], (unsigned long long)__double_as_longlong(amag));
+        atomicMax(&a.vmax_bits[sp], (unsigned long long)__double_as_longlong((double)vmag));
+        atomicMax(&a.amax_bits[sp], (unsigned long long)__double_as_longlong((double)amag));
     }
     __syncthreads();
 }
@@ -669,7 +679,7 @@ __global__ void __launch_bounds__(BS, 896 / BS) k_pass2(StepArgs<T> a) {
     __shared__ bool s_last;
     const int i = blockIdx.x * BS + threadIdx.x;
     const bool active = i < a.n;
-    double vmag = 0.0, amag = 0.0;
+    T vmag = T(0), amag = T(0);
     int sp = 0;
     if (active) {
         prefetch_rows(a, i);
@@ -756,7 +766,7 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
         for (int base = blockIdx.x * BS; base < n; base += stride) {
             const int i = base + threadIdx.x;
             const bool active = i < n;
-            double vmag = 0.0, amag = 0.0;
+            T vmag = T(0), amag = T(0);
             int sp = 0;
             if (active) {
                 prefetch_rows(a, i);

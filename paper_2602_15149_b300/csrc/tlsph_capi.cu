@@ -117,6 +117,7 @@ struct tlsph_ctx {
     double *rest = nullptr;
     int tsize = 0;
     int *hcount = nullptr, *hstart = nullptr, *hbucket = nullptr, *hslot = nullptr, *hlist = nullptr, *hbsum = nullptr;
+    int4 *hcell = nullptr;
     void *accc = nullptr;
     // execution mode (TLSPH_MODE_*), block size, captured graph, persistent-launch barrier
     int mode = 0, bs = 128;
@@ -214,6 +215,7 @@ void free_device(tlsph_ctx *c) {
     c->allocs.clear();
     c->rest = nullptr;
     c->hcount = c->hstart = c->hbucket = c->hslot = c->hlist = c->hbsum = nullptr;
+    c->hcell = nullptr;
     c->accc = nullptr;
     c->nexlist = 0;
     c->exlist = c->expos = nullptr;
@@ -916,6 +918,7 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         DA(c->hbucket, n * sizeof(int));
         DA(c->hslot, n * sizeof(int));
         DA(c->hlist, n * sizeof(int));
+        DA(c->hcell, n * sizeof(int4));
         DA(c->accc, dim * n * sizeof(T));
         CK(cudaMemcpyAsync(c->rest, c->resth.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(c->accc, 0, dim * n * sizeof(T), s));
@@ -1005,7 +1008,8 @@ template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const
     const double dc = ex_dx(c);
     cudaStream_t s = c->stream;
     CK(cudaMemsetAsync(c->hcount, 0, ts * sizeof(int), s));
-    k_contact_count<T><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, DIM, dc, ts, c->hcount, c->hbucket, c->hslot);
+    k_contact_count<T><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, DIM, dc, ts, c->hcount, c->hbucket, c->hslot,
+                                                          c->hcell);
     CKL();
     const int nb = (ts + kHashScanBlock - 1) / kHashScanBlock;
     k_hscan_blocks<<<nb, kHashScanBlock, 0, s>>>(ts, c->hcount, c->hstart, c->hbsum);
@@ -1019,7 +1023,7 @@ template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const
     k_contact_sort<<<blocks_for(ts, 128), 128, 0, s>>>(ts, c->hcount, c->hstart, c->hlist);
     CKL();
     k_contact<T, DIM><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, dc, c->kc, c->rest, ts, c->hcount, c->hstart,
-                                                         c->hlist, (T *)c->accc);
+                                                         c->hlist, c->hcell, (T *)c->accc);
     CKL();
     return TLSPH_OK;
 }
