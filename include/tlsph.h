@@ -6,15 +6,20 @@
  * fixed in the reference configuration:
  *   - the deformation gradient F_i with the kernel-gradient correction L_i
  *     (Sec. 2.4, eq. deformGradTLSPH and the corrected gradient L_i),
- *   - the first Piola-Kirchhoff stress from compressible neo-Hookean
+ *   - the first Piola-Kirchhoff stress from St. Venant-Kirchhoff with the
+ *     spectral strain split (Sec. 2.3.1), compressible neo-Hookean
  *     hyperelasticity (Sec. 2.3.2) or finite-strain J2 plasticity with
  *     exponential-map return (Sec. 2.3.3),
  *   - the symmetric momentum sum with artificial viscosity (Sec. 2.4,
  *     eq. MomentumEqTLSPH, eq. artViscCoef),
  *   - the hyperbolic phase-field damage and its degradation of the stress
  *     (Sec. 2.2, eq. phasefieldddot, eq. phasefieldLapLacian),
- *   - the explicit update of Algorithm 1 with velocity / force boundary
- *     conditions (Sec. 2.5, Sec. 3.3.2) and the step bound eq. dt_criterion.
+ *   - the explicit update of Algorithm 1 or 2 with velocity / force boundary
+ *     conditions, constant or given by user-defined expressions (Sec. 2.5,
+ *     Sec. 3.3, Sec. 3.3.2), contact between bodies, and the step bound
+ *     eq. dt_criterion;
+ * and, around it, a batched form for many specimens and a learned J2
+ * surrogate trained and run on the tensor cores.
  *
  * Conventions for every entry point:
  *   - Every call returns a tlsph_status and never aborts the process.  On an
@@ -232,13 +237,14 @@ tlsph_status tlsph_expr_eval(tlsph_ctx *ctx, int id, int64_t n, const double *va
  * planar convex quad p1..p4; 2D: the segment p1-p2 (x, y).  A reference bond
  * whose segment crosses the notch inside it (relative margin 1e-9) is removed.
  * At most 512 notches. */
-tlsph_status tlsph_add_notch(tlsph_ctx *ctx, const double quad[12]);
+tlsph_status tlsph_add_notch(tlsph_ctx *ctx, const double quad[12]);  /* non-finite coordinates: TLSPH_ERR_ARG */
 
 /* Reference setup, once (Sec. 2.4): cell keys floor((X0 - Xmin) / (R/3) + 1/2),
  * stable sort by (specimen, cell, id), neighbour lists {j != i : |X0j - X0i|^2 < R^2}
  * (FP64, fixed summation order, no FMA) minus notch-crossing bonds, the correction
- * tensors and the initial state.  Errors: ERR_SINGULAR_L if a correction matrix is
- * singular, ERR_OOM, ERR_CUDA.  Calling it again rebuilds from the reference state. */
+ * tensors and the initial state.  Errors: ERR_ARG if two particles of one specimen share a
+ * reference position, ERR_SINGULAR_L if a correction matrix is singular, ERR_OOM (also past
+ * TLSPH_OPT_MEMORY_LIMIT), ERR_CUDA.  Calling it again rebuilds from the reference state. */
 tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *ctx);
 
 /* Advance every specimen by nsteps steps of Algorithm 1 (3 kernels per step),
@@ -295,7 +301,10 @@ enum {
     TLSPH_OPT_BARRIER_TEST = 5, /* testing: the persistent mode's grid barrier waits for one block more than it
                                    launches, so every wait runs out after about a second and tlsph_step /
                                    tlsph_sync return TLSPH_ERR_TIMEOUT (the context stays usable) */
-    TLSPH_OPT_NEIGHBOUR_LAYOUT = 6 /* value TLSPH_LAYOUT_*: how the step kernels walk the neighbour rows */
+    TLSPH_OPT_NEIGHBOUR_LAYOUT = 6, /* value TLSPH_LAYOUT_*: how the step kernels walk the neighbour rows */
+    TLSPH_OPT_MEMORY_LIMIT = 7      /* value in MiB (0 = none): a cap on the device memory the context allocates for
+                                     * its state; an allocation past it returns TLSPH_ERR_OOM as a failed cudaMalloc
+                                     * would, and the context stays usable (tests inject allocation failures with it) */
 };
 /* Neighbour layouts.  The reference setup always builds CSR rows (tlsph_neighbours) and their
  * SELL-32 copy.  When the pair differences j - i of the cell-sorted particles take at most 128

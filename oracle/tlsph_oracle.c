@@ -638,6 +638,8 @@ int orc_set_bc_values(orc_ctx *c, int b, int phase, const double *val, const uin
 
 int orc_add_notch(orc_ctx *c, const double *quad) {
     if (!c || !quad || c->nnotch >= ORC_MAX_NOTCH) return ORC_ERR_ARG;
+    for (int k = 0; k < 12; k++)
+        if (!isfinite(quad[k])) return ORC_ERR_ARG;
     memcpy(c->notch[c->nnotch], quad, 12 * sizeof(double));
     c->nnotch++;
     return ORC_OK;
@@ -845,6 +847,11 @@ int orc_build_neighbours(orc_ctx *c, int method) {
     }
     free(rows);
     free(cnt);
+
+    /* two particles of one specimen at the same reference position are an input error */
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t q = c->row_ptr[i]; q < c->row_ptr[i + 1]; q++)
+            if (ref_r2(c, i, c->col[q]) == 0.0) return ORC_ERR_ARG;
 
     /* correction tensor L_i = -(sum_j gradW_ij (x) r0_ij V0j)^-1 (Sec. 2.4) */
     int d = c->p.dim;

@@ -56,7 +56,8 @@ __device__ __forceinline__ double bc_factor(const BCDev &b, double t) {
     return 1.0;
 }
 
-enum { kFlagNonfinite = 0, kFlagNoconv = 1, kFlagSingular = 2, kFlagRowOverflow = 3, kFlagTimeout = 4, kNumFlags = 8 };
+enum { kFlagNonfinite = 0, kFlagNoconv = 1, kFlagSingular = 2, kFlagRowOverflow = 3, kFlagTimeout = 4,
+       kFlagCoincident = 5, kNumFlags = 8 };
 
 // All pointers of a step (device memory, cell-sorted order).
 template <typename T> struct StepArgs {

@@ -2,6 +2,7 @@
 // neighbour lists, notch cut, correction tensors, SELL-32 neighbour layout.
 //
 // Neighbour predicate (Sec. 2.4): j != i, same specimen, r0^2 < R^2 with
+// (two particles at the same reference position are an input error: the counting pass flags them)
 // r0^2 = ((dx dx + dy dy) + dz dz) in FP64 round-to-nearest without fused
 // multiply-add, so that the lists are bit-identical to any implementation
 // that evaluates the same expression.
@@ -211,7 +212,7 @@ __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long *a, 
 template <bool FILL>
 __global__ void k_neighbours(int64_t n, CellGrid g, double R2, const unsigned long long *skey, const double *Xs /* 3 arrays */,
                              const int *sid /* caller id of sorted k */, NotchSet ns, int *row_len, const int64_t *row_ptr,
-                             int *col) {
+                             int *col, int *flags) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double xi = Xs[k], yi = Xs[n + k], zi = Xs[2 * n + k];
@@ -244,6 +245,7 @@ __global__ void k_neighbours(int64_t n, CellGrid g, double R2, const unsigned lo
                     r2 = __dadd_rn(r2, __dmul_rn(dz2, dz2));
                 }
                 if (!(r2 < R2)) continue;
+                if (!FILL && r2 == 0.0) atomicAdd(&flags[kFlagCoincident], 1);  // two particles at one place
                 if (ns.count) {
                     int64_t a = sid[k] < sid[j] ? k : j, b = sid[k] < sid[j] ? j : k;
                     double P[3] = {Xs[a], Xs[n + a], Xs[2 * n + a]};

@@ -57,6 +57,8 @@ struct tlsph_ctx {
     bool has_j2 = false, has_frac = false, has_visc = false;
     bool leap = false;  // Algorithm 2 (leapfrog) instead of Algorithm 1
     bool record_acc = false;
+    size_t mem_limit = 0, mem_used = 0;  // cap on the context's state allocations (0 = none), and their total
+    std::vector<size_t> alloc_bytes;     // size of each entry of allocs
     double bytes_per_step = 0.0;
     // device memory
     std::vector<void *> allocs;
@@ -179,12 +181,17 @@ struct DeviceScope {
 template <typename P> tlsph_status dalloc(tlsph_ctx *c, P **ptr, size_t bytes) {
     void *q = nullptr;
     if (bytes == 0) bytes = 16;
+    if (c->mem_limit && c->mem_used + bytes > c->mem_limit)
+        return fail(c, TLSPH_ERR_OOM, "device memory limit of %zu MiB reached (TLSPH_OPT_MEMORY_LIMIT)",
+                    c->mem_limit >> 20);
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, TLSPH_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
     c->allocs.push_back(q);
+    c->alloc_bytes.push_back(bytes);
+    c->mem_used += bytes;
     *ptr = reinterpret_cast<P *>(q);
     return TLSPH_OK;
 }
@@ -213,6 +220,8 @@ void free_device(tlsph_ctx *c) {
     drop_graph(c);
     for (void *q : c->allocs) cudaFree(q);
     c->allocs.clear();
+    c->alloc_bytes.clear();
+    c->mem_used = 0;
     c->rest = nullptr;
     c->hcount = c->hstart = c->hbucket = c->hslot = c->hlist = c->hbsum = nullptr;
     c->hcell = nullptr;
@@ -552,7 +561,10 @@ tlsph_status add_halo(tlsph_ctx *c, void *&ptr, size_t elem, int64_t n) {
         CK(cudaStreamSynchronize(c->stream));
         auto it = std::find(c->allocs.begin(), c->allocs.end(), ptr);
         if (it != c->allocs.end()) {
+            const size_t k = (size_t)(it - c->allocs.begin());
             cudaFree(*it);
+            c->mem_used -= c->alloc_bytes[k];
+            c->alloc_bytes.erase(c->alloc_bytes.begin() + (std::ptrdiff_t)k);
             c->allocs.erase(it);
         }
     }
@@ -777,8 +789,10 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     DA(c->row_len, n * sizeof(int));
     DA(c->row_ptr, (n + 1) * sizeof(int64_t));
     NotchSet ns{notchd, nn};
+    DA(c->flags, kNumFlags * sizeof(int));
+    CK(cudaMemsetAsync(c->flags, 0, kNumFlags * sizeof(int), s));
     k_neighbours<false><<<blocks_for(n), kThreads, 0, s>>>(n, g, R2, skey, c->X0d, c->perm, ns, c->row_len, nullptr,
-                                                           nullptr);
+                                                           nullptr, c->flags);
     CKL();
     int64_t *len64;
     DA(len64, (n + 1) * sizeof(int64_t));
@@ -796,12 +810,10 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     if (c->nnz >= (int64_t)1 << 31) return fail(c, TLSPH_ERR_ARG, "too many neighbour pairs for 32-bit indices");
     DA(c->col, std::max<int64_t>(c->nnz, 1) * sizeof(int));
     k_neighbours<true><<<blocks_for(n), kThreads, 0, s>>>(n, g, R2, skey, c->X0d, c->perm, ns, c->row_len, c->row_ptr,
-                                                          c->col);
+                                                          c->col, c->flags);
     CKL();
     // ---- flags, correction tensors
-    DA(c->flags, kNumFlags * sizeof(int));
-    CK(cudaMemsetAsync(c->flags, 0, kNumFlags * sizeof(int), s));
-    for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = 0;
+        for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = 0;
     DA(c->Ahat, 6 * n * sizeof(T));
     k_correction<T><<<blocks_for(n), kThreads, 0, s>>>(n, dim, c->row_ptr, c->col, (const V4<T> *)c->X0V,
                                                        1.0 / R, (T *)c->Ahat, c->flags);
@@ -937,6 +949,8 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     c->parity = 0;
     c->steps = 0;
     c->bytes_per_step = algorithmic_bytes(c, sizeof(T));
+    if (hf[kFlagCoincident])
+        return fail(c, TLSPH_ERR_ARG, "%d particle pairs share a reference position", hf[kFlagCoincident] / 2);
     if (hf[kFlagSingular]) return fail(c, TLSPH_ERR_SINGULAR_L, "%d particles have a singular correction matrix",
                                        hf[kFlagSingular]);
     c->built = true;
@@ -1609,6 +1623,8 @@ tlsph_status tlsph_add_bc(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_
 tlsph_status tlsph_add_notch(tlsph_ctx *c, const double quad[12]) {
     if (!c) return TLSPH_ERR_ARG;
     if (!quad || c->notches.size() / 12 >= 512) return fail(c, TLSPH_ERR_ARG, "add_notch: null or more than 512");
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(quad[k])) return fail(c, TLSPH_ERR_ARG, "add_notch: non-finite coordinate %d", k);
     c->notches.insert(c->notches.end(), quad, quad + 12);
     c->built = false;
     return TLSPH_OK;
@@ -1875,6 +1891,8 @@ tlsph_status tlsph_neighbours(tlsph_ctx *c, int64_t *row_ptr, int32_t *col, int6
     CK(cudaStreamSynchronize(c->stream));
     while (c->allocs.size() > mark) {
         cudaFree(c->allocs.back());
+        c->mem_used -= c->alloc_bytes.back();
+        c->alloc_bytes.pop_back();
         c->allocs.pop_back();
     }
     return TLSPH_OK;
@@ -1937,6 +1955,11 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
         if (value != 64 && value != 128 && value != 256) return fail(c, TLSPH_ERR_ARG, "block must be 64, 128 or 256");
         c->bs = value;
         drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_MEMORY_LIMIT) {
+        if (value < 0) return fail(c, TLSPH_ERR_ARG, "memory limit must be >= 0 MiB");
+        c->mem_limit = (size_t)value << 20;
         return TLSPH_OK;
     }
     if (option == TLSPH_OPT_BARRIER_TEST) {
@@ -2623,6 +2646,8 @@ tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plast
     *count = std::min<int64_t>(h, cap);
     while (c->allocs.size() > mark) {
         cudaFree(c->allocs.back());
+        c->mem_used -= c->alloc_bytes.back();
+        c->alloc_bytes.pop_back();
         c->allocs.pop_back();
     }
     return TLSPH_OK;

@@ -22,6 +22,7 @@ BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
 FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "ACC": 11, "CPINV": 12,
          "STATE": 100}
 OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6
+OPT_MEMORY_LIMIT = 7
 LAYOUT_AUTO, LAYOUT_CSR = 0, 1
 MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 INTEGRATOR_EULER, INTEGRATOR_LEAPFROG = 1, 2

@@ -751,3 +751,18 @@ def test_svk_notched_plate_history_and_damage():
     tip = np.argmax(Hprev)
     X = case.X0
     assert abs(X[tip, 0] - 0.05) < 4 * case.dp and abs(X[tip, 1] - 0.02) < 4 * case.dp
+
+
+def test_coincident_particles_and_bad_notches_are_refused():
+    """Input errors the oracle refuses: two particles of one specimen at one reference position (the
+    kernel sums would divide 0 by 0), and a notch with a non-finite coordinate."""
+    case = W.plate_2d(nx=6, ny=4)
+    X = case.X0.copy()
+    X[5] = X[4]
+    bad = W.Case(**{**case.__dict__, "X0": X})
+    o = make_oracle(bad, build=False)
+    with pytest.raises(RuntimeError):
+        o.build_ref_neighbours()
+    o = make_oracle(case, build=False)
+    with pytest.raises(RuntimeError):
+        o.add_notch(np.array([0.0, 0.0, 0.0, np.nan, 0.0, 0.0, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0]))
