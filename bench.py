@@ -450,7 +450,7 @@ def measure_model_variants(args, shape, device, stream):
         out[name] = {"ms_per_step": ms / steps, "value": case.n * steps / (ms * 1e-3), "status": st}
     t = [v["ms_per_step"] for v in out.values()]
     sizes = {}
-    for sh in ((64, 64, 64), (128, 128, 64), (192, 192, 96)):
+    for sh in ((48, 48, 32), (64, 64, 64), (128, 128, 64), (192, 192, 96), (256, 256, 128)):
         case = W.block_3d(*sh, steps=steps)
         m = case.materials[0]
         case.materials = [W.Material(model=W.MODEL_SVK, rho=m.rho, E=m.E, nu=m.nu, beta1=m.beta1)]

@@ -12,6 +12,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tlsph.h"
 #include "expr_compile.h"
 #include "contact.cuh"
@@ -147,6 +149,13 @@ tlsph_status fail(tlsph_ctx *c, tlsph_status st, const char *fmt, ...) {
     if (c) c->err = buf;
     return st;
 }
+
+// An NVTX range over a C-ABI call, so that a timeline profiler shows the setup, each batch of steps and
+// the autotuner by name (header-only NVTX; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Makes the context's device current for the duration of a call and restores the caller's.
 struct DeviceScope {
@@ -1742,6 +1751,7 @@ tlsph_status tlsph_set_contact(tlsph_ctx *c, double contcoeff, int nbodies, cons
 }
 
 tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
+    NvtxRange nv_("tlsph_build_ref_neighbours");
     DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (c->n <= 0 || c->mats.empty()) return fail(c, TLSPH_ERR_STATE, "no particles");
@@ -1752,6 +1762,7 @@ tlsph_status tlsph_build_ref_neighbours(tlsph_ctx *c) {
 }
 
 tlsph_status tlsph_step_async(tlsph_ctx *c, int64_t nsteps) {
+    NvtxRange nv_("tlsph_step");
     DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before step");
@@ -1976,6 +1987,7 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
 }
 
 tlsph_status tlsph_autotune(tlsph_ctx *c, int trial_steps, tlsph_tuning *best, tlsph_tuning *all) {
+    NvtxRange nv_("tlsph_autotune");
     DeviceScope ds_(c ? c->p.device : -1);
     if (!c) return TLSPH_ERR_ARG;
     if (!c->built) return fail(c, TLSPH_ERR_STATE, "build_ref_neighbours must come before autotune");
