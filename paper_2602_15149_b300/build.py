@@ -8,6 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "_lib", "libtlsph.so")
+DEBUG_LIB = os.path.join(HERE, "_lib", "libtlsph_debug.so")  # with device bounds checks (TLSPH_DEBUG)
 SOURCES = [os.path.join(HERE, "csrc", "tlsph_capi.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -24,20 +25,23 @@ def nvcc_command(out: str = LIB, extra=()):
              "-Xcompiler", "-ffp-contract=off", "-shared", "-o", out, *SOURCES] + list(extra))
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile if the library is missing or older than any source; return its path."""
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build_library(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile if the library is missing or older than any source; return its path.  debug=True builds
+    libtlsph_debug.so, whose kernels check every neighbour index (a bad one sets a flag that the step
+    reports as a status; nothing traps)."""
+    lib = DEBUG_LIB if debug else LIB
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(p) <= t for p in _inputs()):
-            return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = nvcc_command(tmp)
+            return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = nvcc_command(tmp, ["-DTLSPH_DEBUG"] if debug else [])
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -57,7 +57,7 @@ __device__ __forceinline__ double bc_factor(const BCDev &b, double t) {
 }
 
 enum { kFlagNonfinite = 0, kFlagNoconv = 1, kFlagSingular = 2, kFlagRowOverflow = 3, kFlagTimeout = 4,
-       kFlagCoincident = 5, kNumFlags = 8 };
+       kFlagCoincident = 5, kFlagBounds = 6, kNumFlags = 8 };
 
 // All pointers of a step (device memory, cell-sorted order).
 template <typename T> struct StepArgs {
@@ -69,6 +69,7 @@ template <typename T> struct StepArgs {
     const int *soff;       // stencil differences j - i, ascending
     const int2 *runs;      // runs of consecutive differences: (first difference, first entry | length << 8)
     int nsten, nruns;      // stencil entries (0 = SELL-32 rows) and runs (the most of any table)
+    int64_t halo;          // zero records before and after each gathered array (stencil layout)
     int sten_groups;       // stencil tables: 1, or one per specimen (kMaxStencil entries each)
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
     const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) (reference configuration)

@@ -68,6 +68,23 @@ template <typename T> __device__ __forceinline__ bool finite_t(T x) { return isf
 // is skipped (a warp vote), which saves its loads at the faces of a block.  Without RUNS the
 // entries are walked one by one (UNROLL at a time across runs, each reading its difference).
 // SELL-32 layout otherwise: entry k of row i at slice_off[i / 32] + 32 k + i % 32.
+// Debug builds (TLSPH_DEBUG) check every neighbour index before it is used: a stencil slot may point into
+// the zero halo around the gathered arrays, an active neighbour and a CSR entry must be a particle.  A bad
+// index sets a flag (reported by the step as a status) and the access is skipped; nothing traps.
+template <typename T> __device__ __forceinline__ bool neighbour_ok(const StepArgs<T> &a, int j, bool on) {
+#ifdef TLSPH_DEBUG
+    const bool in_particles = j >= 0 && j < a.n;
+    const bool ok = a.nsten > 0 ? (j >= -a.halo && j < a.n + a.halo && (!on || in_particles)) : in_particles;
+    if (!ok) atomicAdd(&a.flags[kFlagBounds], 1);
+    return ok;
+#else
+    (void)a;
+    (void)j;
+    (void)on;
+    return true;
+#endif
+}
+
 template <int UNROLL = 4, bool SKIP = false, bool RUNS = true, typename T, typename Pair>
 __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, Pair &&pair) {
     // the row's stencil table: its specimen's, when each specimen has its own
@@ -81,7 +98,8 @@ __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, 
             for (int b = 0; b < lim; b++) {
                 const bool on = (m >> b) & 1u;
                 if (SKIP && !__any_sync(__activemask(), on)) continue;
-                pair(i + __ldg(off + b), on);
+                const int j = i + __ldg(off + b);
+                if (neighbour_ok(a, j, on)) pair(j, on);
             }
         }
     } else if (a.nsten > 0) {
@@ -102,7 +120,7 @@ __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, 
                 if (k < len) {
                     const bool on = (bits >> k) & 1u;
                     if (SKIP && !__any_sync(__activemask(), on)) continue;
-                    pair(io + k, on);
+                    if (neighbour_ok(a, io + k, on)) pair(io + k, on);
                 }
             }
         }
@@ -111,7 +129,10 @@ __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, 
         const int len = a.row_len[i];
         const int *cp = a.col + base;
 #pragma unroll UNROLL
-        for (int k = 0; k < len; k++) pair(__ldg(cp + 32 * k), true);
+        for (int k = 0; k < len; k++) {
+            const int j = __ldg(cp + 32 * k);
+            if (neighbour_ok(a, j, true)) pair(j, true);
+        }
     }
 }
 

@@ -351,6 +351,7 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.nsten = sten ? c->nsten : 0;
     a.nruns = sten ? c->nruns : 0;
     a.sten_groups = c->sten_groups;
+    a.halo = c->halo;
     a.runs = sten ? c->runs : nullptr;
     a.soff = sten ? c->soff : nullptr;
     a.nmask = sten ? c->nmask : nullptr;
@@ -958,6 +959,7 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     c->parity = 0;
     c->steps = 0;
     c->bytes_per_step = algorithmic_bytes(c, sizeof(T));
+    if (hf[kFlagBounds]) return fail(c, TLSPH_ERR_STATE, "%d neighbour indices out of range in the setup", hf[kFlagBounds]);
     if (hf[kFlagCoincident])
         return fail(c, TLSPH_ERR_ARG, "%d particle pairs share a reference position", hf[kFlagCoincident] / 2);
     if (hf[kFlagSingular]) return fail(c, TLSPH_ERR_SINGULAR_L, "%d particles have a singular correction matrix",
@@ -1376,7 +1378,9 @@ tlsph_status check_flags(tlsph_ctx *c) {
     int64_t dn = hf[kFlagNonfinite] - c->flags_seen[kFlagNonfinite];
     int64_t dc = hf[kFlagNoconv] - c->flags_seen[kFlagNoconv];
     int64_t dt = hf[kFlagTimeout] - c->flags_seen[kFlagTimeout];
+    int64_t db = hf[kFlagBounds] - c->flags_seen[kFlagBounds];
     for (int q = 0; q < kNumFlags; q++) c->flags_seen[q] = hf[q];
+    if (db > 0) return fail(c, TLSPH_ERR_STATE, "%lld neighbour indices out of range (debug build)", (long long)db);
     if (dt > 0) {
         // a persistent launch gave up at a barrier: its steps are incomplete; reset the
         // barrier and the timeout flag so that the context stays usable

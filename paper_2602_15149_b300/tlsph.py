@@ -11,7 +11,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libtlsph.so")
+# the library to load; TLSPH_LIBRARY selects another build, e.g. _lib/libtlsph_debug.so (bounds-checked kernels)
+LIB_PATH = os.environ.get("TLSPH_LIBRARY") or os.path.join(HERE, "_lib", "libtlsph.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_SINGULAR_L, ERR_NONFINITE, ERR_NOCONVERGE, ERR_TIMEOUT, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
