@@ -8,6 +8,8 @@ same conditions written as constants, and within 1e-8 (FP64, max norm relative t
 oracle, whose neighbour sums run in another order (a condition applied at the wrong time level would be off
 by about w dt ~ 1e-2 here).
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -105,10 +107,15 @@ def _plate(integrator=1):
     return case
 
 
+def _without(case, drop):
+    c = copy.copy(case)  # keeps attributes beyond the dataclass fields (batched specimen loads)
+    c.bcs = [b for k, b in enumerate(case.bcs) if k not in drop]
+    return c
+
+
 def _gpu_with(case, exbcs, drop=(), precision=tlsph.FP64, mode=None):
     """exbcs: (mask, kind, comp_mask, [(expr, locals) or None per component], area)."""
-    bcs = [b for k, b in enumerate(case.bcs) if k not in drop]
-    c = W.Case(**{**case.__dict__, "bcs": bcs})
+    c = _without(case, drop)
     g = tlsph.from_case(c, precision=precision, build=False)
     for mask, kind, cm, exprs, area in exbcs:
         ids = [-1 if e is None else g.expr_compile(*e) for e in exprs]
@@ -120,8 +127,7 @@ def _gpu_with(case, exbcs, drop=(), precision=tlsph.FP64, mode=None):
 
 
 def _oracle_with(case, exbcs, drop=()):
-    bcs = [b for k, b in enumerate(case.bcs) if k not in drop]
-    o = make_oracle(W.Case(**{**case.__dict__, "bcs": bcs}))
+    o = make_oracle(_without(case, drop))
     for mask, kind, cm, exprs, area in exbcs:
         o.add_bc_expr(mask, kind, cm, [None if e is None else Expression(e[0], e[1]) for e in exprs], area=area)
     return o
@@ -217,3 +223,18 @@ def test_expression_conditions_3d_match_oracle(integrator):
     u_o = o.read("U")
     assert np.abs(g.read_state("U") - u_o).max() <= 1e-8 * np.abs(u_o).max()
     assert np.abs(u_o[case.X0[:, 2] < dz]).max() == 0.0
+
+
+def test_expression_conditions_with_specimen_clocks():
+    """Batched specimens keep their own clocks (and step sizes): an expression condition on every particle
+    sees its own specimen's t and dt, in the library as in the oracle."""
+    case = W.batched(nspec=6, n_min=40, n_max=300, seed=4, precision="fp64")
+    ex = [(np.ones(case.n, np.uint8), 0, 0b10, [None, ("if(x0 < 2.5*dx, 1e3*t + 0.01*dt/1e-7, skip)", "")], 0.0)]
+    g = _gpu_with(case, ex)
+    o = _oracle_with(case, ex)
+    g.step(150)
+    o.step(150)
+    u_o = o.read("U")
+    assert np.abs(g.read_state("U") - u_o).max() <= 1e-8 * np.abs(u_o).max()
+    ts = [g.time(s) for s in range(6)]
+    assert len({round(t[1], 18) for t in ts}) > 1  # the specimens do run on different steps
