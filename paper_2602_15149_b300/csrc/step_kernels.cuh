@@ -161,50 +161,76 @@ template <typename T> __device__ __forceinline__ void prefetch_rows(const StepAr
 
 // ---------------------------------------------------------------- pass 1a: deformation gradient
 // G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i.  Register-light so
-// that many warps keep neighbour gathers in flight.
-template <typename T, int DIM>
-__device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[DIM][DIM]) {
-    const int n = a.n;
-    const V4<T> xi = a.X0V[i];
-    const V4<T> ui = a.ug_cur[i];
+// that many warps keep neighbour gathers in flight.  Written as pieces (own state, neighbour record,
+// pair term, closing product), which keeps the loop body's live state explicit.
+template <typename T, int DIM> struct GradOwn {
+    V4<T> xi, ui;
     T B[DIM][DIM];
+};
+template <typename T> struct GradRec {
+    V4<T> xj, uj;
+};
+template <typename T, int DIM> __device__ __forceinline__ void grad_begin(const StepArgs<T> &a, int i, GradOwn<T, DIM> &o) {
+    o.xi = a.X0V[i];
+    o.ui = a.ug_cur[i];
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
-        for (int q = 0; q < DIM; q++) B[p][q] = T(0);
-    for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
-        const V4<T> xj = ldg4(a.X0V + j);
-        const V4<T> uj = ldg4(a.ug_cur + j);
-        T d[DIM], du[DIM];
-        d[0] = xj.x - xi.x;
-        d[1] = xj.y - xi.y;
-        du[0] = uj.x - ui.x;
-        du[1] = uj.y - ui.y;
-        if (DIM == 3) {
-            d[DIM - 1] = xj.z - xi.z;
-            du[DIM - 1] = uj.z - ui.z;
-        }
-        const T t = pair_t(pair_r2<T, DIM>(d), a.inv2h);
-        const T Vj = DIM == 3 ? xj.w : xj.z;
-        const T aw = on ? t * t * t * Vj : T(0);
+        for (int q = 0; q < DIM; q++) o.B[p][q] = T(0);
+}
+template <typename T> __device__ __forceinline__ GradRec<T> grad_load(const StepArgs<T> &a, int j) {
+    return GradRec<T>{ldg4(a.X0V + j), ldg4(a.ug_cur + j)};
+}
+template <typename T, int DIM>
+__device__ __forceinline__ void grad_pair(const StepArgs<T> &a, GradOwn<T, DIM> &o, const GradRec<T> &r, bool on) {
+    T d[DIM], du[DIM];
+    d[0] = r.xj.x - o.xi.x;
+    d[1] = r.xj.y - o.xi.y;
+    du[0] = r.uj.x - o.ui.x;
+    du[1] = r.uj.y - o.ui.y;
+    if (DIM == 3) {
+        d[DIM - 1] = r.xj.z - o.xi.z;
+        du[DIM - 1] = r.uj.z - o.ui.z;
+    }
+    const T t = pair_t(pair_r2<T, DIM>(d), a.inv2h);
+    const T Vj = DIM == 3 ? r.xj.w : r.xj.z;
+    const T aw = on ? t * t * t * Vj : T(0);
 #pragma unroll
-        for (int p = 0; p < DIM; p++) {
-            const T c = aw * du[p];
+    for (int p = 0; p < DIM; p++) {
+        const T c = aw * du[p];
 #pragma unroll
-            for (int q = 0; q < DIM; q++) B[p][q] = t_fma(c, d[q], B[p][q]);
-        }
-    });
+        for (int q = 0; q < DIM; q++) o.B[p][q] = t_fma(c, d[q], o.B[p][q]);
+    }
+}
+template <typename T, int DIM>
+__device__ __forceinline__ void grad_finish(const StepArgs<T> &a, int i, const GradOwn<T, DIM> &o, T Gm[DIM][DIM]) {
     T A[3][3];
-    load_ahat<T, DIM>(a.Ahat, n, i, A);
+    load_ahat<T, DIM>(a.Ahat, a.n, i, A);
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) {
-            T s = B[p][0] * A[0][q];
+            T s = o.B[p][0] * A[0][q];
 #pragma unroll
-            for (int r = 1; r < DIM; r++) s = t_fma(B[p][r], A[r][q], s);
+            for (int r = 1; r < DIM; r++) s = t_fma(o.B[p][r], A[r][q], s);
             Gm[p][q] = s;
         }
+}
+template <typename T, int DIM> __device__ __forceinline__ void grad_store(const StepArgs<T> &a, int i, const T Gm[DIM][DIM]) {
+#pragma unroll
+    for (int p = 0; p < DIM; p++)
+#pragma unroll
+        for (int q = 0; q < DIM; q++) a.G[(p * DIM + q) * a.n + i] = Gm[p][q];
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[DIM][DIM]) {
+    GradOwn<T, DIM> o;
+    grad_begin<T, DIM>(a, i, o);
+    for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
+        grad_pair<T, DIM>(a, o, grad_load(a, j), on);
+    });
+    grad_finish<T, DIM>(a, i, o, Gm);
 }
 
 template <typename T, int DIM, int BS>
@@ -214,10 +240,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) k_gradient(StepArgs<T> a) {
     prefetch_rows(a, i);
     T Gm[DIM][DIM];
     dev_gradient<T, DIM>(a, i, Gm);
-#pragma unroll
-    for (int p = 0; p < DIM; p++)
-#pragma unroll
-        for (int q = 0; q < DIM; q++) a.G[(p * DIM + q) * a.n + i] = Gm[p][q];
+    grad_store<T, DIM>(a, i, Gm);
 }
 
 // First moment of the corrected kernel, sum_j V_j w_ij (X_j - X_i): it depends on the reference
@@ -370,217 +393,273 @@ __global__ void __launch_bounds__(BS) k_stress(StepArgs<T> a) {
 }
 
 // ---------------------------------------------------------------- pass 2
+// Pass 2 in pieces: the particle's own state and sums, the neighbour record, the pair term and the
+// closing update (the loop's live state is the own state; the compiler keeps fewer values across it
+// than with one function body).
+template <typename T, int DIM> struct P2Own {
+    V4<T> xi, ui, vsi;
+    MatT<T> m;
+    bool frac;
+    T irho, cvis;
+    T s2[DIM], s3[DIM], Tl[DIM == 3 ? 6 : 3];
+};
+// the neighbour's records: position and volume, velocity (its fourth component is s, or q22 without
+// phase field), Q = P Ahat, displacement and reference mass
+template <typename T> struct P2Rec {
+    V4<T> xj, vsj, q0, q1, uj;
+    T q2;
+};
+template <typename T, int DIM, bool FRAC>
+__device__ __forceinline__ void p2_begin(const StepArgs<T> &a, int i, P2Own<T, DIM> &o) {
+    o.xi = a.X0V[i];
+    o.ui = a.ug_cur[i];
+    o.vsi = a.vs_cur[i];
+    o.m = a.mats[a.mid[i]];
+    o.frac = FRAC && o.m.fracture;
+    o.irho = T(1) / o.m.rho;
+    o.cvis = o.m.beta1 * o.m.c0;
+#pragma unroll
+    for (int p = 0; p < DIM; p++) o.s2[p] = o.s3[p] = T(0);
+#pragma unroll
+    for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) o.Tl[p] = T(0);
+}
 template <typename T, int DIM, bool FRAC, bool VISC>
-__device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
+__device__ __forceinline__ P2Rec<T> p2_load(const StepArgs<T> &a, int j) {
+    P2Rec<T> r;
+    r.xj = ldg4(a.X0V + j);
+    r.vsj = V4<T>{T(0), T(0), T(0), T(0)};
+    if (VISC || FRAC) r.vsj = ldg4(a.vs_cur + j);
+    r.q0 = ldg4(a.Qa + j);
+    if (DIM == 3) {
+        r.q1 = ldg4(a.Qb + j);
+        r.q2 = FRAC ? __ldg(a.Qc + j) : (VISC ? r.vsj.w : __ldg(&a.vs_cur[j].w));
+    }
+    if (VISC) r.uj = ldg4(a.ug_cur + j);
+    return r;
+}
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void p2_pair(const StepArgs<T> &a, P2Own<T, DIM> &o, const P2Rec<T> &r, bool on) {
+    const V4<T> &xi = o.xi, &ui = o.ui, &vsi = o.vsi;
+    const MatT<T> &m = o.m;
+    const bool frac = o.frac;
+    const T irho = o.irho, cvis = o.cvis;
+    T *s2 = o.s2, *s3 = o.s3, *Tl = o.Tl;
+    (void)ui;
+    (void)irho;
+    (void)cvis;
+    (void)m;
+    const V4<T> &xj = r.xj;
+    T d[DIM];
+    d[0] = xj.x - xi.x;
+    d[1] = xj.y - xi.y;
+    if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
+    const T r2 = pair_r2<T, DIM>(d);
+    const T t = pair_t(r2, a.inv2h);
+    const T w = on ? t * t * t : T(0);
+    const T Vj = DIM == 3 ? xj.w : xj.z;
+    const T aw = w * Vj;
+    T Qd[DIM];
+    const V4<T> &vsj = r.vsj;
+    if (DIM == 3) {
+        const V4<T> &q0 = r.q0, &q1 = r.q1;
+        const T q2 = r.q2;
+        Qd[0] = t_fma(q0.z, d[DIM - 1], t_fma(q0.y, d[1], q0.x * d[0]));
+        Qd[1] = t_fma(q1.y, d[DIM - 1], t_fma(q1.x, d[1], q0.w * d[0]));
+        Qd[DIM - 1] = t_fma(q2, d[DIM - 1], t_fma(q1.w, d[1], q1.z * d[0]));
+    } else {
+        const V4<T> &q0 = r.q0;
+        Qd[0] = t_fma(q0.y, d[1], q0.x * d[0]);
+        Qd[1] = t_fma(q0.w, d[1], q0.z * d[0]);
+    }
+#pragma unroll
+    for (int p = 0; p < DIM; p++) s2[p] = t_fma(aw, Qd[p], s2[p]);
+    if (VISC || frac) {
+        if (VISC) {
+            const V4<T> &uj = r.uj;
+            const T mj = DIM == 3 ? uj.w : xj.w;  // reference mass m0_j
+            T dv[DIM], dx[DIM];
+            dv[0] = vsj.x - vsi.x;
+            dv[1] = vsj.y - vsi.y;
+            dx[0] = d[0] + (uj.x - ui.x);
+            dx[1] = d[1] + (uj.y - ui.y);
+            if (DIM == 3) {
+                dv[DIM - 1] = vsj.z - vsi.z;
+                dx[DIM - 1] = d[DIM - 1] + (uj.z - ui.z);
+            }
+            T vx = t_fma(dv[1], dx[1], dv[0] * dx[0]);
+            T vX = t_fma(dv[1], d[1], dv[0] * d[0]);
+            if (DIM == 3) {
+                vx = t_fma(dv[DIM - 1], dx[DIM - 1], vx);
+                vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
+            }
+            if (on && vx < T(0)) {  // pair in relative compression
+                const T G = pair_div(a.h * vX, r2 + a.visc_eps);
+                const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
+                const T c = mj * pi * w;
+#pragma unroll
+                for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
+            }
+        }
+        if (frac) {
+            const T c = on ? (vsi.w - vsj.w) * aw / r2 : T(0);
+            const T c0 = c * d[0], c1 = c * d[1];
+            Tl[0] = t_fma(c0, d[0], Tl[0]);
+            Tl[1] = t_fma(c1, d[1], Tl[1]);
+            if (DIM == 3) {
+                Tl[2] = t_fma(c * d[2], d[2], Tl[2]);
+                Tl[3] = t_fma(c0, d[1], Tl[3]);
+                Tl[4] = t_fma(c0, d[2], Tl[4]);
+                Tl[5] = t_fma(c1, d[2], Tl[5]);
+            } else {
+                Tl[2] = t_fma(c0, d[1], Tl[2]);
+            }
+        }
+    }
+}
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2Own<T, DIM> &o, T &vmag, T &amag) {
     const int n = a.n;
     const int sp = a.spec[i];
+    const V4<T> &xi = o.xi, &vsi = o.vsi;
+    const MatT<T> &m = o.m;
+    const bool frac = o.frac;
+    const T irho = o.irho;
+    const T *s2 = o.s2, *s3 = o.s3, *Tl = o.Tl;
+    (void)Tl;
+    (void)frac;
+    T s1[DIM];
     {
-        const V4<T> xi = a.X0V[i];
-        const V4<T> ui = a.ug_cur[i];
-        const V4<T> vsi = a.vs_cur[i];
-        const MatT<T> m = a.mats[a.mid[i]];
-        const bool frac = FRAC && m.fracture;
-        const T irho = T(1) / m.rho;
-        const T cvis = m.beta1 * m.c0;
-        T s1[DIM], s2[DIM], s3[DIM], Tl[DIM == 3 ? 6 : 3];
-        {
-            const V4<T> m1 = a.S1[i];  // sum_j V_j w d, fixed in the reference configuration
-            s1[0] = m1.x;
-            s1[1] = m1.y;
-            if (DIM == 3) s1[DIM - 1] = m1.z;
-        }
-#pragma unroll
-        for (int p = 0; p < DIM; p++) s2[p] = s3[p] = T(0);
-#pragma unroll
-        for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) Tl[p] = T(0);
-        for_each_neighbour<4>(a, i, [&](const int j, const bool on) {
-            const V4<T> xj = ldg4(a.X0V + j);
-            T d[DIM];
-            d[0] = xj.x - xi.x;
-            d[1] = xj.y - xi.y;
-            if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
-            const T r2 = pair_r2<T, DIM>(d);
-            const T t = pair_t(r2, a.inv2h);
-            const T w = on ? t * t * t : T(0);
-            const T Vj = DIM == 3 ? xj.w : xj.z;
-            const T aw = w * Vj;
-            T Qd[DIM];
-            // the neighbour's velocity record (its fourth component is s, or q22 without phase field)
-            V4<T> vsj = V4<T>{T(0), T(0), T(0), T(0)};
-            if (VISC || FRAC) vsj = ldg4(a.vs_cur + j);
-            if (DIM == 3) {
-                const V4<T> q0 = ldg4(a.Qa + j), q1 = ldg4(a.Qb + j);
-                const T q2 = FRAC ? __ldg(a.Qc + j) : (VISC ? vsj.w : __ldg(&a.vs_cur[j].w));
-                Qd[0] = t_fma(q0.z, d[DIM - 1], t_fma(q0.y, d[1], q0.x * d[0]));
-                Qd[1] = t_fma(q1.y, d[DIM - 1], t_fma(q1.x, d[1], q0.w * d[0]));
-                Qd[DIM - 1] = t_fma(q2, d[DIM - 1], t_fma(q1.w, d[1], q1.z * d[0]));
-            } else {
-                const V4<T> q0 = ldg4(a.Qa + j);
-                Qd[0] = t_fma(q0.y, d[1], q0.x * d[0]);
-                Qd[1] = t_fma(q0.w, d[1], q0.z * d[0]);
-            }
-#pragma unroll
-            for (int p = 0; p < DIM; p++) s2[p] = t_fma(aw, Qd[p], s2[p]);
-            if (VISC || frac) {
-                if (VISC) {
-                    const V4<T> uj = ldg4(a.ug_cur + j);
-                    const T mj = DIM == 3 ? uj.w : xj.w;  // reference mass m0_j
-                    T dv[DIM], dx[DIM];
-                    dv[0] = vsj.x - vsi.x;
-                    dv[1] = vsj.y - vsi.y;
-                    dx[0] = d[0] + (uj.x - ui.x);
-                    dx[1] = d[1] + (uj.y - ui.y);
-                    if (DIM == 3) {
-                        dv[DIM - 1] = vsj.z - vsi.z;
-                        dx[DIM - 1] = d[DIM - 1] + (uj.z - ui.z);
-                    }
-                    T vx = t_fma(dv[1], dx[1], dv[0] * dx[0]);
-                    T vX = t_fma(dv[1], d[1], dv[0] * d[0]);
-                    if (DIM == 3) {
-                        vx = t_fma(dv[DIM - 1], dx[DIM - 1], vx);
-                        vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
-                    }
-                    if (on && vx < T(0)) {  // pair in relative compression
-                        const T G = pair_div(a.h * vX, r2 + a.visc_eps);
-                        const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
-                        const T c = mj * pi * w;
-#pragma unroll
-                        for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
-                    }
-                }
-                if (frac) {
-                    const T c = on ? (vsi.w - vsj.w) * aw / r2 : T(0);
-                    const T c0 = c * d[0], c1 = c * d[1];
-                    Tl[0] = t_fma(c0, d[0], Tl[0]);
-                    Tl[1] = t_fma(c1, d[1], Tl[1]);
-                    if (DIM == 3) {
-                        Tl[2] = t_fma(c * d[2], d[2], Tl[2]);
-                        Tl[3] = t_fma(c0, d[1], Tl[3]);
-                        Tl[4] = t_fma(c0, d[2], Tl[4]);
-                        Tl[5] = t_fma(c1, d[2], Tl[5]);
-                    } else {
-                        Tl[2] = t_fma(c0, d[1], Tl[2]);
-                    }
-                }
-            }
-        });
-        // own matrices
-        T Qi[DIM][DIM];
-        if (DIM == 3) {
-            const V4<T> q0 = a.Qa[i], q1 = a.Qb[i];
-            Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
-            Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
-            Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = FRAC ? a.Qc[i] : vsi.w;
-        } else {
-            const V4<T> q0 = a.Qa[i];
-            Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
-        }
-        T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int p = 0; p < DIM; p++) {
-            T f = s2[p];
-#pragma unroll
-            for (int q = 0; q < DIM; q++) f = t_fma(Qi[p][q], s1[q], f);
-            acc[p] = f * irho;
-            if (VISC) {
-                T v = T(0);
-#pragma unroll
-                for (int q = 0; q < DIM; q++) v = t_fma(a.Vm[(p * DIM + q) * n + i], s3[q], v);
-                acc[p] -= v;
-            }
-            acc[p] += a.grav[p];
-            if (a.accc) acc[p] += a.accc[p * n + i];
-        }
-        // forces act at t_n (Algorithm 1) or t_{n+1/2} (Algorithm 2); velocity BCs hold at t_{n+1}
-        const double dt = a.dt[sp], t_1 = a.t[sp] + dt, t_n = a.t[sp] + (a.leap ? 0.5 * dt : 0.0);
-        const int g = a.bcgrp[i];
-        const T mass = DIM == 3 ? m.rho * xi.w : xi.w;
-        double vset[3];
-        int vmask = 0;
-        if (g) {
-            for (int b = 0; b < kMaxBcPerParticle; b++) {
-                const int id = a.grp_bcs[4 * g + b];
-                if (id < 0) break;
-                const BCDev bc = a.bcs[id];
-                if (bc.kind == 0) {  // velocity: value at t_{n+1}
-                    const double f = bc_factor(bc, t_1);
-                    if (f < 0.0) continue;
-                    for (int p = 0; p < DIM; p++) {
-                        double val;
-                        if ((bc.comp_mask & (1 << p)) && dev_bc_value(a, bc, i, b, 0, p, f, val)) {
-                            vset[p] = val;
-                            vmask |= 1 << p;
-                        }
-                    }
-                } else {  // forces at t_n
-                    const double f = bc_factor(bc, t_n);
-                    if (f < 0.0) continue;
-                    for (int p = 0; p < DIM; p++) {
-                        double val;
-                        if (!(bc.comp_mask & (1 << p)) || !dev_bc_value(a, bc, i, b, 0, p, f, val)) continue;
-                        if (bc.kind == 1) acc[p] += (T)(val * bc.area / (double)mass);
-                        else if (bc.kind == 2) acc[p] += (T)val;
-                        else acc[p] += (T)(val * bc.inv_count / (double)mass);
-                    }
-                }
-            }
-        }
-        // phase field (eq. phasefieldddot)
-        T s_new = FRAC ? vsi.w : T(1);
-        if (frac) {
-            T A[3][3];
-            load_ahat<T, DIM>(a.Ahat, n, i, A);
-            T AT;
-            if (DIM == 3)
-                AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + A[2][2] * Tl[2] +
-                     T(2) * (A[0][1] * Tl[3] + A[0][2] * Tl[4] + A[1][2] * Tl[5]);
-            else
-                AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
-            const T lap = T(-2) * AT;
-            const T Hh = a.H[i], si = vsi.w, sd = a.sdot[i];
-            const T e0 = m.eps0, c2e = m.c0 * m.c0 / (T(2) * e0);
-            // eq. phasefieldddot with its local terms at the new time level:
-            // sdot_{n+1} = (sdot_n + dt r_n) / (1 + dt gamma + dt^2 k)
-            const T r = c2e * (T(2) * e0 * lap + (T(1) - si) / (T(2) * e0) - T(2) * si * Hh / m.Gc);
-            const T kk = c2e * (T(1) / (T(2) * e0) + T(2) * Hh / m.Gc);
-            const T gam = m.c0 / e0 * t_sqrt(T(4) * e0 * Hh / m.Gc + T(1));
-            const T dts = (T)dt;
-            const T sd_new = (sd + dts * r) / (T(1) + dts * gam + dts * dts * kk);
-            a.sdot[i] = sd_new;
-            // s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1), s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2)
-            s_new = t_min(T(1), t_max(T(0), si + (T)(a.leap ? 0.5 * dt : dt) * sd_new));
-        }
-        // update: v_{n+1} = v_n + dt a; u_{n+1} = u_n + dt v_{n+1} (Algorithm 1) or
-        // u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2, u64 holding u_{n+1/2})
-        const V4<T> vo = a.leap ? a.v_own[i] : vsi;
-        T vn[3] = {vo.x, vo.y, vo.z};
-        const T dtT = (T)dt;
-#pragma unroll
-        for (int p = 0; p < DIM; p++) {
-            vn[p] = vn[p] + dtT * acc[p];
-            if (vmask & (1 << p)) vn[p] = (T)vset[p];
-        }
-        double un[3];
-#pragma unroll
-        for (int p = 0; p < DIM; p++) {
-            un[p] = a.u64[p * n + i] + (a.leap ? 0.5 * dt : dt) * (double)vn[p];
-            a.u64[p * n + i] = un[p];
-        }
-        a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), DIM == 3 ? mass : T(0)};
-        a.vs_next[i] = V4<T>{vn[0], vn[1], DIM == 3 ? vn[DIM - 1] : T(0), s_new};
-        if (a.acc_out)
-#pragma unroll
-            for (int p = 0; p < DIM; p++) a.acc_out[p * n + i] = acc[p];
-        T vv = T(0), aa = T(0);
-#pragma unroll
-        for (int p = 0; p < DIM; p++) {
-            vv += vn[p] * vn[p];
-            aa += acc[p] * acc[p];
-        }
-        vmag = t_sqrt(vv);
-        amag = t_sqrt(aa);
-        if (!(finite_t(vmag) && finite_t(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
+        const V4<T> m1 = a.S1[i];  // sum_j V_j w d, fixed in the reference configuration
+        s1[0] = m1.x;
+        s1[1] = m1.y;
+        if (DIM == 3) s1[DIM - 1] = m1.z;
     }
+    // own matrices
+    T Qi[DIM][DIM];
+    if (DIM == 3) {
+        const V4<T> q0 = a.Qa[i], q1 = a.Qb[i];
+        Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
+        Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
+        Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = FRAC ? a.Qc[i] : vsi.w;
+    } else {
+        const V4<T> q0 = a.Qa[i];
+        Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
+    }
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int p = 0; p < DIM; p++) {
+        T f = s2[p];
+#pragma unroll
+        for (int q = 0; q < DIM; q++) f = t_fma(Qi[p][q], s1[q], f);
+        acc[p] = f * irho;
+        if (VISC) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < DIM; q++) v = t_fma(a.Vm[(p * DIM + q) * n + i], s3[q], v);
+            acc[p] -= v;
+        }
+        acc[p] += a.grav[p];
+        if (a.accc) acc[p] += a.accc[p * n + i];
+    }
+    // forces act at t_n (Algorithm 1) or t_{n+1/2} (Algorithm 2); velocity BCs hold at t_{n+1}
+    const double dt = a.dt[sp], t_1 = a.t[sp] + dt, t_n = a.t[sp] + (a.leap ? 0.5 * dt : 0.0);
+    const int g = a.bcgrp[i];
+    const T mass = DIM == 3 ? m.rho * xi.w : xi.w;
+    double vset[3];
+    int vmask = 0;
+    if (g) {
+        for (int b = 0; b < kMaxBcPerParticle; b++) {
+            const int id = a.grp_bcs[4 * g + b];
+            if (id < 0) break;
+            const BCDev bc = a.bcs[id];
+            if (bc.kind == 0) {  // velocity: value at t_{n+1}
+                const double f = bc_factor(bc, t_1);
+                if (f < 0.0) continue;
+                for (int p = 0; p < DIM; p++) {
+                    double val;
+                    if ((bc.comp_mask & (1 << p)) && dev_bc_value(a, bc, i, b, 0, p, f, val)) {
+                        vset[p] = val;
+                        vmask |= 1 << p;
+                    }
+                }
+            } else {  // forces at t_n
+                const double f = bc_factor(bc, t_n);
+                if (f < 0.0) continue;
+                for (int p = 0; p < DIM; p++) {
+                    double val;
+                    if (!(bc.comp_mask & (1 << p)) || !dev_bc_value(a, bc, i, b, 0, p, f, val)) continue;
+                    if (bc.kind == 1) acc[p] += (T)(val * bc.area / (double)mass);
+                    else if (bc.kind == 2) acc[p] += (T)val;
+                    else acc[p] += (T)(val * bc.inv_count / (double)mass);
+                }
+            }
+        }
+    }
+    // phase field (eq. phasefieldddot)
+    T s_new = FRAC ? vsi.w : T(1);
+    if (frac) {
+        T A[3][3];
+        load_ahat<T, DIM>(a.Ahat, n, i, A);
+        T AT;
+        if (DIM == 3)
+            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + A[2][2] * Tl[2] +
+                 T(2) * (A[0][1] * Tl[3] + A[0][2] * Tl[4] + A[1][2] * Tl[5]);
+        else
+            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
+        const T lap = T(-2) * AT;
+        const T Hh = a.H[i], si = vsi.w, sd = a.sdot[i];
+        const T e0 = m.eps0, c2e = m.c0 * m.c0 / (T(2) * e0);
+        // eq. phasefieldddot with its local terms at the new time level:
+        // sdot_{n+1} = (sdot_n + dt r_n) / (1 + dt gamma + dt^2 k)
+        const T r = c2e * (T(2) * e0 * lap + (T(1) - si) / (T(2) * e0) - T(2) * si * Hh / m.Gc);
+        const T kk = c2e * (T(1) / (T(2) * e0) + T(2) * Hh / m.Gc);
+        const T gam = m.c0 / e0 * t_sqrt(T(4) * e0 * Hh / m.Gc + T(1));
+        const T dts = (T)dt;
+        const T sd_new = (sd + dts * r) / (T(1) + dts * gam + dts * dts * kk);
+        a.sdot[i] = sd_new;
+        // s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1), s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2)
+        s_new = t_min(T(1), t_max(T(0), si + (T)(a.leap ? 0.5 * dt : dt) * sd_new));
+    }
+    // update: v_{n+1} = v_n + dt a; u_{n+1} = u_n + dt v_{n+1} (Algorithm 1) or
+    // u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2, u64 holding u_{n+1/2})
+    const V4<T> vo = a.leap ? a.v_own[i] : vsi;
+    T vn[3] = {vo.x, vo.y, vo.z};
+    const T dtT = (T)dt;
+#pragma unroll
+    for (int p = 0; p < DIM; p++) {
+        vn[p] = vn[p] + dtT * acc[p];
+        if (vmask & (1 << p)) vn[p] = (T)vset[p];
+    }
+    double un[3];
+#pragma unroll
+    for (int p = 0; p < DIM; p++) {
+        un[p] = a.u64[p * n + i] + (a.leap ? 0.5 * dt : dt) * (double)vn[p];
+        a.u64[p * n + i] = un[p];
+    }
+    a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), DIM == 3 ? mass : T(0)};
+    a.vs_next[i] = V4<T>{vn[0], vn[1], DIM == 3 ? vn[DIM - 1] : T(0), s_new};
+    if (a.acc_out)
+#pragma unroll
+        for (int p = 0; p < DIM; p++) a.acc_out[p * n + i] = acc[p];
+    T vv = T(0), aa = T(0);
+#pragma unroll
+    for (int p = 0; p < DIM; p++) {
+        vv += vn[p] * vn[p];
+        aa += acc[p] * acc[p];
+    }
+    vmag = t_sqrt(vv);
+    amag = t_sqrt(aa);
+    if (!(finite_t(vmag) && finite_t(amag))) atomicAdd(&a.flags[kFlagNonfinite], 1);
+}
+
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
+    P2Own<T, DIM> o;
+    p2_begin<T, DIM, FRAC>(a, i, o);
+    for_each_neighbour<4>(a, i, [&](const int j, const bool on) {
+        p2_pair<T, DIM, FRAC, VISC>(a, o, p2_load<T, DIM, FRAC, VISC>(a, j), on);
+    });
+    p2_finish<T, DIM, FRAC, VISC>(a, i, o, vmag, amag);
 }
 
 // Velocity boundary conditions of particle i at time t: the constrained components of v take the

@@ -23,6 +23,7 @@ CASES = {
     "taylor_bar": lambda a: W.taylor_bar(dx=a.dx or 0.4e-3),
 }
 MODES = {"launch": tlsph.MODE_LAUNCH, "graph": tlsph.MODE_GRAPH, "persistent": tlsph.MODE_PERSISTENT}
+LAYOUTS = {"auto": tlsph.LAYOUT_AUTO, "csr": tlsph.LAYOUT_CSR}
 
 
 def main(argv=None):
@@ -37,6 +38,7 @@ def main(argv=None):
     ap.add_argument("--dx", type=float)
     ap.add_argument("--model", choices=["nh", "svk"])
     ap.add_argument("--mode", choices=sorted(MODES), default="launch")
+    ap.add_argument("--layout", choices=sorted(LAYOUTS), default="auto")
     a = ap.parse_args(argv)
     import torch
 
@@ -44,6 +46,7 @@ def main(argv=None):
     stream = torch.cuda.Stream(device=0)
     g = tlsph.from_case(case, stream=stream.cuda_stream)
     g.set_option(tlsph.OPT_MODE, MODES[a.mode])
+    g.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, LAYOUTS[a.layout])
     g.step(a.warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -56,7 +59,8 @@ def main(argv=None):
     info = g.get_info()
     print(json.dumps({"case": case.name, "particles": case.n, "steps": a.steps, "ms_per_step": ms,
                       "particle_steps_per_s": case.n / (ms * 1e-3), "status": int(status),
-                      "kernel_launches": info["kernel_launches"], "neighbour_pairs": info["nnz"]}))
+                      "kernel_launches": info["kernel_launches"], "neighbour_pairs": info["nnz"],
+                      "layout": a.layout, "stencil_entries": info["stencil"]}))
     g.close()
     return 0 if status == tlsph.OK else 1
 

@@ -10,6 +10,9 @@ pytestmark = pytest.mark.gpu
 
 CASES = {
     "plate_fp64": lambda: W.plate_2d(),
+    "plate_odd_rows_fp32": lambda: W.plate_2d(nx=100, ny=21, precision="fp32"),
+    "block_j2_odd_planes": lambda: W.block_3d(nx=40, ny=9, nz=7),
+    "crack_branching": lambda: W.crack_branching(nx=120, ny=48),
     "block_j2": lambda: W.block_3d(nx=24, ny=20, nz=16),
     "notched_pf": lambda: W.notched_plate(nx=100, ny=40),
     "block_j2_fp64": lambda: W.block_3d(nx=16, ny=14, nz=12, precision="fp64"),
