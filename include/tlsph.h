@@ -414,7 +414,8 @@ tlsph_status tlsph_mlp_load(tlsph_mlp *mlp, const char *path);
  * context keeps its own copy; no network object stays alive). */
 tlsph_status tlsph_load_surrogate(tlsph_ctx *ctx, const char *path, int scope);
 /* Cumulative since tlsph_set_surrogate: counts[0] particle updates served by the network,
- * counts[1] J2 updates that fell outside the envelope (exact return map), counts[2] elastic
+ * counts[1] J2 updates served by the exact return map because they fell outside the envelope or
+ * because the network's C_p^-1 was not symmetric positive definite, counts[2] elastic
  * trial states kept exact under TLSPH_SURROGATE_PLASTIC. */
 tlsph_status tlsph_surrogate_counts(tlsph_ctx *ctx, int64_t counts[3]);
 /* Return-map samples of the current state without advancing it: every J2 particle is a

@@ -341,8 +341,10 @@ template <typename T> TL_HD M3<T> expm1_mat(const M3<T> &X) {
 }
 
 template <typename T> struct J2Tol;
+// FP32 stops when the bracket is two ulps wide: adjacent floats are up to 1.19e-7 apart relative to the
+// larger, so a narrower width could not be met when the residual's rounding stays above res sy0.
 template <> struct J2Tol<float> {
-    static constexpr float res = 1e-5f, width = 1e-7f;
+    static constexpr float res = 1e-5f, width = 2.5e-7f;
     static constexpr int maxit = 100;
 };
 template <> struct J2Tol<double> {

@@ -1005,9 +1005,12 @@ __device__ __forceinline__ bool sur_features(const StepArgs<float> &a, const Sur
 
 // Apply the network's outputs yn (normalised) to particle i: P = elastic predictor + correction,
 // C_p^-1 += F^-1 db F^-T with det C_p^-1 = 1 (eq. Fp_iso_proj), eps_p += max(0, increment), and
-// the pass-2 matrices.
+// the pass-2 matrices.  The outputs are kept only if the new C_p^-1 is symmetric positive definite
+// (leading minors of I + K positive) and the stress finite; otherwise nothing is written and the
+// function returns false, so that the exact update serves the particle (a metric that is not
+// positive definite would leave later return maps without a bracket).
 template <int DIM, bool FRAC>
-__device__ __forceinline__ void sur_apply(const StepArgs<float> &a, const SurrogateDev &s, int i, const M3<float> &G,
+__device__ __forceinline__ bool sur_apply(const StepArgs<float> &a, const SurrogateDev &s, int i, const M3<float> &G,
                                           const float yn[16]) {
     const int n = a.n;
     float yr[16];
@@ -1041,7 +1044,14 @@ __device__ __forceinline__ void sur_apply(const StepArgs<float> &a, const Surrog
     Kn.a[2] = Kn.a[6] = K6[4];
     Kn.a[5] = Kn.a[7] = K6[5];
     for (int q = 0; q < 9; q++) Kn.a[q] += dK.a[q];
-    const float fm1 = expm1f(-log1pf(det_eye_plus_m1(Kn)) / 3.0f);
+    const float dm1 = det_eye_plus_m1(Kn);
+    {
+        const float a00 = 1.0f + Kn.a[0], a11 = 1.0f + Kn.a[4];
+        bool ok = isfinite(dm1) && dm1 > -1.0f && a00 > 0.0f && a00 * a11 - Kn.a[1] * Kn.a[1] > 0.0f;
+        for (int q = 0; q < 9; q++) ok = ok && isfinite(P.a[q]) && isfinite(Kn.a[q]);
+        if (!ok) return false;
+    }
+    const float fm1 = expm1f(-log1pf(dm1) / 3.0f);
     for (int q = 0; q < 9; q++) Kn.a[q] = Kn.a[q] * (1.0f + fm1);
     a.K[0 * n + i] = Kn.a[0] + fm1;
     a.K[1 * n + i] = Kn.a[4] + fm1;
@@ -1051,6 +1061,7 @@ __device__ __forceinline__ void sur_apply(const StepArgs<float> &a, const Surrog
     a.K[5 * n + i] = Kn.a[5];
     a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
     dev_write_qvm_fi<float, DIM, FRAC>(a, i, Fi, P, 1.0f + kin.Jm1);
+    return true;
 }
 
 __device__ __forceinline__ void sur_count(unsigned long long *counters, int n_mlp, int n_out, int n_el) {
@@ -1099,8 +1110,12 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
         if (__syncthreads_or(use)) {  // block-uniform
             mlp_forward_block(sm);
             if (use) {
-                sur_apply<DIM, FRAC>(a, s, i, G, sm.Y[threadIdx.x]);
-                n_mlp++;
+                if (sur_apply<DIM, FRAC>(a, s, i, G, sm.Y[threadIdx.x])) {
+                    n_mlp++;
+                } else {  // rejected output: the exact update serves the particle
+                    exact[i] = 1;
+                    n_out++;
+                }
             }
         }
         __syncthreads();
@@ -1146,8 +1161,12 @@ __global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<f
                 break;
             }
             if (use) {
-                sur_apply<DIM, FRAC>(a, s, i, G, yn);
-                n_mlp++;
+                if (sur_apply<DIM, FRAC>(a, s, i, G, yn)) {
+                    n_mlp++;
+                } else {  // rejected output: the exact update serves the particle
+                    exact[i] = 1;
+                    n_out++;
+                }
             }
         }
     }
