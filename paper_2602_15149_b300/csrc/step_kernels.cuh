@@ -492,7 +492,16 @@ __device__ __forceinline__ void p2_pair(const StepArgs<T> &a, P2Own<T, DIM> &o, 
                 vx = t_fma(dv[DIM - 1], dx[DIM - 1], vx);
                 vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
             }
-            if (on && vx < T(0)) {  // pair in relative compression
+            if (DIM == 3) {
+                // computed for every pair and kept for pairs in relative compression (the others add
+                // exact zeros), so the entries of a run form one block without branches (measured
+                // faster in 3D; the 2D pass keeps the branch, which is faster there)
+                const T G = pair_div(a.h * vX, r2 + a.visc_eps);
+                const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
+                const T c = on && vx < T(0) ? mj * pi * w : T(0);
+#pragma unroll
+                for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
+            } else if (on && vx < T(0)) {  // pair in relative compression
                 const T G = pair_div(a.h * vX, r2 + a.visc_eps);
                 const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
                 const T c = mj * pi * w;
