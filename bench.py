@@ -208,6 +208,19 @@ def oracle_sample(seconds=15.0, shape=(32, 32, 16)):
                       f"after 1 warm-up step ({el:.1f} s), FP64 OpenMP"}
 
 
+def oracle_sample_one_thread(seconds=8.0, shape=(32, 32, 16)):
+    """oracle_sample on one host thread (a child process with OMP_NUM_THREADS=1, since the OpenMP
+    runtime of this process already holds its thread count); None if the child fails."""
+    code = ("import json, bench; r = bench.oracle_sample(%r, %r); print(json.dumps(r))" % (seconds, tuple(shape)))
+    env = {**os.environ, "OMP_NUM_THREADS": "1"}
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=seconds * 10 + 120)
+        return json.loads(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle (the method as plainly written) on the host cores.
     Its step is one time step of a bounded sample of the workload: the same lattice recipe,
@@ -619,6 +632,10 @@ def run_ours(args):
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
+    if cpu is not None:  # the same sample on one host thread, beside the all-cores figure
+        one = oracle_sample_one_thread()
+        if one is not None:
+            cpu["one_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
