@@ -665,7 +665,8 @@ template <typename T, int DIM, bool FRAC, bool VISC>
 __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
     P2Own<T, DIM> o;
     p2_begin<T, DIM, FRAC>(a, i, o);
-    for_each_neighbour<4>(a, i, [&](const int j, const bool on) {
+    // entry by entry, four at a time across runs (measured faster than the unrolled runs, as in k_gradient)
+    for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
         p2_pair<T, DIM, FRAC, VISC>(a, o, p2_load<T, DIM, FRAC, VISC>(a, j), on);
     });
     p2_finish<T, DIM, FRAC, VISC>(a, i, o, vmag, amag);
