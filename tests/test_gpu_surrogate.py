@@ -137,6 +137,30 @@ def test_fallback_outside_envelope_is_the_exact_step(torch):
     assert used == 0 and fallback == 120 * case.n and elastic == 0
 
 
+@pytest.mark.parametrize("path", [tlsph.TENSOR_TCGEN05, tlsph.TENSOR_MMA_SYNC])
+def test_indefinite_network_state_is_refused(torch, path):
+    """A network whose b_e correction is -10 I would leave C_p^-1 indefinite: every output is refused,
+    nothing of it is written, and the exact return map serves the particle, so the run is the exact
+    one bit for bit and all updates count as served exactly."""
+    case = W.block_3d(nx=14, ny=12, nz=9)
+    exact = tlsph.from_case(case)
+    exact.step(60)
+    net = tlsph.MLP(batch=256)
+    net.set_params(tlsph.pack_params(ref.init_params(seed=2)))
+    net.set_tensor_path(path)
+    norm = identity_norm()  # out = out_mean + out_std * network
+    norm[48 + 9:48 + 12] = 1e-30  # (a std must be positive)
+    norm[32 + 9:32 + 12] = -10.0  # db = -10 I whatever the network says
+    net.set_normalization(norm)
+    g = tlsph.from_case(case)
+    g.set_surrogate(net)
+    g.step(60)
+    assert np.array_equal(g.read_state("U"), exact.read_state("U"))
+    assert np.array_equal(g.read_state("EPSP"), exact.read_state("EPSP"))
+    used, fallback, elastic = g.surrogate_counts()
+    assert used == 0 and fallback == 60 * case.n and elastic == 0
+
+
 @pytest.mark.parametrize("scope,path", [(tlsph.SURROGATE_ALL, tlsph.TENSOR_TCGEN05),
                                         (tlsph.SURROGATE_PLASTIC, tlsph.TENSOR_TCGEN05),
                                         (tlsph.SURROGATE_ALL, tlsph.TENSOR_MMA_SYNC)])
