@@ -1074,6 +1074,35 @@ __device__ __forceinline__ bool sur_apply(const StepArgs<float> &a, const Surrog
     return true;
 }
 
+// The surrogate inputs of the tile of 128 particles starting at particle base (G, C_p^-1 - I, eps_p and
+// material ids) into L2 by the TMA unit while the current tile runs through the network: thread r of the
+// tile's threads issues one bulk prefetch for one array, over the whole 16-byte units of the tile's slice
+// (aligned, and inside the array).  A hint only: nothing depends on it.
+template <int DIM>
+__device__ __forceinline__ void sur_prefetch_tile(const StepArgs<float> &a, int base, int r) {
+    const int n = a.n;
+    if (base >= n) return;
+    const int cnt = min(128, n - base);
+    const int na = DIM * DIM + 6;
+    const char *lo = nullptr, *hi = nullptr;
+    if (r < na) {
+        const float *arr = r < DIM * DIM ? a.G + (int64_t)r * n : a.K + (int64_t)(r - DIM * DIM) * n;
+        lo = reinterpret_cast<const char *>(arr + base);
+        hi = reinterpret_cast<const char *>(arr + base + cnt);
+    } else if (r == na) {
+        lo = reinterpret_cast<const char *>(a.ep + base);
+        hi = reinterpret_cast<const char *>(a.ep + base + cnt);
+    } else if (r == na + 1) {
+        lo = reinterpret_cast<const char *>(a.mid + base);
+        hi = reinterpret_cast<const char *>(a.mid + base + cnt);
+    } else {
+        return;
+    }
+    const uintptr_t a0 = (reinterpret_cast<uintptr_t>(lo) + 15) & ~(uintptr_t)15;
+    const uintptr_t a1 = reinterpret_cast<uintptr_t>(hi) & ~(uintptr_t)15;
+    if (a1 > a0) prefetch_l2_bulk(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
+}
+
 __device__ __forceinline__ void sur_count(unsigned long long *counters, int n_mlp, int n_out, int n_el) {
     for (int o = 16; o > 0; o >>= 1) {
         n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
@@ -1107,6 +1136,7 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i = tile * 128 + threadIdx.x;
         const bool active = i < n;
+        sur_prefetch_tile<DIM>(a, (tile + gridDim.x) * 128, threadIdx.x);
         bool use = false;
         float xn[16];
         M3<float> G = m3_zero<float>();
@@ -1151,6 +1181,7 @@ __global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<f
     for (int tile = blockIdx.x * kTcGroups + g; tile < ntiles; tile += gridDim.x * kTcGroups) {
         const int i = tile * 128 + r;
         const bool active = i < n;
+        sur_prefetch_tile<DIM>(a, (tile + gridDim.x * kTcGroups) * 128, r);
         bool use = false;
         float xn[16];
         M3<float> G = m3_zero<float>();
