@@ -117,6 +117,7 @@ typedef struct orc_ctx {
     int contact;
     double kc, dc;
     double *rest;
+    double *kfric;  /* per body <kfric>, or NULL (no friction) */
     double *accc;
 } orc_ctx;
 
@@ -510,7 +511,7 @@ orc_ctx *orc_create(const orc_params *p) {
 }
 
 static void free_particles(orc_ctx *c) {
-    free(c->rest); free(c->accc);
+    free(c->rest); free(c->accc); free(c->kfric);
     free(c->X0); free(c->vol); free(c->u); free(c->v); free(c->acc); free(c->s); free(c->sdot);
     free(c->sdd); free(c->lap); free(c->pf_b); free(c->pf_k); free(c->pf_g); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
     free(c->P); free(c->L); free(c->status); free(c->row_ptr); free(c->col); free(c->perm);
@@ -1019,10 +1020,18 @@ static double bc_factor(const orc_bc *b, double t) {
 /*   F_i = (k delta - c (v_i - v_j).n) n,                                 */
 /* for which a head-on pair leaves with relative speed e times the one  */
 /* it came with (the damped oscillator's half period).                  */
+/* Friction (<kfric>, also unstated; reading): Coulomb's law, the       */
+/* tangential force opposing the sliding velocity v_t = v_ij - v_n n     */
+/* with magnitude mu max(f_n, 0) while sliding, regularised near rest    */
+/* by a viscous bound c_t |v_t| with c_t = 2 sqrt(k m*) (the critical    */
+/* damping of the normal spring), so that an explicit step does not     */
+/* chatter around v_t = 0:                                              */
+/*   F_i = f_n n - min(mu max(f_n, 0), c_t |v_t|) v_t / |v_t|,            */
+/* mu = (mu_i + mu_j) / 2.                                               */
 /* ------------------------------------------------------------------ */
 int orc_contact_force(int dim, double dc, double kc, const double *xi, const double *xj, const double *vi,
                       const double *vj, double mi, double mj, double cinv_i, double cinv_j, double ei, double ej,
-                      double *F) {
+                      double mu, double *F) {
     double d[3] = {0, 0, 0}, r2 = 0.0;
     F[0] = F[1] = F[2] = 0.0;
     for (int k = 0; k < dim; k++) {
@@ -1044,6 +1053,18 @@ int orc_contact_force(int dim, double dc, double kc, const double *xi, const dou
     for (int k = 0; k < dim; k++) vn += (vi[k] - vj[k]) * d[k] / r;
     double f = kn * (dc - r) - cd * vn;
     for (int k = 0; k < dim; k++) F[k] = f * d[k] / r;
+    if (mu > 0.0 && f > 0.0) {
+        double vt[3] = {0, 0, 0}, vt2 = 0.0;
+        for (int k = 0; k < dim; k++) {
+            vt[k] = (vi[k] - vj[k]) - vn * d[k] / r;
+            vt2 += vt[k] * vt[k];
+        }
+        if (vt2 > 0.0) {
+            double vtm = sqrt(vt2);
+            double ft = fmin(mu * f, 2.0 * sqrt(kn * ms) * vtm);
+            for (int k = 0; k < dim; k++) F[k] -= ft * vt[k] / vtm;
+        }
+    }
     return 1;
 }
 
@@ -1064,8 +1085,9 @@ static void contact_accel(orc_ctx *c) {
             double xj[3], F[3];
             for (int k = 0; k < 3; k++) xj[k] = c->X0[3 * j + k] + c->u[3 * j + k];
             const orc_material *mj = &c->mat[c->mid[j]];
+            const double mu = c->kfric ? 0.5 * (c->kfric[c->spec[i]] + c->kfric[c->spec[j]]) : 0.0;
             if (orc_contact_force(d, c->dc, c->kc, xi, xj, &c->v[3 * i], &c->v[3 * j], massi, mj->rho * c->vol[j],
-                                  mat_cinv(mi), mat_cinv(mj), c->rest[c->spec[i]], c->rest[c->spec[j]], F))
+                                  mat_cinv(mi), mat_cinv(mj), c->rest[c->spec[i]], c->rest[c->spec[j]], mu, F))
                 for (int k = 0; k < d; k++) a[k] += F[k] / massi;
         }
         for (int k = 0; k < 3; k++) c->accc[3 * i + k] = a[k];
@@ -1088,6 +1110,17 @@ int orc_set_contact(orc_ctx *c, double kc, double dc, int nspec, const double *r
     c->dc = dc;
     c->contact = 1;
     c->built = 0;
+    return ORC_OK;
+}
+
+/* Friction coefficients <kfric> per body (after orc_set_contact; all 0 = no friction). */
+int orc_set_contact_friction(orc_ctx *c, int nspec, const double *kfric) {
+    if (!c || !c->contact || nspec != c->nspec || !kfric) return ORC_ERR_ARG;
+    for (int s = 0; s < nspec; s++)
+        if (!(kfric[s] >= 0.0 && isfinite(kfric[s]))) return ORC_ERR_ARG;
+    free(c->kfric);
+    c->kfric = (double *)malloc(sizeof(double) * nspec);
+    memcpy(c->kfric, kfric, sizeof(double) * nspec);
     return ORC_OK;
 }
 

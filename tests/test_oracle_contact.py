@@ -62,6 +62,89 @@ def test_head_on_pair_restitution_and_duration(e):
     assert abs(m1 * v1[0] + m2 * v2[0] - m1 * v0) < 1e-12 * m1 * v0
 
 
+# ---------------------------------------------------------------- friction (<kfric>)
+def _split(F, d):
+    n = d / np.linalg.norm(d)
+    fn = F @ n
+    return fn, F - fn * n
+
+
+@pytest.mark.parametrize("mu", [0.1, 0.6])
+def test_friction_is_tangential_bounded_dissipative_and_reciprocal(mu):
+    """Coulomb's law in every contact: the friction changes only the tangential part of the pair force, its
+    size never exceeds mu times the compressive normal force, it opposes the sliding velocity, there is none
+    while the pair pulls apart under tension, and j feels the opposite force."""
+    rng = np.random.default_rng(7)
+    seen_sliding = seen_tension = 0
+    for _ in range(400):
+        xi, xj = rng.uniform(0, 1e-2, 2), rng.uniform(0, 1e-2, 2)
+        vi, vj = rng.normal(size=2) * rng.choice([1e-4, 1.0, 30.0]), rng.normal(size=2)
+        d = xi - xj
+        if np.linalg.norm(d) >= 1e-2:
+            continue
+        F0 = contact_force(2, 1e-2, 5.0, xi, xj, vi, vj, 0.5, 0.7, STEEL, SOFT, 0.9, 0.6)
+        F = contact_force(2, 1e-2, 5.0, xi, xj, vi, vj, 0.5, 0.7, STEEL, SOFT, 0.9, 0.6, mu=mu)
+        Fji = contact_force(2, 1e-2, 5.0, xj, xi, vj, vi, 0.7, 0.5, SOFT, STEEL, 0.6, 0.9, mu=mu)
+        assert np.allclose(F, -Fji, rtol=1e-13, atol=1e-300)
+        fn0, ft0 = _split(F0, d)
+        fn, ft = _split(F, d)
+        scale = abs(fn0) + np.linalg.norm(F)
+        assert abs(fn - fn0) <= 1e-12 * scale and np.linalg.norm(ft0) <= 1e-12 * scale
+        vt = (vi - vj) - ((vi - vj) @ d) * d / (d @ d)
+        if fn0 <= 0:
+            seen_tension += 1
+            assert np.linalg.norm(ft) <= 1e-12 * scale
+            continue
+        assert np.linalg.norm(ft) <= mu * fn0 * (1 + 1e-12)
+        assert ft @ vt <= 0
+        assert abs(ft[0] * vt[1] - ft[1] * vt[0]) <= 1e-9 * np.linalg.norm(ft) * np.linalg.norm(vt)
+        seen_sliding += np.linalg.norm(ft) >= mu * fn0 * (1 - 1e-12)
+    assert seen_sliding > 20 and seen_tension >= 3
+
+
+def test_friction_is_coulomb_when_sliding_and_vanishes_at_rest():
+    """A pair pressed together (no normal motion) and sliding fast feels exactly mu f_n; as the sliding speed
+    goes to zero the friction goes to zero in proportion to it (no jump for an explicit step to chatter on).
+    The crossover speed is mu delta w / 2 (about 0.07 m/s for this soft pair at 1% overlap)."""
+    dc, kc, mu = 1e-2, 5.0, 0.4
+    xi, xj = np.array([0.0, 0.0]), np.array([0.99 * dc, 0.0])
+    fn = -contact_force(2, dc, kc, xi, xj, np.zeros(2), np.zeros(2), 0.5, 0.5, SOFT, SOFT, 1.0, 1.0)[0]
+    assert fn > 0
+    for vt in (5.0, 50.0):
+        F = contact_force(2, dc, kc, xi, xj, np.array([0.0, vt]), np.zeros(2), 0.5, 0.5, SOFT, SOFT, 1.0, 1.0, mu)
+        assert abs(F[1] + mu * fn) <= 1e-12 * mu * fn
+        assert abs(-F[0] - fn) <= 1e-12 * fn
+    r = [contact_force(2, dc, kc, xi, xj, np.array([0.0, v]), np.zeros(2), 0.5, 0.5, SOFT, SOFT, 1.0, 1.0, mu)[1] / v
+         for v in (1e-9, 1e-8, 1e-7)]
+    assert r[0] < 0 and abs(r[1] / r[0] - 1) < 1e-9 and abs(r[2] / r[0] - 1) < 1e-9
+
+
+def test_sliding_pair_stops_as_coulomb_predicts():
+    """A particle pressed onto another by a constant load and sliding at v0 decelerates at mu f_n / m*
+    (Coulomb) and never slides back: it stops after about m* v0 / (mu f_n).  Soft pair at 1% overlap, whose
+    crossover speed (0.05 m/s) is 1% of v0, with w dt = 0.025 as the solver's Courant number gives."""
+    dc, kc, mu, m1, m2, v0 = 1e-2, 5.0, 0.3, 0.8, 0.4, 5.0
+    ms = m1 * m2 / (m1 + m2)
+    x1, x2 = np.array([0.0, 0.0]), np.array([0.99 * dc, 0.0])
+    fn = -contact_force(2, dc, kc, x1, x2, np.zeros(2), np.zeros(2), m1, m2, SOFT, SOFT, 1.0, 1.0)[0]
+    k = fn / (0.01 * dc)
+    t_stop = ms * v0 / (mu * fn)
+    dt = 0.025 / math.sqrt(k / ms)
+    v1, v2 = np.array([0.0, v0]), np.zeros(2)
+    t, t_end, vrel = 0.0, None, []
+    for _ in range(int(1.2 * t_stop / dt)):
+        F = contact_force(2, dc, kc, x1, x2, v1, v2, m1, m2, SOFT, SOFT, 1.0, 1.0, mu)
+        F[0] = 0.0  # the normal load is held (the pair stays pressed at the same overlap)
+        v1 = v1 + dt * F / m1
+        v2 = v2 - dt * F / m2
+        t += dt
+        vrel.append(v1[1] - v2[1])
+        if t_end is None and vrel[-1] <= 1e-3 * v0:
+            t_end = t
+    assert t_end is not None and abs(t_end - t_stop) < 0.03 * t_stop
+    assert min(vrel) >= -1e-9 * v0 and abs(vrel[-1]) < 1e-6 * v0
+
+
 def _plates(e, v=1.0, n=8, model="nh", beta1=None):
     """Two touching 8 x 8 plates (closest rows one spacing apart, the contact distance) closing at 2 v.  The
     contact spring's w dt is about 0.15 at C_CFL = 0.05."""
