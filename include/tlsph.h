@@ -188,10 +188,19 @@ tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int com
  *   F_i = (k delta - 2 zeta sqrt(k m*) (v_i - v_j).n) n,  delta = dc - r,  n = (x_i - x_j)/r,
  *   k = contcoeff E* dc^(dim-2),  1/E* = (1 - nu_i^2)/E_i + (1 - nu_j^2)/E_j,  m* = m_i m_j/(m_i + m_j),
  *   zeta = -ln e / sqrt(pi^2 + ln^2 e),  e = (e_i + e_j)/2 (restitution[body], in (0, 1]),
- * under which a head-on pair separates with e times its approach speed; no friction.  Pairs are found
+ * under which a head-on pair separates with e times its approach speed (friction: tlsph_set_contact_friction).
+ * Pairs are found
  * every step in the current configuration (FP64 positions).  Must come after tlsph_create_particles and
  * before tlsph_build_ref_neighbours; nbodies = the number of specimens.  Not with TLSPH_MODE_PERSISTENT. */
 tlsph_status tlsph_set_contact(tlsph_ctx *ctx, double contcoeff, int nbodies, const double *restitution);
+/* Friction between bodies (<kfric> of Sec. 3.3, default 0 = none), one coefficient per body (>= 0, finite).
+ * The paper does not state its friction law either; the one built is Coulomb's, regularised near rest by
+ * the critical damping of the normal spring: each contact pair pressed together (f_n = k delta - c v_n > 0)
+ * also feels  -min(mu f_n, 2 sqrt(k m*) |v_t|) v_t/|v_t|,  v_t = (v_i - v_j) - ((v_i - v_j).n) n,
+ * mu = (mu_i + mu_j)/2: exactly mu f_n while sliding faster than mu f_n / (2 sqrt(k m*)), and proportional
+ * to the sliding speed below it (no jump at rest for the explicit step).  After tlsph_set_contact and
+ * before tlsph_build_ref_neighbours; TLSPH_ERR_STATE without contact, TLSPH_ERR_ARG for a bad count or value. */
+tlsph_status tlsph_set_contact_friction(tlsph_ctx *ctx, int nbodies, const double *kfric);
 
 /* ---- User-defined expressions (Sec. 3.3, user-defined expressions; the tables of built-in variables,
  * functions and operators).

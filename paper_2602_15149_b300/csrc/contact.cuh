@@ -6,6 +6,9 @@
 //   delta = dc - r,  n = (x_i - x_j) / r,  k = kc E* dc^(dim - 2),  1/E* = (1 - nu_i^2)/E_i + (1 - nu_j^2)/E_j,
 //   m* = m_i m_j / (m_i + m_j),  e = (e_i + e_j) / 2,  zeta = -ln e / sqrt(pi^2 + ln^2 e),
 //   F_i = (k delta - 2 zeta sqrt(k m*) (v_i - v_j).n) n.
+// With friction coefficients per body (<kfric>), Coulomb friction regularised near rest by the critical
+// damping of the normal spring, c_t = 2 sqrt(k m*): the force gains -min(mu max(f_n, 0), c_t |v_t|) v_t/|v_t|,
+// v_t = v_ij - (v_ij.n) n the sliding velocity and mu = (mu_i + mu_j) / 2.
 //
 // The pairs are found every step in the current configuration (FP64 positions X0 + u) on a spatial hash
 // of cells of size dc: count the particles per bucket, scan, fill the bucket lists, sort each list by
@@ -123,7 +126,7 @@ __global__ void k_contact_sort(int tsize, const int *hcount, const int *hstart, 
 // Contact acceleration of every particle from the current u and v (the step's level).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0d, double dc, double kc,
-                                                 const double *rest, int tsize, const int *hcount,
+                                                 const double *rest, const double *kfric, int tsize, const int *hcount,
                                                  const int *hstart, const int *hlist, const int4 *hcell, T *accc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -180,8 +183,26 @@ __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0
 #pragma unroll
                     for (int k = 0; k < DIM; k++) vn += (vi[k] - vj[k]) * d[k] / r;
                     const double f = kn * (dc - r) - 2.0 * zeta * sqrt(kn * ms) * vn;
+                    double F[3];
 #pragma unroll
-                    for (int k = 0; k < DIM; k++) acc[k] += f * d[k] / r / massi;
+                    for (int k = 0; k < DIM; k++) F[k] = f * d[k] / r;
+                    const double mu = kfric ? 0.5 * (kfric[si] + kfric[a.spec[j]]) : 0.0;
+                    if (mu > 0.0 && f > 0.0) {  // friction (only while the pair is pressed together)
+                        double vt[3], vt2 = 0.0;
+#pragma unroll
+                        for (int k = 0; k < DIM; k++) {
+                            vt[k] = (vi[k] - vj[k]) - vn * d[k] / r;
+                            vt2 += vt[k] * vt[k];
+                        }
+                        if (vt2 > 0.0) {
+                            const double vtm = sqrt(vt2);
+                            const double ft = fmin(mu * f, 2.0 * sqrt(kn * ms) * vtm);
+#pragma unroll
+                            for (int k = 0; k < DIM; k++) F[k] -= ft * vt[k] / vtm;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < DIM; k++) acc[k] += F[k] / massi;
                 }
             }
 #pragma unroll

@@ -119,6 +119,8 @@ struct tlsph_ctx {
     double kc = 0.0;
     std::vector<double> resth;
     double *rest = nullptr;
+    std::vector<double> kfrich;   // friction coefficient per body (empty = none)
+    double *kfric = nullptr;
     int tsize = 0;
     int *hcount = nullptr, *hstart = nullptr, *hbucket = nullptr, *hslot = nullptr, *hlist = nullptr, *hbsum = nullptr;
     int4 *hcell = nullptr;
@@ -232,6 +234,7 @@ void free_device(tlsph_ctx *c) {
     c->alloc_bytes.clear();
     c->mem_used = 0;
     c->rest = nullptr;
+    c->kfric = nullptr;
     c->hcount = c->hstart = c->hbucket = c->hslot = c->hlist = c->hbsum = nullptr;
     c->hcell = nullptr;
     c->accc = nullptr;
@@ -944,6 +947,10 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
         DA(c->accc, dim * n * sizeof(T));
         CK(cudaMemcpyAsync(c->rest, c->resth.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(c->accc, 0, dim * n * sizeof(T), s));
+        if (!c->kfrich.empty()) {
+            DA(c->kfric, ns_ * sizeof(double));
+            CK(cudaMemcpyAsync(c->kfric, c->kfrich.data(), ns_ * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
     }
     // first moment of the corrected kernel (reference configuration)
     DA(c->S1, n * sizeof(V4<T>));
@@ -1047,8 +1054,8 @@ template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const
     CKL();
     k_contact_sort<<<blocks_for(ts, 128), 128, 0, s>>>(ts, c->hcount, c->hstart, c->hlist);
     CKL();
-    k_contact<T, DIM><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, dc, c->kc, c->rest, ts, c->hcount, c->hstart,
-                                                         c->hlist, c->hcell, (T *)c->accc);
+    k_contact<T, DIM><<<blocks_for(n, 128), 128, 0, s>>>(a, c->X0d, dc, c->kc, c->rest, c->kfric, ts, c->hcount,
+                                                         c->hstart, c->hlist, c->hcell, (T *)c->accc);
     CKL();
     return TLSPH_OK;
 }
@@ -1750,6 +1757,23 @@ tlsph_status tlsph_set_contact(tlsph_ctx *c, double contcoeff, int nbodies, cons
     c->contact = true;
     c->kc = contcoeff;
     c->resth.assign(restitution, restitution + nbodies);
+    c->built = false;
+    return TLSPH_OK;
+}
+
+tlsph_status tlsph_set_contact_friction(tlsph_ctx *c, int nbodies, const double *kfric) {
+    if (!c) return TLSPH_ERR_ARG;
+    if (!c->contact) return fail(c, TLSPH_ERR_STATE, "set_contact must come before set_contact_friction");
+    if (nbodies != c->nspec || !kfric)
+        return fail(c, TLSPH_ERR_ARG, "set_contact_friction: need one coefficient per specimen (%d)", c->nspec);
+    bool any = false;
+    for (int b = 0; b < nbodies; b++) {
+        if (!(kfric[b] >= 0.0 && std::isfinite(kfric[b])))
+            return fail(c, TLSPH_ERR_ARG, "set_contact_friction: coefficient of body %d must be finite and >= 0", b);
+        any = any || kfric[b] > 0.0;
+    }
+    if (any) c->kfrich.assign(kfric, kfric + nbodies);
+    else c->kfrich.clear();
     c->built = false;
     return TLSPH_OK;
 }

@@ -40,8 +40,8 @@ EXPORTS = ["tlsph_create", "tlsph_destroy", "tlsph_last_error", "tlsph_set_mater
            "tlsph_mlp_train_step", "tlsph_mlp_gradients", "tlsph_mlp_forward", "tlsph_set_surrogate",
            "tlsph_surrogate_counts", "tlsph_j2_samples",
            "tlsph_mlp_set_tensor_path", "tlsph_expr_check", "tlsph_expr_compile", "tlsph_add_bc_expr",
-           "tlsph_apply_expr", "tlsph_expr_eval", "tlsph_set_contact", "tlsph_mlp_save", "tlsph_mlp_load",
-           "tlsph_load_surrogate"]
+           "tlsph_apply_expr", "tlsph_expr_eval", "tlsph_set_contact", "tlsph_set_contact_friction", "tlsph_mlp_save",
+           "tlsph_mlp_load", "tlsph_load_surrogate"]
 MLP_NUM_PARAMS = 37264
 SURROGATE_ALL, SURROGATE_PLASTIC = 0, 1
 TENSOR_MMA_SYNC, TENSOR_TCGEN05 = 0, 1
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "tlsph_apply_expr": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
         "tlsph_expr_eval": (C.c_int, [P, C.c_int, C.c_int64, D, D, U8]),
         "tlsph_set_contact": (C.c_int, [P, C.c_double, C.c_int, D]),
+        "tlsph_set_contact_friction": (C.c_int, [P, C.c_int, D]),
         "tlsph_mlp_save": (C.c_int, [P, C.c_char_p]),
         "tlsph_mlp_load": (C.c_int, [P, C.c_char_p]),
         "tlsph_load_surrogate": (C.c_int, [P, C.c_char_p, C.c_int]),
@@ -214,10 +215,14 @@ class TLSPH:
         q = np.ascontiguousarray(quad, np.float64).reshape(12)
         self._ck(self.lib.tlsph_add_notch(self.ctx, _d(q)), "add_notch")
 
-    def set_contact(self, contcoeff, restitution):
-        """Contact between the bodies (specimens): potential multiplier and one restitution per body."""
+    def set_contact(self, contcoeff, restitution, kfric=None):
+        """Contact between the bodies (specimens): potential multiplier, one restitution per body and,
+        optionally, one friction coefficient per body."""
         r = np.ascontiguousarray(restitution, np.float64)
         self._ck(self.lib.tlsph_set_contact(self.ctx, contcoeff, r.size, _d(r)), "set_contact")
+        if kfric is not None:
+            f = np.ascontiguousarray(kfric, np.float64)
+            self._ck(self.lib.tlsph_set_contact_friction(self.ctx, f.size, _d(f)), "set_contact_friction")
 
     def expr_compile(self, expr, locals_=""):
         """Compile a user-defined expression; returns its id."""
@@ -493,7 +498,7 @@ def from_case(case, precision=None, device=0, build=True, stream=None) -> TLSPH:
     for q in case.notches:
         t.add_notch(q)
     if getattr(case, "contact", None):
-        t.set_contact(case.contact["contcoeff"], case.contact["restitution"])
+        t.set_contact(case.contact["contcoeff"], case.contact["restitution"], case.contact.get("kfric"))
     for b in getattr(case, "expr_bcs", []):
         ids = [-1 if e is None else t.expr_compile(e[0], e[1]) for e in b.exprs]
         t.add_bc_expr(b.mask, b.kind, b.comp_mask, ids, b.t_start, b.t_end, b.area)

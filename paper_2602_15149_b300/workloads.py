@@ -123,7 +123,8 @@ class Case:
     integrator: int = 1         # 1: Algorithm 1 (symplectic Euler), 2: Algorithm 2 (leapfrog)
     expr_bcs: list = field(default_factory=list)  # ExprBC
     expr_ics: list = field(default_factory=list)  # (field "U" or "V", [(text, locals) or None per component])
-    contact: dict | None = None  # {"contcoeff": kc, "restitution": [e per specimen]}: bodies = specimens
+    contact: dict | None = None  # {"contcoeff": kc, "restitution": [e per specimen], optional "kfric": [mu per
+    #                              specimen]}: bodies = specimens
 
     @property
     def n(self) -> int:
@@ -237,10 +238,12 @@ def cantilever_beam(dx=0.5e-3, L0=0.2, H0=0.02, clamp=1.5e-3, steps=20000, preci
 
 
 def flyer_plate(n=100, dx=0.01, gap=0.05, v=200.0, steps=20000, precision="fp32", contcoeff=5.0, restitution=0.95,
-                model="j2"):
+                model="j2", kfric=None, v_shear=0.0):
     """Two identical square plates (specimens 0 and 1 = the two bodies) moving towards each other along y;
     the lower one at +v, the upper one at -v.  J2 steel as the paper's case (rho 7870, E 200 GPa, nu 0.29,
-    sigma_y0 400 MPa, H 100 MPa, artificial viscosity 0.05), or "nh" for the same elastic constants."""
+    sigma_y0 400 MPa, H 100 MPa, artificial viscosity 0.05), or "nh" for the same elastic constants.
+    kfric: friction coefficient of both bodies (None = the paper's default, none); v_shear: the plates also
+    slide past each other along x at +-v_shear."""
     lo, _ = lattice((n, n), dx)
     hi, _ = lattice((n, n), dx, origin=(0.0, n * dx + gap))
     X = np.vstack([lo, hi])
@@ -249,11 +252,15 @@ def flyer_plate(n=100, dx=0.01, gap=0.05, v=200.0, steps=20000, precision="fp32"
     v0 = np.zeros((2 * m, 2))
     v0[:m, 1] = v
     v0[m:, 1] = -v
+    v0[:m, 0] = v_shear  # optional sliding of the lower plate along the contact plane
+    v0[m:, 0] = -v_shear
     mat = Material(model=MODEL_J2 if model == "j2" else MODEL_NH, rho=7870.0, E=200e9, nu=0.29,
                    sigma_y0=400e6 if model == "j2" else 0.0, H_hard=100e6 if model == "j2" else 0.0, beta1=0.05)
     case = Case("flyer_plate_" + model, 2, dx, 1.5 * dx, 0.01, DT_CFL_STATIC, 0.0, [mat], X, np.full(2 * m, dx * dx), v0,
                 np.zeros(2 * m, np.int32), spec, [], [], steps, precision)
     case.contact = {"contcoeff": contcoeff, "restitution": [restitution, restitution]}
+    if kfric is not None:  # <kfric> per body (the paper's case leaves it at 0)
+        case.contact["kfric"] = [kfric, kfric]
     return case
 
 

@@ -24,6 +24,8 @@ def make_oracle(case: W.Case, build=True, method=None, **kw) -> Oracle:
         o.add_notch(q)
     if getattr(case, "contact", None):
         o.set_contact(case.contact["contcoeff"], case.contact["restitution"])
+        if case.contact.get("kfric") is not None:
+            o.set_contact_friction(case.contact["kfric"])
     for b in getattr(case, "expr_bcs", []):
         o.add_bc_expr(b.mask, b.kind, b.comp_mask, [None if e is None else Expression(e[0], e[1]) for e in b.exprs],
                       b.t_start, b.t_end, b.area)

@@ -2,7 +2,8 @@
 FP64 oracle, through the C-ABI, and the paper's flyer-plate impact (Sec. 4) at its published size.
 
 Parity: two touching 8 x 8 plates colliding (FP64 within 1e-8 of the largest displacement, FP32 within
-1e-4), both integrators; momentum conserved to rounding; launch and graph modes bit-identical.
+1e-4), both integrators, and the same plates sliding past each other with friction (<kfric>); momentum
+conserved to rounding; launch and graph modes bit-identical.
 Flyer plate: what the paper states about its run (the figures carry no numbers) -- plasticity starts at
 the contact interface, the impact is symmetric about the mid-plane, and the plates spread laterally.
 """
@@ -30,6 +31,46 @@ def test_colliding_plates_match_oracle(integrator, precision, tol):
         assert np.abs(g.read_state("U") - u_o).max() <= tol * np.abs(u_o).max()
         v_o = o.read("V")
         assert np.abs(g.read_state("V") - v_o).max() <= tol * np.abs(v_o).max()
+
+
+def _sliding_plates(kfric, v_shear=1.0):
+    """The touching 8 x 8 plates of the parity test, closing at 2 x 2 m/s and sliding past each other at
+    2 x v_shear along the contact plane, with friction coefficient kfric on both bodies."""
+    case = W.flyer_plate(n=8, dx=1e-3, gap=0.0, v=2.0, restitution=0.8, model="nh", precision="fp64",
+                         kfric=kfric, v_shear=v_shear)
+    case.cfl = 0.05
+    return case
+
+
+@pytest.mark.parametrize("precision,tol", [(tlsph.FP64, 1e-8), (tlsph.FP32_U64, 1e-4)])
+def test_sliding_plates_with_friction_match_oracle(precision, tol):
+    case = _sliding_plates(0.3)
+    o = make_oracle(case)
+    g = tlsph.from_case(case, precision=precision)
+    for _ in range(3):
+        o.step(100)
+        g.step(100)
+        for f in ("U", "V"):
+            a = o.read(f)
+            assert np.abs(g.read_state(f) - a).max() <= tol * np.abs(a).max(), f
+
+
+def test_friction_slows_the_sliding_and_keeps_momentum():
+    """With friction the plates' relative sliding speed drops during the contact (without it, it does not
+    change beyond what the impact's elastic waves carry), and the total momentum is kept to rounding."""
+    out = {}
+    for mu in (0.0, 0.5):
+        case = _sliding_plates(mu)
+        m = case.materials[0].rho * case.vol
+        g = tlsph.from_case(case, precision=tlsph.FP64)
+        p0 = (m[:, None] * g.read_state("V")).sum(axis=0)
+        g.step(300)
+        v = g.read_state("V")
+        p = (m[:, None] * v).sum(axis=0)
+        assert np.abs(p - p0).max() <= 1e-12 * (m * 3.0).sum()
+        lo = case.specimen_id == 0
+        out[mu] = v[lo, 0].mean() - v[~lo, 0].mean()
+    assert out[0.5] < 0.8 * out[0.0], out
 
 
 def test_momentum_and_modes():
