@@ -85,7 +85,9 @@ enum {
     TLSPH_BC_VEL = 0,        /* masked velocity components are set to value * ramp(t_{n+1}) */
     TLSPH_BC_TRACTION = 1,   /* a += value * ramp(t_n) * area / m_i   (type 2, N/m^2) */
     TLSPH_BC_ACCEL = 2,      /* a += value * ramp(t_n)                (type 3, m/s^2) */
-    TLSPH_BC_POINTFORCE = 3  /* a += value * ramp(t_n) / (count * m_i) (type 1, N, shared by the masked particles) */
+    TLSPH_BC_POINTFORCE = 3, /* a += value * ramp(t_n) / (count * m_i) (type 1, N, shared by the masked particles) */
+    TLSPH_BC_PHASE_BOUND = 4 /* <restrictphi>: s_{n+1} = max(s_{n+1}, value[0] * ramp(t_{n+1})) for particles with a
+                                phase field (component bit 0; with an expression, skipped values leave s alone) */
 };
 /* fields for tlsph_read_state / tlsph_write_state */
 enum {

@@ -236,6 +236,8 @@ class Oracle:
         for b, kind, cm, exprs in self._exbcs:
             if kind == 0:
                 phases = [(0, 1.0)] + ([(1, 0.5)] if leap else [])
+            elif kind == 4:  # phase-field bound: the new level s_{n+1}
+                phases = [(0, 1.0)]
             else:
                 phases = [(0, 0.5 if leap else 0.0)]
             for phase, off in phases:

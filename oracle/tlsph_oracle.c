@@ -46,6 +46,7 @@
 #define ORC_BC_TRACTION 1
 #define ORC_BC_ACCEL 2
 #define ORC_BC_POINTFORCE 3
+#define ORC_BC_PHASE_BOUND 4 /* <restrictphi> (Sec. 3.3): s >= value at t_{n+1}, component 0 */
 
 #define ORC_DT_FIXED 0
 #define ORC_DT_ADAPTIVE 1
@@ -605,7 +606,7 @@ int orc_create_particles(orc_ctx *c, int64_t n, const double *X0, const double *
 
 int orc_add_bc(orc_ctx *c, const uint8_t *mask, int kind, int comp_mask, const double *value, double t_start,
                double t_end, double ramp, double area) {
-    if (!c || !mask || !value || c->n <= 0 || c->nbc >= ORC_MAX_BC || kind < 0 || kind > 3) return ORC_ERR_ARG;
+    if (!c || !mask || !value || c->n <= 0 || c->nbc >= ORC_MAX_BC || kind < 0 || kind > 4) return ORC_ERR_ARG;
     orc_bc *b = &c->bc[c->nbc];
     memset(b, 0, sizeof *b);
     b->kind = kind;
@@ -1296,7 +1297,7 @@ static int one_step(orc_ctx *c) {
         double t_n = c->t[c->spec[i]] + (leap ? 0.5 * c->dt[c->spec[i]] : 0.0);
         for (int b = 0; b < c->nbc; b++) {
             const orc_bc *bc = &c->bc[b];
-            if (bc->kind == ORC_BC_VEL || !bc->mask[i]) continue;
+            if (bc->kind == ORC_BC_VEL || bc->kind == ORC_BC_PHASE_BOUND || !bc->mask[i]) continue;
             double f = bc_factor(bc, t_n);
             if (f < 0.0) continue;
             for (int k = 0; k < d; k++) {
@@ -1369,7 +1370,17 @@ static int one_step(orc_ctx *c) {
             c->sdot[i] = sd1;
             /* s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1); s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2) */
             double sn = c->s[i] + du * c->sdot[i];
-            c->s[i] = sn < 0.0 ? 0.0 : (sn > 1.0 ? 1.0 : sn); /* reading: s kept in [0, 1] */
+            sn = sn < 0.0 ? 0.0 : (sn > 1.0 ? 1.0 : sn); /* reading: s kept in [0, 1] */
+            /* <restrictphi> (Sec. 3.3, used in Sec. 4 to keep particles near loads intact): the particles a
+             * bound covers keep s_{n+1} >= its value at t_{n+1}; reading: s alone is raised, sdot is kept */
+            for (int b = 0; b < c->nbc; b++) {
+                const orc_bc *bc = &c->bc[b];
+                if (bc->kind != ORC_BC_PHASE_BOUND || !bc->mask[i] || !(bc->comp_mask & 1)) continue;
+                double f = bc_factor(bc, t1), val;
+                if (f < 0.0 || !bc_value(bc, 0, i, 0, f, &val)) continue;
+                if (sn < val) sn = val;
+            }
+            c->s[i] = sn;
         }
         memcpy(&c->Fp[9 * i], &Fpn[9 * i], 9 * sizeof(double));
         c->ep[i] = epn[i];

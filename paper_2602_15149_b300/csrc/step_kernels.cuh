@@ -581,6 +581,7 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
             const int id = a.grp_bcs[4 * g + b];
             if (id < 0) break;
             const BCDev bc = a.bcs[id];
+            if (bc.kind == 4) continue;  // phase-field bound: applied with the update of s below
             if (bc.kind == 0) {  // velocity: value at t_{n+1}
                 const double f = bc_factor(bc, t_1);
                 if (f < 0.0) continue;
@@ -628,6 +629,16 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
         a.sdot[i] = sd_new;
         // s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1), s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2)
         s_new = t_min(T(1), t_max(T(0), si + (T)(a.leap ? 0.5 * dt : dt) * sd_new));
+        // <restrictphi> (Sec. 3.3): a phase-field bound covering the particle keeps s_{n+1} >= its value at t_{n+1}
+        for (int b = 0; g && b < kMaxBcPerParticle; b++) {
+            const int id = a.grp_bcs[4 * g + b];
+            if (id < 0) break;
+            const BCDev bc = a.bcs[id];
+            if (bc.kind != 4 || !(bc.comp_mask & 1)) continue;
+            const double f = bc_factor(bc, t_1);
+            double val;
+            if (f >= 0.0 && dev_bc_value(a, bc, i, b, 0, 0, f, val)) s_new = t_max(s_new, (T)val);
+        }
     }
     // update: v_{n+1} = v_n + dt a; u_{n+1} = u_n + dt v_{n+1} (Algorithm 1) or
     // u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2, u64 holding u_{n+1/2})
@@ -1418,7 +1429,7 @@ __global__ void __launch_bounds__(128) k_expr_bcs(StepArgs<T> a, const int *exli
             const int nph = (bc.kind == 0 && a.leap) ? 2 : 1;
             for (int ph = 0; ph < nph; ph++) {
                 double off;
-                if (bc.kind == 0) off = ph == 0 ? dt : 0.5 * dt;
+                if (bc.kind == 0 || bc.kind == 4) off = ph == 0 ? dt : 0.5 * dt;  // the new level t_{n+1}
                 else off = a.leap ? 0.5 * dt : 0.0;
                 v[9] = t + off;
                 bool sk;

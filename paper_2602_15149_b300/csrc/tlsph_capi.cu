@@ -1622,7 +1622,7 @@ tlsph_status tlsph_add_bc(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_
                           double t_start, double t_end, double ramp, double area) {
     if (!c) return TLSPH_ERR_ARG;
     if (c->n <= 0) return fail(c, TLSPH_ERR_STATE, "create_particles must come before add_bc");
-    if (!mask || !value || kind < 0 || kind > 3) return fail(c, TLSPH_ERR_ARG, "add_bc: bad kind or null array");
+    if (!mask || !value || kind < 0 || kind > 4) return fail(c, TLSPH_ERR_ARG, "add_bc: bad kind or null array");
     if (c->bcs.size() >= 32767) return fail(c, TLSPH_ERR_ARG, "too many boundary conditions");
     BCHost b;
     b.kind = kind;

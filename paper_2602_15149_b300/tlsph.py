@@ -19,7 +19,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_SINGULAR_L, ERR_NONFINITE, ERR_NOCONVERGE, E
 FP64, FP32_U64 = 0, 1
 DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
 MODEL_SVK, MODEL_NH, MODEL_J2 = 1, 2, 3
-BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
+BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE, BC_PHASE_BOUND = 0, 1, 2, 3, 4
 FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "F": 8, "ACC": 11, "CPINV": 12,
          "STATE": 100}
 OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6

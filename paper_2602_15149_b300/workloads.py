@@ -56,7 +56,7 @@ REF_WAVE_SPEED = 5856.0  # m/s, sets ramp durations (see the module docstring)
 
 MODEL_SVK, MODEL_NH, MODEL_J2 = 1, 2, 3
 _MODELS = {"svk": MODEL_SVK, "nh": MODEL_NH}
-BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE = 0, 1, 2, 3
+BC_VEL, BC_TRACTION, BC_ACCEL, BC_POINTFORCE, BC_PHASE_BOUND = 0, 1, 2, 3, 4
 DT_FIXED, DT_ADAPTIVE, DT_CFL_STATIC = 0, 1, 2
 
 
