@@ -510,7 +510,7 @@ __device__ __forceinline__ void p2_pair(const StepArgs<T> &a, P2Own<T, DIM> &o, 
             }
         }
         if (frac) {
-            const T c = on ? (vsi.w - vsj.w) * aw / r2 : T(0);
+            const T c = on ? pair_div((vsi.w - vsj.w) * aw, r2) : T(0);  // fast division in FP32, as the viscosity
             const T c0 = c * d[0], c1 = c * d[1];
             Tl[0] = t_fma(c0, d[0], Tl[0]);
             Tl[1] = t_fma(c1, d[1], Tl[1]);
