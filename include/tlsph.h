@@ -191,9 +191,9 @@ tlsph_status tlsph_add_bc(tlsph_ctx *ctx, const uint8_t *mask, int kind, int com
  *   k = contcoeff E* dc^(dim-2),  1/E* = (1 - nu_i^2)/E_i + (1 - nu_j^2)/E_j,  m* = m_i m_j/(m_i + m_j),
  *   zeta = -ln e / sqrt(pi^2 + ln^2 e),  e = (e_i + e_j)/2 (restitution[body], in (0, 1]),
  * under which a head-on pair separates with e times its approach speed (friction: tlsph_set_contact_friction).
- * Pairs are found
- * every step in the current configuration (FP64 positions).  Must come after tlsph_create_particles and
- * before tlsph_build_ref_neighbours; nbodies = the number of specimens.  Not with TLSPH_MODE_PERSISTENT. */
+ * Pairs are found every step in the current configuration (FP64 positions).  Must come after
+ * tlsph_create_particles and before tlsph_build_ref_neighbours; nbodies = the number of specimens.
+ * Not with TLSPH_MODE_PERSISTENT. */
 tlsph_status tlsph_set_contact(tlsph_ctx *ctx, double contcoeff, int nbodies, const double *restitution);
 /* Friction between bodies (<kfric> of Sec. 3.3, default 0 = none), one coefficient per body (>= 0, finite).
  * The paper does not state its friction law either; the one built is Coulomb's, regularised near rest by
