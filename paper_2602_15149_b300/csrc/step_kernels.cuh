@@ -676,8 +676,9 @@ template <typename T, int DIM, bool FRAC, bool VISC>
 __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
     P2Own<T, DIM> o;
     p2_begin<T, DIM, FRAC>(a, i, o);
-    // entry by entry, four at a time across runs (measured faster than the unrolled runs, as in k_gradient)
-    for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
+    // entry by entry, four (3D) or two (2D) at a time across runs: measured faster than the unrolled runs
+    // and than other depths (crack-branching plate: 0.139 ms at two, 0.145 at four, 0.148 at eight)
+    for_each_neighbour<DIM == 3 ? 4 : 2, false, false>(a, i, [&](const int j, const bool on) {
         p2_pair<T, DIM, FRAC, VISC>(a, o, p2_load<T, DIM, FRAC, VISC>(a, j), on);
     });
     p2_finish<T, DIM, FRAC, VISC>(a, i, o, vmag, amag);
