@@ -93,6 +93,27 @@ def test_momentum_and_modes():
         g.step(2)
 
 
+def test_friction_arguments_are_checked():
+    case = _sliding_plates(None)
+    g = tlsph.from_case(case, precision=tlsph.FP64, build=False)
+    g2 = tlsph.TLSPH(case.dim, case.h, tlsph.FP64, dx=case.dp)
+    g2.set_materials(case.materials)
+    g2.create_particles(case.X0, case.vol, specimen_id=case.specimen_id)
+    with pytest.raises(tlsph.TLSPHError) as e:  # no contact yet
+        g2._ck(g2.lib.tlsph_set_contact_friction(g2.ctx, 2, tlsph._d(np.array([0.1, 0.1]))), "friction")
+    assert e.value.status == tlsph.ERR_STATE
+    for bad in ([0.1], [0.1, -0.2], [0.1, np.inf], [np.nan, 0.0]):
+        with pytest.raises(tlsph.TLSPHError) as e:
+            g.set_contact(case.contact["contcoeff"], case.contact["restitution"], bad)
+        assert e.value.status == tlsph.ERR_ARG
+    g.set_contact(case.contact["contcoeff"], case.contact["restitution"], [0.0, 0.0])  # zero = none
+    g.build_ref_neighbours()
+    ref = tlsph.from_case(case, precision=tlsph.FP64)
+    g.step(50)
+    ref.step(50)
+    assert np.array_equal(g.read_state("U"), ref.read_state("U"))
+
+
 def test_contact_needs_a_shared_clock():
     case = _plates(0.8)
     case.dt_mode = W.DT_ADAPTIVE
