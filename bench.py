@@ -83,23 +83,26 @@ def bf16_peak():
     return FALLBACK_BF16_TFLOPS, "fallback"
 
 
-def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True):
+def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True, fused=False):
     """Algorithmic HBM bytes per launch of each kernel of a step (every particle's own records
     read / written once, neighbour gathers served on chip, neighbour indices read once per
-    neighbour pass: 4 B per pair, the CSR definition, also when the kernels walk the stencil
-    layout) for the library's layout.  Mirrors algorithmic_bytes() in tlsph_capi.cu."""
+    neighbour pass: 4 B per pair, the CSR definition, also when the kernels walk the stencil or
+    lattice layout) for the library's layout.  Mirrors algorithmic_bytes() in tlsph_capi.cu.
+    fused: the stress runs in the tail of the deformation-gradient kernel, so F - I and the
+    viscosity sum never go through memory ("gradient" then holds both passes, "stress" 0)."""
     v4, nsym, q = 4 * ts, (6 if dim == 3 else 3), dim * dim * ts
-    grad = n * (4 + 8 / 32 + 2 * v4 + nsym * ts + dim * dim * ts) + 4 * nnz
-    stress = n * (dim * dim * ts + nsym * ts + 2 + q + dim * dim * ts)
+    vi, fr = (1 if visc else 0), (1 if frac else 0)
+    grad = n * (4 + 8 / 32 + (2 + (1 if vi + fr else 0)) * v4 + nsym * ts + dim * dim * ts + vi * dim * ts
+                + fr * ts) + 4 * nnz
+    stress = n * (dim * dim * ts + nsym * ts + 2 + v4 + (3 * v4 if dim == 3 else v4) + vi * 2 * dim * ts)
     if j2:
         stress += n * 2 * 7 * ts
     if frac:
         stress += n * (v4 + 2 * ts)
-    p2 = n * (4 + 8 / 32 + 4 * v4 + q + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4) + 4 * nnz  # incl. first moment S1
-    if visc:
-        p2 += n * dim * dim * ts
-    if frac:
-        p2 += n * (nsym * ts + 3 * ts)
+    p2 = n * (4 + 8 / 32 + 3 * v4 + q + vi * dim * ts + 2 + 4 + 2 + 2 * 8 * dim + 2 * v4 + fr * 4 * ts) + 4 * nnz
+    if fused:
+        # G and the viscosity sum stay in registers; Ahat is read once
+        grad, stress = grad + stress - n * (2 * (dim * dim + vi * dim) * ts + nsym * ts), 0.0
     return {"gradient": grad, "stress": stress, "pass2": p2}
 
 

@@ -151,6 +151,8 @@ typedef struct {
     int64_t max_row;        /* largest neighbour count */
     double bytes_per_step;  /* algorithmic HBM bytes of one step of this configuration */
     int64_t stencil;        /* entries of the stencil neighbour layout in use (0 = SELL-32 rows) */
+    int64_t lattice_nx;     /* row pitch NX of the lattice layout in use (0 = none) */
+    int64_t lattice_nxny;   /* layer pitch NXNY of the lattice layout in use (0 = none) */
 } tlsph_info;
 
 /* Create a context.  params is copied.  Errors: ERR_ARG (bad dim/h/precision),
@@ -313,20 +315,34 @@ enum {
                                    launches, so every wait runs out after about a second and tlsph_step /
                                    tlsph_sync return TLSPH_ERR_TIMEOUT (the context stays usable) */
     TLSPH_OPT_NEIGHBOUR_LAYOUT = 6, /* value TLSPH_LAYOUT_*: how the step kernels walk the neighbour rows */
-    TLSPH_OPT_MEMORY_LIMIT = 7      /* value in MiB (0 = none): a cap on the device memory the context allocates for
+    TLSPH_OPT_MEMORY_LIMIT = 7,     /* value in MiB (0 = none): a cap on the device memory the context allocates for
                                      * its state; an allocation past it returns TLSPH_ERR_OOM as a failed cudaMalloc
                                      * would, and the context stays usable (tests inject allocation failures with it) */
+    TLSPH_OPT_LATTICE_ROWS_GRADIENT = 8, /* lattice layout: rows per thread of the deformation-gradient kernel, 1
+                                          * (default) or 2 */
+    TLSPH_OPT_LATTICE_ROWS_FORCE = 9,    /* lattice layout: rows per thread of the force kernel, 1, 2 (default) or 4 */
+    TLSPH_OPT_FUSE_STRESS = 10           /* lattice layout: 1 computes the stress in the tail of the
+                                          * deformation-gradient kernel (two launches per step), 0 (default) in its
+                                          * own pass (measured faster on the 1M-particle J2 block: the fused kernel
+                                          * needs the stress pass's registers during its neighbour walk) */
 };
 /* Neighbour layouts.  The reference setup always builds CSR rows (tlsph_neighbours) and their
  * SELL-32 copy.  When the pair differences j - i of the cell-sorted particles take at most 128
  * distinct values (a lattice in lattice order: one particle per fine cell, the cells filling a
  * box), it also builds the stencil layout: the sorted differences and one bit mask per row.
- * Both visit every row's neighbours in ascending sorted index, so they give bit-identical
- * steps; the stencil one reads no index stream and its gathers coalesce.
- *  TLSPH_LAYOUT_AUTO: the stencil layout when it was built (default), else SELL-32;
- *  TLSPH_LAYOUT_CSR:  SELL-32 rows always. */
+ * In a 3D FP32 context with one specimen whose differences all lie on the lattice ball
+ * dx + NX dy + NXNY dz, dx^2 + dy^2 + dz^2 <= 9 (a lattice of spacing R / 3), it also builds the
+ * lattice layout: one mask word per layer dz of the ball, walked by kernels that know the ball at
+ * compile time.  All three visit every row's neighbours in ascending sorted index with the same
+ * pair arithmetic, so they give bit-identical steps; the stencil and lattice ones read no index
+ * stream and their gathers coalesce.
+ *  TLSPH_LAYOUT_AUTO:    the lattice layout when it was built (default), else the stencil layout
+ *                        when it was built, else SELL-32;
+ *  TLSPH_LAYOUT_CSR:     SELL-32 rows always;
+ *  TLSPH_LAYOUT_STENCIL: the stencil layout when it was built, else SELL-32. */
 #define TLSPH_LAYOUT_AUTO 0
 #define TLSPH_LAYOUT_CSR 1
+#define TLSPH_LAYOUT_STENCIL 2
 /* How a step is executed:
  *  TLSPH_MODE_LAUNCH:     three kernel launches per step (deformation gradient, stress, force and damage);
  *  TLSPH_MODE_GRAPH:      the same kernels replayed from a CUDA graph of two steps (fewer launch gaps);

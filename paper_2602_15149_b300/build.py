@@ -21,8 +21,10 @@ def nvcc_command(out: str = LIB, extra=()):
     # --fmad=false: no implicit multiply-add contraction, so a kernel's rounding does not depend
     # on the code around it (execution modes and block sizes give bit-identical steps); the hot
     # loops write their fused multiply-adds explicitly.
+    # --split-compile 0: the device code's optimisation passes run on all host cores
     return (["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
-             "-Xcompiler", "-ffp-contract=off", "-shared", "-o", out, *SOURCES] + list(extra))
+             "-Xcompiler", "-ffp-contract=off", "--split-compile", "0", "-shared", "-o", out, *SOURCES]
+            + list(extra))
 
 
 def build_library(force: bool = False, verbose: bool = False, debug: bool = False) -> str:

@@ -71,16 +71,20 @@ template <typename T> struct StepArgs {
     int nsten, nruns;      // stencil entries (0 = SELL-32 rows) and runs (the most of any table)
     int64_t halo;          // zero records before and after each gathered array (stencil layout)
     int sten_groups;       // stencil tables: 1, or one per specimen (kMaxStencil entries each)
+    int lat_nx, lat_nxny;  // lattice walk (lattice.cuh): row and layer pitch, 0 = off
+    const unsigned *lmask; // lattice walk: one mask word per layer, 7 arrays of n
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
-    const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) (reference configuration)
+    const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) / V_i (reference configuration)
     const V4<T> *ug_cur;   // gathered displacement copy (x, y, z, m0 in 3D)
     V4<T> *ug_next;
     const V4<T> *vs_cur;   // (vx, vy, vz, s)
     V4<T> *vs_next;
-    V4<T> *Qa, *Qb;        // P_i Ahat_i: 3D (q00 q01 q02 q10), (q11 q12 q20 q21); 2D Qa = (q00 q01 q10 q11)
-    T *Qc;                 // 3D q22
+    V4<T> *Qa, *Qb;        // V_i P_i Ahat_i: 3D (q00 q01 q02 q10), (q11 q12 q20 q21); 2D Qa = (q00 q01 q10 q11)
+    V4<T> *XQ;             // 3D pass-2 record of the stress pass: (x, y, z of X0V, V_i q22)
     T *G;                  // F - I from k_gradient, dim*dim arrays of n
-    T *Vm;                 // J F^-T Ahat, dim*dim arrays of n
+    T *S3;                 // viscosity sum of pass 1a (without its factor h / rho_i), dim arrays of n
+    T *Av;                 // viscous acceleration J F^-T Ahat S3 h / rho_i, dim arrays of n; null without viscosity
+    T *LAP;                // phase-field Laplacian of pass 1a
     const T *Ahat;         // inverse of sum V w d d^T: 6 arrays of n (2D uses xx, yy, xy)
     T *K;                  // J2 state C_p^-1 - I, 6 arrays of n
     T *ep;                 // equivalent plastic strain

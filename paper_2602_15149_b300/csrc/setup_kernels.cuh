@@ -410,3 +410,23 @@ __global__ void k_stencil_mask(int64_t n, const int64_t *row_ptr, const int *col
 }
 
 }  // namespace tl
+
+namespace tl {
+// Row masks of the lattice walk (lattice.cuh) from the stencil masks: stencil entry s of the table
+// becomes bit map[s].y of layer word map[s].x.
+__global__ void k_lattice_mask(int64_t n, int nsten, const unsigned *nmask, const int2 *map, unsigned *lmask) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned w[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (int s = 0; s < nsten; s++) {
+        if ((nmask[(int64_t)(s >> 5) * n + i] >> (s & 31)) & 1u) {
+            const int2 m = map[s];
+#pragma unroll
+            for (int L = 0; L < 7; L++)
+                if (m.x == L) w[L] |= 1u << m.y;
+        }
+    }
+#pragma unroll
+    for (int L = 0; L < 7; L++) lmask[(int64_t)L * n + i] = w[L];
+}
+}  // namespace tl

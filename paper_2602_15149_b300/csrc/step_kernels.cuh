@@ -18,6 +18,7 @@
 #pragma once
 #include "common.cuh"
 #include "expr_eval.cuh"
+#include "lattice.cuh"
 #include "mlp.cuh"
 #include "mlp_tc.cuh"
 
@@ -136,11 +137,22 @@ __device__ __forceinline__ void for_each_neighbour(const StepArgs<T> &a, int i, 
     }
 }
 
-// |X_j - X_i| for the kernel weight: r2 rsqrt(r2) in FP32 (one special-function op), sqrt in FP64.
-__device__ __forceinline__ float pair_dist(float r2) { return r2 * rsqrtf(r2); }
+// |X_j - X_i| for the kernel weight: r2 rsqrt(r2) in FP32 (one special-function op: the approximate
+// reciprocal square root with subnormals flushed, which r2 of two distinct particles never is), sqrt in
+// FP64.  r2 = 0 (a dropped entry reading the zero halo) gives NaN, which the pair bodies select away.
+__device__ __forceinline__ float pair_dist(float r2) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+    return r2 * r;
+}
 __device__ __forceinline__ double pair_dist(double r2) { return sqrt(r2); }
-// x / y of the viscosity term: fast division in FP32, IEEE division in FP64.
-__device__ __forceinline__ float pair_div(float x, float y) { return __fdividef(x, y); }
+// x / y of the viscosity and Laplacian terms: the approximate division (subnormals flushed) in FP32, IEEE
+// division in FP64.
+__device__ __forceinline__ float pair_div(float x, float y) {
+    float q;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(q) : "f"(x), "f"(y));
+    return q;
+}
 __device__ __forceinline__ double pair_div(double x, double y) { return x / y; }
 
 // |X_j - X_i|^2 of a pair and the Wendland C2 factor t = max(1 - r / (2h), 0) (w = t^3).
@@ -153,6 +165,11 @@ template <typename T, int DIM> __device__ __forceinline__ T pair_r2(const T d[DI
 template <typename T> __device__ __forceinline__ T pair_t(T r2, T inv2h) {
     return t_max(t_fma(-pair_dist(r2), inv2h, T(1)), T(0));
 }
+// The same without the clamp at zero, for the step's pair bodies: a kept pair has r0 < R, and an
+// entry the mask drops has its weight selected to zero after the cube, so the clamp adds nothing.
+template <typename T> __device__ __forceinline__ T pair_t_kept(T r2, T inv2h) {
+    return t_fma(-pair_dist(r2), inv2h, T(1));
+}
 
 // Prefetch the SELL-32 slice of row i to L2 (no index stream in the stencil layout).
 template <typename T> __device__ __forceinline__ void prefetch_rows(const StepArgs<T> &a, int i) {
@@ -160,28 +177,59 @@ template <typename T> __device__ __forceinline__ void prefetch_rows(const StepAr
 }
 
 // ---------------------------------------------------------------- pass 1a: deformation gradient
-// G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i.  Register-light so
-// that many warps keep neighbour gathers in flight.  Written as pieces (own state, neighbour record,
-// pair term, closing product), which keeps the loop body's live state explicit.
+// G_i = F_i - I = (sum_j V_j w_ij (u_j - u_i) (X_j - X_i)^T) Ahat_i, and in the same walk the two other
+// sums over the neighbours of the state at the step's start, which share the pair's distance, weight
+// and displacement difference:
+//   the artificial viscosity (VISC): s3_i = sum_j m_j w g (beta2 h g - beta1 c0) (X_j - X_i), over the
+//   pairs in relative compression, (v_j - v_i).(x_j - x_i) < 0 with x = X + u, where
+//   g = (v_j - v_i).(X_j - X_i) / (r^2 + eps).  Times h / rho_i this is sum_j m_j pi_ij w (X_j - X_i)
+//   (eq. artViscCoef), which the stress pass turns into the viscous acceleration J F^-T Ahat s3 h / rho_i;
+//   the phase-field Laplacian (FRAC): lap_i = -2 Ahat_i : sum_j (s_i - s_j) V_j w d d^T / r^2
+//   (eq. phasefieldLapLacian).
+// Written as pieces (own state, neighbour record, pair term, closing product), which keeps the loop
+// body's live state explicit.
 template <typename T, int DIM> struct GradOwn {
-    V4<T> xi, ui;
+    V4<T> xi, ui, vsi;
+    bool frac;
+    T cvis, b2h;  // beta1 c0 and beta2 h of the particle's material
     T B[DIM][DIM];
+    T s3[DIM], Tl[DIM == 3 ? 6 : 3];
 };
 template <typename T> struct GradRec {
-    V4<T> xj, uj;
+    V4<T> xj, uj, vsj;
 };
-template <typename T, int DIM> __device__ __forceinline__ void grad_begin(const StepArgs<T> &a, int i, GradOwn<T, DIM> &o) {
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void grad_begin(const StepArgs<T> &a, int i, GradOwn<T, DIM> &o) {
     o.xi = a.X0V[i];
     o.ui = a.ug_cur[i];
+    o.vsi = V4<T>{T(0), T(0), T(0), T(1)};
+    if (VISC || FRAC) o.vsi = a.vs_cur[i];
+    o.frac = false;
+    o.cvis = o.b2h = T(0);
+    if (VISC || FRAC) {
+        const MatT<T> &m = a.mats[a.mid[i]];
+        o.frac = FRAC && m.fracture;
+        o.cvis = m.beta1 * m.c0;
+        o.b2h = m.beta2 * a.h;
+    }
 #pragma unroll
-    for (int p = 0; p < DIM; p++)
+    for (int p = 0; p < DIM; p++) {
+        o.s3[p] = T(0);
 #pragma unroll
         for (int q = 0; q < DIM; q++) o.B[p][q] = T(0);
+    }
+#pragma unroll
+    for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) o.Tl[p] = T(0);
 }
-template <typename T> __device__ __forceinline__ GradRec<T> grad_load(const StepArgs<T> &a, int j) {
-    return GradRec<T>{ldg4(a.X0V + j), ldg4(a.ug_cur + j)};
+template <typename T, bool FRAC, bool VISC> __device__ __forceinline__ GradRec<T> grad_load(const StepArgs<T> &a, int j) {
+    GradRec<T> r;
+    r.xj = ldg4(a.X0V + j);
+    r.uj = ldg4(a.ug_cur + j);
+    r.vsj = V4<T>{T(0), T(0), T(0), T(0)};
+    if (VISC || FRAC) r.vsj = ldg4(a.vs_cur + j);
+    return r;
 }
-template <typename T, int DIM>
+template <typename T, int DIM, bool FRAC, bool VISC>
 __device__ __forceinline__ void grad_pair(const StepArgs<T> &a, GradOwn<T, DIM> &o, const GradRec<T> &r, bool on) {
     T d[DIM], du[DIM];
     d[0] = r.xj.x - o.xi.x;
@@ -192,18 +240,66 @@ __device__ __forceinline__ void grad_pair(const StepArgs<T> &a, GradOwn<T, DIM> 
         d[DIM - 1] = r.xj.z - o.xi.z;
         du[DIM - 1] = r.uj.z - o.ui.z;
     }
-    const T t = pair_t(pair_r2<T, DIM>(d), a.inv2h);
+    const T r2 = pair_r2<T, DIM>(d);
+    const T t = pair_t_kept(r2, a.inv2h);
+    const T w = t * t * t;
     const T Vj = DIM == 3 ? r.xj.w : r.xj.z;
-    const T aw = on ? t * t * t * Vj : T(0);
+    const T aw = on ? w * Vj : T(0);
 #pragma unroll
     for (int p = 0; p < DIM; p++) {
         const T c = aw * du[p];
 #pragma unroll
         for (int q = 0; q < DIM; q++) o.B[p][q] = t_fma(c, d[q], o.B[p][q]);
     }
+    if (VISC) {
+        const V4<T> &vsi = o.vsi, &vsj = r.vsj;
+        const T mj = DIM == 3 ? r.uj.w : r.xj.w;  // reference mass m0_j
+        T dv[DIM];
+        dv[0] = vsj.x - vsi.x;
+        dv[1] = vsj.y - vsi.y;
+        if (DIM == 3) dv[DIM - 1] = vsj.z - vsi.z;
+        // (v_j - v_i).(X_j - X_i), then + (v_j - v_i).(u_j - u_i) for the current separation
+        T vX = dv[0] * d[0];
+        vX = t_fma(dv[1], d[1], vX);
+        if (DIM == 3) vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
+        T vx = t_fma(dv[0], du[0], vX);
+        vx = t_fma(dv[1], du[1], vx);
+        if (DIM == 3) vx = t_fma(dv[DIM - 1], du[DIM - 1], vx);
+        if (DIM == 3) {
+            // computed for every pair and kept for pairs in relative compression (the others add exact
+            // zeros), so the pair body has no branch (measured faster in 3D; the 2D pass keeps the branch)
+            const T g = pair_div(vX, r2 + a.visc_eps);
+            const T c = on && vx < T(0) ? mj * w * g * t_fma(o.b2h, g, -o.cvis) : T(0);
+#pragma unroll
+            for (int p = 0; p < DIM; p++) o.s3[p] = t_fma(c, d[p], o.s3[p]);
+        } else if (on && vx < T(0)) {  // pair in relative compression
+            const T g = pair_div(vX, r2 + a.visc_eps);
+            const T c = mj * w * g * t_fma(o.b2h, g, -o.cvis);
+#pragma unroll
+            for (int p = 0; p < DIM; p++) o.s3[p] = t_fma(c, d[p], o.s3[p]);
+        }
+    }
+    if (FRAC && o.frac) {
+        T *Tl = o.Tl;
+        const T c = on ? pair_div((o.vsi.w - r.vsj.w) * aw, r2) : T(0);  // fast division in FP32, as the viscosity
+        const T c0 = c * d[0], c1 = c * d[1];
+        Tl[0] = t_fma(c0, d[0], Tl[0]);
+        Tl[1] = t_fma(c1, d[1], Tl[1]);
+        if (DIM == 3) {
+            Tl[2] = t_fma(c * d[2], d[2], Tl[2]);
+            Tl[3] = t_fma(c0, d[1], Tl[3]);
+            Tl[4] = t_fma(c0, d[2], Tl[4]);
+            Tl[5] = t_fma(c1, d[2], Tl[5]);
+        } else {
+            Tl[2] = t_fma(c0, d[1], Tl[2]);
+        }
+    }
 }
-template <typename T, int DIM>
-__device__ __forceinline__ void grad_finish(const StepArgs<T> &a, int i, const GradOwn<T, DIM> &o, T Gm[DIM][DIM]) {
+// G = B Ahat, and the closing of the other two sums: the viscosity sum as it is (s3), the Laplacian
+// lap = -2 Ahat : Tl (0 without phase field).
+template <typename T, int DIM, bool FRAC>
+__device__ __forceinline__ void grad_finish(const StepArgs<T> &a, int i, const GradOwn<T, DIM> &o, T Gm[DIM][DIM],
+                                            T &lap) {
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, a.n, i, A);
 #pragma unroll
@@ -215,36 +311,55 @@ __device__ __forceinline__ void grad_finish(const StepArgs<T> &a, int i, const G
             for (int r = 1; r < DIM; r++) s = t_fma(o.B[p][r], A[r][q], s);
             Gm[p][q] = s;
         }
+    lap = T(0);
+    if (FRAC && o.frac) {
+        const T *Tl = o.Tl;
+        T AT;
+        if (DIM == 3)
+            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + A[2][2] * Tl[2] +
+                 T(2) * (A[0][1] * Tl[3] + A[0][2] * Tl[4] + A[1][2] * Tl[5]);
+        else
+            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
+        lap = T(-2) * AT;
+    }
 }
-template <typename T, int DIM> __device__ __forceinline__ void grad_store(const StepArgs<T> &a, int i, const T Gm[DIM][DIM]) {
+// F - I to G; the viscosity sum to S3 and the Laplacian to LAP for the stress pass and pass 2.
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void grad_store(const StepArgs<T> &a, int i, const GradOwn<T, DIM> &o, const T Gm[DIM][DIM],
+                                           T lap) {
 #pragma unroll
     for (int p = 0; p < DIM; p++)
 #pragma unroll
         for (int q = 0; q < DIM; q++) a.G[(p * DIM + q) * a.n + i] = Gm[p][q];
+    if (VISC)
+#pragma unroll
+        for (int p = 0; p < DIM; p++) a.S3[p * a.n + i] = o.s3[p];
+    if (FRAC) a.LAP[i] = lap;
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, T Gm[DIM][DIM]) {
-    GradOwn<T, DIM> o;
-    grad_begin<T, DIM>(a, i, o);
+template <typename T, int DIM, bool FRAC, bool VISC>
+__device__ __forceinline__ void dev_gradient(const StepArgs<T> &a, int i, GradOwn<T, DIM> &o, T Gm[DIM][DIM], T &lap) {
+    grad_begin<T, DIM, FRAC, VISC>(a, i, o);
     for_each_neighbour<4, false, false>(a, i, [&](const int j, const bool on) {
-        grad_pair<T, DIM>(a, o, grad_load(a, j), on);
+        grad_pair<T, DIM, FRAC, VISC>(a, o, grad_load<T, FRAC, VISC>(a, j), on);
     });
-    grad_finish<T, DIM>(a, i, o, Gm);
+    grad_finish<T, DIM, FRAC>(a, i, o, Gm, lap);
 }
 
-template <typename T, int DIM, int BS>
+template <typename T, int DIM, bool FRAC, bool VISC, int BS>
 __global__ void __launch_bounds__(BS, 1024 / BS) k_gradient(StepArgs<T> a) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= a.n) return;
     prefetch_rows(a, i);
-    T Gm[DIM][DIM];
-    dev_gradient<T, DIM>(a, i, Gm);
-    grad_store<T, DIM>(a, i, Gm);
+    GradOwn<T, DIM> o;
+    T Gm[DIM][DIM], lap;
+    dev_gradient<T, DIM, FRAC, VISC>(a, i, o, Gm, lap);
+    grad_store<T, DIM, FRAC, VISC>(a, i, o, Gm, lap);
 }
 
-// First moment of the corrected kernel, sum_j V_j w_ij (X_j - X_i): it depends on the reference
-// configuration only, so the setup computes it once for pass 2 (same terms, same order).
+// First moment of the corrected kernel over the particle's volume, sum_j V_j w_ij (X_j - X_i) / V_i: it
+// depends on the reference configuration only, so the setup computes it once for pass 2 (which holds
+// Q_i V_i, so that Q_i sum_j V_j w d = (V_i Q_i) S1_i).
 template <typename T, int DIM> __global__ void k_first_moment(StepArgs<T> a, V4<T> *S1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -263,17 +378,20 @@ template <typename T, int DIM> __global__ void k_first_moment(StepArgs<T> a, V4<
 #pragma unroll
         for (int p = 0; p < DIM; p++) s1[p] = t_fma(aw, d[p], s1[p]);
     });
-    S1[i] = V4<T>{s1[0], s1[1], s1[2], T(0)};
+    const T Vi = DIM == 3 ? xi.w : xi.z;
+    S1[i] = V4<T>{s1[0] / Vi, s1[1] / Vi, s1[2] / Vi, T(0)};
 }
 
 // ---------------------------------------------------------------- pass 1b: stress
-template <typename T, int DIM, bool FRAC>
-__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J);
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J, T irho,
+                                              const T *s3v);
 
-// Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and the
-// per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i.
+// Soft particles (eq. defGrad_phase), NH / J2 stress, history functional, and what pass 2 takes of
+// the particle: Q_i = P_i Ahat_i and the viscous acceleration.  s3v: the particle's viscosity sum when
+// the caller holds it, else null (read from S3).
 template <typename T, int DIM, bool FRAC, bool DIAG>
-__device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T Gm[DIM][DIM]) {
+__device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T Gm[DIM][DIM], const T *s3v = nullptr) {
     const int n = a.n;
     M3<T> G = m3_zero<T>();
 #pragma unroll
@@ -328,24 +446,29 @@ __device__ __forceinline__ void dev_stress(const StepArgs<T> &a, int i, const T 
         a.psi_out[i] = psi;
         return;
     }
-    dev_write_qvm<T, DIM, FRAC>(a, i, F, P, T(1) + kin.Jm1);
+    dev_write_qvm<T, DIM>(a, i, F, P, T(1) + kin.Jm1, T(1) / m.rho, s3v);
 }
 
-// Per-particle matrices of pass 2: Q_i = P_i Ahat_i, Vm_i = J_i F_i^-T Ahat_i (in-plane block).
-// In 3D, q22 goes to Qc, or, in a step without phase field (s is constant), to the fourth
-// component of the particle's current velocity record, so that pass 2 gathers five float4
-// records per neighbour instead of five and a float.
-template <typename T, int DIM, bool FRAC>
-__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J);
-template <typename T, int DIM, bool FRAC>
-__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J) {
+// What pass 2 takes of particle i: V_i Q_i with Q_i = P_i Ahat_i (3D: q00 q01 q02 q10 | q11 q12 q20 q21 in
+// Qa, Qb, and q22 in the fourth place of XQ = (x, y, z, q22) beside the particle's reference position, so
+// that pass 2 gathers three float4 records per neighbour; 2D: Qa) and, in a step with viscosity (Av set),
+// the viscous acceleration
+// Av_i = Vm_i s3_i h / rho_i with Vm_i = J_i F_i^-T Ahat_i (in-plane block), the viscosity sum s3_i of
+// pass 1a closed with the particle's own matrices.
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J,
+                                                 T irho, const T *s3v);
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm(const StepArgs<T> &a, int i, const M3<T> &F, const M3<T> &P, T J, T irho,
+                                              const T *s3v) {
     M3<T> Fi;
     inverse(F, Fi);
-    dev_write_qvm_fi<T, DIM, FRAC>(a, i, Fi, P, J);
+    dev_write_qvm_fi<T, DIM>(a, i, Fi, P, J, irho, s3v);
 }
 // The same, given F^-1.
-template <typename T, int DIM, bool FRAC>
-__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J) {
+template <typename T, int DIM>
+__device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, const M3<T> &Fi, const M3<T> &P, T J,
+                                                 T irho, const T *s3v) {
     const int n = a.n;
     T A[3][3];
     load_ahat<T, DIM>(a.Ahat, n, i, A);
@@ -366,18 +489,27 @@ __device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, co
             ok = ok && finite_t(s1) && finite_t(s2);
         }
     if (!ok) atomicAdd(&a.flags[kFlagNonfinite], 1);
+    const V4<T> xi = a.X0V[i];
+    const T Vi = DIM == 3 ? xi.w : xi.z;
     if (DIM == 3) {
-        a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[0][DIM - 1], Qm[1][0]};
-        a.Qb[i] = V4<T>{Qm[1][1], Qm[1][DIM - 1], Qm[DIM - 1][0], Qm[DIM - 1][1]};
-        if (FRAC) a.Qc[i] = Qm[DIM - 1][DIM - 1];
-        else reinterpret_cast<T *>(const_cast<V4<T> *>(a.vs_cur))[4 * i + 3] = Qm[DIM - 1][DIM - 1];
+        a.Qa[i] = V4<T>{Vi * Qm[0][0], Vi * Qm[0][1], Vi * Qm[0][DIM - 1], Vi * Qm[1][0]};
+        a.Qb[i] = V4<T>{Vi * Qm[1][1], Vi * Qm[1][DIM - 1], Vi * Qm[DIM - 1][0], Vi * Qm[DIM - 1][1]};
+        a.XQ[i] = V4<T>{xi.x, xi.y, xi.z, Vi * Qm[DIM - 1][DIM - 1]};
     } else {
-        a.Qa[i] = V4<T>{Qm[0][0], Qm[0][1], Qm[1][0], Qm[1][1]};
+        a.Qa[i] = V4<T>{Vi * Qm[0][0], Vi * Qm[0][1], Vi * Qm[1][0], Vi * Qm[1][1]};
     }
+    if (a.Av) {
+        T s3[DIM];
 #pragma unroll
-    for (int p = 0; p < DIM; p++)
+        for (int q = 0; q < DIM; q++) s3[q] = (s3v ? s3v[q] : a.S3[q * n + i]) * (a.h * irho);
 #pragma unroll
-        for (int q = 0; q < DIM; q++) a.Vm[(p * DIM + q) * n + i] = Vm[p][q];
+        for (int p = 0; p < DIM; p++) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < DIM; q++) v = t_fma(Vm[p][q], s3[q], v);
+            a.Av[p * n + i] = v;
+        }
+    }
 }
 
 template <typename T, int DIM, bool FRAC, bool DIAG, int BS>
@@ -397,72 +529,40 @@ __global__ void __launch_bounds__(BS) k_stress(StepArgs<T> a) {
 // closing update (the loop's live state is the own state; the compiler keeps fewer values across it
 // than with one function body).
 template <typename T, int DIM> struct P2Own {
-    V4<T> xi, ui, vsi;
-    MatT<T> m;
-    bool frac;
-    T irho, cvis;
-    T s2[DIM], s3[DIM], Tl[DIM == 3 ? 6 : 3];
+    V4<T> xi;
+    T s2[DIM];
 };
-// the neighbour's records: position and volume, velocity (its fourth component is s, or q22 without
-// phase field), Q = P Ahat, displacement and reference mass
+// the neighbour's records: position (3D with q22 beside it), V Q with Q = P Ahat
 template <typename T> struct P2Rec {
-    V4<T> xj, vsj, q0, q1, uj;
-    T q2;
+    V4<T> xj, q0, q1;
 };
-template <typename T, int DIM, bool FRAC>
+template <typename T, int DIM>
 __device__ __forceinline__ void p2_begin(const StepArgs<T> &a, int i, P2Own<T, DIM> &o) {
     o.xi = a.X0V[i];
-    o.ui = a.ug_cur[i];
-    o.vsi = a.vs_cur[i];
-    o.m = a.mats[a.mid[i]];
-    o.frac = FRAC && o.m.fracture;
-    o.irho = T(1) / o.m.rho;
-    o.cvis = o.m.beta1 * o.m.c0;
 #pragma unroll
-    for (int p = 0; p < DIM; p++) o.s2[p] = o.s3[p] = T(0);
-#pragma unroll
-    for (int p = 0; p < (DIM == 3 ? 6 : 3); p++) o.Tl[p] = T(0);
+    for (int p = 0; p < DIM; p++) o.s2[p] = T(0);
 }
-template <typename T, int DIM, bool FRAC, bool VISC>
-__device__ __forceinline__ P2Rec<T> p2_load(const StepArgs<T> &a, int j) {
+template <typename T, int DIM> __device__ __forceinline__ P2Rec<T> p2_load(const StepArgs<T> &a, int j) {
     P2Rec<T> r;
-    r.xj = ldg4(a.X0V + j);
-    r.vsj = V4<T>{T(0), T(0), T(0), T(0)};
-    if (VISC || FRAC) r.vsj = ldg4(a.vs_cur + j);
+    r.xj = ldg4((DIM == 3 ? a.XQ : a.X0V) + j);
     r.q0 = ldg4(a.Qa + j);
-    if (DIM == 3) {
-        r.q1 = ldg4(a.Qb + j);
-        r.q2 = FRAC ? __ldg(a.Qc + j) : (VISC ? r.vsj.w : __ldg(&a.vs_cur[j].w));
-    }
-    if (VISC) r.uj = ldg4(a.ug_cur + j);
+    if (DIM == 3) r.q1 = ldg4(a.Qb + j);
     return r;
 }
-template <typename T, int DIM, bool FRAC, bool VISC>
+// One pair of pass 2: s2 += w (V_j Q_j) (X_j - X_i).
+template <typename T, int DIM>
 __device__ __forceinline__ void p2_pair(const StepArgs<T> &a, P2Own<T, DIM> &o, const P2Rec<T> &r, bool on) {
-    const V4<T> &xi = o.xi, &ui = o.ui, &vsi = o.vsi;
-    const MatT<T> &m = o.m;
-    const bool frac = o.frac;
-    const T irho = o.irho, cvis = o.cvis;
-    T *s2 = o.s2, *s3 = o.s3, *Tl = o.Tl;
-    (void)ui;
-    (void)irho;
-    (void)cvis;
-    (void)m;
-    const V4<T> &xj = r.xj;
+    const V4<T> &xi = o.xi, &xj = r.xj;
     T d[DIM];
     d[0] = xj.x - xi.x;
     d[1] = xj.y - xi.y;
     if (DIM == 3) d[DIM - 1] = xj.z - xi.z;
-    const T r2 = pair_r2<T, DIM>(d);
-    const T t = pair_t(r2, a.inv2h);
-    const T w = on ? t * t * t : T(0);
-    const T Vj = DIM == 3 ? xj.w : xj.z;
-    const T aw = w * Vj;
+    const T t = pair_t_kept(pair_r2<T, DIM>(d), a.inv2h);
+    const T aw = on ? t * t * t : T(0);
     T Qd[DIM];
-    const V4<T> &vsj = r.vsj;
     if (DIM == 3) {
         const V4<T> &q0 = r.q0, &q1 = r.q1;
-        const T q2 = r.q2;
+        const T q2 = xj.w;
         Qd[0] = t_fma(q0.z, d[DIM - 1], t_fma(q0.y, d[1], q0.x * d[0]));
         Qd[1] = t_fma(q1.y, d[DIM - 1], t_fma(q1.x, d[1], q0.w * d[0]));
         Qd[DIM - 1] = t_fma(q2, d[DIM - 1], t_fma(q1.w, d[1], q1.z * d[0]));
@@ -472,73 +572,21 @@ __device__ __forceinline__ void p2_pair(const StepArgs<T> &a, P2Own<T, DIM> &o, 
         Qd[1] = t_fma(q0.w, d[1], q0.z * d[0]);
     }
 #pragma unroll
-    for (int p = 0; p < DIM; p++) s2[p] = t_fma(aw, Qd[p], s2[p]);
-    if (VISC || frac) {
-        if (VISC) {
-            const V4<T> &uj = r.uj;
-            const T mj = DIM == 3 ? uj.w : xj.w;  // reference mass m0_j
-            T dv[DIM], dx[DIM];
-            dv[0] = vsj.x - vsi.x;
-            dv[1] = vsj.y - vsi.y;
-            dx[0] = d[0] + (uj.x - ui.x);
-            dx[1] = d[1] + (uj.y - ui.y);
-            if (DIM == 3) {
-                dv[DIM - 1] = vsj.z - vsi.z;
-                dx[DIM - 1] = d[DIM - 1] + (uj.z - ui.z);
-            }
-            T vx = t_fma(dv[1], dx[1], dv[0] * dx[0]);
-            T vX = t_fma(dv[1], d[1], dv[0] * d[0]);
-            if (DIM == 3) {
-                vx = t_fma(dv[DIM - 1], dx[DIM - 1], vx);
-                vX = t_fma(dv[DIM - 1], d[DIM - 1], vX);
-            }
-            if (DIM == 3) {
-                // computed for every pair and kept for pairs in relative compression (the others add
-                // exact zeros), so the entries of a run form one block without branches (measured
-                // faster in 3D; the 2D pass keeps the branch, which is faster there)
-                const T G = pair_div(a.h * vX, r2 + a.visc_eps);
-                const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
-                const T c = on && vx < T(0) ? mj * pi * w : T(0);
-#pragma unroll
-                for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
-            } else if (on && vx < T(0)) {  // pair in relative compression
-                const T G = pair_div(a.h * vX, r2 + a.visc_eps);
-                const T pi = t_fma(m.beta2, G, -cvis) * G * irho;
-                const T c = mj * pi * w;
-#pragma unroll
-                for (int p = 0; p < DIM; p++) s3[p] = t_fma(c, d[p], s3[p]);
-            }
-        }
-        if (frac) {
-            const T c = on ? pair_div((vsi.w - vsj.w) * aw, r2) : T(0);  // fast division in FP32, as the viscosity
-            const T c0 = c * d[0], c1 = c * d[1];
-            Tl[0] = t_fma(c0, d[0], Tl[0]);
-            Tl[1] = t_fma(c1, d[1], Tl[1]);
-            if (DIM == 3) {
-                Tl[2] = t_fma(c * d[2], d[2], Tl[2]);
-                Tl[3] = t_fma(c0, d[1], Tl[3]);
-                Tl[4] = t_fma(c0, d[2], Tl[4]);
-                Tl[5] = t_fma(c1, d[2], Tl[5]);
-            } else {
-                Tl[2] = t_fma(c0, d[1], Tl[2]);
-            }
-        }
-    }
+    for (int p = 0; p < DIM; p++) o.s2[p] = t_fma(aw, Qd[p], o.s2[p]);
 }
 template <typename T, int DIM, bool FRAC, bool VISC>
 __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2Own<T, DIM> &o, T &vmag, T &amag) {
     const int n = a.n;
     const int sp = a.spec[i];
-    const V4<T> &xi = o.xi, &vsi = o.vsi;
-    const MatT<T> &m = o.m;
-    const bool frac = o.frac;
-    const T irho = o.irho;
-    const T *s2 = o.s2, *s3 = o.s3, *Tl = o.Tl;
-    (void)Tl;
-    (void)frac;
+    const V4<T> &xi = o.xi;
+    const V4<T> vsi = a.vs_cur[i];
+    const MatT<T> m = a.mats[a.mid[i]];
+    const bool frac = FRAC && m.fracture;
+    const T irho = T(1) / m.rho;
+    const T *s2 = o.s2;
     T s1[DIM];
     {
-        const V4<T> m1 = a.S1[i];  // sum_j V_j w d, fixed in the reference configuration
+        const V4<T> m1 = a.S1[i];  // sum_j V_j w d / V_i, fixed in the reference configuration
         s1[0] = m1.x;
         s1[1] = m1.y;
         if (DIM == 3) s1[DIM - 1] = m1.z;
@@ -549,7 +597,7 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
         const V4<T> q0 = a.Qa[i], q1 = a.Qb[i];
         Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[0][DIM - 1] = q0.z;
         Qi[1][0] = q0.w; Qi[1][1] = q1.x; Qi[1][DIM - 1] = q1.y;
-        Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = FRAC ? a.Qc[i] : vsi.w;
+        Qi[DIM - 1][0] = q1.z; Qi[DIM - 1][1] = q1.w; Qi[DIM - 1][DIM - 1] = a.XQ[i].w;
     } else {
         const V4<T> q0 = a.Qa[i];
         Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
@@ -561,12 +609,7 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
 #pragma unroll
         for (int q = 0; q < DIM; q++) f = t_fma(Qi[p][q], s1[q], f);
         acc[p] = f * irho;
-        if (VISC) {
-            T v = T(0);
-#pragma unroll
-            for (int q = 0; q < DIM; q++) v = t_fma(a.Vm[(p * DIM + q) * n + i], s3[q], v);
-            acc[p] -= v;
-        }
+        if (VISC) acc[p] -= a.Av[p * n + i];  // viscous acceleration of the stress pass
         acc[p] += a.grav[p];
         if (a.accc) acc[p] += a.accc[p * n + i];
     }
@@ -608,15 +651,7 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
     // phase field (eq. phasefieldddot)
     T s_new = FRAC ? vsi.w : T(1);
     if (frac) {
-        T A[3][3];
-        load_ahat<T, DIM>(a.Ahat, n, i, A);
-        T AT;
-        if (DIM == 3)
-            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + A[2][2] * Tl[2] +
-                 T(2) * (A[0][1] * Tl[3] + A[0][2] * Tl[4] + A[1][2] * Tl[5]);
-        else
-            AT = A[0][0] * Tl[0] + A[1][1] * Tl[1] + T(2) * A[0][1] * Tl[2];
-        const T lap = T(-2) * AT;
+        const T lap = a.LAP[i];  // Laplacian of pass 1a
         const T Hh = a.H[i], si = vsi.w, sd = a.sdot[i];
         const T e0 = m.eps0, c2e = m.c0 * m.c0 / (T(2) * e0);
         // eq. phasefieldddot with its local terms at the new time level:
@@ -675,11 +710,11 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
 template <typename T, int DIM, bool FRAC, bool VISC>
 __device__ __forceinline__ void dev_pass2(const StepArgs<T> &a, int i, T &vmag, T &amag) {
     P2Own<T, DIM> o;
-    p2_begin<T, DIM, FRAC>(a, i, o);
+    p2_begin<T, DIM>(a, i, o);
     // entry by entry, four (3D) or two (2D) at a time across runs: measured faster than the unrolled runs
     // and than other depths (crack-branching plate: 0.139 ms at two, 0.145 at four, 0.148 at eight)
     for_each_neighbour<DIM == 3 ? 4 : 2, false, false>(a, i, [&](const int j, const bool on) {
-        p2_pair<T, DIM, FRAC, VISC>(a, o, p2_load<T, DIM, FRAC, VISC>(a, j), on);
+        p2_pair<T, DIM>(a, o, p2_load<T, DIM>(a, j), on);
     });
     p2_finish<T, DIM, FRAC, VISC>(a, i, o, vmag, amag);
 }
@@ -821,6 +856,131 @@ __global__ void __launch_bounds__(BS, 896 / BS) k_pass2(StepArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------- lattice kernels (3D, FP32)
+// The two neighbour passes walking the ball of lattice.cuh instead of a difference table: the same
+// pair bodies (grad_pair, p2_pair) in the same order per row, P rows per thread.  Debug builds check
+// every record index against the zero halo and every kept entry against the particle range.
+template <typename T> __device__ __forceinline__ bool lat_index_ok(const StepArgs<T> &a, int j) {
+#ifdef TLSPH_DEBUG
+    const bool ok = j >= -a.halo && j < a.n + a.halo;
+    if (!ok) atomicAdd(&a.flags[kFlagBounds], 1);
+    return ok;
+#else
+    (void)a;
+    (void)j;
+    return true;
+#endif
+}
+// Blocks per SM the lattice kernels are compiled for (register budget): pass 1 with one or two rows per
+// thread, pass 2 with one, two or four.
+#ifndef TLSPH_LAT_GRAD_MINB
+#define TLSPH_LAT_GRAD_MINB 6
+#endif
+#ifndef TLSPH_LAT_P2_MINB
+#define TLSPH_LAT_P2_MINB 6
+#endif
+#ifndef TLSPH_LAT_P4_MINB
+#define TLSPH_LAT_P4_MINB 5
+#endif
+template <typename T, bool FRAC, bool VISC, int P> struct GradLatWalk {
+    const StepArgs<T> &a;
+    int NX, NXNY;
+    GradOwn<T, 3> o[P];
+    __device__ __forceinline__ GradRec<T> load(int j) const {
+        if (!lat_index_ok(a, j)) j = a.n;  // debug builds: read a zero record instead
+        return grad_load<T, FRAC, VISC>(a, j);
+    }
+    __device__ __forceinline__ void pair(int p, const GradRec<T> &r, int j, bool on) {
+        if (neighbour_ok(a, j, on)) grad_pair<T, 3, FRAC, VISC>(a, o[p], r, on);
+    }
+};
+// Pass 1 on the lattice: F - I and the viscosity and Laplacian sums of P rows per thread, then (FUSE)
+// their stress and what pass 2 takes of them in the same thread, or (!FUSE) F - I and the sums to
+// memory for a separate stress pass.
+template <typename T, bool FRAC, bool VISC, bool FUSE, int P, int BS>
+__global__ void __launch_bounds__(BS, FUSE ? 5 : (P == 1 ? 8 : TLSPH_LAT_GRAD_MINB)) k_gradient_lat(StepArgs<T> a) {
+    const int t = blockIdx.x * BS + threadIdx.x;
+    const int NX = a.lat_nx;
+    const int i0 = lat_first_row<P>(t, NX);
+    if (i0 >= a.n) return;
+    GradLatWalk<T, FRAC, VISC, P> w{a, NX, a.lat_nxny};
+    bool act[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        act[p] = i0 + p * NX < a.n;
+        grad_begin<T, 3, FRAC, VISC>(a, act[p] ? i0 + p * NX : i0, w.o[p]);
+    }
+    lat_walk<P>(w, a.lmask, a.n, i0, act);
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        if (!act[p]) continue;
+        const int i = i0 + p * NX;
+        T Gm[3][3], lap;
+        grad_finish<T, 3, FRAC>(a, i, w.o[p], Gm, lap);
+        if (FUSE) {
+            if (FRAC) a.LAP[i] = lap;
+            dev_stress<T, 3, FRAC, false>(a, i, Gm, w.o[p].s3);
+        } else {
+            grad_store<T, 3, FRAC, VISC>(a, i, w.o[p], Gm, lap);
+        }
+    }
+}
+
+template <typename T, int P> struct P2LatWalk {
+    const StepArgs<T> &a;
+    int NX, NXNY;
+    P2Own<T, 3> o[P];
+    __device__ __forceinline__ P2Rec<T> load(int j) const {
+        if (!lat_index_ok(a, j)) j = a.n;
+        return p2_load<T, 3>(a, j);
+    }
+    __device__ __forceinline__ void pair(int p, const P2Rec<T> &r, int j, bool on) {
+        if (neighbour_ok(a, j, on)) p2_pair<T, 3>(a, o[p], r, on);
+    }
+};
+// Pass 2 on the lattice: forces, damage, conditions and the update of P rows per thread; the last block
+// advances the clocks (as k_pass2).
+template <typename T, bool FRAC, bool VISC, int P, int BS>
+__global__ void __launch_bounds__(BS, P == 1 ? 8 : (P == 2 ? TLSPH_LAT_P2_MINB : TLSPH_LAT_P4_MINB)) k_pass2_lat(StepArgs<T> a) {
+    __shared__ bool s_last;
+    const int t = blockIdx.x * BS + threadIdx.x;
+    const int NX = a.lat_nx;
+    const int i0 = lat_first_row<P>(t, NX);
+    bool act[P];
+    T vmag[P], amag[P];
+    int sp[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        act[p] = i0 + p * NX < a.n;
+        vmag[p] = amag[p] = T(0);
+        sp[p] = 0;
+    }
+    if (act[0]) {
+        P2LatWalk<T, P> w{a, NX, a.lat_nxny};
+#pragma unroll
+        for (int p = 0; p < P; p++) p2_begin<T, 3>(a, act[p] ? i0 + p * NX : i0, w.o[p]);
+        lat_walk<P>(w, a.lmask, a.n, i0, act);
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            if (!act[p]) continue;
+            const int i = i0 + p * NX;
+            sp[p] = a.spec[i];
+            p2_finish<T, 3, FRAC, VISC>(a, i, w.o[p], vmag[p], amag[p]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; p++) dev_block_maxima<T, BS>(a, act[p], sp[p], vmag[p], amag[p]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        dev_finalize(a);
+        if (threadIdx.x == 0) *a.done = 0u;
+    }
+}
+
 // ---------------------------------------------------------------- persistent step loop
 // Bounded grid barrier of a cooperative launch: every block arrives once per phase; a
 // block that waits longer than limit_cycles (about a second) flags kFlagTimeout and all
@@ -878,9 +1038,11 @@ __global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps,
             const int i = base + threadIdx.x;
             if (i < n) {
                 prefetch_rows(a, i);
-                T Gm[DIM][DIM];
-                dev_gradient<T, DIM>(a, i, Gm);
-                dev_stress<T, DIM, FRAC, false>(a, i, Gm);
+                GradOwn<T, DIM> o;
+                T Gm[DIM][DIM], lap;
+                dev_gradient<T, DIM, FRAC, VISC>(a, i, o, Gm, lap);
+                if (FRAC) a.LAP[i] = lap;
+                dev_stress<T, DIM, FRAC, false>(a, i, Gm, o.s3);
             }
         }
         if (step > 0 && blockIdx.x == 0) dev_finalize(a);
@@ -1082,7 +1244,7 @@ __device__ __forceinline__ bool sur_apply(const StepArgs<float> &a, const Surrog
     a.K[4 * n + i] = Kn.a[2];
     a.K[5 * n + i] = Kn.a[5];
     a.ep[i] = a.ep[i] + fmaxf(yr[15], 0.0f);  // irreversible
-    dev_write_qvm_fi<float, DIM, FRAC>(a, i, Fi, P, 1.0f + kin.Jm1);
+    dev_write_qvm_fi<float, DIM>(a, i, Fi, P, 1.0f + kin.Jm1, 1.0f / m.rho, nullptr);
     return true;
 }
 

@@ -76,10 +76,15 @@ struct tlsph_ctx {
     int sten_groups = 1;          // stencil tables (one per specimen)
     int64_t halo = 0;             // zero elements before and after each gathered array (stencil layout)
     unsigned *nmask = nullptr;    // row masks over the stencil
+    int lat_nx = 0, lat_nxny = 0; // lattice walk (3D FP32 lattices): row and layer pitch, 0 = none
+    unsigned *lmask = nullptr;    // lattice walk: one mask word per layer, 7 arrays of n
+    int lat_rows_grad = 1, lat_rows_force = 2;  // rows per thread of the two lattice kernels
+    bool fuse_stress = false;     // the stress runs in the tail of the deformation-gradient kernel
     int layout = TLSPH_LAYOUT_AUTO;
     void *S1 = nullptr;  // sum_j V_j w_ij (X_j - X_i)
-    void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr}, *Vm = nullptr;
-    void *Qa = nullptr, *Qb = nullptr, *Qc = nullptr, *G = nullptr;
+    void *X0V = nullptr, *ug[2] = {nullptr, nullptr}, *vs[2] = {nullptr, nullptr};
+    void *S3 = nullptr, *Av = nullptr, *LAP = nullptr;  // viscosity sum, viscous acceleration, Laplacian
+    void *Qa = nullptr, *Qb = nullptr, *XQ = nullptr, *G = nullptr;
     void *Ahat = nullptr, *K = nullptr, *ep = nullptr, *H = nullptr, *sdot = nullptr;
     double *u64 = nullptr;
     uint16_t *mid = nullptr, *bcgrp = nullptr;
@@ -252,6 +257,8 @@ void free_device(tlsph_ctx *c) {
     c->runs = nullptr;
     c->soff = nullptr;
     c->nmask = nullptr;
+    c->lat_nx = c->lat_nxny = 0;
+    c->lmask = nullptr;
     c->Fd = c->Pd = c->psid = c->accd = nullptr;
     c->bar = nullptr;
     c->sur_W = nullptr;
@@ -350,7 +357,7 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.slice_off = c->slice_off;
     a.row_len = c->row_len;
     a.col = c->sell;
-    const bool sten = c->layout == TLSPH_LAYOUT_AUTO && c->nsten > 0;
+    const bool sten = c->layout != TLSPH_LAYOUT_CSR && c->nsten > 0;
     a.nsten = sten ? c->nsten : 0;
     a.nruns = sten ? c->nruns : 0;
     a.sten_groups = c->sten_groups;
@@ -358,6 +365,10 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.runs = sten ? c->runs : nullptr;
     a.soff = sten ? c->soff : nullptr;
     a.nmask = sten ? c->nmask : nullptr;
+    const bool lat = c->layout == TLSPH_LAYOUT_AUTO && c->lat_nx > 0;
+    a.lat_nx = lat ? c->lat_nx : 0;
+    a.lat_nxny = lat ? c->lat_nxny : 0;
+    a.lmask = lat ? c->lmask : nullptr;
     a.X0V = (const V4<T> *)c->X0V;
     a.S1 = (const V4<T> *)c->S1;
     a.ug_cur = (const V4<T> *)c->ug[cur];
@@ -366,9 +377,11 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.vs_next = (V4<T> *)c->vs[nxt];
     a.Qa = (V4<T> *)c->Qa;
     a.Qb = (V4<T> *)c->Qb;
-    a.Qc = (T *)c->Qc;
+    a.XQ = (V4<T> *)c->XQ;
     a.G = (T *)c->G;
-    a.Vm = (T *)c->Vm;
+    a.S3 = (T *)c->S3;
+    a.Av = c->has_visc ? (T *)c->Av : nullptr;
+    a.LAP = (T *)c->LAP;
     a.Ahat = (const T *)c->Ahat;
     a.K = (T *)c->K;
     a.ep = (T *)c->ep;
@@ -471,14 +484,79 @@ double algorithmic_bytes(const tlsph_ctx *c, size_t ts) {
     const int d = c->p.dim;
     const double n = (double)c->n, nnz = (double)c->nnz;
     const double v4 = 4.0 * ts, nsym = d == 3 ? 6 : 3, q = d * d * ts;
-    const double grad = n * (4 + 8.0 / 32 + 2 * v4 + nsym * ts + d * d * ts) + 4.0 * nnz;
-    double stress = n * (d * d * ts + nsym * ts + 2 + q + d * d * ts);
+    const double vi = c->has_visc ? 1 : 0, fr = c->has_frac ? 1 : 0;
+    // pass 1a: row, own X0V and u (and v, s for the viscosity or the Laplacian), Ahat; writes G, the
+    // viscosity sum, the Laplacian
+    const double grad = n * (4 + 8.0 / 32 + (2 + (vi + fr > 0 ? 1 : 0)) * v4 + nsym * ts + d * d * ts + vi * d * ts +
+                             fr * ts) + 4.0 * nnz;
+    // pass 1b: G, the viscosity sum, Ahat, material id, own X0V; writes V Q (3D with the position beside q22:
+    // three float4) and the viscous acceleration
+    double stress = n * (d * d * ts + nsym * ts + 2 + v4 + (d == 3 ? 3 * v4 : v4) + vi * 2 * d * ts);
     if (c->has_j2) stress += n * 2 * 7 * ts;
     if (c->has_frac) stress += n * (v4 + 2 * ts);
-    double p2 = n * (4 + 8.0 / 32 + 4 * v4 + q + 2 + 4 + 2 + 2 * 8.0 * d + 2 * v4) + 4.0 * nnz;  // + first moment
-    if (c->has_visc) p2 += n * d * d * ts;
-    if (c->has_frac) p2 += n * (nsym * ts + 3 * ts);
+    // pass 2: row, own X0V, v and s, first moment, Q, viscous acceleration, ids, FP64 u read and
+    // written, new u and v records; Laplacian, H and sdot with the phase field
+    const double p2 = n * (4 + 8.0 / 32 + 3 * v4 + q + vi * d * ts + 2 + 4 + 2 + 2 * 8.0 * d + 2 * v4 + fr * 4 * ts) +
+                      4.0 * nnz;
     return grad + stress + p2;
+}
+
+// Lattice walk (lattice.cuh) for a 3D stencil table whose differences all lie on the ball
+// dx + NX dy + NXNY dz, dx^2 + dy^2 + dz^2 <= 9.  NX is found from the entry (-2, 1, 0), the smallest
+// difference above 3; NXNY is the first difference above 3 NX + 3 under which every difference of the
+// table falls on the ball (the entry (0, 0, 1)).  A table that is not such a lattice keeps the stencil
+// walk.  The zero halo grows to the records the walk reads for up to four rows per thread.
+tlsph_status build_lattice(tlsph_ctx *c, const int *D, int nst) {
+    c->lat_nx = c->lat_nxny = 0;
+    int d1 = -1;
+    for (int s = 0; s < nst; s++)
+        if (D[s] > 3) {
+            d1 = D[s];
+            break;
+        }
+    if (d1 < 0) return TLSPH_OK;
+    const int64_t NX = (int64_t)d1 + 2;
+    if (NX < 8) return TLSPH_OK;
+    struct Pt { int dx, dy, dz; };
+    std::vector<Pt> ball;
+    for (int dz = -3; dz <= 3; dz++)
+        for (int dy = -3; dy <= 3; dy++)
+            for (int dx = -3; dx <= 3; dx++)
+                if (lat_entry(dx, dy, dz)) ball.push_back(Pt{dx, dy, dz});
+    std::vector<int2> map(nst);
+    int64_t NXNY = 0;
+    for (int s0 = 0; s0 < nst && NXNY == 0; s0++) {
+        if (D[s0] <= 3 * NX + 3) continue;
+        const int64_t cand = D[s0];
+        if (cand < 7 * NX) continue;  // layers must not overlap
+        bool all = true;
+        for (int s = 0; s < nst && all; s++) {
+            bool found = false;
+            for (const Pt &q : ball)
+                if (q.dx + NX * q.dy + cand * q.dz == (int64_t)D[s]) {
+                    map[s] = make_int2(q.dz + 3, lat_bit(q.dx, q.dy, q.dz));
+                    found = true;
+                    break;
+                }
+            all = found;
+        }
+        if (all) NXNY = cand;
+    }
+    if (NXNY == 0 || NXNY > (int64_t)1 << 30) return TLSPH_OK;
+    int64_t halo = c->halo;
+    for (int p = 0; p < 4; p++)
+        for (const Pt &q : ball) halo = std::max<int64_t>(halo, std::abs(q.dx + NX * (q.dy + p) + NXNY * q.dz));
+    int2 *map_d;
+    DA(map_d, nst * sizeof(int2));
+    DA(c->lmask, (size_t)kLatLayers * c->n * sizeof(unsigned));
+    CK(cudaMemcpyAsync(map_d, map.data(), nst * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
+    k_lattice_mask<<<blocks_for(c->n), kThreads, 0, c->stream>>>(c->n, nst, c->nmask, map_d, c->lmask);
+    CKL();
+    CK(cudaStreamSynchronize(c->stream));  // map is read before the host vector ends
+    c->halo = halo;
+    c->lat_nx = (int)NX;
+    c->lat_nxny = (int)NXNY;
+    return TLSPH_OK;
 }
 
 // Stencil layout of the CSR rows (lattice inputs), one table per specimen: the distinct pair
@@ -558,6 +636,7 @@ tlsph_status build_stencil(tlsph_ctx *c) {
     c->halo = halo;
     c->sten_groups = G;
     c->nsten = nmax;
+    if (G == 1 && c->p.dim == 3 && c->p.precision == TLSPH_FP32_U64) return build_lattice(c, D.data(), nst[0]);
     return TLSPH_OK;
 }
 
@@ -862,19 +941,22 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     DA(c->u64, 3 * n * sizeof(double));
     CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
     if (c->nsten > 0) {
-        c->Qa = c->Qb = c->Qc = nullptr;
+        c->Qa = c->Qb = c->XQ = nullptr;
         st = add_halo(c, c->Qa, sizeof(V4<T>), n);
         if (st == TLSPH_OK) st = add_halo(c, c->Qb, sizeof(V4<T>), dim == 3 ? n : 1);
-        if (st == TLSPH_OK) st = add_halo(c, c->Qc, sizeof(T), dim == 3 ? n : 1);
+        if (st == TLSPH_OK) st = add_halo(c, c->XQ, sizeof(V4<T>), dim == 3 ? n : 1);
         if (st != TLSPH_OK) return st;
     } else {
         DA(c->Qa, n * sizeof(V4<T>));
         DA(c->Qb, (dim == 3 ? n : 1) * sizeof(V4<T>));
-        DA(c->Qc, (dim == 3 ? n : 1) * sizeof(T));
+        DA(c->XQ, (dim == 3 ? n : 1) * sizeof(V4<T>));
     }
     CK(cudaMemsetAsync(c->Qa, 0, n * sizeof(V4<T>), s));
     DA(c->G, dim * dim * n * sizeof(T));
-    DA(c->Vm, dim * dim * n * sizeof(T));
+    DA(c->S3, dim * n * sizeof(T));
+    DA(c->Av, dim * n * sizeof(T));
+    DA(c->LAP, n * sizeof(T));
+    CK(cudaMemsetAsync(c->LAP, 0, n * sizeof(T), s));
     DA(c->K, 6 * n * sizeof(T));
     CK(cudaMemsetAsync(c->K, 0, 6 * n * sizeof(T), s));
     DA(c->ep, n * sizeof(T));
@@ -1060,7 +1142,42 @@ template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const
     return TLSPH_OK;
 }
 
-// ---- one step as three kernel launches (gradient, stress, force-and-damage)
+// ---- the lattice kernels (3D FP32 lattices): P rows per thread, 128 threads per block
+constexpr int kLatThreads = 128;
+inline unsigned lat_blocks(const tlsph_ctx *c, int P) {
+    const int64_t rows = (int64_t)P * c->lat_nx;
+    return blocks_for((c->n + rows - 1) / rows * c->lat_nx, kLatThreads);
+}
+template <bool FRAC, bool VISC> tlsph_status launch_gradient_lat(tlsph_ctx *c, const StepArgs<float> &a, bool fuse) {
+    const unsigned nb = lat_blocks(c, c->lat_rows_grad);
+    if (c->lat_rows_grad == 2) {
+        if (fuse) k_gradient_lat<float, FRAC, VISC, true, 2, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_gradient_lat<float, FRAC, VISC, false, 2, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+    } else {
+        if (fuse) k_gradient_lat<float, FRAC, VISC, true, 1, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_gradient_lat<float, FRAC, VISC, false, 1, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+    }
+    CKL();
+    return TLSPH_OK;
+}
+template <bool FRAC> tlsph_status launch_pass2_lat(tlsph_ctx *c, const StepArgs<float> &a) {
+    const unsigned nb = lat_blocks(c, c->lat_rows_force);
+    if (c->lat_rows_force == 4) {
+        if (c->has_visc) k_pass2_lat<float, FRAC, true, 4, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_pass2_lat<float, FRAC, false, 4, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+    } else if (c->lat_rows_force == 2) {
+        if (c->has_visc) k_pass2_lat<float, FRAC, true, 2, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_pass2_lat<float, FRAC, false, 2, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+    } else {
+        if (c->has_visc) k_pass2_lat<float, FRAC, true, 1, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_pass2_lat<float, FRAC, false, 1, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+    }
+    CKL();
+    return TLSPH_OK;
+}
+
+// ---- one step as three kernel launches (gradient, stress, force-and-damage); on a 3D FP32 lattice two
+// (the stress in the tail of the gradient kernel) unless the surrogate serves the stress
 template <typename T, int DIM, bool FRAC, int BS>
 tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
     const unsigned nb = blocks_for(c->n, BS);
@@ -1096,27 +1213,50 @@ tlsph_status step_launches(tlsph_ctx *c, int64_t nsteps, bool timing) {
             tlsph_status st = contact_launches<T, DIM>(c, a);
             if (st != TLSPH_OK) return st;
         }
-        k_gradient<T, DIM, BS><<<nb, BS, 0, c->stream>>>(a);
-        CKL();
-        stop(1);
-        start(2);
-        bool done_sur = false;
-        if constexpr (std::is_same<T, float>::value) {
-            if (c->sur_on) {
-                tlsph_status st = launch_stress_sur<DIM, FRAC>(c, a);
+        constexpr bool lat_ok = DIM == 3 && std::is_same<T, float>::value;
+        const bool lat = lat_ok && a.lat_nx > 0;
+        const bool fused = lat && c->fuse_stress && !c->sur_on;
+        if constexpr (lat_ok) {
+            if (lat) {
+                tlsph_status st = c->has_visc ? launch_gradient_lat<FRAC, true>(c, a, fused)
+                                              : launch_gradient_lat<FRAC, false>(c, a, fused);
                 if (st != TLSPH_OK) return st;
-                done_sur = true;
             }
         }
-        if (!done_sur) {
-            k_stress<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
+        if (!lat) {
+            if (c->has_visc) k_gradient<T, DIM, FRAC, true, BS><<<nb, BS, 0, c->stream>>>(a);
+            else k_gradient<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
             CKL();
         }
-        stop(2);
+        stop(1);
+        if (!fused) {
+            start(2);
+            bool done_sur = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (c->sur_on) {
+                    tlsph_status st = launch_stress_sur<DIM, FRAC>(c, a);
+                    if (st != TLSPH_OK) return st;
+                    done_sur = true;
+                }
+            }
+            if (!done_sur) {
+                k_stress<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
+                CKL();
+            }
+            stop(2);
+        }
         start(0);
-        if (c->has_visc) k_pass2<T, DIM, FRAC, true, BS><<<nb, BS, 0, c->stream>>>(a);
-        else k_pass2<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
-        CKL();
+        if constexpr (lat_ok) {
+            if (lat) {
+                tlsph_status st = launch_pass2_lat<FRAC>(c, a);
+                if (st != TLSPH_OK) return st;
+            }
+        }
+        if (!lat) {
+            if (c->has_visc) k_pass2<T, DIM, FRAC, true, BS><<<nb, BS, 0, c->stream>>>(a);
+            else k_pass2<T, DIM, FRAC, false, BS><<<nb, BS, 0, c->stream>>>(a);
+            CKL();
+        }
         stop(0);
         if (!c->leap) c->parity ^= 1;
         c->steps++;
@@ -1231,12 +1371,12 @@ template <typename T> tlsph_status diag_pass(tlsph_ctx *c) {
     StepArgs<T> a = make_args<T>(c);
     const unsigned nb = blocks_for(n);
     if (c->p.dim == 3) {
-        k_gradient<T, 3, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 3, false, false, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
         if (c->has_frac) k_stress<T, 3, true, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         else k_stress<T, 3, false, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
     } else {
-        k_gradient<T, 2, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, 2, false, false, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
         if (c->has_frac) k_stress<T, 2, true, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         else k_stress<T, 2, false, true, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
@@ -1956,7 +2096,10 @@ tlsph_status tlsph_get_info(tlsph_ctx *c, tlsph_info *out) {
     out->nnz = c->built ? c->nnz : -1;
     out->max_row = c->max_row;
     out->bytes_per_step = c->bytes_per_step;
-    out->stencil = (c->layout == TLSPH_LAYOUT_AUTO) ? c->nsten : 0;
+    out->stencil = (c->layout != TLSPH_LAYOUT_CSR) ? c->nsten : 0;
+    const bool lat = c->layout == TLSPH_LAYOUT_AUTO && c->lat_nx > 0;
+    out->lattice_nx = lat ? c->lat_nx : 0;
+    out->lattice_nxny = lat ? c->lat_nxny : 0;
     out->noconverge = out->nonfinite = 0;
     if (c->built) {
         int hf[kNumFlags];
@@ -2006,8 +2149,21 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
         return TLSPH_OK;
     }
     if (option == TLSPH_OPT_NEIGHBOUR_LAYOUT) {
-        if (value != TLSPH_LAYOUT_AUTO && value != TLSPH_LAYOUT_CSR) return fail(c, TLSPH_ERR_ARG, "bad layout");
+        if (value != TLSPH_LAYOUT_AUTO && value != TLSPH_LAYOUT_CSR && value != TLSPH_LAYOUT_STENCIL)
+            return fail(c, TLSPH_ERR_ARG, "bad layout");
         c->layout = value;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_LATTICE_ROWS_GRADIENT || option == TLSPH_OPT_LATTICE_ROWS_FORCE) {
+        if (value != 1 && value != 2 && !(value == 4 && option == TLSPH_OPT_LATTICE_ROWS_FORCE))
+            return fail(c, TLSPH_ERR_ARG, "rows per thread must be 1 or 2 (or 4 in the force kernel)");
+        (option == TLSPH_OPT_LATTICE_ROWS_GRADIENT ? c->lat_rows_grad : c->lat_rows_force) = value;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_FUSE_STRESS) {
+        c->fuse_stress = value != 0;
         drop_graph(c);
         return TLSPH_OK;
     }
@@ -2662,7 +2818,7 @@ tlsph_status tlsph_j2_samples(tlsph_ctx *c, int stride_elastic, int stride_plast
         using T = decltype(tag);
         constexpr int D = decltype(dimc)::value;
         StepArgs<T> a = make_args<T>(c);
-        k_gradient<T, D, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
+        k_gradient<T, D, false, false, kThreads><<<nb, kThreads, 0, c->stream>>>(a);
         CKL();
         k_j2_samples<T, D, false><<<nb, kThreads, 0, c->stream>>>(a, stride_elastic, stride_plastic, salt, flag,
                                                                    nullptr, x, y, pnorm, cap);

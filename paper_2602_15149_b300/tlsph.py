@@ -24,7 +24,8 @@ FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "
          "STATE": 100}
 OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6
 OPT_MEMORY_LIMIT = 7
-LAYOUT_AUTO, LAYOUT_CSR = 0, 1
+OPT_LATTICE_ROWS_GRADIENT, OPT_LATTICE_ROWS_FORCE, OPT_FUSE_STRESS = 8, 9, 10
+LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_STENCIL = 0, 1, 2
 MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 INTEGRATOR_EULER, INTEGRATOR_LEAPFROG = 1, 2
 MODE_NAMES = {MODE_LAUNCH: "launch", MODE_GRAPH: "graph", MODE_PERSISTENT: "persistent"}
@@ -63,7 +64,7 @@ class Material(C.Structure):
 class Info(C.Structure):
     _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("noconverge", C.c_int64),
                 ("nonfinite", C.c_int64), ("nnz", C.c_int64), ("max_row", C.c_int64), ("bytes_per_step", C.c_double),
-                ("stencil", C.c_int64)]
+                ("stencil", C.c_int64), ("lattice_nx", C.c_int64), ("lattice_nxny", C.c_int64)]
 
 
 class Tuning(C.Structure):

@@ -67,3 +67,60 @@ def test_irregular_particles_keep_sell_rows():
     assert g.get_info()["stencil"] == 0
     g.step(10)
     assert np.all(np.isfinite(g.read_state("U")))
+
+
+def pf_block(nx=16, ny=12, nz=10):
+    """3D jittered block of a brittle SVK solid with the phase field, pressed at 1 m/s after a ramp."""
+    case = W.block_3d(nx=nx, ny=ny, nz=nz, jitter=0.01, seed=5, v_press=1.0)
+    case.materials = [W.Material(model=W.MODEL_SVK, rho=2450.0, E=32e9, nu=0.2, beta1=0.2, fracture=1, Gc=30.0,
+                                 eps0=2.0 * case.dp, s_lim=0.1)]
+    case.bcs[1].ramp = 300 * 0.3 * case.h / W.REF_WAVE_SPEED
+    return case
+
+
+# (case, nx, ny)
+LATTICE_CASES = {
+    "block_j2": (lambda: W.block_3d(nx=24, ny=20, nz=16), 24, 20),
+    # odd y and z counts: the two rows of a thread straddle a z plane, and the last thread has one row
+    "block_j2_odd_planes": (lambda: W.block_3d(nx=40, ny=9, nz=7), 40, 9),
+    # without jitter no pair lies at exactly 3 dp: the table holds 92 of the ball's 122 entries
+    "block_j2_no_jitter": (lambda: W.block_3d(nx=20, ny=18, nz=10, jitter=0.0), 20, 18),
+    "svk_phase_field_block": (pf_block, 16, 12),
+}
+
+
+@pytest.mark.parametrize("which", sorted(LATTICE_CASES))
+@pytest.mark.parametrize("rows", [(1, 2), (2, 1), (1, 1), (2, 2), (1, 4), (2, 4)])
+@pytest.mark.parametrize("fuse", [1, 0])
+def test_lattice_layout_is_bit_identical_to_stencil_and_csr(which, rows, fuse):
+    # the lattice kernels walk the ball at compile time, rows per thread 1 or 2, with the stress in the
+    # gradient kernel or in its own pass: same pairs, same order, same arithmetic as the table walks
+    make, nx, ny = LATTICE_CASES[which]
+    case = make()
+    lat, sten, csr = tlsph.from_case(case), tlsph.from_case(case), tlsph.from_case(case)
+    sten.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, tlsph.LAYOUT_STENCIL)
+    csr.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, tlsph.LAYOUT_CSR)
+    lat.set_option(tlsph.OPT_LATTICE_ROWS_GRADIENT, rows[0])
+    lat.set_option(tlsph.OPT_LATTICE_ROWS_FORCE, rows[1])
+    lat.set_option(tlsph.OPT_FUSE_STRESS, fuse)
+    info = lat.get_info()
+    assert info["lattice_nx"] == nx and info["lattice_nxny"] == nx * ny, info
+    assert sten.get_info()["lattice_nx"] == 0 and sten.get_info()["stencil"] > 0
+    assert csr.get_info()["lattice_nx"] == 0 and csr.get_info()["stencil"] == 0
+    for g in (lat, sten, csr):
+        g.step(120)
+    for f in ("U", "V", "S", "P", "F", "EPSP"):
+        a, b, c = lat.read_state(f), sten.read_state(f), csr.read_state(f)
+        assert np.array_equal(a, b), f
+        assert np.array_equal(a, c), f
+    assert lat.time() == sten.time() == csr.time()
+    assert lat.get_info()["kernel_launches"] < sten.get_info()["kernel_launches"] or not fuse
+
+
+def test_lattice_layout_only_where_it_applies():
+    # FP64, 2D, several specimens and a jitter that reaches the next lattice shell keep the table walks
+    assert tlsph.from_case(W.block_3d(nx=16, ny=14, nz=12, precision="fp64")).get_info()["lattice_nx"] == 0
+    assert tlsph.from_case(W.plate_2d(nx=100, ny=21, precision="fp32")).get_info()["lattice_nx"] == 0
+    wide = tlsph.from_case(W.block_3d(nx=16, ny=16, nz=12, jitter=0.08))
+    assert wide.get_info()["stencil"] > 122 or wide.get_info()["stencil"] == 0
+    assert wide.get_info()["lattice_nx"] == 0
