@@ -403,6 +403,12 @@ static double j2_residual(const double *N, const double *Fpn, const double *C, d
  * reading (tolerances, not given in the paper): bracket epsilon
  * 1e-12 sigma_y/mu, at most 60 doublings, stop at |r| <= 1e-10 sigma_y0 or
  * |R - L| <= 1e-14 R, at most 100 Illinois iterations.
+ * reading (the bracket): r(dgamma) of eq. J2_residual falls from r(0) = f > 0
+ * to about -sigma_y where the frozen flow has removed the deviatoric stress and
+ * rises again beyond, so it has a root below that minimum.  A doubling step that
+ * lands past the minimum with r still positive (r rose) has stepped over the
+ * negative interval; a golden-section search for the minimum of r between the
+ * last two points then stops at the first point with r <= 0.
  */
 int orc_j2_update(const double *F, const double *Fpn, double epn, const orc_material *m, double *Fp_out,
                   double *ep_out, double *S, double *dgamma, int *iters) {
@@ -437,11 +443,39 @@ int orc_j2_update(const double *F, const double *Fpn, double epn, const orc_mate
         double R = (sig_tr - syn) / (3.0 * mu + Hh);
         if (R < eps_b) R = eps_b;
         double rR = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, R);
+        double Rp = 0.0; /* the point before R (r(0) = f > 0) */
         int nd = 0;
         while (rR > 0.0 && nd < 60) { /* double the upper end until r(R) <= 0 */
-            R *= 2.0;
-            rR = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, R);
+            double Rn = 2.0 * R;
+            double rn = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, Rn);
             nd++;
+            if (rn > 0.0 && rn >= rR) {
+                /* past the minimum of r without a sign change: golden-section search on [Rp, Rn] */
+                const double g = 0.6180339887498949;
+                double a = Rp, b = Rn;
+                double c1 = b - g * (b - a), d1 = a + g * (b - a);
+                double rc = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, c1);
+                double rd = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, d1);
+                int found = 0;
+                for (int k = 0; k < 80 && !found; k++) {
+                    if (rc <= 0.0) { R = c1; rR = rc; found = 1; break; }
+                    if (rd <= 0.0) { R = d1; rR = rd; found = 1; break; }
+                    if (rc < rd) {
+                        b = d1; d1 = c1; rd = rc;
+                        c1 = b - g * (b - a);
+                        rc = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, c1);
+                    } else {
+                        a = c1; c1 = d1; rc = rd;
+                        d1 = a + g * (b - a);
+                        rd = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, d1);
+                    }
+                }
+                if (!found) { R = Rn; rR = rn; }
+                break;
+            }
+            Rp = R;
+            R = Rn;
+            rR = rn;
         }
         if (!(rR <= 0.0)) status = 1;
         double x = R, rx = rR;

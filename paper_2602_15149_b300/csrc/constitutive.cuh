@@ -438,15 +438,62 @@ TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6
         r.sy0 = m.sy0;
         r.Hh = m.Hh;
         r.epn = ep;
-        // bracket: L = 0, R = max((sigma_tr - sigma_y) / (3 mu + H), eps), doubled until r(R) <= 0
+        // bracket: L = 0, R = max((sigma_tr - sigma_y) / (3 mu + H), eps), doubled until r(R) <= 0.  r falls
+        // from f to about -sigma_y where the frozen flow has removed the deviator and rises again beyond:
+        // a doubling that lands past that minimum with r still positive (r rose) has stepped over the
+        // negative interval, and a golden-section search for the minimum on the last interval stops at
+        // the first point with r <= 0.
         T L = T(0), rL = f;
         T eps_b = T(1e-12) * syn / m.mu;
         const T R0 = t_max(f / (T(3) * m.mu + m.Hh), eps_b);
         T R = R0;
         T rR = r(R);
+        T Rp = T(0);
         for (int nd = 0; rR > T(0) && nd < 60; nd++) {
-            R *= T(2);
-            rR = r(R);
+            const T Rn = T(2) * R;
+            const T rn = r(Rn);
+            if (rn > T(0) && rn >= rR) {
+                const T g = T(0.6180339887498949);
+                T a = Rp, b = Rn;
+                T c1 = b - g * (b - a), d1 = a + g * (b - a);
+                T rc = r(c1), rd = r(d1);
+                bool found = false;
+                for (int k = 0; k < 80; k++) {
+                    if (rc <= T(0)) {
+                        R = c1;
+                        rR = rc;
+                        found = true;
+                        break;
+                    }
+                    if (rd <= T(0)) {
+                        R = d1;
+                        rR = rd;
+                        found = true;
+                        break;
+                    }
+                    if (rc < rd) {
+                        b = d1;
+                        d1 = c1;
+                        rd = rc;
+                        c1 = b - g * (b - a);
+                        rc = r(c1);
+                    } else {
+                        a = c1;
+                        c1 = d1;
+                        rc = rd;
+                        d1 = a + g * (b - a);
+                        rd = r(d1);
+                    }
+                }
+                if (!found) {
+                    R = Rn;
+                    rR = rn;
+                }
+                break;
+            }
+            Rp = R;
+            R = Rn;
+            rR = rn;
         }
         T x = R;
         if (!(rR <= T(0))) {

@@ -7,6 +7,7 @@ a textbook result.  None needs a GPU.
 import math
 
 import numpy as np
+from scipy.optimize import brentq
 import pytest
 import scipy.linalg as sla
 
@@ -332,10 +333,7 @@ def test_j2_frame_indifference_and_unloading():
 
 
 def test_j2_converges_on_large_increments():
-    """Illinois with bracket doubling converges for trial stresses up to twice the yield stress.
-
-    (Beyond about 2 sigma_y the doubled bracket can step over the minimum of sigma_eq along the frozen
-    flow direction; explicit steps stay far below that.)"""
+    """Illinois with bracket doubling converges for trial stresses up to twice the yield stress."""
     rng = np.random.default_rng(13)
     for e in [0.0015, 0.002, 0.0025]:
         F = _trial_F(rng, e, 2e-3)
@@ -343,6 +341,56 @@ def test_j2_converges_on_large_increments():
         assert r["status"] == 0 and r["iters"] < 40
         sig = _sigma_eq_from_state(F, r["Fp"], STEEL_J2)
         assert abs(sig - (STEEL_J2.sigma_y0 + STEEL_J2.H_hard * r["ep"])) <= 1e-8 * sig
+
+
+def _j2_first_root(F, mat):
+    """The smallest root of eq. J2_residual along the frozen trial flow direction from F_p = I, found
+    independently of the oracle: scipy's expm for the flow, a dense scan for the first sign change and
+    brentq inside it."""
+    lam, mu = lame(mat.E, mat.nu)
+    C = F.T @ F
+    J = np.linalg.det(F)
+
+    def seq(Fp):
+        Fpi = np.linalg.inv(Fp)
+        Cb = J ** (-2 / 3) * (Fpi.T @ C @ Fpi)
+        M = mu * (Cb - np.trace(Cb) / 3 * np.eye(3))
+        return math.sqrt(1.5 * np.sum(M * M)), M
+
+    s0, M0 = seq(np.eye(3))
+    N = 1.5 / s0 * M0
+
+    def r(dg):
+        Fp = sla.expm(dg * N)
+        Fp = Fp * np.linalg.det(Fp) ** (-1 / 3)
+        return seq(Fp)[0] - (mat.sigma_y0 + mat.H_hard * dg)
+
+    x = np.linspace(0.0, 4.0 * (s0 - mat.sigma_y0) / (3 * mu), 801)[1:]
+    rv = np.array([r(v) for v in x])
+    k = int(np.argmax(rv <= 0.0))
+    assert rv[k] <= 0.0
+    return s0, brentq(r, x[k - 1] if k else 0.0, x[k], xtol=1e-18, rtol=1e-14)
+
+
+def test_j2_far_outside_the_yield_surface_finds_the_first_root():
+    """Trial stresses of 2 to 6 sigma_y (one random strain increment of 0.3%): the residual of
+    eq. J2_residual is V-shaped along the frozen flow, and doubling the bracket from the small-strain
+    estimate steps over its negative interval.  The search must still stop at the first root, the one
+    an independent scan with scipy's matrix exponential finds, on the yield surface."""
+    rng = np.random.default_rng(1)
+    seen = 0
+    for _ in range(20):
+        F = np.eye(3) + rng.normal(scale=3e-3, size=(3, 3))
+        r = O.j2_update(F, np.eye(3), 0.0, STEEL_J2)
+        s0, dg_ref = _j2_first_root(F, STEEL_J2)
+        if s0 <= STEEL_J2.sigma_y0:
+            continue
+        seen += s0 > 3.5 * STEEL_J2.sigma_y0
+        assert r["status"] == 0
+        assert abs(r["dgamma"] - dg_ref) <= 1e-9 * dg_ref
+        sig = _sigma_eq_from_state(F, r["Fp"], STEEL_J2)
+        assert abs(sig - (STEEL_J2.sigma_y0 + STEEL_J2.H_hard * r["ep"])) <= 1e-8 * sig
+    assert seen >= 5  # the cases a plain doubling misses
 
 
 # ---------------------------------------------------------------- phase field
