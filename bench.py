@@ -12,7 +12,7 @@ autotuned launch) and the learned form (the J2 update served by a network traine
 return-map samples of this block, against the plain step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--no-batched] [--no-surrogate] [--no-cpu]
+                    [--no-batched] [--no-surrogate] [--no-cpu] [--paper-cases]
 
 Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
 method as plainly written, test infrastructure) on a bounded sample of the
@@ -45,10 +45,11 @@ SHAPE = (128, 128, 64)
 FALLBACK_HBM_GBS = 6400.0
 FALLBACK_BF16_TFLOPS = 1400.0
 MLP_FLOP_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16)  # 73,728
-# FP32 operations per neighbour pair of the 3D J2 step with viscosity, counted from the loop bodies
-# (an FMA counts 2; rsqrt 1): k_gradient 38; k_pass2 54, plus 15 for a pair in relative compression
-# (taken as half of the pairs).  Peak: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz.
-FLOP_PER_PAIR = {"gradient": 38.0, "pass2": 54.0 + 0.5 * 15.0}
+# FP32 operations per neighbour pair of the 3D J2 step with viscosity, counted from the pair bodies
+# (an FMA counts 2; rsqrt, reciprocal 1): the deformation-gradient pass 39 for F - I plus 28 for the
+# viscosity sum (3D computes it for every pair and keeps it for pairs in compression); the force pass
+# 35.  Peak: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz.
+FLOP_PER_PAIR = {"gradient": 39.0 + 28.0, "pass2": 35.0}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 # DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
@@ -107,25 +108,35 @@ def kernel_bytes(dim, nnz, n, ts=4, j2=True, frac=False, visc=True, fused=False)
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running.  mark(t0, t1) sets the
+    window the summary covers (host wall-clock seconds); ensure_sample() keeps the GPU busy with the
+    same work until a sample lands in that window when the timed region was shorter than the
+    sampling interval."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
         self.index = index
         self.proc = None
         self.path = os.path.join(tempfile.gettempdir(), f"tlsph_clocks_{os.getpid()}.csv")
+        self.window = None
+        self.extended_s = 0.0
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # wait for nvidia-smi's first line, so that sampling runs before the timed region starts
+        t0 = time.time()
+        while self.proc and time.time() - t0 < 5.0 and not self._rows():
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
@@ -134,27 +145,54 @@ class ClockSampler:
             self.proc.wait()
             self.f.close()
 
-    def summary(self):
-        if not self.proc or not os.path.exists(self.path):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm, smax, reasons = [], [], set()
+    def _rows(self):
+        """(host time, sm MHz, max MHz, reasons) of every sample written so far."""
+        import datetime
+        out = []
+        if not os.path.exists(self.path):
+            return out
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, smax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for k, nm in enumerate(names):
-                if f[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+            out.append((ts, sm, smax, {nm for k, nm in enumerate(names) if f[6 + k].lower().startswith("active")}))
+        return out
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def ensure_sample(self, busy, limit_s=3.0):
+        """If no sample lies in the window, call busy() (more of the same steps, untimed) until one lands."""
+        if not self.proc or self.window is None:
+            return
+        t0, t1 = self.window
+        start = time.time()
+        while not [r for r in self._rows() if t0 <= r[0] <= t1 + self.extended_s] and time.time() - start < limit_s:
+            busy()
+            self.extended_s = time.time() - t1
+        self.extended_s = max(self.extended_s, 0.0)
+
+    def summary(self):
+        rows = self._rows()
+        if self.window is not None:
+            t0, t1 = self.window
+            rows = [r for r in rows if t0 <= r[0] <= t1 + self.extended_s]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set()
+        for r in rows:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "window": ("the timed region" if self.extended_s == 0.0 else
+                           f"the timed region and {self.extended_s:.2f} s more of the same steps (the region was "
+                           f"shorter than the 200 ms sampling interval)")}
 
 
 def dist_env():
@@ -284,12 +322,20 @@ def measure_batched(args, device, stream):
     particles = int(sum_over_ranks(case.n, dev))
     info = g.get_info()
     g.close()
+    # algorithmic bytes of one step of this rank's specimens (the library's model: own records once per
+    # pass, 4 B per neighbour pair per neighbour pass), summed over ranks, against the measured copy peak
+    step_bytes = sum_over_ranks(info["bytes_per_step"], dev)
+    peak, peak_src = peaks()
+    achieved = step_bytes / (ms / steps * 1e-3) / 1e9
     return {"workload": f"batched_2d {args.batch_specimens} specimens, {particles} particles, "
                         f"log-uniform 500-50k each, NH/J2, own clocks", "particles": particles,
             "specimens": args.batch_specimens, "steps": steps, "ms_per_step": ms / steps,
             "value": particles * steps / (ms * 1e-3), "unit": UNIT, "tuned": best, "candidates": allt,
             "sharding": f"specimens by rank ({ws} ranks, no collective on the data path)",
-            "setup_s": setup_s, "status": int(st), "mean_neighbours": info["nnz"] / case.n}
+            "setup_s": setup_s, "status": int(st), "mean_neighbours": info["nnz"] / case.n,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src, "algorithmic_bytes_per_step": step_bytes,
+                         "bytes_per_particle_step": step_bytes / particles}}
 
 
 def timed_steps(g, steps, stream, dev):
@@ -488,12 +534,13 @@ def measure_surrogate(args, shape, device, stream, plain):
     from paper_2602_15149_b300 import surrogate, tlsph
 
     dev = torch.device("cuda", device)
-    case = W.block_3d(*shape, steps=args.steps)
+    steps = args.sur_steps  # the configuration's run length, whatever --steps the headline takes
+    case = W.block_3d(*shape, steps=steps)
     n = case.n
     every = 20
-    points = max(1, args.steps // every)
+    points = max(1, steps // every)
     t0 = time.perf_counter()
-    x, y, pn = surrogate.generate_samples(case, n_target=args.sur_samples, steps=args.steps, every=every,
+    x, y, pn = surrogate.generate_samples(case, n_target=args.sur_samples, steps=steps, every=every,
                                       stride_elastic=16, stride_plastic=8, device=device,
                                       stream=stream.cuda_stream, per_call=2 * args.sur_samples // points)
     gen_s = time.perf_counter() - t0
@@ -507,11 +554,16 @@ def measure_surrogate(args, shape, device, stream, plain):
     del x, y, pn
     torch.cuda.empty_cache()
 
+    # the plain (exact) step over the same steps: the reference of both accuracy and speed
     exact = tlsph.from_case(case, device=device, stream=stream.cuda_stream)
-    exact.step(args.steps)
+    exact.step(args.warmup)
+    ms_exact, st_exact = timed_steps(exact, steps - args.warmup, stream, dev)
     ue, epe = exact.read_state("U"), exact.read_state("EPSP")
     exact.close()
-    out = {"workload": f"block_3d_j2 {'x'.join(map(str, shape))}, same as the plain step",
+    plain_value = n * (steps - args.warmup) / (ms_exact * 1e-3)
+    out = {"workload": f"block_3d_j2 {'x'.join(map(str, shape))}, {steps} steps (the configuration's run), "
+                       f"samples every {every} steps of the exact run", "steps": steps,
+           "plain": {"ms_per_step": ms_exact / (steps - args.warmup), "value": plain_value, "status": st_exact},
            "samples": m, "train_samples": ntr, "sample_gen_s": gen_s, "training": info, "stress_error": err,
            "network": "16-128-128-128-16 SiLU, bf16 weights, fp32 accumulation (tcgen05.mma with TMEM "
                       "accumulators; mma.sync m16n8k16 for comparison)"}
@@ -523,26 +575,27 @@ def measure_surrogate(args, shape, device, stream, plain):
         g.set_surrogate(net, scope)
         net.set_tensor_path(tlsph.TENSOR_TCGEN05)
         g.step(args.warmup)
-        ms, st = timed_steps(g, args.steps - args.warmup, stream, dev)
-        steps_t = args.steps - args.warmup
+        ms, st = timed_steps(g, steps - args.warmup, stream, dev)
+        steps_t = steps - args.warmup
         used, outside, elastic = g.surrogate_counts()
         noconv = g.get_info()["noconverge"]
         us, eps = g.read_state("U"), g.read_state("EPSP")
         g.set_option(tlsph.OPT_KERNEL_TIMING, 1)
-        g.step(min(args.steps, 100))
+        g.step(100)
         kt = g.kernel_times()
         g.close()
         stress_ms = kt["stress_ms"] / max(kt["stress_launches"], 1)
-        mlp_rows = used / max(args.steps, 1)  # network rows per launch (warm-up + timed steps)
+        mlp_rows = used / max(steps, 1)  # network rows per launch (warm-up + timed steps)
         tflops = MLP_FLOP_PER_ROW * mlp_rows / (stress_ms * 1e-3) / 1e12
         peak, src = bf16_peak()
         out[name] = {"tensor_path": "tcgen05" if path == tlsph.TENSOR_TCGEN05 else "mma.sync",
                      "ms_per_step": ms / steps_t, "value": n * steps_t / (ms * 1e-3), "unit": UNIT,
-                     "vs_plain": (n * steps_t / (ms * 1e-3)) / plain["value"],
+                     "vs_plain": (n * steps_t / (ms * 1e-3)) / plain_value,
                      "status": st, "noconverge": noconv, "rows_network": used, "rows_outside_envelope": outside,
                      "rows_elastic_exact": elastic,
                      "network_fraction": used / max(used + outside + elastic, 1),
                      "stress_kernel_ms": stress_ms, "plain_stress_kernel_ms": plain["stress_ms"],
+                     "stress_error_p99": err["p99"],
                      "rel_l2_u_vs_exact": float(np.linalg.norm(us - ue) / np.linalg.norm(ue)),
                      "max_abs_eps_p_diff": float(np.abs(eps - epe).max()),
                      "tensor": {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
@@ -581,11 +634,14 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        t_a = time.time()
         e0.record(stream)
         g.step_async(args.steps)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    st = g.sync(check=False)
+        clk.mark(t_a, time.time())
+        st = g.sync(check=False)
+        clk.ensure_sample(lambda: (g.step_async(200), torch.cuda.synchronize(dev)))
     barrier()
     ms = e0.elapsed_time(e1)
     launches = g.get_info()["kernel_launches"] - l0
@@ -614,24 +670,31 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     g2 = tlsph.from_case(case, device=local, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
     for _ in range(args.steps):
         g2.step(1)
     u = g2.read_state("U")
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
+    e2e_steps_s = time.perf_counter() - t1
     g2.close()
     e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_steps_s = max_over_ranks(e2e_steps_s, dev)
+    e2e_setup_s = e2e_s - e2e_steps_s
     h2d = n * (8 * 3 + 8 + 4 + 8 * 3) + sum(n for _ in case.bcs)
     d2h = u.nbytes + 8 * 4 * args.steps
 
     batched = measure_batched(args, local, stream) if not args.no_batched else None
     sur = measure_surrogate(args, shape, local, stream, plain) if not args.no_surrogate else None
-    leapfrog = measure_leapfrog(args, shape, local, stream, plain)
-    phase_field = measure_phase_field(args, local, stream)
-    crack_b = measure_crack_branching(args, local, stream) if not args.no_crack else None
-    flyer = measure_flyer_plate(args, local, stream) if not args.no_crack else None
-    taylor = measure_taylor_bar(args, local, stream) if not args.no_crack else None
-    variants = measure_model_variants(args, shape, local, stream) if not args.no_crack else None
+    # the paper's reproductions and the other integrator / laws: opt-in (--paper-cases)
+    paper = args.paper_cases
+    leapfrog = measure_leapfrog(args, shape, local, stream, plain) if paper else None
+    phase_field = measure_phase_field(args, local, stream) if paper else None
+    crack_b = measure_crack_branching(args, local, stream) if paper else None
+    flyer = measure_flyer_plate(args, local, stream) if paper else None
+    taylor = measure_taylor_bar(args, local, stream) if paper else None
+    variants = measure_model_variants(args, shape, local, stream) if paper else None
     if rank != 0:
         return 0
     cpu = oracle_sample() if not args.no_cpu else None
@@ -646,7 +709,9 @@ def run_ours(args):
         "config": {"workload": f"block_3d_j2 {'x'.join(map(str, shape))} jittered lattice, J2 plasticity, top "
                                "pressed at 5 m/s (FP32 fields, FP64 displacement)", "particles": n, "neighbour_pairs": nnz,
                    "mean_neighbours": nnz / n, "l2": "inputs larger than L2 (~1.3 GB of state), no flush",
-                   "neighbour_layout": (f"stencil ({info['stencil']} differences, 16 B row masks)"
+                   "neighbour_layout": (f"lattice (ball of 122 entries, NX {info['lattice_nx']}, NXNY "
+                                        f"{info['lattice_nxny']}, one mask word per layer)" if info["lattice_nx"] else
+                                        f"stencil ({info['stencil']} differences, 16 B row masks)"
                                         if info["stencil"] else "SELL-32 CSR rows"),
                    "parallelism": f"replicas x{ws} (independent blocks)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -663,10 +728,18 @@ def run_ours(args):
                 "step": sum(FLOP_PER_PAIR.values()) * nnz / (ms / args.steps * 1e-3) / 1e12},
         "clocks": clk.summary(),
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                "d2h_bytes_per_step": d2h / args.steps},
+                "d2h_bytes_per_step": d2h / args.steps, "setup_s": e2e_setup_s,
+                "steps_value": ws * n * args.steps / e2e_steps_s,
+                "note": "value includes the reference setup (sort, neighbour rows, masks) from host arrays; "
+                        "steps_value is the stepping alone, a status read back after every step"},
         "gpu_launches": launches,
         "batched": batched,
         "surrogate": sur,
+        "surrogate_vs_plain": sur["all"]["vs_plain"] if sur else None,
+        "surrogate_status": sur["all"]["status"] if sur else None,
+        "surrogate_noconverge": sur["all"]["noconverge"] if sur else None,
+        "surrogate_stress_err_p99": sur["stress_error"]["p99"] if sur else None,
+        "surrogate_rel_l2_u": sur["all"]["rel_l2_u_vs_exact"] if sur else None,
         "leapfrog": leapfrog,
         "phase_field": phase_field,
         "crack_branching": crack_b,
@@ -692,7 +765,12 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-specimens measurement")
     ap.add_argument("--batch-specimens", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
-    ap.add_argument("--no-crack", action="store_true", help="skip the crack-branching, flyer-plate and Taylor-bar cases")
+    ap.add_argument("--paper-cases", action="store_true",
+                    help="also run the paper's reproductions (crack branching, flyer plate, Taylor bar, the five "
+                         "material variants and the size study), Algorithm 2 and the phase-field plate")
+    ap.add_argument("--sur-steps", type=int, default=2000,
+                    help="run length of the surrogate leg: samples, exact run and network run (the "
+                         "configuration's 2000 steps, whatever --steps is)")
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
     ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")

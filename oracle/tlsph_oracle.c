@@ -408,7 +408,8 @@ static double j2_residual(const double *N, const double *Fpn, const double *C, d
  * rises again beyond, so it has a root below that minimum.  A doubling step that
  * lands past the minimum with r still positive (r rose) has stepped over the
  * negative interval; a golden-section search for the minimum of r between the
- * last two points then stops at the first point with r <= 0.
+ * last two points then stops at the first point with r <= 0 (and the doubling
+ * goes on if it finds none: near r = 0 rounding alone can make r rise).
  */
 int orc_j2_update(const double *F, const double *Fpn, double epn, const orc_material *m, double *Fp_out,
                   double *ep_out, double *S, double *dgamma, int *iters) {
@@ -470,8 +471,8 @@ int orc_j2_update(const double *F, const double *Fpn, double epn, const orc_mate
                         rd = j2_residual(N, Fpn, C, J, mu, sy0, Hh, epn, d1);
                     }
                 }
-                if (!found) { R = Rn; rR = rn; }
-                break;
+                if (found) break;
+                /* no point below zero (r rose only by rounding near r = 0): keep doubling */
             }
             Rp = R;
             R = Rn;

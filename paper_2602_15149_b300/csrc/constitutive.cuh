@@ -442,7 +442,8 @@ TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6
         // from f to about -sigma_y where the frozen flow has removed the deviator and rises again beyond:
         // a doubling that lands past that minimum with r still positive (r rose) has stepped over the
         // negative interval, and a golden-section search for the minimum on the last interval stops at
-        // the first point with r <= 0.
+        // the first point with r <= 0 (the doubling goes on if it finds none: near r = 0 rounding alone
+        // can make r rise).
         T L = T(0), rL = f;
         T eps_b = T(1e-12) * syn / m.mu;
         const T R0 = t_max(f / (T(3) * m.mu + m.Hh), eps_b);
@@ -485,11 +486,8 @@ TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6
                         rd = r(d1);
                     }
                 }
-                if (!found) {
-                    R = Rn;
-                    rR = rn;
-                }
-                break;
+                if (found) break;
+                // no point below zero (r rose only by rounding near r = 0): keep doubling
             }
             Rp = R;
             R = Rn;

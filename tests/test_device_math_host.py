@@ -5,6 +5,7 @@ with nvcc as host code, so the GPU's SVK (spectral split), NH and J2 (C_p^-1 for
 the CPU in both FP64 and FP32, without a GPU.
 """
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -73,6 +74,23 @@ def test_j2_cpinv_form_matches_fp_oracle(hc, prec, tol):
         assert np.abs(Cpi - Fpi @ Fpi.T).max() <= tol
         nplastic += ro["dgamma"] > 0
     assert nplastic > 50
+
+
+@pytest.mark.parametrize("prec", ["d", "f"])
+def test_j2_barely_yielding_states_converge(hc, prec):
+    """Trial states just above the yield surface (f / sigma_y from 1e-8 to 1e-3), where the residual is at
+    the level of rounding: the bracket search must not mistake a rounding rise of r for its minimum."""
+    fn = hc.hc_j2_d if prec == "d" else hc.hc_j2_f
+    rng = np.random.default_rng(7)
+    lam, mu = lame(STEEL_J2.E, STEEL_J2.nu)
+    # the deviatoric strain at which a trial state reaches the yield surface from F_p = I, about
+    e_y = STEEL_J2.sigma_y0 / (math.sqrt(6.0) * mu)
+    for k in range(400):
+        over = 10.0 ** rng.uniform(-8, -3)
+        F = _trial_F(rng, e_y * (1.0 + over), rng.uniform(-1e-3, 1e-3))
+        st, S, ep, Cpi = _j2(fn, F, np.eye(3), 0.0)
+        assert st == 0, (k, over)
+        assert np.all(np.isfinite(S))
 
 
 @pytest.mark.parametrize("prec,tol", [("d", 1e-9), ("f", 2e-3)])

@@ -1,5 +1,6 @@
 """Parity at the full sizes of the measured workloads, in the configuration bench.py times
-(FP32 fields with FP64 displacement, kernel launches of 128 threads, stencil layout).
+(FP32 fields with FP64 displacement, kernel launches of 128 threads, the lattice layout for the 3D
+block and the stencil layout for the 2D cases).
 
 * 3D J2 block, 128 x 128 x 64 = 1,048,576 particles: neighbour lists and cell sort bit-exact
   against the oracle's cell search; after the benchmark's 2000 steps, F and P of every particle
@@ -40,7 +41,7 @@ def fp_from_cpinv(cp):
 def test_block_1m_setup_bit_exact_and_state_parity():
     case = W.block_3d()
     g = tlsph.from_case(case)
-    assert g.n == 1 << 20 and g.get_info()["stencil"] > 0
+    assert g.n == 1 << 20 and g.get_info()["stencil"] > 0 and g.get_info()["lattice_nx"] == 128
     o = make_oracle(case)
     rp_o, col_o = o.neighbours()
     rp_g, col_g = g.neighbours()
