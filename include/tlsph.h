@@ -87,7 +87,10 @@ enum {
     TLSPH_BC_ACCEL = 2,      /* a += value * ramp(t_n)                (type 3, m/s^2) */
     TLSPH_BC_POINTFORCE = 3, /* a += value * ramp(t_n) / (count * m_i) (type 1, N, shared by the masked particles) */
     TLSPH_BC_PHASE_BOUND = 4 /* <restrictphi>: s_{n+1} = max(s_{n+1}, value[0] * ramp(t_{n+1})) for particles with a
-                                phase field (component bit 0; with an expression, skipped values leave s alone) */
+                                phase field (Algorithm 2: also s_{n+1/2} with the value at t_{n+1/2}).  comp_mask
+                                must hold bit 0 and value[0] lie in [0, 1] (else TLSPH_ERR_ARG); an expression's
+                                value is kept in [0, 1] and a skipped one leaves s alone.  On particles without a
+                                phase field the condition does nothing */
 };
 /* fields for tlsph_read_state / tlsph_write_state */
 enum {
@@ -283,7 +286,13 @@ int64_t tlsph_field_bytes(const tlsph_ctx *ctx, int field);
  * out[0] kinetic sum m |v|^2 / 2, out[1] strain sum V psi_e (degraded),
  * out[2] fracture sum V Gc ((1 - s)^2 / (4 eps0) + eps0 |grad s|^2),
  * out[3] plastic work sum V (sigma_y0 eps_p + H eps_p^2 / 2),
- * out[4] time of specimen 0, out[5] current step size of specimen 0. */
+ * out[4] external work Wext since the reference setup: every step adds, for each particle, the
+ *        work of its external forces along the step's displacement increment u_{n+1} - u_n
+ *        (Algorithm 1: dt v_{n+1}; Algorithm 2: dt (v_n + v_{n+1}) / 2).  External forces are
+ *        gravity and the force conditions (traction, acceleration, point force) and, on a
+ *        component a velocity condition holds, its reaction m (v_{n+1} - v_n) / dt - m a with a
+ *        the acceleration of the particle's interactions (stress, viscosity, contact),
+ * out[5] time of specimen 0 (tlsph_time gives any specimen's time and step size). */
 tlsph_status tlsph_energies(tlsph_ctx *ctx, double out[6]);
 
 /* Time and current step size of one specimen. */
@@ -475,7 +484,11 @@ tlsph_status tlsph_j2_samples(tlsph_ctx *ctx, int stride_elastic, int stride_pla
  * first call before any stream capture.  Errors: TLSPH_ERR_ARG if n < 1 or
  * n > TLSPH_NOALLOC_MAX_PARTICLES, dim is not 2 or 3, h or support <= 0, or a required
  * pointer is NULL; TLSPH_ERR_CUDA if the device or the scratch address is unavailable or
- * a launch fails. */
+ * a launch fails.  Inputs that tlsph_build_ref_neighbours refuses with TLSPH_ERR_ARG (a
+ * non-finite coordinate, a negative specimen id, or a cell grid whose keys, specimens x
+ * cells, reach 9e18) are found on the device, after the call has returned: then every
+ * perm entry is -1, so a caller that checks perm[0] >= 0 once the stream is done never
+ * takes an order computed from overflowed keys. */
 tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, int64_t n, int dim, double h, double support,
                                      const double *X0, const int32_t *specimen_id, int32_t *perm);
 

@@ -27,7 +27,8 @@ FIELDS = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, 
 class _Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("h", C.c_double), ("support", C.c_double), ("cfl", C.c_double),
                 ("dt_mode", C.c_int), ("fixed_dt", C.c_double), ("gravity", C.c_double * 3),
-                ("visc_literal", C.c_int), ("lap_uncorrected", C.c_int), ("integrator", C.c_int)]
+                ("visc_literal", C.c_int), ("lap_uncorrected", C.c_int), ("integrator", C.c_int),
+                ("pf_explicit", C.c_int)]
 
 
 class _Material(C.Structure):
@@ -133,10 +134,10 @@ class Oracle:
     def __init__(self, dim: int, h: float, cfl: float = 0.3, dt_mode: int = DT_CFL_STATIC,
                  fixed_dt: float = 0.0, gravity=(0.0, 0.0, 0.0), support: float = 2.0,
                  visc_literal: bool = False, lap_uncorrected: bool = False, integrator: int = 1,
-                 dx: float | None = None):
+                 dx: float | None = None, pf_explicit: bool = False):
         self.lib = load_oracle()
         p = _Params(dim, h, support, cfl, dt_mode, fixed_dt, (C.c_double * 3)(*gravity), int(visc_literal),
-                    int(lap_uncorrected), int(integrator))
+                    int(lap_uncorrected), int(integrator), int(pf_explicit))
         self.ctx = self.lib.orc_create(C.byref(p))
         if not self.ctx:
             raise ValueError("invalid oracle parameters")
@@ -236,8 +237,8 @@ class Oracle:
         for b, kind, cm, exprs in self._exbcs:
             if kind == 0:
                 phases = [(0, 1.0)] + ([(1, 0.5)] if leap else [])
-            elif kind == 4:  # phase-field bound: the new level s_{n+1}
-                phases = [(0, 1.0)]
+            elif kind == 4:  # phase-field bound: the new level s_{n+1} (Algorithm 2: also s_{n+1/2})
+                phases = [(0, 1.0)] + ([(1, 0.5)] if leap else [])
             else:
                 phases = [(0, 0.5 if leap else 0.0)]
             for phase, off in phases:
@@ -298,7 +299,8 @@ class Oracle:
     def energies(self):
         out = np.zeros(6)
         _check(self.lib.orc_energies(self.ctx, _dp(out)), "energies")
-        return {"KE": out[0], "SE": out[1], "FE": out[2], "PW": out[3], "t": out[4], "dt": out[5]}
+        return {"KE": out[0], "SE": out[1], "FE": out[2], "PW": out[3], "Wext": out[4], "t": out[5],
+                "dt": self.time()[1]}
 
     def time(self, spec: int = 0):
         t, dt = C.c_double(), C.c_double()

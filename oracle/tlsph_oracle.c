@@ -66,6 +66,8 @@ typedef struct {
     int visc_literal;   /* 0: Pv = -J pi F^-T (dissipative reading), 1: literal +J pi F^-1 */
     int lap_uncorrected;/* 0: Laplacian uses the corrected gradient, 1: raw kernel gradient */
     int integrator;     /* 1 (or 0): Algorithm 1, symplectic Euler; 2: Algorithm 2, leapfrog */
+    int pf_explicit;    /* 0: the phase field's local terms at the new time level (reading); 1: the printed
+                         * explicit update sdot_{n+1} = sdot_n + dt sddot_n of Algorithm 1 */
 } orc_params;
 
 typedef struct {
@@ -97,6 +99,8 @@ typedef struct orc_ctx {
     int nspec;
     double *X0, *vol, *u, *v, *acc, *s, *sdot, *sdd, *Hh, *Fp, *ep;
     double *lap, *pf_b, *pf_k, *pf_g;  /* phase-field terms of the current step */
+    double *aext;                /* acceleration of the external forces of the current step (n x 3) */
+    double *wext;                /* work of the external forces on each particle since the reference setup */
     int32_t *mid, *spec;
     double *F, *P, *L;           /* per-particle 3x3 (L: in-plane block) */
     int32_t *status;             /* per-particle return-map status */
@@ -549,6 +553,7 @@ orc_ctx *orc_create(const orc_params *p) {
 static void free_particles(orc_ctx *c) {
     free(c->rest); free(c->accc); free(c->kfric);
     free(c->X0); free(c->vol); free(c->u); free(c->v); free(c->acc); free(c->s); free(c->sdot);
+    free(c->aext); free(c->wext);
     free(c->sdd); free(c->lap); free(c->pf_b); free(c->pf_k); free(c->pf_g); free(c->Hh); free(c->Fp); free(c->ep); free(c->mid); free(c->spec); free(c->F);
     free(c->P); free(c->L); free(c->status); free(c->row_ptr); free(c->col); free(c->perm);
     free(c->t); free(c->dt); free(c->vmax); free(c->amax); free(c->cmax);
@@ -596,6 +601,8 @@ int orc_create_particles(orc_ctx *c, int64_t n, const double *X0, const double *
     c->u = xcalloc(n * 3, sizeof(double));
     c->v = xcalloc(n * 3, sizeof(double));
     c->acc = xcalloc(n * 3, sizeof(double));
+    c->aext = xcalloc(n * 3, sizeof(double));
+    c->wext = xcalloc(n, sizeof(double));
     c->s = xcalloc(n, sizeof(double));
     c->sdot = xcalloc(n, sizeof(double));
     c->sdd = xcalloc(n, sizeof(double));
@@ -642,6 +649,9 @@ int orc_create_particles(orc_ctx *c, int64_t n, const double *X0, const double *
 int orc_add_bc(orc_ctx *c, const uint8_t *mask, int kind, int comp_mask, const double *value, double t_start,
                double t_end, double ramp, double area) {
     if (!c || !mask || !value || c->n <= 0 || c->nbc >= ORC_MAX_BC || kind < 0 || kind > 4) return ORC_ERR_ARG;
+    /* a phase-field bound acts on s (component 0) with a value in [0, 1] */
+    if (kind == ORC_BC_PHASE_BOUND && (!(comp_mask & 1) || !(value[0] >= 0.0 && value[0] <= 1.0)))
+        return ORC_ERR_ARG;
     orc_bc *b = &c->bc[c->nbc];
     memset(b, 0, sizeof *b);
     b->kind = kind;
@@ -1250,7 +1260,17 @@ static int one_step(orc_ctx *c) {
             }
             if (is_fracture(c, i)) {
                 double sh = c->s[i] + 0.5 * dt * c->sdot[i];
-                c->s[i] = sh < 0.0 ? 0.0 : (sh > 1.0 ? 1.0 : sh);
+                sh = sh < 0.0 ? 0.0 : (sh > 1.0 ? 1.0 : sh);
+                /* <restrictphi>: the bound holds at the half level too, with its value at t_{n+1/2} */
+                for (int b = 0; b < c->nbc; b++) {
+                    const orc_bc *bc = &c->bc[b];
+                    if (bc->kind != ORC_BC_PHASE_BOUND || !bc->mask[i] || !(bc->comp_mask & 1)) continue;
+                    double f = bc_factor(bc, th), val;
+                    if (f < 0.0 || !bc_value(bc, 1, i, 0, f, &val)) continue;
+                    val = val < 0.0 ? 0.0 : (val > 1.0 ? 1.0 : val); /* an expression's value, kept in [0, 1] */
+                    if (sh < val) sh = val;
+                }
+                c->s[i] = sh;
             }
         }
     }
@@ -1326,7 +1346,12 @@ static int one_step(orc_ctx *c) {
                 lap += 2.0 * (c->s[i] - c->s[j]) * c->vol[j] * rg / (r * r);
             }
         }
-        for (int k = 0; k < d; k++) a[k] += c->p.gravity[k] + (c->contact ? c->accc[3 * i + k] : 0.0);
+        /* external forces (gravity and the force conditions) are kept apart as well, for their work */
+        double ae[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < d; k++) {
+            a[k] += c->p.gravity[k] + (c->contact ? c->accc[3 * i + k] : 0.0);
+            ae[k] = c->p.gravity[k];
+        }
         double mass = rho_i * c->vol[i];
         /* force BCs at the time of the forces: t_n (Algorithm 1), t_{n+1/2} (Algorithm 2) */
         double t_n = c->t[c->spec[i]] + (leap ? 0.5 * c->dt[c->spec[i]] : 0.0);
@@ -1338,12 +1363,18 @@ static int one_step(orc_ctx *c) {
             for (int k = 0; k < d; k++) {
                 double val;
                 if (!(bc->comp_mask & (1 << k)) || !bc_value(bc, 0, i, k, f, &val)) continue;
-                if (bc->kind == ORC_BC_TRACTION) a[k] += val * bc->area / mass;
-                else if (bc->kind == ORC_BC_ACCEL) a[k] += val;
-                else a[k] += val / ((double)bc->count * mass);
+                double aek;
+                if (bc->kind == ORC_BC_TRACTION) aek = val * bc->area / mass;
+                else if (bc->kind == ORC_BC_ACCEL) aek = val;
+                else aek = val / ((double)bc->count * mass);
+                a[k] += aek;
+                ae[k] += aek;
             }
         }
-        for (int k = 0; k < 3; k++) c->acc[3 * i + k] = k < d ? a[k] : 0.0;
+        for (int k = 0; k < 3; k++) {
+            c->acc[3 * i + k] = k < d ? a[k] : 0.0;
+            c->aext[3 * i + k] = k < d ? ae[k] : 0.0;
+        }
         c->lap[i] = lap;
         if (is_fracture(c, i)) {
             /* eq. phasefieldddot: sdd = r - gamma sdot, with
@@ -1374,6 +1405,7 @@ static int one_step(orc_ctx *c) {
         /* v_{n+1} = v_n + dt a (Algorithm 1: a_n; Algorithm 2: a_{n+1/2}, from the saved v_n) */
         const double *vold = leap ? &vn_save[3 * i] : &c->v[3 * i];
         for (int k = 0; k < 3; k++) vn[k] = vold[k] + (k < d ? dt * c->acc[3 * i + k] : 0.0);
+        int vmask = 0;
         for (int b = 0; b < c->nbc; b++) { /* velocity BCs at t_{n+1} */
             const orc_bc *bc = &c->bc[b];
             if (bc->kind != ORC_BC_VEL || !bc->mask[i]) continue;
@@ -1381,8 +1413,27 @@ static int one_step(orc_ctx *c) {
             if (f < 0.0) continue;
             for (int k = 0; k < d; k++) {
                 double val;
-                if ((bc->comp_mask & (1 << k)) && bc_value(bc, 0, i, k, f, &val)) vn[k] = val;
+                if ((bc->comp_mask & (1 << k)) && bc_value(bc, 0, i, k, f, &val)) {
+                    vn[k] = val;
+                    vmask |= 1 << k;
+                }
             }
+        }
+        /* external work (Sec. 3.5 energy tracking): the work of the external forces along the step's
+         * displacement increment u_{n+1} - u_n, which is dt v_{n+1} (Algorithm 1) or dt (v_n + v_{n+1}) / 2
+         * (Algorithm 2).  On a component a velocity condition holds, the external force is its reaction
+         * m (v_{n+1} - v_n) / dt - m a_interactions (a_interactions = a - a_ext) */
+        {
+            const double mass = c->mat[c->mid[i]].rho * c->vol[i];
+            double wk = 0.0;
+            for (int k = 0; k < d; k++) {
+                const double aext = c->aext[3 * i + k];
+                const double fe = (vmask & (1 << k)) ? mass * ((vn[k] - vold[k]) / dt - (c->acc[3 * i + k] - aext))
+                                                     : mass * aext;
+                const double dk = leap ? 0.5 * dt * (vold[k] + vn[k]) : dt * vn[k];
+                wk += fe * dk;
+            }
+            c->wext[i] += wk;
         }
         double vv = 0.0, aa = 0.0;
         /* u_{n+1} = u_n + dt v_{n+1} (Algorithm 1); u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2) */
@@ -1399,8 +1450,11 @@ static int one_step(orc_ctx *c) {
         if (vv > c->vmax[sp]) c->vmax[sp] = vv;
         if (aa > c->amax[sp]) c->amax[sp] = aa;
         if (is_fracture(c, i)) {
-            double sd1 = (c->sdot[i] + dt * c->pf_b[i]) /
-                         (1.0 + dt * c->pf_g[i] + dt * dt * c->pf_k[i]);
+            /* the printed form (pf_explicit): sddot_n = r_n - gamma sdot_n (r holds the local stiffness term
+             * at s_n), sdot_{n+1} = sdot_n + dt sddot_n */
+            double sd1 = c->p.pf_explicit ? c->sdot[i] + dt * (c->pf_b[i] - c->pf_g[i] * c->sdot[i])
+                                          : (c->sdot[i] + dt * c->pf_b[i]) /
+                                                (1.0 + dt * c->pf_g[i] + dt * dt * c->pf_k[i]);
             c->sdd[i] = (sd1 - c->sdot[i]) / dt;
             c->sdot[i] = sd1;
             /* s_{n+1} = s_n + dt sdot_{n+1} (Algorithm 1); s_{n+1/2} + dt/2 sdot_{n+1} (Algorithm 2) */
@@ -1413,6 +1467,7 @@ static int one_step(orc_ctx *c) {
                 if (bc->kind != ORC_BC_PHASE_BOUND || !bc->mask[i] || !(bc->comp_mask & 1)) continue;
                 double f = bc_factor(bc, t1), val;
                 if (f < 0.0 || !bc_value(bc, 0, i, 0, f, &val)) continue;
+                val = val < 0.0 ? 0.0 : (val > 1.0 ? 1.0 : val); /* an expression's value, kept in [0, 1] */
                 if (sn < val) sn = val;
             }
             c->s[i] = sn;
@@ -1542,7 +1597,10 @@ int orc_write(orc_ctx *c, int field, const double *in) {
  * out[0] kinetic sum 1/2 m |v|^2, out[1] strain sum V psi_e (degraded),
  * out[2] fracture sum V Gc ((1-s)^2/(4 eps0) + eps0 |grad s|^2),
  * out[3] plastic work sum V (sigma_y0 eps_p + H eps_p^2 / 2),
- * out[4] time of specimen 0, out[5] step size of specimen 0.
+ * out[4] external work since the start: the sum over steps and particles of the work of the
+ *        external forces (gravity, force conditions, reactions of velocity conditions) along the
+ *        step's displacement increment (one_step),
+ * out[5] time of specimen 0.
  */
 int orc_energies(orc_ctx *c, double *out) {
     if (!c || !out || !c->built) return ORC_ERR_STATE;
@@ -1551,13 +1609,14 @@ int orc_energies(orc_ctx *c, double *out) {
     double *Fb = (double *)malloc(sizeof(double) * 9 * n), *Pb = (double *)malloc(sizeof(double) * 9 * n);
     double *psi = (double *)malloc(sizeof(double) * n);
     eval_FP(c, Fb, Pb, psi);
-    double ke = 0, se = 0, fe = 0, pw = 0;
+    double ke = 0, se = 0, fe = 0, pw = 0, we = 0;
     for (int64_t i = 0; i < n; i++) {
         const orc_material *m = &c->mat[c->mid[i]];
         double vv = 0.0;
         for (int k = 0; k < d; k++) vv += c->v[3 * i + k] * c->v[3 * i + k];
         ke += 0.5 * m->rho * c->vol[i] * vv;
         se += c->vol[i] * psi[i];
+        we += c->wext[i];
         if (m->model == ORC_MODEL_J2)
             pw += c->vol[i] * (m->sigma_y0 * c->ep[i] + 0.5 * m->H_hard * c->ep[i] * c->ep[i]);
         if (is_fracture(c, i)) {
@@ -1577,8 +1636,8 @@ int orc_energies(orc_ctx *c, double *out) {
     out[1] = se;
     out[2] = fe;
     out[3] = pw;
-    out[4] = c->t[0];
-    out[5] = c->dt[0];
+    out[4] = we;
+    out[5] = c->t[0];
     free(Fb);
     free(Pb);
     free(psi);

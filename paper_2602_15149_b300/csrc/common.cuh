@@ -91,6 +91,7 @@ template <typename T> struct StepArgs {
     T *H;                  // history functional
     T *sdot;               // phase-field rate
     double *u64;           // FP64 displacement, 3 arrays of n
+    double *wext;          // work of the external forces on each particle since the start (FP64)
     const uint16_t *mid;
     const int *spec;
     const uint16_t *bcgrp;     // 0 = no condition, else group g -> grp_bcs[4 g .. 4 g + 3]

@@ -603,6 +603,8 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
         Qi[0][0] = q0.x; Qi[0][1] = q0.y; Qi[1][0] = q0.z; Qi[1][1] = q0.w;
     }
     T acc[3] = {T(0), T(0), T(0)};
+    T acc_in[3] = {T(0), T(0), T(0)};  // the acceleration of the interactions (stress, viscosity, contact)
+    double aext[3] = {0.0, 0.0, 0.0};  // and of the external forces (gravity, force conditions)
 #pragma unroll
     for (int p = 0; p < DIM; p++) {
         T f = s2[p];
@@ -610,7 +612,9 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
         for (int q = 0; q < DIM; q++) f = t_fma(Qi[p][q], s1[q], f);
         acc[p] = f * irho;
         if (VISC) acc[p] -= a.Av[p * n + i];  // viscous acceleration of the stress pass
+        acc_in[p] = acc[p] + (a.accc ? a.accc[p * n + i] : T(0));
         acc[p] += a.grav[p];
+        aext[p] = (double)a.grav[p];
         if (a.accc) acc[p] += a.accc[p * n + i];
     }
     // forces act at t_n (Algorithm 1) or t_{n+1/2} (Algorithm 2); velocity BCs hold at t_{n+1}
@@ -641,9 +645,10 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
                 for (int p = 0; p < DIM; p++) {
                     double val;
                     if (!(bc.comp_mask & (1 << p)) || !dev_bc_value(a, bc, i, b, 0, p, f, val)) continue;
-                    if (bc.kind == 1) acc[p] += (T)(val * bc.area / (double)mass);
-                    else if (bc.kind == 2) acc[p] += (T)val;
-                    else acc[p] += (T)(val * bc.inv_count / (double)mass);
+                    const double ae = bc.kind == 1 ? val * bc.area / (double)mass
+                                                   : (bc.kind == 2 ? val : val * bc.inv_count / (double)mass);
+                    acc[p] += (T)ae;
+                    aext[p] += ae;
                 }
             }
         }
@@ -672,13 +677,15 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
             if (bc.kind != 4 || !(bc.comp_mask & 1)) continue;
             const double f = bc_factor(bc, t_1);
             double val;
-            if (f >= 0.0 && dev_bc_value(a, bc, i, b, 0, 0, f, val)) s_new = t_max(s_new, (T)val);
+            // an expression's value is kept in [0, 1]
+            if (f >= 0.0 && dev_bc_value(a, bc, i, b, 0, 0, f, val)) s_new = t_max(s_new, (T)fmin(fmax(val, 0.0), 1.0));
         }
     }
     // update: v_{n+1} = v_n + dt a; u_{n+1} = u_n + dt v_{n+1} (Algorithm 1) or
     // u_{n+1/2} + dt/2 v_{n+1} (Algorithm 2, u64 holding u_{n+1/2})
     const V4<T> vo = a.leap ? a.v_own[i] : vsi;
     T vn[3] = {vo.x, vo.y, vo.z};
+    const T vo_c[3] = {vo.x, vo.y, vo.z};
     const T dtT = (T)dt;
 #pragma unroll
     for (int p = 0; p < DIM; p++) {
@@ -690,6 +697,20 @@ __device__ __forceinline__ void p2_finish(const StepArgs<T> &a, int i, const P2O
     for (int p = 0; p < DIM; p++) {
         un[p] = a.u64[p * n + i] + (a.leap ? 0.5 * dt : dt) * (double)vn[p];
         a.u64[p * n + i] = un[p];
+    }
+    // work of the external forces along the step's displacement increment u_{n+1} - u_n (Algorithm 1:
+    // dt v_{n+1}; Algorithm 2: dt (v_n + v_{n+1}) / 2): gravity and force conditions, and on a component a
+    // velocity condition holds the reaction m (v_{n+1} - v_n) / dt - m a_interactions
+    if (g || a.grav[0] != T(0) || a.grav[1] != T(0) || a.grav[2] != T(0)) {
+        double wk = 0.0;
+#pragma unroll
+        for (int p = 0; p < DIM; p++) {
+            const double fe = (vmask & (1 << p)) ? (double)mass * (((double)vn[p] - (double)vo_c[p]) / dt - (double)acc_in[p])
+                                                 : (double)mass * aext[p];
+            const double du = a.leap ? 0.5 * dt * ((double)vo_c[p] + (double)vn[p]) : dt * (double)vn[p];
+            wk += fe * du;
+        }
+        a.wext[i] += wk;
     }
     a.ug_next[i] = V4<T>{(T)un[0], (T)un[1], DIM == 3 ? (T)un[DIM - 1] : T(0), DIM == 3 ? mass : T(0)};
     a.vs_next[i] = V4<T>{vn[0], vn[1], DIM == 3 ? vn[DIM - 1] : T(0), s_new};
@@ -760,7 +781,20 @@ __global__ void __launch_bounds__(BS) k_predict(StepArgs<T> a) {
     }
     dev_velocity_bcs<T, DIM>(a, i, th, vh, 1);
     T sh = v.w;
-    if (FRAC && a.mats[a.mid[i]].fracture) sh = t_min(T(1), t_max(T(0), v.w + (T)(0.5 * dt) * a.sdot[i]));
+    if (FRAC && a.mats[a.mid[i]].fracture) {
+        sh = t_min(T(1), t_max(T(0), v.w + (T)(0.5 * dt) * a.sdot[i]));
+        // <restrictphi>: a phase-field bound holds at the half level too, with its value at t_{n+1/2}
+        const int g = a.bcgrp[i];
+        for (int b = 0; g && b < kMaxBcPerParticle; b++) {
+            const int id = a.grp_bcs[4 * g + b];
+            if (id < 0) break;
+            const BCDev bc = a.bcs[id];
+            if (bc.kind != 4 || !(bc.comp_mask & 1)) continue;
+            const double f = bc_factor(bc, th);
+            double val;
+            if (f >= 0.0 && dev_bc_value(a, bc, i, b, 1, 0, f, val)) sh = t_max(sh, (T)fmin(fmax(val, 0.0), 1.0));
+        }
+    }
     a.ug_half[i] = V4<T>{uf[0], uf[1], DIM == 3 ? uf[DIM - 1] : T(0), DIM == 3 ? a.ug_next[i].w : T(0)};
     a.vs_half[i] = V4<T>{vh[0], vh[1], DIM == 3 ? vh[DIM - 1] : T(0), sh};
 }
@@ -1406,9 +1440,9 @@ __global__ void __launch_bounds__(BS) k_stress_exact(StepArgs<float> a, const ui
 // grad s and the energy densities of the current state (FP64 sums).
 template <typename T, int DIM, bool FRAC>
 __global__ void __launch_bounds__(128) k_energy(StepArgs<T> a, double *out) {
-    __shared__ double red[4][4];
+    __shared__ double red[5][4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double e[4] = {0, 0, 0, 0};
+    double e[5] = {0, 0, 0, 0, 0};
     if (i < a.n) {
         const int n = a.n;
         const MatT<T> m = a.mats[a.mid[i]];
@@ -1418,6 +1452,7 @@ __global__ void __launch_bounds__(128) k_energy(StepArgs<T> a, double *out) {
         const double vv = (double)vsi.x * vsi.x + (double)vsi.y * vsi.y + (double)vsi.z * vsi.z;
         e[0] = 0.5 * (double)m.rho * V * vv;
         e[1] = V * (double)a.psi_out[i];
+        e[4] = a.wext[i];
         if (m.model == 3) {
             const double ep = a.ep[i];
             e[3] = V * ((double)m.sy0 * ep + 0.5 * (double)m.Hh * ep * ep);
@@ -1448,13 +1483,13 @@ __global__ void __launch_bounds__(128) k_energy(StepArgs<T> a, double *out) {
             e[2] = V * (double)m.Gc * (om * om / (4.0 * (double)m.eps0) + (double)m.eps0 * g2);
         }
     }
-    for (int q = 0; q < 4; q++)
+    for (int q = 0; q < 5; q++)
         for (int o = 16; o > 0; o >>= 1) e[q] += __shfl_xor_sync(0xffffffffu, e[q], o);
     if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 4; q++) red[q][threadIdx.x >> 5] = e[q];
+        for (int q = 0; q < 5; q++) red[q][threadIdx.x >> 5] = e[q];
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 5; q++) {
             double s = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[q][w];
             atomicAdd(&out[q], s);
@@ -1589,7 +1624,7 @@ __global__ void __launch_bounds__(128) k_expr_bcs(StepArgs<T> a, const int *exli
             const int e = bc.expr[k];
             if (e < 0 || !(bc.comp_mask & (1 << k))) continue;
             const ExProg pr = progs[e];
-            const int nph = (bc.kind == 0 && a.leap) ? 2 : 1;
+            const int nph = ((bc.kind == 0 || bc.kind == 4) && a.leap) ? 2 : 1;
             for (int ph = 0; ph < nph; ph++) {
                 double off;
                 if (bc.kind == 0 || bc.kind == 4) off = ph == 0 ? dt : 0.5 * dt;  // the new level t_{n+1}

@@ -87,6 +87,7 @@ struct tlsph_ctx {
     void *Qa = nullptr, *Qb = nullptr, *XQ = nullptr, *G = nullptr;
     void *Ahat = nullptr, *K = nullptr, *ep = nullptr, *H = nullptr, *sdot = nullptr;
     double *u64 = nullptr;
+    double *wext = nullptr;  // work of the external forces per particle (FP64)
     uint16_t *mid = nullptr, *bcgrp = nullptr;
     int *spec = nullptr;
     int16_t *grp_bcs = nullptr;
@@ -388,6 +389,7 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.H = (T *)c->H;
     a.sdot = (T *)c->sdot;
     a.u64 = c->u64;
+    a.wext = c->wext;
     a.mid = c->mid;
     a.spec = c->spec;
     a.bcgrp = c->bcgrp;
@@ -940,6 +942,8 @@ template <typename T> tlsph_status build_impl(tlsph_ctx *c) {
     // ---- state
     DA(c->u64, 3 * n * sizeof(double));
     CK(cudaMemsetAsync(c->u64, 0, 3 * n * sizeof(double), s));
+    DA(c->wext, n * sizeof(double));
+    CK(cudaMemsetAsync(c->wext, 0, n * sizeof(double), s));
     if (c->nsten > 0) {
         c->Qa = c->Qb = c->XQ = nullptr;
         st = add_halo(c, c->Qa, sizeof(V4<T>), n);
@@ -1399,12 +1403,11 @@ template <typename T> tlsph_status energies_impl(tlsph_ctx *c, double *out) {
         else k_energy<T, 2, false><<<nb, kThreads, 0, c->stream>>>(a, c->energy);
     }
     CKL();
-    double e[4];
+    double e[5];
     CK(cudaMemcpyAsync(e, c->energy, sizeof e, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&out[4], c->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&out[5], c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&out[5], c->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    for (int q = 0; q < 4; q++) out[q] = e[q];
+    for (int q = 0; q < 5; q++) out[q] = e[q];
     return TLSPH_OK;
 }
 
@@ -1427,7 +1430,7 @@ int field_comps(const tlsph_ctx *c, int field) {
 
 size_t state_bytes(const tlsph_ctx *c) {
     const size_t ts = c->p.precision == TLSPH_FP64 ? 8 : 4, n = (size_t)c->n;
-    return 64 + n * (3 * 8 + 2 * 4 * ts + ts * (1 + 1 + 6 + 1)) + (size_t)c->nspec * 2 * 8 +
+    return 64 + n * (3 * 8 + 2 * 4 * ts + ts * (1 + 1 + 6 + 1) + 8) + (size_t)c->nspec * 2 * 8 +
            (c->leap ? (size_t)c->p.dim * n * ts : 0);
 }
 
@@ -1496,7 +1499,8 @@ template <typename T> tlsph_status state_io(tlsph_ctx *c, char *blob /* host */,
                     {c->H, n * ts},               {c->K, 6 * n * ts},
                     {c->ep, n * ts},              {c->t, (size_t)c->nspec * 8},
                     {c->dt, (size_t)c->nspec * 8},
-                    {c->accd, c->leap ? (size_t)c->p.dim * n * ts : 0}};  // a_{n-1/2} of Algorithm 2
+                    {c->accd, c->leap ? (size_t)c->p.dim * n * ts : 0},  // a_{n-1/2} of Algorithm 2
+                    {c->wext, n * 8}};
     int64_t hdr[8] = {0x54534c50485354LL, (int64_t)n, c->p.precision, c->nspec, c->steps, c->p.dim, 0, 0};
     cudaStream_t s = c->stream;
     if (save) {
@@ -1556,7 +1560,7 @@ template <typename T> std::vector<Snap> snap_parts(tlsph_ctx *c) {
             {c->ep, n * ts},           {c->t, ns * 8},                         {c->dt, ns * 8},
             {c->vmax, ns * 8},         {c->amax, ns * 8},                      {c->last_v, ns * 8},
             {c->last_a, ns * 8},       {c->flags, kNumFlags * sizeof(int)},     {c->done, sizeof(unsigned int)},
-            {c->bar, 2 * sizeof(unsigned int)}};
+            {c->bar, 2 * sizeof(unsigned int)}, {c->wext, n * 8}};
 }
 
 template <typename T>
@@ -1763,6 +1767,10 @@ tlsph_status tlsph_add_bc(tlsph_ctx *c, const uint8_t *mask, int kind, int comp_
     if (!c) return TLSPH_ERR_ARG;
     if (c->n <= 0) return fail(c, TLSPH_ERR_STATE, "create_particles must come before add_bc");
     if (!mask || !value || kind < 0 || kind > 4) return fail(c, TLSPH_ERR_ARG, "add_bc: bad kind or null array");
+    if (kind == TLSPH_BC_PHASE_BOUND && !(comp_mask & 1))
+        return fail(c, TLSPH_ERR_ARG, "add_bc: a phase-field bound acts on component 0 (bit 0 of comp_mask)");
+    if (kind == TLSPH_BC_PHASE_BOUND && !(value[0] >= 0.0 && value[0] <= 1.0))
+        return fail(c, TLSPH_ERR_ARG, "add_bc: a phase-field bound takes a value in [0, 1]");
     if (c->bcs.size() >= 32767) return fail(c, TLSPH_ERR_ARG, "too many boundary conditions");
     BCHost b;
     b.kind = kind;
@@ -2215,8 +2223,9 @@ struct NAScratch {
     int64_t hoff[256 * kNABlk];
     int64_t bsum[64];
     int64_t bscan[64];
-    double bbox[8];
+    double bbox[8];  // min xyz, max xyz, specimens (largest id + 1), count of non-finite coordinates or negative ids
     CellGrid grid;
+    int refused;     // inputs the context's reference setup refuses: every perm entry becomes -1
 };
 
 // every GPU that loads the library holds this array until the process exits
@@ -2225,15 +2234,30 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NAScratc
 std::mutex g_na_mutex;
 void *g_na_ptr[128] = {nullptr};
 
-__global__ void k_na_bbox(int64_t n, int dim, const double *X, double *out) {
+__global__ void k_na_bbox(int64_t n, int dim, const double *X, const int32_t *spec, double *out) {
     __shared__ double smin[3][32], smax[3][32];
+    __shared__ int sbad, sspec;
+    if (threadIdx.x == 0) {
+        sbad = 0;
+        sspec = 0;
+    }
+    __syncthreads();
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    int bad = 0, smaxid = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         for (int k = 0; k < dim; k++) {
             double x = X[dim * i + k];
+            bad += isfinite(x) ? 0 : 1;  // fmin / fmax below would drop a NaN silently
             mn[k] = fmin(mn[k], x);
             mx[k] = fmax(mx[k], x);
         }
+        if (spec) {
+            bad += spec[i] < 0 ? 1 : 0;
+            smaxid = max(smaxid, spec[i]);
+        }
+    }
+    if (bad) atomicAdd(&sbad, bad);
+    atomicMax(&sspec, smaxid);
     for (int k = 0; k < 3; k++)
         for (int o = 16; o > 0; o >>= 1) {
             mn[k] = fmin(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
@@ -2258,34 +2282,48 @@ __global__ void k_na_bbox(int64_t n, int dim, const double *X, double *out) {
             out[k] = a;
             out[3 + k] = b;
         }
+        out[6] = (double)sspec + 1.0;
+        out[7] = (double)sbad;
     }
 }
 
-// the same grid as the context's reference setup: cells R/3, nc = floor((max - min) / cs + 1/2) + 1
-__global__ void k_na_grid(int dim, double cs, const double *bbox, CellGrid *g) {
+// the same grid as the context's reference setup: cells R/3, nc = floor((max - min) / cs + 1/2) + 1, and the
+// same refusals: a non-finite coordinate or negative specimen id, or keys (specimens x cells) of 9e18 or more
+__global__ void k_na_grid(int dim, double cs, const double *bbox, CellGrid *g, int *refused) {
     g->dim = dim;
     g->cs = cs;
+    bool ok = bbox[7] == 0.0;
+    double maxkey = bbox[6];
     for (int k = 0; k < 3; k++) {
         g->xmin[k] = bbox[k];
-        g->nc[k] = (int64_t)floor(__dadd_rn(__ddiv_rn(__dsub_rn(bbox[3 + k], bbox[k]), cs), 0.5)) + 1;
+        const double ncd = floor(__dadd_rn(__ddiv_rn(__dsub_rn(bbox[3 + k], bbox[k]), cs), 0.5)) + 1.0;
+        ok = ok && isfinite(ncd);
+        maxkey *= ncd;
+        g->nc[k] = ok && ncd < 9.0e18 ? (int64_t)ncd : 1;
     }
+    ok = ok && maxkey < 9.0e18;
+    *refused = ok ? 0 : 1;
 }
 
 __global__ void k_na_keys(int64_t n, int dim, const double *X, const int32_t *spec, const CellGrid *gp,
-                          unsigned long long *key, int *id) {
+                          const int *refused, unsigned long long *key, int *id) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    id[i] = (int)i;
+    if (*refused) {  // the sort still runs on zero keys; k_na_copy writes -1
+        key[i] = 0ull;
+        return;
+    }
     const CellGrid g = *gp;
     int64_t c[3] = {0, 0, 0};
     for (int k = 0; k < dim; k++) c[k] = cell_coord(X[dim * i + k], g.xmin[k], g.cs);
     int64_t sp = spec ? (int64_t)spec[i] : 0;
     key[i] = (unsigned long long)((((sp * g.nc[2] + c[2]) * g.nc[1] + c[1]) * g.nc[0]) + c[0]);
-    id[i] = (int)i;
 }
 
-__global__ void k_na_copy(int64_t n, const int *src, int32_t *dst) {
+__global__ void k_na_copy(int64_t n, const int *src, const int *refused, int32_t *dst) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i];
+    if (i < n) dst[i] = *refused ? -1 : src[i];
 }
 
 }  // namespace
@@ -2326,9 +2364,10 @@ extern "C" tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, i
         const int64_t nblk = (n + kSortTile - 1) / kSortTile;
         const int64_t m = 256 * nblk;
         const unsigned nb = (unsigned)((m + kScanBlock - 1) / kScanBlock);
-        k_na_bbox<<<1, 1024, 0, s>>>(n, dim, X0, sc->bbox);
-        k_na_grid<<<1, 1, 0, s>>>(dim, support * h / 3.0, sc->bbox, &sc->grid);
-        k_na_keys<<<blocks_for(n), kThreads, 0, s>>>(n, dim, X0, specimen_id, &sc->grid, sc->keys[0], sc->vals[0]);
+        k_na_bbox<<<1, 1024, 0, s>>>(n, dim, X0, specimen_id, sc->bbox);
+        k_na_grid<<<1, 1, 0, s>>>(dim, support * h / 3.0, sc->bbox, &sc->grid, &sc->refused);
+        k_na_keys<<<blocks_for(n), kThreads, 0, s>>>(n, dim, X0, specimen_id, &sc->grid, &sc->refused, sc->keys[0],
+                                                     sc->vals[0]);
         // stable LSD radix sort over all 64 key bits: 8 passes, the result lands in buffer 0
         for (int pass = 0; pass < 8; pass++) {
             const int cur = pass & 1, shift = 8 * pass;
@@ -2339,7 +2378,7 @@ extern "C" tlsph_status tlsph_cell_sort_noalloc(int device, void *cuda_stream, i
             k_radix_scatter<<<(unsigned)nblk, 32, 0, s>>>(n, sc->keys[cur], sc->vals[cur], shift, sc->hoff,
                                                           sc->keys[cur ^ 1], sc->vals[cur ^ 1]);
         }
-        k_na_copy<<<blocks_for(n), kThreads, 0, s>>>(n, sc->vals[0], perm);
+        k_na_copy<<<blocks_for(n), kThreads, 0, s>>>(n, sc->vals[0], &sc->refused, perm);
         if (cudaGetLastError() != cudaSuccess) st = TLSPH_ERR_CUDA;
     }
     cudaSetDevice(prev);

@@ -303,7 +303,8 @@ class TLSPH:
     def energies(self):
         out = np.zeros(6)
         self._ck(self.lib.tlsph_energies(self.ctx, _d(out)), "energies")
-        return {"KE": out[0], "SE": out[1], "FE": out[2], "PW": out[3], "t": out[4], "dt": out[5]}
+        return {"KE": out[0], "SE": out[1], "FE": out[2], "PW": out[3], "Wext": out[4], "t": out[5],
+                "dt": self.time()[1]}
 
     def time(self, specimen=0):
         t, dt = C.c_double(), C.c_double()

@@ -107,6 +107,12 @@ def test_notched_plate_phase_field(precision):
     assert np.abs(s_g - s_o).max() <= 1e-3
     H_o, H_g = o.read("H"), g.read_state("H")
     assert rel_l2(H_g, H_o) <= 1e-3
+    # fracture energy (the regularised crack functional) and the work of the tractions
+    eo, eg = o.energies(), g.energies()
+    etol = 1e-6 if precision == tlsph.FP64 else 2e-3
+    for k in ("FE", "Wext", "KE", "SE"):
+        assert abs(eg[k] - eo[k]) <= etol * abs(eo[k]), (k, eg[k], eo[k])
+    assert eo["FE"] > 0 and eo["Wext"] > 0
 
 
 def test_stress_and_energies_match():
@@ -118,8 +124,9 @@ def test_stress_and_energies_match():
     assert rel_l2(g.read_state("P"), o.read("P")) <= 1e-8
     assert rel_l2(g.read_state("F"), o.read("F")) <= 1e-10
     eo, eg = o.energies(), g.energies()
-    for k in ["KE", "SE", "PW"]:
+    for k in ["KE", "SE", "PW", "Wext"]:  # Wext: the reactions of the pressing and the fixed face
         assert abs(eg[k] - eo[k]) <= 1e-8 * max(abs(eo[k]), 1e-30), (k, eg[k], eo[k])
+    assert eo["Wext"] > 0
 
 
 def test_cpinv_matches_oracle_plastic_state():
@@ -199,3 +206,25 @@ def test_errors_are_statuses():
     with pytest.raises(tlsph.TLSPHError) as e:
         t.create_particles(np.array([[np.nan, 0.0]]), np.array([1.0]))
     assert e.value.status == tlsph.ERR_ARG
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_external_work_of_a_constant_traction_on_the_gpu(integrator):
+    """A clamped bar pulled by a constant traction: the GPU's Wext equals sum f . u of its own displacement
+    (the work of a constant force along the path is its value times the displacement) and the oracle's
+    Wext, under both integrators."""
+    case = W.plate_2d(nx=40, ny=6, beta1=0.0, beta2=0.0)
+    X = case.X0
+    left = np.isclose(X[:, 0], X[:, 0].min()).astype(np.uint8)
+    right = np.isclose(X[:, 0], X[:, 0].max())
+    case.bcs = [W.BC(left, W.BC_VEL, 0b11, (0.0, 0.0, 0.0)),
+                W.BC(right.astype(np.uint8), W.BC_TRACTION, 0b01, (2e8, 0.0, 0.0), area=case.dp)]
+    case.integrator = integrator
+    o = make_oracle(case)
+    g = gpu(case, precision=tlsph.FP64)
+    o.step(400)
+    g.step(400)
+    w = g.energies()["Wext"]
+    ref = np.sum(2e8 * case.dp * g.read_state("U")[right, 0])
+    assert abs(w - ref) <= 1e-12 * abs(ref)
+    assert abs(w - o.energies()["Wext"]) <= 1e-9 * abs(ref)

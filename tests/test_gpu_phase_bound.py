@@ -23,11 +23,13 @@ def _cases():
     return near, {"constant": const, "expression": expr}
 
 
+@pytest.mark.parametrize("integrator", [1, 2])
 @pytest.mark.parametrize("which", ["constant", "expression"])
 @pytest.mark.parametrize("precision,tol", [(tlsph.FP64, 1e-5), (tlsph.FP32_U64, 1e-4)])
-def test_phase_bound_matches_oracle(which, precision, tol):
+def test_phase_bound_matches_oracle(which, precision, tol, integrator):
     near, cases = _cases()
     case = cases[which]
+    case.integrator = integrator
     o = make_oracle(case)
     g = tlsph.from_case(case, precision=precision)
     for _ in range(3):
@@ -45,3 +47,34 @@ def test_phase_bound_is_refused_for_a_bad_kind():
     g = tlsph.from_case(case, build=False)
     with pytest.raises(tlsph.TLSPHError):
         g.add_bc(np.ones(case.n, np.uint8), 5, 1, (1.0, 0.0, 0.0))
+
+
+def test_full_bound_under_algorithm_2_keeps_the_plate_intact_on_the_gpu():
+    """Bound 1 on every particle under Algorithm 2: the half level is bounded as well, so the plate moves as
+    the same plate without a phase field (FP64, 1e-9)."""
+    import copy
+
+    case = _plate()
+    case.integrator = 2
+    bounded = _with(case, [W.BC(np.ones(case.n, np.uint8), W.BC_PHASE_BOUND, 1, (1.0, 0.0, 0.0))])
+    intact = copy.copy(case)
+    intact.materials = [copy.copy(m) for m in case.materials]
+    for m in intact.materials:
+        m.fracture = False
+    a = tlsph.from_case(bounded, precision=tlsph.FP64)
+    b = tlsph.from_case(intact, precision=tlsph.FP64)
+    a.step(300)
+    b.step(300)
+    assert np.all(a.read_state("S") == 1.0)
+    ua, ub = a.read_state("U"), b.read_state("U")
+    assert np.abs(ua - ub).max() <= 1e-9 * np.abs(ub).max()
+
+
+def test_bad_phase_bounds_are_refused_by_the_library():
+    case = _plate()
+    g = tlsph.from_case(case, build=False)
+    all_ = np.ones(case.n, np.uint8)
+    for value, comp in ((1.5, 1), (-0.1, 1), (float("nan"), 1), (0.5, 2)):
+        with pytest.raises(tlsph.TLSPHError) as e:
+            g.add_bc(all_, W.BC_PHASE_BOUND, comp, (value, 0.0, 0.0))
+        assert e.value.status == tlsph.ERR_ARG

@@ -8,6 +8,7 @@ a region acts exactly like the same constant bound on that region."""
 import copy
 
 import numpy as np
+import pytest
 
 from paper_2602_15149_b300 import workloads as W
 from tests.oracle_cases import make_oracle
@@ -45,9 +46,13 @@ def test_zero_bound_changes_nothing():
         assert np.array_equal(sa, sb) and np.array_equal(ua, ub)
 
 
-def test_full_bound_keeps_the_plate_intact():
-    """s = 1 everywhere: no damage, and the displacement is that of the plate without a phase field."""
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_full_bound_keeps_the_plate_intact(integrator):
+    """s = 1 everywhere: no damage, and the displacement is that of the plate without a phase field.  Under
+    Algorithm 2 this needs the bound at the half level as well: the forces and the degradation of a step are
+    taken at s_{n+1/2}, which a negative sdot would otherwise pull below 1."""
     case = _plate()
+    case.integrator = integrator
     assert case.materials[0].fracture
     bounded = _with(case, [W.BC(np.ones(case.n, np.uint8), BOUND, 1, (1.0, 0.0, 0.0))])
     intact = copy.copy(case)
@@ -83,3 +88,28 @@ def test_expression_bound_equals_the_constant_bound_on_its_region():
     _, b = _run(expr, 300)
     for (sa, ua), (sb, ub) in zip(a, b):
         assert np.array_equal(sa, sb) and np.array_equal(ua, ub)
+
+
+def test_expression_bound_is_kept_in_the_unit_interval():
+    """An expression bound of 1.5 acts as the bound 1 (s stays a fraction), and one of -0.5 as no bound."""
+    case = _plate()
+    all_ = np.ones(case.n, np.uint8)
+    one = _with(case, [W.BC(all_, BOUND, 1, (1.0, 0.0, 0.0))])
+    big = _with(case, exbcs=[W.ExprBC(all_, BOUND, 1, [("1.5", ""), None, None])])
+    neg = _with(case, exbcs=[W.ExprBC(all_, BOUND, 1, [("-0.5", ""), None, None])])
+    _, a = _run(one, 200)
+    _, b = _run(big, 200)
+    _, c = _run(case, 200)
+    _, d = _run(neg, 200)
+    for (sa, ua), (sb, ub) in zip(a, b):
+        assert np.array_equal(sa, sb) and np.array_equal(ua, ub) and sb.max() <= 1.0
+    for (sc, uc), (sd, ud) in zip(c, d):
+        assert np.array_equal(sc, sd) and np.array_equal(uc, ud)
+
+
+def test_bad_phase_bounds_are_refused():
+    o = make_oracle(_plate())
+    all_ = np.ones(o.n, np.uint8)
+    for value, comp in ((1.5, 1), (-0.1, 1), (float("nan"), 1), (0.5, 2), (0.5, 0)):
+        with pytest.raises(RuntimeError):
+            o.add_bc(all_, BOUND, comp, (value, 0.0, 0.0))
