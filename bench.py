@@ -195,6 +195,16 @@ class ClockSampler:
                            f"shorter than the 200 ms sampling interval)")}
 
 
+def configure_layout(g, args):
+    """The neighbour walk of the timed context (--layout, --rows-gradient, --rows-force, --fuse-stress)."""
+    from paper_2602_15149_b300 import tlsph
+    g.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, {"auto": tlsph.LAYOUT_AUTO, "stencil": tlsph.LAYOUT_STENCIL,
+                                              "csr": tlsph.LAYOUT_CSR}[args.layout])
+    g.set_option(tlsph.OPT_LATTICE_ROWS_GRADIENT, args.rows_gradient)
+    g.set_option(tlsph.OPT_LATTICE_ROWS_FORCE, args.rows_force)
+    g.set_option(tlsph.OPT_FUSE_STRESS, 1 if args.fuse_stress else 0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -620,6 +630,7 @@ def run_ours(args):
     case = W.block_3d(*shape, steps=args.steps)
     n = case.n
     g = tlsph.from_case(case, device=local, stream=stream.cuda_stream)
+    configure_layout(g, args)
     info = g.get_info()
     nnz = info["nnz"]
 
@@ -713,7 +724,9 @@ def run_ours(args):
                                         f"{info['lattice_nxny']}, one mask word per layer)" if info["lattice_nx"] else
                                         f"stencil ({info['stencil']} differences, 16 B row masks)"
                                         if info["stencil"] else "SELL-32 CSR rows"),
-                   "parallelism": f"replicas x{ws} (independent blocks)"},
+                   "parallelism": f"replicas x{ws} (independent blocks)",
+                   "walk": {"layout": args.layout, "rows_gradient": args.rows_gradient, "rows_force": args.rows_force,
+                            "fuse_stress": bool(args.fuse_stress)}},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
@@ -774,6 +787,15 @@ def main():
     ap.add_argument("--sur-samples", type=int, default=10_000_000, help="return-map samples for training")
     ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--sur-train-s", type=float, default=90.0, help="training time limit (s)")
+    ap.add_argument("--layout", default="auto", choices=["auto", "stencil", "csr"],
+                    help="neighbour walk of the headline step: auto (the lattice walk on this block), the stencil "
+                         "table walk, or SELL-32 rows (for comparing the walks; the metric uses auto)")
+    ap.add_argument("--rows-gradient", type=int, default=1, choices=[1, 2],
+                    help="lattice walk: rows per thread of the deformation-gradient kernel")
+    ap.add_argument("--rows-force", type=int, default=2, choices=[1, 2, 4],
+                    help="lattice walk: rows per thread of the force kernel")
+    ap.add_argument("--fuse-stress", action="store_true",
+                    help="lattice walk: the stress in the tail of the deformation-gradient kernel")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()

@@ -512,8 +512,13 @@ __device__ __forceinline__ void dev_write_qvm_fi(const StepArgs<T> &a, int i, co
     }
 }
 
+// FP32: eight blocks of 128 threads per SM (64 registers; the J2 return map's rare plastic branch spills a
+// little), measured 11% faster on the 1M-particle J2 block than the unbounded 91 registers
+#ifndef TLSPH_STRESS_MINB
+#define TLSPH_STRESS_MINB 8
+#endif
 template <typename T, int DIM, bool FRAC, bool DIAG, int BS>
-__global__ void __launch_bounds__(BS) k_stress(StepArgs<T> a) {
+__global__ void __launch_bounds__(BS, sizeof(T) == 4 ? TLSPH_STRESS_MINB * 128 / BS : 1) k_stress(StepArgs<T> a) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= a.n) return;
     T Gm[DIM][DIM];

@@ -69,6 +69,27 @@ def test_block_1m_setup_bit_exact_and_state_parity():
     assert err_g <= 1e-4 and err_p <= 1e-4 and err_pp <= 1e-4
 
 
+
+@pytest.mark.slow
+def test_block_1m_trajectory_1000_steps():
+    """The metric's workload run step for step: the 1,048,576-particle J2 block for 1000 steps on the GPU
+    (FP32 fields, FP64 displacement, the lattice walk the benchmark times) and in the FP64 oracle on the
+    host cores (about ten minutes).  The scope's FP32 bar is relative L2 1e-4 on u; the other fields'
+    FP32 errors against the FP64 oracle are bounded here and printed."""
+    case = W.block_3d(steps=1000)
+    g = tlsph.from_case(case)
+    assert g.get_info()["lattice_nx"] == 128
+    g.step(1000)
+    assert g.get_info()["noconverge"] == 0 and g.get_info()["nonfinite"] == 0
+    o = make_oracle(case)
+    o.step(1000)
+    err = {f: rel_l2(g.read_state(f), o.read(f)) for f in ("U", "V", "F", "P", "EPSP")}
+    ep = o.read("EPSP")
+    print("1M J2 block, 1000 steps, FP32 against the FP64 oracle (relative L2):", err, "eps_p max", ep.max())
+    assert ep.max() > 0.0  # the block yields within the run
+    assert err["U"] <= 1e-4, err
+    assert err["F"] <= 1e-4 and err["P"] <= 1e-3 and err["V"] <= 1e-3 and err["EPSP"] <= 1e-2, err
+
 def test_notched_plate_full_size():
     case = W.notched_plate()
     assert case.n == 100_000
