@@ -112,7 +112,7 @@ def load_oracle():
     lib.orc_contact_energy.argtypes = [C.c_void_p]
     lib.orc_contact_energy.restype = C.c_double
     lib.orc_contact_force.argtypes = [C.c_int, C.c_double, C.c_double, D, D, D, D, C.c_double, C.c_double,
-                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, D]
+                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, D]
     lib.orc_set_contact_friction.argtypes = [C.c_void_p, C.c_int, D]
     lib.orc_prepare_step.argtypes = [C.c_void_p]
     _lib = lib
@@ -358,8 +358,9 @@ def svk_stress(F, s, mat: OracleMaterial):
 
 
 def contact_force(dim, dc, contcoeff, xi, xj, vi, vj, mi, mj, mat_i: OracleMaterial, mat_j: OracleMaterial,
-                  e_i, e_j, mu=0.0):
-    """Contact force on particle i from particle j (zero out of contact); mu = the pair's friction coefficient."""
+                  e_i, e_j, mu=0.0, dt=0.0):
+    """Contact force on particle i from particle j (zero out of contact); mu = the pair's friction coefficient,
+    dt = the step the force acts over (> 0 caps friction so that it at most stops the sliding in one step)."""
     lib = load_oracle()
     a = [np.zeros(3) for _ in range(4)]
     for dst, src in zip(a, (xi, xj, vi, vj)):
@@ -367,7 +368,7 @@ def contact_force(dim, dc, contcoeff, xi, xj, vi, vj, mi, mj, mat_i: OracleMater
     F = np.zeros(3)
     ci = (1 - mat_i.nu ** 2) / mat_i.E
     cj = (1 - mat_j.nu ** 2) / mat_j.E
-    lib.orc_contact_force(dim, dc, contcoeff, *[_dp(x) for x in a], mi, mj, ci, cj, e_i, e_j, mu, _dp(F))
+    lib.orc_contact_force(dim, dc, contcoeff, *[_dp(x) for x in a], mi, mj, ci, cj, e_i, e_j, mu, dt, _dp(F))
     return F[:dim]
 
 

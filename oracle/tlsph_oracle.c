@@ -1072,12 +1072,15 @@ static double bc_factor(const orc_bc *b, double t) {
 /* by a viscous bound c_t |v_t| with c_t = 2 sqrt(k m*) (the critical    */
 /* damping of the normal spring), so that an explicit step does not     */
 /* chatter around v_t = 0:                                              */
-/*   F_i = f_n n - min(mu max(f_n, 0), c_t |v_t|) v_t / |v_t|,            */
-/* mu = (mu_i + mu_j) / 2.                                               */
+/*   F_i = f_n n - min(mu max(f_n, 0), c_t |v_t|, m* |v_t| / dt) v_t/|v_t|,*/
+/* mu = (mu_i + mu_j) / 2.  The last bound (dt > 0: the step the force   */
+/* acts over) lets friction at most stop the sliding in one explicit     */
+/* step; it is below c_t |v_t| only when the normal spring's omega dt    */
+/* exceeds 1/2, where c_t |v_t| alone would reverse v_t.                 */
 /* ------------------------------------------------------------------ */
 int orc_contact_force(int dim, double dc, double kc, const double *xi, const double *xj, const double *vi,
                       const double *vj, double mi, double mj, double cinv_i, double cinv_j, double ei, double ej,
-                      double mu, double *F) {
+                      double mu, double dt, double *F) {
     double d[3] = {0, 0, 0}, r2 = 0.0;
     F[0] = F[1] = F[2] = 0.0;
     for (int k = 0; k < dim; k++) {
@@ -1108,6 +1111,7 @@ int orc_contact_force(int dim, double dc, double kc, const double *xi, const dou
         if (vt2 > 0.0) {
             double vtm = sqrt(vt2);
             double ft = fmin(mu * f, 2.0 * sqrt(kn * ms) * vtm);
+            if (dt > 0.0) ft = fmin(ft, ms * vtm / dt);
             for (int k = 0; k < dim; k++) F[k] -= ft * vt[k] / vtm;
         }
     }
@@ -1133,7 +1137,8 @@ static void contact_accel(orc_ctx *c) {
             const orc_material *mj = &c->mat[c->mid[j]];
             const double mu = c->kfric ? 0.5 * (c->kfric[c->spec[i]] + c->kfric[c->spec[j]]) : 0.0;
             if (orc_contact_force(d, c->dc, c->kc, xi, xj, &c->v[3 * i], &c->v[3 * j], massi, mj->rho * c->vol[j],
-                                  mat_cinv(mi), mat_cinv(mj), c->rest[c->spec[i]], c->rest[c->spec[j]], mu, F))
+                                  mat_cinv(mi), mat_cinv(mj), c->rest[c->spec[i]], c->rest[c->spec[j]], mu,
+                                  c->dt[c->spec[i]], F))
                 for (int k = 0; k < d; k++) a[k] += F[k] / massi;
         }
         for (int k = 0; k < 3; k++) c->accc[3 * i + k] = a[k];

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0
     const int4 own = hcell[i];  // the cells the particles were filed under
     const int64_t ci[3] = {own.x, own.y, own.z};
     const int si = a.spec[i];
+    const double dt = a.dt[si];  // bodies in contact share one clock
     const MatT<T> mi = a.mats[a.mid[i]];
     const V4<T> Xi = a.X0V[i];
     const double massi = DIM == 3 ? (double)mi.rho * (double)Xi.w : (double)Xi.w;
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(128) k_contact(StepArgs<T> a, const double *X0
                         }
                         if (vt2 > 0.0) {
                             const double vtm = sqrt(vt2);
-                            const double ft = fmin(mu * f, 2.0 * sqrt(kn * ms) * vtm);
+                            // Coulomb, regularised near rest, and at most stopping the sliding in one step
+                            const double ft = fmin(fmin(mu * f, 2.0 * sqrt(kn * ms) * vtm), ms * vtm / dt);
 #pragma unroll
                             for (int k = 0; k < DIM; k++) F[k] -= ft * vt[k] / vtm;
                         }

@@ -209,3 +209,30 @@ def test_symmetric_collision():
     hi = hi.reshape(n, n, 2)[::-1]
     assert np.abs(hi[..., 0] - lo[..., 0]).max() <= 1e-9 * np.abs(u).max()
     assert np.abs(hi[..., 1] + lo[..., 1]).max() <= 1e-9 * np.abs(u).max()
+
+
+def test_friction_stops_the_sliding_at_most_in_one_step():
+    """With a step long for the contact spring (omega dt = 2, where the viscous regularisation alone would
+    reverse the sliding), friction is capped at m* |v_t| / dt: one explicit step brings the pair's relative
+    tangential velocity to zero and not past it.  With a short step (omega dt = 0.1) the cap is inactive."""
+    dc, kc, mu = 1e-2, 5.0, 0.5
+    m1 = m2 = 0.5
+    xi, xj = np.array([0.0, 0.0]), np.array([0.009, 0.0])  # pressed: r < dc
+    fn = -contact_force(2, dc, kc, xi, xj, np.zeros(2), np.zeros(2), m1, m2, SOFT, SOFT, 1.0, 1.0)[0]
+    assert fn > 0
+    kn = kc / (2 * (1 - SOFT.nu ** 2) / SOFT.E)
+    ms = m1 * m2 / (m1 + m2)
+    omega = math.sqrt(kn / ms)
+    vt = 0.5 * mu * fn / (2 * math.sqrt(kn * ms))  # slow enough that the viscous bound is below Coulomb
+    vi = np.array([0.0, vt])
+    for wdt, capped in ((2.0, True), (0.1, False)):
+        dt = wdt / omega
+        F = contact_force(2, dc, kc, xi, xj, vi, np.zeros(2), m1, m2, SOFT, SOFT, 1.0, 1.0, mu, dt)
+        Fu = contact_force(2, dc, kc, xi, xj, vi, np.zeros(2), m1, m2, SOFT, SOFT, 1.0, 1.0, mu)
+        ft = -F[1]
+        if capped:
+            assert abs(ft - ms * vt / dt) <= 1e-12 * ft
+            assert vt - ft / ms * dt >= -1e-15  # relative tangential velocity after the step (pair's own frame)
+            assert ft < -Fu[1]
+        else:
+            assert ft == -Fu[1]
