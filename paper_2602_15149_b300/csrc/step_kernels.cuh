@@ -1068,8 +1068,15 @@ template <typename T> __device__ __forceinline__ bool grid_sync(const GridBarrie
 // nsteps steps in one cooperative launch: phase A (gradient + stress per particle, no
 // neighbour dependency between them), barrier, phase B (force, damage, update), barrier.
 // Block 0 advances the clocks of the previous step while phase A runs.
+// FP32: eight blocks of 128 threads per SM (64 registers).  The kernel holds the neighbour walks and the
+// J2 update in one body; left free it took 100-144 registers, and its latency-bound walks ran at a third
+// fewer warps than the separate kernels (512-specimen batch: 1.73 against 1.08 ms per step at 64).
+#ifndef TLSPH_PERSIST_MINB
+#define TLSPH_PERSIST_MINB 8
+#endif
 template <typename T, int DIM, bool FRAC, bool VISC, int BS>
-__global__ void __launch_bounds__(BS, 1) k_persistent(StepArgs<T> a, int nsteps, GridBarrier bar) {
+__global__ void __launch_bounds__(BS, sizeof(T) == 4 ? TLSPH_PERSIST_MINB * 128 / BS : 1) k_persistent(StepArgs<T> a, int nsteps,
+                                                                                                   GridBarrier bar) {
     const int n = a.n;
     const int stride = gridDim.x * BS;
     for (int step = 0; step < nsteps; step++) {
