@@ -196,13 +196,16 @@ class ClockSampler:
 
 
 def configure_layout(g, args):
-    """The neighbour walk of the timed context (--layout, --rows-gradient, --rows-force, --fuse-stress)."""
+    """The neighbour walk of the timed context (--layout, --rows-gradient, --rows-force, --fuse-stress,
+    --patch, --zstream)."""
     from paper_2602_15149_b300 import tlsph
     g.set_option(tlsph.OPT_NEIGHBOUR_LAYOUT, {"auto": tlsph.LAYOUT_AUTO, "stencil": tlsph.LAYOUT_STENCIL,
                                               "csr": tlsph.LAYOUT_CSR}[args.layout])
     g.set_option(tlsph.OPT_LATTICE_ROWS_GRADIENT, args.rows_gradient)
     g.set_option(tlsph.OPT_LATTICE_ROWS_FORCE, args.rows_force)
     g.set_option(tlsph.OPT_FUSE_STRESS, 1 if args.fuse_stress else 0)
+    g.set_option(tlsph.OPT_LATTICE_PATCH, args.patch)
+    g.set_option(tlsph.OPT_LATTICE_ZSTREAM, args.zstream)
 
 
 def dist_env():
@@ -726,7 +729,8 @@ def run_ours(args):
                                         if info["stencil"] else "SELL-32 CSR rows"),
                    "parallelism": f"replicas x{ws} (independent blocks)",
                    "walk": {"layout": args.layout, "rows_gradient": args.rows_gradient, "rows_force": args.rows_force,
-                            "fuse_stress": bool(args.fuse_stress)}},
+                            "fuse_stress": bool(args.fuse_stress), "patch": args.patch,
+                            "zstream": args.zstream}},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
@@ -796,6 +800,10 @@ def main():
                     help="lattice walk: rows per thread of the force kernel")
     ap.add_argument("--fuse-stress", action="store_true",
                     help="lattice walk: the stress in the tail of the deformation-gradient kernel")
+    ap.add_argument("--patch", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="lattice walk: x width of a block's patch of rows (0: whole x lines)")
+    ap.add_argument("--zstream", type=int, default=0,
+                    help="lattice walk: planes per thread of the force pass streaming along z (0: off)")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice of the J2 block (the metric's workload is 128,128,64; smaller shapes for profiling)")
     args = ap.parse_args()

@@ -330,10 +330,21 @@ enum {
     TLSPH_OPT_LATTICE_ROWS_GRADIENT = 8, /* lattice layout: rows per thread of the deformation-gradient kernel, 1
                                           * (default) or 2 */
     TLSPH_OPT_LATTICE_ROWS_FORCE = 9,    /* lattice layout: rows per thread of the force kernel, 1, 2 (default) or 4 */
-    TLSPH_OPT_FUSE_STRESS = 10           /* lattice layout: 1 computes the stress in the tail of the
+    TLSPH_OPT_FUSE_STRESS = 10,          /* lattice layout: 1 computes the stress in the tail of the
                                           * deformation-gradient kernel (two launches per step), 0 (default) in its
                                           * own pass (measured faster on the 1M-particle J2 block: the fused kernel
                                           * needs the stress pass's registers during its neighbour walk) */
+    TLSPH_OPT_LATTICE_PATCH = 11,        /* lattice layout: how the two neighbour kernels hand rows to blocks.  0
+                                          * (default): a block of 128 threads takes whole x lines of the lattice
+                                          * (the rows i with the same i / NX); 32, 64 or 128: a block takes that many
+                                          * consecutive x of 128 / value groups of lines, so its neighbour records
+                                          * overlap more in L1.  Every choice sums each particle's pairs in the same
+                                          * order: the steps are bit-identical. */
+    TLSPH_OPT_LATTICE_ZSTREAM = 12       /* lattice layout: value k > 0 runs the force kernel with a column of k
+                                          * planes per thread: the thread walks its planes (and three more on each
+                                          * side) once, keeps the sums of the seven rows a plane serves in registers
+                                          * and loads each neighbour record once for all of them.  0 (default): one
+                                          * thread per TLSPH_OPT_LATTICE_ROWS_FORCE rows.  Bit-identical steps. */
 };
 /* Neighbour layouts.  The reference setup always builds CSR rows (tlsph_neighbours) and their
  * SELL-32 copy.  When the pair differences j - i of the cell-sorted particles take at most 128

@@ -72,6 +72,8 @@ template <typename T> struct StepArgs {
     int64_t halo;          // zero records before and after each gathered array (stencil layout)
     int sten_groups;       // stencil tables: 1, or one per specimen (kMaxStencil entries each)
     int lat_nx, lat_nxny;  // lattice walk (lattice.cuh): row and layer pitch, 0 = off
+    int lat_cw;            // lattice walk: x width of a block's patch of rows (0 = whole rows, lattice.cuh)
+    int lat_zc;            // lattice force pass streaming along z: planes per thread (0 = off)
     const unsigned *lmask; // lattice walk: one mask word per layer, 7 arrays of n
     const V4<T> *X0V;      // 3D (x, y, z, V0); 2D (x, y, V0, m0)
     const V4<T> *S1;       // sum_j V_j w_ij (X_j - X_i) / V_i (reference configuration)

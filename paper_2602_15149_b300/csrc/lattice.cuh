@@ -45,11 +45,12 @@ __host__ __device__ constexpr int lat_bit(int dx, int dy, int dz) {
 static_assert(lat_bit(3, 0, 0) == 17 && lat_bit(0, 3, 0) == 28 && lat_bit(0, 0, 3) == 0, "ball layout");
 static_assert(lat_bit(2, 2, 1) == 24 && lat_bit(1, 2, 2) == 20, "ball layout");
 
-// Row table of the ball, indexed [dz + 3][dy + 3]: half width in x (-1: no row) and the place of the
-// row's first entry in its layer word.
+// Row table of the ball, indexed [dz + 3][dy + 3]: half width in x (-1: no row), the place of the
+// row's first entry in its layer word and the row's number of entries.
 struct LatRows {
     signed char ext[7][7];
     unsigned char first[7][7];
+    unsigned char width[7][7];  // entries of the row: 2 ext + 1, or 0 without a row
 };
 __host__ __device__ constexpr LatRows lat_rows_table() {
     LatRows t{};
@@ -58,6 +59,7 @@ __host__ __device__ constexpr LatRows lat_rows_table() {
             const int e = lat_ext(dy, dz);
             t.ext[dz + 3][dy + 3] = (signed char)e;
             t.first[dz + 3][dy + 3] = (unsigned char)(e >= 0 ? lat_bit(-e, dy, dz) : 0);
+            t.width[dz + 3][dy + 3] = (unsigned char)(e >= 0 ? 2 * e + 1 : 0);
         }
     return t;
 }
@@ -121,6 +123,27 @@ template <int P, typename W> __device__ __forceinline__ void lat_walk(W &w, cons
 template <int P> __device__ __forceinline__ int lat_first_row(int t, int NX) {
     const int sr = t / NX;
     return sr * P * NX + (t - sr * NX);
+}
+
+// First row of thread tl of block b, and whether the thread owns rows.  The rows are cut into lines of
+// NX (the rows i with the same i / NX: an x line of the lattice).
+//   cw = 0: a block takes BS consecutive threads of lat_first_row (whole lines, P per thread group).
+//   cw > 0 (a multiple of 32 that divides BS): a block takes a patch of cw consecutive x of BS / cw
+//   groups of P consecutive lines; the blocks of a band of (BS / cw) P lines run along x first.  The
+//   neighbour records of a patch (cw + 6 x, BS / cw P + 6 lines, 7 layers) are far fewer than those
+//   of whole lines, so more of them stay in L1 while the block walks.  Threads past the end of a line
+//   own nothing.  Either way every row i < n belongs to exactly one thread and one p.
+template <int P, int BS>
+__device__ __forceinline__ int lat_block_row(int b, int tl, int NX, int cw, bool &owns) {
+    if (cw == 0) {
+        owns = true;
+        return lat_first_row<P>(b * BS + tl, NX);
+    }
+    const int chunks = (NX + cw - 1) / cw;
+    const int band = b / chunks, g = tl / cw;
+    const int x = (b - band * chunks) * cw + (tl - g * cw);
+    owns = x < NX;
+    return ((band * (BS / cw) + g) * P) * NX + x;
 }
 
 }  // namespace tl

@@ -938,10 +938,10 @@ template <typename T, bool FRAC, bool VISC, int P> struct GradLatWalk {
 // memory for a separate stress pass.
 template <typename T, bool FRAC, bool VISC, bool FUSE, int P, int BS>
 __global__ void __launch_bounds__(BS, FUSE ? 5 : (P == 1 ? 8 : TLSPH_LAT_GRAD_MINB)) k_gradient_lat(StepArgs<T> a) {
-    const int t = blockIdx.x * BS + threadIdx.x;
     const int NX = a.lat_nx;
-    const int i0 = lat_first_row<P>(t, NX);
-    if (i0 >= a.n) return;
+    bool owns;
+    const int i0 = lat_block_row<P, BS>(blockIdx.x, threadIdx.x, NX, a.lat_cw, owns);
+    if (!owns || i0 >= a.n) return;
     GradLatWalk<T, FRAC, VISC, P> w{a, NX, a.lat_nxny};
     bool act[P];
 #pragma unroll
@@ -982,15 +982,15 @@ template <typename T, int P> struct P2LatWalk {
 template <typename T, bool FRAC, bool VISC, int P, int BS>
 __global__ void __launch_bounds__(BS, P == 1 ? 8 : (P == 2 ? TLSPH_LAT_P2_MINB : TLSPH_LAT_P4_MINB)) k_pass2_lat(StepArgs<T> a) {
     __shared__ bool s_last;
-    const int t = blockIdx.x * BS + threadIdx.x;
     const int NX = a.lat_nx;
-    const int i0 = lat_first_row<P>(t, NX);
+    bool owns;
+    const int i0 = lat_block_row<P, BS>(blockIdx.x, threadIdx.x, NX, a.lat_cw, owns);
     bool act[P];
     T vmag[P], amag[P];
     int sp[P];
 #pragma unroll
     for (int p = 0; p < P; p++) {
-        act[p] = i0 + p * NX < a.n;
+        act[p] = owns && i0 + p * NX < a.n;
         vmag[p] = amag[p] = T(0);
         sp[p] = 0;
     }
@@ -1009,6 +1009,150 @@ __global__ void __launch_bounds__(BS, P == 1 ? 8 : (P == 2 ? TLSPH_LAT_P2_MINB :
     }
 #pragma unroll
     for (int p = 0; p < P; p++) dev_block_maxima<T, BS>(a, act[p], sp[p], vmag[p], amag[p]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        dev_finalize(a);
+        if (threadIdx.x == 0) *a.done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- force pass streaming along z
+// Pass 2 on the lattice with a column of planes per thread: thread (q, c) takes the rows
+// i = z NXNY + c of planes z = q zc .. q zc + zc - 1 (c < NXNY: the place in a plane).  It walks the
+// planes zp = q zc - 3 .. q zc + zc + 2 once and keeps the sums of the seven rows that plane zp serves,
+// z = zp + 3 - k in slot k (entry dz = k - 3 of the ball), in registers.  A neighbour record
+// zp NXNY + c + dy NX + dx is loaded once and added to every slot whose ball holds (dx, dy, dz): 29
+// records per plane for 122 pairs, against one record per pair for one row per thread.  After plane zp
+// the row of slot 6 has all its entries; its sum is parked in G and the slots move up by one.  The rows
+// are updated (p2_finish) after the walk.
+//
+// Each row still receives its entries in ascending difference (planes ascending, then rows dy and dx
+// ascending within a plane), so the step is bit-identical to the other walks.
+template <typename T> struct ZsState {
+    P2Own<T, 3> o[7];
+    unsigned am;  // bit k: slot k holds a row of this thread's planes
+};
+template <int AY, int DX, int DZ, typename T>
+__device__ __forceinline__ void zs_dz(const StepArgs<T> &a, ZsState<T> &s, const P2Rec<T> &r, int j, const unsigned (&lm)[7]) {
+    constexpr int M = lat_ext(DX, AY);
+    if constexpr (DZ <= M) {
+        if constexpr (!(DX == 0 && AY == 0 && DZ == 0)) {
+            constexpr int k = DZ + 3;
+            if (s.am & (1u << k)) {
+                const bool on = ((lm[k] >> (DX + lat_ext(AY, DZ))) & 1u) != 0u;
+                if (neighbour_ok(a, j, on)) p2_pair<T, 3>(a, s.o[k], r, on);
+            }
+        }
+        zs_dz<AY, DX, DZ + 1>(a, s, r, j, lm);
+    }
+}
+template <int AY, int DX, typename T>
+__device__ __forceinline__ void zs_dx(const StepArgs<T> &a, ZsState<T> &s, int rb, const unsigned (&lm)[7]) {
+    constexpr int E = lat_ext(AY, 0);
+    if constexpr (DX <= E) {
+        int j = rb + DX;
+        if (!lat_index_ok(a, j)) j = a.n;
+        const P2Rec<T> r = p2_load<T, 3>(a, j);
+        zs_dz<AY, DX, -lat_ext(DX, AY)>(a, s, r, rb + DX, lm);
+        zs_dx<AY, DX + 1>(a, s, rb, lm);
+    }
+}
+// Row dy = +-AY of plane zp.  lm[k] holds slot k's layer word moved so that bit 0 is the first entry of
+// this row; it moves on past the row for the next one.
+template <int AY, typename T>
+__device__ __forceinline__ void zs_row(const StepArgs<T> &a, ZsState<T> &s, int rb, int dy, unsigned (&lm)[7]) {
+    zs_dx<AY, -lat_ext(AY, 0)>(a, s, rb, lm);
+#pragma unroll
+    for (int k = 0; k < 7; k++) lm[k] >>= c_lat_rows.width[k][dy + 3];
+}
+#ifndef TLSPH_ZS_MINB
+#define TLSPH_ZS_MINB 5
+#endif
+template <typename T, bool FRAC, bool VISC, int BS>
+__global__ void __launch_bounds__(BS, TLSPH_ZS_MINB) k_pass2_zs(StepArgs<T> a) {
+    __shared__ bool s_last;
+    const int NX = a.lat_nx, NXNY = a.lat_nxny, zc = a.lat_zc;
+    const int64_t t = (int64_t)blockIdx.x * BS + threadIdx.x;
+    const int q = (int)(t / NXNY), c = (int)(t - (int64_t)q * NXNY);
+    const int nz = (int)((a.n + NXNY - 1) / NXNY);
+    const int zb = q * zc, ze = min(zb + zc, nz);
+    T vmax = T(0), amax = T(0);
+    int sp = 0;
+    bool any = false;
+    if (zb < nz) {
+        ZsState<T> s;
+        s.am = 0u;
+#pragma unroll
+        for (int k = 0; k < 7; k++) {
+            s.o[k].xi = V4<T>{T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int p = 0; p < 3; p++) s.o[k].s2[p] = T(0);
+        }
+#pragma unroll 1
+        for (int zp = zb - 3; zp < ze + 3; zp++) {
+            // slot 0 takes the row z = zp + 3, whose first entries (dz = -3) lie in plane zp
+            {
+                const int zn = zp + 3;
+                const int64_t in = (int64_t)zn * NXNY + c;
+                const bool act = zn >= zb && zn < ze && in < a.n;
+                s.am = (s.am << 1) & 0x7fu;
+                if (act) {
+                    s.am |= 1u;
+                    const V4<T> x = a.X0V[in];
+                    s.o[0].xi = V4<T>{x.x, x.y, x.z, T(0)};
+                }
+#pragma unroll
+                for (int p = 0; p < 3; p++) s.o[0].s2[p] = T(0);
+            }
+            if (zp >= 0 && zp < nz && s.am != 0u) {
+                unsigned lm[7];
+#pragma unroll
+                for (int k = 0; k < 7; k++)
+                    lm[k] = (s.am >> k) & 1u ? __ldg(a.lmask + (int64_t)k * a.n + (int64_t)(zp + 3 - k) * NXNY + c) : 0u;
+                const int pb = zp * NXNY + c;
+#pragma unroll 1
+                for (int dy = -3; dy <= 3; dy++) {
+                    const int rb = pb + dy * NX;
+                    switch (dy < 0 ? -dy : dy) {
+                    case 0: zs_row<0>(a, s, rb, dy, lm); break;
+                    case 1: zs_row<1>(a, s, rb, dy, lm); break;
+                    case 2: zs_row<2>(a, s, rb, dy, lm); break;
+                    default: zs_row<3>(a, s, rb, dy, lm); break;
+                    }
+                }
+            }
+            // slot 6 (z = zp - 3) has its last entries (dz = +3): its sum goes to the first three arrays of
+            // G (F - I, which the stress pass has consumed), to be finished after the walk
+            if (s.am & 0x40u) {
+                const int i = (zp - 3) * NXNY + c;
+#pragma unroll
+                for (int p = 0; p < 3; p++) a.G[p * a.n + i] = s.o[6].s2[p];
+            }
+#pragma unroll
+            for (int k = 6; k > 0; k--) s.o[k] = s.o[k - 1];
+        }
+        // the update of the thread's rows, with the registers of the walk free again
+#pragma unroll 1
+        for (int z = zb; z < ze; z++) {
+            const int i = z * NXNY + c;
+            if (i >= a.n) break;
+            P2Own<T, 3> f;
+            f.xi = a.X0V[i];
+#pragma unroll
+            for (int p = 0; p < 3; p++) f.s2[p] = a.G[p * a.n + i];
+            T vmag, amag;
+            p2_finish<T, 3, FRAC, VISC>(a, i, f, vmag, amag);
+            sp = a.spec[i];
+            any = true;
+            vmax = fmax(vmax, vmag);
+            amax = fmax(amax, amag);
+        }
+    }
+    dev_block_maxima<T, BS>(a, any, sp, vmax, amax);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;

@@ -79,6 +79,8 @@ struct tlsph_ctx {
     int lat_nx = 0, lat_nxny = 0; // lattice walk (3D FP32 lattices): row and layer pitch, 0 = none
     unsigned *lmask = nullptr;    // lattice walk: one mask word per layer, 7 arrays of n
     int lat_rows_grad = 1, lat_rows_force = 2;  // rows per thread of the two lattice kernels
+    int lat_cw = 0;               // lattice kernels: x width of a block's patch of rows, 0 = whole rows
+    int lat_zc = 0;               // lattice force pass streaming along z: planes per thread, 0 = off
     bool fuse_stress = false;     // the stress runs in the tail of the deformation-gradient kernel
     int layout = TLSPH_LAYOUT_AUTO;
     void *S1 = nullptr;  // sum_j V_j w_ij (X_j - X_i)
@@ -370,6 +372,8 @@ template <typename T> StepArgs<T> make_args(tlsph_ctx *c) {
     a.lat_nx = lat ? c->lat_nx : 0;
     a.lat_nxny = lat ? c->lat_nxny : 0;
     a.lmask = lat ? c->lmask : nullptr;
+    a.lat_cw = lat ? c->lat_cw : 0;
+    a.lat_zc = lat ? c->lat_zc : 0;
     a.X0V = (const V4<T> *)c->X0V;
     a.S1 = (const V4<T> *)c->S1;
     a.ug_cur = (const V4<T> *)c->ug[cur];
@@ -1149,6 +1153,11 @@ template <typename T, int DIM> tlsph_status contact_launches(tlsph_ctx *c, const
 // ---- the lattice kernels (3D FP32 lattices): P rows per thread, 128 threads per block
 constexpr int kLatThreads = 128;
 inline unsigned lat_blocks(const tlsph_ctx *c, int P) {
+    if (c->lat_cw > 0) {  // bands of (threads / cw) P lines, each cut into patches cw wide along x
+        const int64_t lines = (c->n + c->lat_nx - 1) / c->lat_nx;
+        const int64_t band = (int64_t)(kLatThreads / c->lat_cw) * P;
+        return (unsigned)((lines + band - 1) / band * ((c->lat_nx + c->lat_cw - 1) / c->lat_cw));
+    }
     const int64_t rows = (int64_t)P * c->lat_nx;
     return blocks_for((c->n + rows - 1) / rows * c->lat_nx, kLatThreads);
 }
@@ -1165,6 +1174,14 @@ template <bool FRAC, bool VISC> tlsph_status launch_gradient_lat(tlsph_ctx *c, c
     return TLSPH_OK;
 }
 template <bool FRAC> tlsph_status launch_pass2_lat(tlsph_ctx *c, const StepArgs<float> &a) {
+    if (c->lat_zc > 0) {  // a column of zc planes per thread
+        const int64_t nz = (c->n + c->lat_nxny - 1) / c->lat_nxny;
+        const unsigned nb = blocks_for((int64_t)c->lat_nxny * ((nz + c->lat_zc - 1) / c->lat_zc), kLatThreads);
+        if (c->has_visc) k_pass2_zs<float, FRAC, true, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        else k_pass2_zs<float, FRAC, false, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
+        CKL();
+        return TLSPH_OK;
+    }
     const unsigned nb = lat_blocks(c, c->lat_rows_force);
     if (c->lat_rows_force == 4) {
         if (c->has_visc) k_pass2_lat<float, FRAC, true, 4, kLatThreads><<<nb, kLatThreads, 0, c->stream>>>(a);
@@ -2172,6 +2189,19 @@ tlsph_status tlsph_set_option(tlsph_ctx *c, int option, int value) {
     }
     if (option == TLSPH_OPT_FUSE_STRESS) {
         c->fuse_stress = value != 0;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_LATTICE_ZSTREAM) {
+        if (value < 0) return fail(c, TLSPH_ERR_ARG, "planes per thread must be >= 0");
+        c->lat_zc = value;
+        drop_graph(c);
+        return TLSPH_OK;
+    }
+    if (option == TLSPH_OPT_LATTICE_PATCH) {
+        if (value != 0 && value != 32 && value != 64 && value != 128)
+            return fail(c, TLSPH_ERR_ARG, "patch width must be 0, 32, 64 or 128");
+        c->lat_cw = value;
         drop_graph(c);
         return TLSPH_OK;
     }

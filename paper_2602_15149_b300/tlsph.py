@@ -24,7 +24,8 @@ FIELD = {"U": 0, "V": 1, "X": 2, "S": 3, "SDOT": 4, "H": 5, "EPSP": 6, "P": 7, "
          "STATE": 100}
 OPT_KERNEL_TIMING, OPT_RECORD_ACC, OPT_MODE, OPT_BLOCK, OPT_BARRIER_TEST, OPT_NEIGHBOUR_LAYOUT = 1, 2, 3, 4, 5, 6
 OPT_MEMORY_LIMIT = 7
-OPT_LATTICE_ROWS_GRADIENT, OPT_LATTICE_ROWS_FORCE, OPT_FUSE_STRESS = 8, 9, 10
+OPT_LATTICE_ROWS_GRADIENT, OPT_LATTICE_ROWS_FORCE, OPT_FUSE_STRESS, OPT_LATTICE_PATCH = 8, 9, 10, 11
+OPT_LATTICE_ZSTREAM = 12
 LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_STENCIL = 0, 1, 2
 MODE_LAUNCH, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 INTEGRATOR_EULER, INTEGRATOR_LEAPFROG = 1, 2

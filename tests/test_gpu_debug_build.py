@@ -24,10 +24,16 @@ cases = {"block_stencil": lambda: W.block_3d(nx=16, ny=12, nz=10),
          "notched_phase_field": lambda: W.notched_plate(nx=60, ny=24, model="svk"),
          "batched_tables": lambda: W.batched(nspec=12, n_min=40, n_max=400, seed=3),
          "irregular_csr": lambda: W.block_3d(nx=9, ny=8, nz=7, jitter=0.3, seed=5),
-         "contact": lambda: W.flyer_plate(n=10, dx=1e-3, gap=0.0, v=2.0, model="nh", precision="fp64")}
+         "contact": lambda: W.flyer_plate(n=10, dx=1e-3, gap=0.0, v=2.0, model="nh", precision="fp64"),
+         "lattice_zstream": lambda: W.block_3d(nx=24, ny=20, nz=16),
+         "lattice_patch": lambda: W.block_3d(nx=40, ny=9, nz=7)}
+options = {"lattice_zstream": {tlsph.OPT_LATTICE_ZSTREAM: 5},
+           "lattice_patch": {tlsph.OPT_LATTICE_PATCH: 32, tlsph.OPT_LATTICE_ROWS_FORCE: 4}}
 out = {}
 for name, make in cases.items():
     g = tlsph.from_case(make())
+    for k, v in options.get(name, {}).items():
+        g.set_option(k, v)
     st = g.step(100, check=False)
     out[name] = {"status": int(st), "u": g.read_state("U").tolist(), "stencil": g.get_info()["stencil"]}
 print(json.dumps(out))

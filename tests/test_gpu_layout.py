@@ -117,6 +117,65 @@ def test_lattice_layout_is_bit_identical_to_stencil_and_csr(which, rows, fuse):
     assert lat.get_info()["kernel_launches"] < sten.get_info()["kernel_launches"] or not fuse
 
 
+@pytest.mark.parametrize("which", sorted(LATTICE_CASES))
+@pytest.mark.parametrize("patch", [32, 64, 128])
+@pytest.mark.parametrize("rows", [(1, 2), (2, 4), (1, 1)])
+def test_lattice_patches_are_bit_identical_to_whole_lines(which, patch, rows):
+    # blocks that take patches of x (none of these lattices has an x line a multiple of 32 long but the
+    # 128-wide patch of the 24 and 40 wide ones: the last patch of each band has idle threads) give the
+    # same step as blocks that take whole lines
+    make, _, _ = LATTICE_CASES[which]
+    case = make()
+    ref, pat = tlsph.from_case(case), tlsph.from_case(case)
+    for g in (ref, pat):
+        g.set_option(tlsph.OPT_LATTICE_ROWS_GRADIENT, rows[0])
+        g.set_option(tlsph.OPT_LATTICE_ROWS_FORCE, rows[1])
+    pat.set_option(tlsph.OPT_LATTICE_PATCH, patch)
+    assert pat.get_info()["lattice_nx"] > 0
+    for g in (ref, pat):
+        g.step(60)
+    for f in ("U", "V", "S", "P", "F", "EPSP"):
+        assert np.array_equal(ref.read_state(f), pat.read_state(f)), f
+    assert ref.time() == pat.time()
+    with pytest.raises(tlsph.TLSPHError):
+        pat.set_option(tlsph.OPT_LATTICE_PATCH, 48)
+
+
+@pytest.mark.parametrize("which", sorted(LATTICE_CASES))
+@pytest.mark.parametrize("zc", [1, 3, 5, 64])
+def test_force_pass_streaming_along_z_is_bit_identical(which, zc):
+    # columns of zc planes per thread (one plane; chunks that do not divide the plane count; one chunk
+    # for the whole lattice): each row still adds its entries in ascending difference
+    make, _, _ = LATTICE_CASES[which]
+    case = make()
+    ref, zs = tlsph.from_case(case), tlsph.from_case(case)
+    zs.set_option(tlsph.OPT_LATTICE_ZSTREAM, zc)
+    for g in (ref, zs):
+        g.step(60)
+    for f in ("U", "V", "S", "P", "F", "EPSP"):
+        assert np.array_equal(ref.read_state(f), zs.read_state(f)), f
+    assert ref.time() == zs.time()
+    # the energy sums meet in FP64 atomics across blocks, whose order varies from run to run
+    e_ref, e_zs = ref.energies(), zs.energies()
+    assert all(np.isclose(e_ref[k], e_zs[k], rtol=1e-12, atol=0) for k in e_ref), (e_ref, e_zs)
+    with pytest.raises(tlsph.TLSPHError):
+        zs.set_option(tlsph.OPT_LATTICE_ZSTREAM, -1)
+
+
+def test_force_pass_streaming_along_z_in_graphs_and_with_kernel_timing():
+    case = W.block_3d(nx=24, ny=20, nz=16)
+    ref, zs = tlsph.from_case(case), tlsph.from_case(case)
+    zs.set_option(tlsph.OPT_LATTICE_ZSTREAM, 4)
+    zs.set_option(tlsph.OPT_MODE, tlsph.MODE_GRAPH)
+    ref.step(30)
+    zs.step(30)
+    zs.set_option(tlsph.OPT_KERNEL_TIMING, 1)
+    ref.step(10)
+    zs.step(10)
+    assert zs.kernel_times()["pass2_launches"] > 0
+    assert np.array_equal(ref.read_state("U"), zs.read_state("U"))
+
+
 def test_lattice_layout_only_where_it_applies():
     # FP64, 2D, several specimens and a jitter that reaches the next lattice shell keep the table walks
     assert tlsph.from_case(W.block_3d(nx=16, ny=14, nz=12, precision="fp64")).get_info()["lattice_nx"] == 0
