@@ -1467,6 +1467,18 @@ __device__ __forceinline__ void sur_prefetch_tile(const StepArgs<float> &a, int 
     if (a1 > a0) prefetch_l2_bulk(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
 }
 
+// Append row i (when need) to the list of rows left to the exact update: one atomic per warp.  All 32
+// lanes of the warp call it.
+__device__ __forceinline__ void sur_list_push(int *list, unsigned *nlist, bool need, int i) {
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m == 0u) return;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned base = 0u;
+    if (lane == 0u) base = atomicAdd(nlist, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (need) list[base + (unsigned)__popc(m & ((1u << lane) - 1u))] = i;
+}
+
 __device__ __forceinline__ void sur_count(unsigned long long *counters, int n_mlp, int n_out, int n_el) {
     for (int o = 16; o > 0; o >>= 1) {
         n_mlp += __shfl_xor_sync(0xffffffffu, n_mlp, o);
@@ -1485,11 +1497,11 @@ __device__ __forceinline__ void sur_count(unsigned long long *counters, int n_ml
 // normalised features lie inside the training envelope takes the plastic corrections of P and of
 // its state from the network (BF16 mma.sync, FP32 accumulation) on top of the closed-form
 // elastic predictor; with scope 1 only particles whose trial state yields do.  Every other
-// particle is marked in exact[] for k_stress_exact, which runs next.  A tile in which no
+// particle goes to the list exact (nexact rows) for k_stress_exact, which runs next.  A tile in which no
 // particle uses the network skips the forward pass.
 // counters: [0] network, [1] J2 outside the envelope, [2] elastic trial states (scope 1).
 template <int DIM, bool FRAC>
-__global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, SurrogateDev s, uint8_t *exact,
+__global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, SurrogateDev s, int *exact, unsigned *nexact,
                                                        unsigned long long *counters) {
     extern __shared__ __align__(16) unsigned char smraw[];
     MlpSmem &sm = *reinterpret_cast<MlpSmem *>(smraw);
@@ -1508,8 +1520,8 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
             for (int p = 0; p < DIM; p++)
                 for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
             use = sur_features<DIM, FRAC>(a, s, i, G, xn, n_out, n_el);
-            exact[i] = use ? 0 : 1;
         }
+        bool need = active && !use;
         for (int c = 0; c < 16; c++) sm.X[threadIdx.x][c] = __float2bfloat16_rn(use ? xn[c] : 0.0f);
         if (__syncthreads_or(use)) {  // block-uniform
             mlp_forward_block(sm);
@@ -1517,11 +1529,12 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
                 if (sur_apply<DIM, FRAC>(a, s, i, G, sm.Y[threadIdx.x])) {
                     n_mlp++;
                 } else {  // rejected output: the exact update serves the particle
-                    exact[i] = 1;
+                    need = true;
                     n_out++;
                 }
             }
         }
+        sur_list_push(exact, nexact, need, i);
         __syncthreads();
     }
     sur_count(counters, n_mlp, n_out, n_el);
@@ -1532,8 +1545,8 @@ __global__ void __launch_bounds__(128, 2) k_stress_sur(StepArgs<float> a, Surrog
 // particles.  A wait on the tensor cores that runs out sets kFlagTimeout and ends the group's
 // work (its remaining particles keep their old state).
 template <int DIM, bool FRAC>
-__global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<float> a, SurrogateDev s,
-                                                                     uint8_t *exact, unsigned long long *counters) {
+__global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<float> a, SurrogateDev s, int *exact,
+                                                                     unsigned *nexact, unsigned long long *counters) {
     extern __shared__ __align__(16) unsigned char smraw[];
     MlpTcSmem &sm = *reinterpret_cast<MlpTcSmem *>(smraw);
     mlp_tc_setup(sm, s);
@@ -1553,8 +1566,8 @@ __global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<f
             for (int p = 0; p < DIM; p++)
                 for (int q = 0; q < DIM; q++) G(p, q) = a.G[(p * DIM + q) * n + i];
             use = sur_features<DIM, FRAC>(a, s, i, G, xn, n_out, n_el);
-            exact[i] = use ? 0 : 1;
         }
+        bool need = active && !use;
         if (!use)
             for (int c = 0; c < 16; c++) xn[c] = 0.0f;
         mlp_tc_put_row(sm, g, r, xn);
@@ -1569,27 +1582,33 @@ __global__ void __launch_bounds__(128 * kTcGroups, 1) k_stress_sur_tc(StepArgs<f
                 if (sur_apply<DIM, FRAC>(a, s, i, G, yn)) {
                     n_mlp++;
                 } else {  // rejected output: the exact update serves the particle
-                    exact[i] = 1;
+                    need = true;
                     n_out++;
                 }
             }
         }
+        sur_list_push(exact, nexact, need, i);
     }
     mlp_tc_finish(sm, g, phase, pending);
     sur_count(counters, n_mlp, n_out, n_el);
 }
 
-// The exact constitutive update of the particles k_stress_sur left to it (exact[i] = 1).
+// The exact constitutive update of the particles the network pass left to it: the nexact rows of the
+// list exact, in the order the network pass appended them (each particle's update is its own, so the
+// order does not change a result).  Consecutive threads take consecutive list entries, so a warp's lanes
+// all work however few and scattered the rows are.
 template <int DIM, bool FRAC, int BS>
-__global__ void __launch_bounds__(BS) k_stress_exact(StepArgs<float> a, const uint8_t *exact) {
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= a.n || !exact[i]) return;
-    float Gm[DIM][DIM];
+__global__ void __launch_bounds__(BS) k_stress_exact(StepArgs<float> a, const int *exact, const unsigned *nexact) {
+    const unsigned cnt = *nexact;
+    for (unsigned k = blockIdx.x * BS + threadIdx.x; k < cnt; k += gridDim.x * BS) {
+        const int i = exact[k];
+        float Gm[DIM][DIM];
 #pragma unroll
-    for (int p = 0; p < DIM; p++)
+        for (int p = 0; p < DIM; p++)
 #pragma unroll
-        for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * a.n + i];
-    dev_stress<float, DIM, FRAC, false>(a, i, Gm);
+            for (int q = 0; q < DIM; q++) Gm[p][q] = a.G[(p * DIM + q) * a.n + i];
+        dev_stress<float, DIM, FRAC, false>(a, i, Gm);
+    }
 }
 
 // ---------------------------------------------------------------- diagnostics

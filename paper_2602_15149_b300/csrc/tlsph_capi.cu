@@ -107,7 +107,8 @@ struct tlsph_ctx {
     __nv_bfloat16 *sur_W = nullptr;
     float *sur_bias = nullptr, *sur_norm = nullptr;
     unsigned long long *sur_count = nullptr;  // network, outside the envelope, elastic trial
-    uint8_t *sur_exact = nullptr;             // particles left to the exact update in a step
+    int *sur_exact = nullptr;                 // list of the particles left to the exact update in a step
+    unsigned *sur_nexact = nullptr;           // and its length
     int sur_tensor = TLSPH_TENSOR_TCGEN05;    // tensor path of the network pass
     int sur_scope = 0;
     // user-defined expressions (Sec. 3.3): compiled programs, their device tables (uploaded when the set
@@ -268,6 +269,7 @@ void free_device(tlsph_ctx *c) {
     c->sur_bias = c->sur_norm = nullptr;
     c->sur_count = nullptr;
     c->sur_exact = nullptr;
+    c->sur_nexact = nullptr;
     c->sur_on = false;
     c->built = false;
 }
@@ -1117,9 +1119,12 @@ template <int DIM, bool FRAC> tlsph_status launch_stress_sur(tlsph_ctx *c, const
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int64_t ctas = (c->n + threads - 1) / threads;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * nsm, ctas));
-    kern<<<grid, threads, smem, c->stream>>>(a, sur_dev(c), c->sur_exact, c->sur_count);
+    CK(cudaMemsetAsync(c->sur_nexact, 0, sizeof(unsigned), c->stream));
+    kern<<<grid, threads, smem, c->stream>>>(a, sur_dev(c), c->sur_exact, c->sur_nexact, c->sur_count);
     CKL();
-    k_stress_exact<DIM, FRAC, kThreads><<<blocks_for(c->n), kThreads, 0, c->stream>>>(a, c->sur_exact);
+    // a grid-stride walk of the list, at most eight blocks per SM
+    const unsigned gx = (unsigned)std::min<int64_t>(blocks_for(c->n), (int64_t)8 * std::max(nsm, 1));
+    k_stress_exact<DIM, FRAC, kThreads><<<gx, kThreads, 0, c->stream>>>(a, c->sur_exact, c->sur_nexact);
     CKL();
     return TLSPH_OK;
 }
@@ -2790,7 +2795,8 @@ tlsph_status tlsph_set_surrogate(tlsph_ctx *c, const tlsph_mlp *m, int scope) {
         DA(c->sur_bias, (3 * kHid + kOut) * 4);
         DA(c->sur_norm, 96 * 4);
         DA(c->sur_count, 3 * sizeof(unsigned long long));
-        DA(c->sur_exact, c->n);
+        DA(c->sur_exact, c->n * sizeof(int));
+        DA(c->sur_nexact, sizeof(unsigned));
     }
     CK(cudaStreamSynchronize(m->stream));
     CK(cudaMemcpyAsync(c->sur_W, m->Wb, kNumWeights * 2, cudaMemcpyDeviceToDevice, c->stream));
