@@ -9,8 +9,8 @@ block and the stencil layout for the 2D cases).
 * 2D notched phase-field plate, 500 x 200 = 100,000 particles, against the oracle run step for
   step over the full 4000 steps (compared every 500 steps): u and s within 1e-4 (relative L2)
   throughout, the damage of every particle within 1e-3 over the first 1000 steps (later, a
-  particle that breaks a step earlier or later differs by more), the bounds of the phase field
-  and the irreversibility of the history functional.
+  particle that breaks a step earlier or later differs by more: at most one particle in a thousand
+  may), the bounds of the phase field and the irreversibility of the history functional.
 * 512 independent 2D specimens (about 6M particles): after 300 steps of the whole batch, the
   smallest, a median and the largest specimen against the oracle run of that specimen alone.
 
@@ -107,11 +107,14 @@ def test_notched_plate_full_size():
         s_g, s_o = g.read_state("S"), o.read("S")
         es = float(np.abs(s_g - s_o).max())
         rs = rel_l2(s_g, s_o)
-        print("notched 500 x 200, %d steps: rel-L2(u) %.3e max |ds| %.3e rel-L2(s) %.3e min s %.4f"
-              % (500 * (k + 1), eu, es, rs, s_o.min()))
+        off = float(np.mean(np.abs(s_g - s_o) > 1e-3))
+        print("notched 500 x 200, %d steps: rel-L2(u) %.3e max |ds| %.3e rel-L2(s) %.3e min s %.4f, "
+              "share of particles off by more than 1e-3 %.2e" % (500 * (k + 1), eu, es, rs, s_o.min(), off))
         assert eu <= 1e-4 and rs <= 1e-4
         if 500 * (k + 1) <= 1000:  # the stated bars hold over the first 1000 steps
             assert es <= 1e-3
+        else:  # later, only particles at the crack front that break a step apart may differ more
+            assert off <= 1e-3
         assert s_g.min() >= 0.0 and s_g.max() <= 1.0
     info = g.get_info()
     assert info["nonfinite"] == 0
