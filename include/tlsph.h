@@ -328,7 +328,8 @@ enum {
                                      * its state; an allocation past it returns TLSPH_ERR_OOM as a failed cudaMalloc
                                      * would, and the context stays usable (tests inject allocation failures with it) */
     TLSPH_OPT_LATTICE_ROWS_GRADIENT = 8, /* lattice layout: rows per thread of the deformation-gradient kernel, 1
-                                          * (default) or 2 */
+                                          * (default) or 2 (without phase field in paired FP32 arithmetic,
+                                          * bit-identical to one row) */
     TLSPH_OPT_LATTICE_ROWS_FORCE = 9,    /* lattice layout: rows per thread of the force kernel, 1, 2 (default) or 4 */
     TLSPH_OPT_FUSE_STRESS = 10,          /* lattice layout: 1 computes the stress in the tail of the
                                           * deformation-gradient kernel (two launches per step), 0 (default) in its

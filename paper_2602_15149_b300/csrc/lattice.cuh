@@ -119,6 +119,59 @@ template <int P, typename W> __device__ __forceinline__ void lat_walk(W &w, cons
     }
 }
 
+// The walk of two rows with one pair body for both (W::pair2(record, j, on0, on1), e.g. in paired FP32
+// arithmetic): a record outside one row's ball is computed for that row too, with its entry off.  The
+// entries of each row are visited in the same order as by lat_walk.  (Splitting off the records only one
+// row uses, at the x edges of a ball row, into one-row bodies measured slower: the edge loops cost more
+// instructions than the packed bodies they save.)
+template <int EU, typename W>
+__device__ __forceinline__ void lat_row_pk(W &w, int rb, const int e[2], const unsigned bits[2]) {
+#pragma unroll
+    for (int k = 0; k <= 2 * EU; k++) {
+        const int dx = k - EU;
+        const int j = rb + dx;
+        const auto rec = w.load(j);
+        const bool on0 = dx >= -e[0] && dx <= e[0] && ((bits[0] >> k) & 1u) != 0u;
+        const bool on1 = dx >= -e[1] && dx <= e[1] && ((bits[1] >> k) & 1u) != 0u;
+        w.pair2(rec, j, on0, on1);
+    }
+}
+template <typename W> __device__ __forceinline__ void lat_walk_pk(W &w, const unsigned *lmask, int n, int i0,
+                                                                const bool act[2]) {
+#pragma unroll 1
+    for (int L = 0; L < kLatLayers; L++) {
+        unsigned lm[2];
+#pragma unroll
+        for (int p = 0; p < 2; p++) lm[p] = act[p] ? __ldg(lmask + (int64_t)L * n + i0 + p * w.NX) : 0u;
+        const int M = c_lat_rows.ext[L][3];
+        const int base = i0 + (L - 3) * w.NXNY;
+#pragma unroll 1
+        for (int yp = -M; yp <= M + 1; yp++) {
+            int e[2];
+            unsigned bits[2];
+            int EU = -1;
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const int dy = yp - p;
+                e[p] = dy >= -M && dy <= M ? (int)c_lat_rows.ext[L][dy + 3] : -1;
+                EU = e[p] > EU ? e[p] : EU;
+            }
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const int dy = yp - p;
+                bits[p] = e[p] >= 0 ? (lm[p] >> c_lat_rows.first[L][dy + 3]) << (EU - e[p]) : 0u;
+            }
+            const int rb = base + yp * w.NX;
+            switch (EU) {
+            case 0: lat_row_pk<0>(w, rb, e, bits); break;
+            case 1: lat_row_pk<1>(w, rb, e, bits); break;
+            case 2: lat_row_pk<2>(w, rb, e, bits); break;
+            default: lat_row_pk<3>(w, rb, e, bits); break;
+            }
+        }
+    }
+}
+
 // Rows of thread t: i0 = (t / NX) P NX + t % NX; threads = ceil(n / (P NX)) NX.
 template <int P> __device__ __forceinline__ int lat_first_row(int t, int NX) {
     const int sr = t / NX;

@@ -911,9 +911,12 @@ template <typename T> __device__ __forceinline__ bool lat_index_ok(const StepArg
 #endif
 }
 // Blocks per SM the lattice kernels are compiled for (register budget): pass 1 with one or two rows per
-// thread, pass 2 with one, two or four.
+// thread (two rows: in paired FP32 without phase field), pass 2 with one, two or four.
 #ifndef TLSPH_LAT_GRAD_MINB
 #define TLSPH_LAT_GRAD_MINB 6
+#endif
+#ifndef TLSPH_LAT_GRAD_PK_MINB  // pass 1 with two rows in paired FP32 (96 registers)
+#define TLSPH_LAT_GRAD_PK_MINB 5
 #endif
 #ifndef TLSPH_LAT_P2_MINB
 #define TLSPH_LAT_P2_MINB 6
@@ -933,15 +936,139 @@ template <typename T, bool FRAC, bool VISC, int P> struct GradLatWalk {
         if (neighbour_ok(a, j, on)) grad_pair<T, 3, FRAC, VISC>(a, o[p], r, on);
     }
 };
+// Pass 1 for two rows in paired FP32 (fma.rn.f32x2 and its add and multiply, one instruction for the
+// same operation of both rows): lane 0 is row i0, lane 1 row i0 + NX.  Each lane repeats grad_pair's
+// operations in its order and rounding (a - b as a + (-b), fma(-r, 1/2h, 1) as fma(r, -1/2h, 1), both
+// exact rewritings), so the two rows get the bit patterns the scalar body gives them.  Without phase
+// field only.
+__device__ __forceinline__ float2 f2_bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <bool VISC> struct GradOwnPk {
+    float2 nx[3], nu[3], nv[3];  // -X_i, -u_i, -v_i of the two rows
+    float2 b2h, ncvis;           // beta2 h and -beta1 c0 of the rows' materials
+    float2 B[3][3], s3[3];
+};
+template <bool VISC> struct GradLatWalkPk {
+    const StepArgs<float> &a;
+    int NX, NXNY;
+    GradOwnPk<VISC> o;
+    __device__ __forceinline__ GradRec<float> load(int j) const {
+        if (!lat_index_ok(a, j)) j = a.n;
+        return grad_load<float, false, VISC>(a, j);
+    }
+    __device__ __forceinline__ void pair2(const GradRec<float> &r, int j, bool on0, bool on1) {
+        if (!neighbour_ok(a, j, on0 || on1)) return;
+        float2 d[3], du[3];
+        d[0] = f2_add(f2_bc(r.xj.x), o.nx[0]);
+        d[1] = f2_add(f2_bc(r.xj.y), o.nx[1]);
+        du[0] = f2_add(f2_bc(r.uj.x), o.nu[0]);
+        du[1] = f2_add(f2_bc(r.uj.y), o.nu[1]);
+        d[2] = f2_add(f2_bc(r.xj.z), o.nx[2]);
+        du[2] = f2_add(f2_bc(r.uj.z), o.nu[2]);
+        float2 r2 = f2_mul(d[0], d[0]);
+        r2 = f2_fma(d[1], d[1], r2);
+        r2 = f2_fma(d[2], d[2], r2);
+        float2 rs;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.x) : "f"(r2.x));
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs.y) : "f"(r2.y));
+        const float2 t = f2_fma(f2_mul(r2, rs), f2_bc(-a.inv2h), f2_bc(1.0f));
+        const float2 w = f2_mul(f2_mul(t, t), t);
+        float2 aw = f2_mul(w, f2_bc(r.xj.w));
+        aw.x = on0 ? aw.x : 0.0f;
+        aw.y = on1 ? aw.y : 0.0f;
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+            const float2 c = f2_mul(aw, du[p]);
+#pragma unroll
+            for (int q = 0; q < 3; q++) o.B[p][q] = f2_fma(c, d[q], o.B[p][q]);
+        }
+        if (VISC) {
+            float2 dv[3];
+            dv[0] = f2_add(f2_bc(r.vsj.x), o.nv[0]);
+            dv[1] = f2_add(f2_bc(r.vsj.y), o.nv[1]);
+            dv[2] = f2_add(f2_bc(r.vsj.z), o.nv[2]);
+            float2 vX = f2_mul(dv[0], d[0]);
+            vX = f2_fma(dv[1], d[1], vX);
+            vX = f2_fma(dv[2], d[2], vX);
+            float2 vx = f2_fma(dv[0], du[0], vX);
+            vx = f2_fma(dv[1], du[1], vx);
+            vx = f2_fma(dv[2], du[2], vx);
+            const float2 den = f2_add(r2, f2_bc(a.visc_eps));
+            float2 g;
+            asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(g.x) : "f"(vX.x), "f"(den.x));
+            asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(g.y) : "f"(vX.y), "f"(den.y));
+            float2 c = f2_mul(f2_mul(f2_mul(f2_bc(r.uj.w), w), g), f2_fma(o.b2h, g, o.ncvis));
+            c.x = on0 && vx.x < 0.0f ? c.x : 0.0f;
+            c.y = on1 && vx.y < 0.0f ? c.y : 0.0f;
+#pragma unroll
+            for (int p = 0; p < 3; p++) o.s3[p] = f2_fma(c, d[p], o.s3[p]);
+        }
+    }
+};
+// Rows i0 and i0 + NX (active flags act) of the paired pass 1: set up, walk, and the rows' F - I and sums
+// to memory as k_gradient_lat stores them.
+template <bool VISC>
+__device__ __forceinline__ void grad_lat_pk(const StepArgs<float> &a, int i0, const bool act[2]) {
+    const int NX = a.lat_nx;
+    GradLatWalkPk<VISC> w{a, NX, a.lat_nxny};
+    GradOwn<float, 3> so[2];
+#pragma unroll
+    for (int p = 0; p < 2; p++) grad_begin<float, 3, false, VISC>(a, act[p] ? i0 + p * NX : i0, so[p]);
+    w.o.nx[0] = make_float2(-so[0].xi.x, -so[1].xi.x);
+    w.o.nx[1] = make_float2(-so[0].xi.y, -so[1].xi.y);
+    w.o.nx[2] = make_float2(-so[0].xi.z, -so[1].xi.z);
+    w.o.nu[0] = make_float2(-so[0].ui.x, -so[1].ui.x);
+    w.o.nu[1] = make_float2(-so[0].ui.y, -so[1].ui.y);
+    w.o.nu[2] = make_float2(-so[0].ui.z, -so[1].ui.z);
+    w.o.nv[0] = make_float2(-so[0].vsi.x, -so[1].vsi.x);
+    w.o.nv[1] = make_float2(-so[0].vsi.y, -so[1].vsi.y);
+    w.o.nv[2] = make_float2(-so[0].vsi.z, -so[1].vsi.z);
+    w.o.b2h = make_float2(so[0].b2h, so[1].b2h);
+    w.o.ncvis = make_float2(-so[0].cvis, -so[1].cvis);
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        w.o.s3[p] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 3; q++) w.o.B[p][q] = make_float2(0.0f, 0.0f);
+    }
+    lat_walk_pk(w, a.lmask, a.n, i0, act);
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        so[0].s3[p] = w.o.s3[p].x;
+        so[1].s3[p] = w.o.s3[p].y;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            so[0].B[p][q] = w.o.B[p][q].x;
+            so[1].B[p][q] = w.o.B[p][q].y;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        if (!act[p]) continue;
+        const int i = i0 + p * NX;
+        float Gm[3][3], lap;
+        grad_finish<float, 3, false>(a, i, so[p], Gm, lap);
+        grad_store<float, 3, false, VISC>(a, i, so[p], Gm, lap);
+    }
+}
+
 // Pass 1 on the lattice: F - I and the viscosity and Laplacian sums of P rows per thread, then (FUSE)
 // their stress and what pass 2 takes of them in the same thread, or (!FUSE) F - I and the sums to
 // memory for a separate stress pass.
 template <typename T, bool FRAC, bool VISC, bool FUSE, int P, int BS>
-__global__ void __launch_bounds__(BS, FUSE ? 5 : (P == 1 ? 8 : TLSPH_LAT_GRAD_MINB)) k_gradient_lat(StepArgs<T> a) {
+__global__ void __launch_bounds__(BS, FUSE ? 5 : (P == 1 ? 8 : (FRAC ? TLSPH_LAT_GRAD_MINB : TLSPH_LAT_GRAD_PK_MINB)))
+    k_gradient_lat(StepArgs<T> a) {
     const int NX = a.lat_nx;
     bool owns;
     const int i0 = lat_block_row<P, BS>(blockIdx.x, threadIdx.x, NX, a.lat_cw, owns);
     if (!owns || i0 >= a.n) return;
+    if constexpr (P == 2 && !FRAC && !FUSE && sizeof(T) == 4) {  // two rows in paired FP32
+        const bool act2[2] = {true, i0 + NX < a.n};
+        grad_lat_pk<VISC>(a, i0, act2);
+        return;
+    }
     GradLatWalk<T, FRAC, VISC, P> w{a, NX, a.lat_nxny};
     bool act[P];
 #pragma unroll
