@@ -428,13 +428,17 @@ tlsph_status tlsph_mlp_gradients(tlsph_mlp *mlp, const float *x, const float *y,
 /* y = network(x) for n raw rows (denormalised outputs); outside[r] (may be NULL) = 1 when row r
  * lies outside the envelope.  TLSPH_ERR_TIMEOUT if a wait on the tensor cores ran out. */
 tlsph_status tlsph_mlp_forward(tlsph_mlp *mlp, int64_t n, const float *x, float *y, int32_t *outside);
-/* Tensor-core path of the inference kernels (tlsph_mlp_forward and the surrogate pass of a context
- * that tlsph_set_surrogate gives this network):
+/* Tensor-core path of the network's kernels (tlsph_mlp_forward, the surrogate pass of a context that
+ * tlsph_set_surrogate gives this network, and the GEMMs of tlsph_mlp_train_step and
+ * tlsph_mlp_gradients):
  *  TLSPH_TENSOR_TCGEN05 (default): tcgen05.mma, M = 128 x N = 128 (16 for the output layer) x K = 16,
- *    operands in shared memory, FP32 accumulators in tensor memory, one CTA of 128 threads per tile
- *    of 128 rows;
- *  TLSPH_TENSOR_MMA_SYNC: warp-level mma.sync.m16n8k16, activations in registers.
- * Both take BF16 operands and accumulate in FP32; they differ only in summation order. */
+ *    operands in shared memory, FP32 accumulators in tensor memory; inference in CTAs of four groups
+ *    of 128 threads, each group a tile of 128 rows; training one CTA of 128 threads per 128 x 128
+ *    output tile;
+ *  TLSPH_TENSOR_MMA_SYNC: warp-level mma.sync.m16n8k16 (inference with the activations in registers).
+ * Both take BF16 operands and accumulate in FP32; they differ only in summation order.  A wait on the
+ * tensor cores that runs out (about a second) makes the call that syncs on it (tlsph_mlp_forward,
+ * tlsph_mlp_gradients, tlsph_mlp_train_step with a loss pointer) return TLSPH_ERR_TIMEOUT. */
 #define TLSPH_TENSOR_MMA_SYNC 0
 #define TLSPH_TENSOR_TCGEN05 1
 tlsph_status tlsph_mlp_set_tensor_path(tlsph_mlp *mlp, int path);

@@ -270,4 +270,124 @@ __global__ void __launch_bounds__(128 * kTcGroups, 1) k_mlp_forward_tc(int64_t n
     mlp_tc_finish(sm, g, phase, pending);
 }
 
+// ------------------------------------------------------------------ training GEMM on tcgen05
+// C[M x N] = A[M x K] B[N x K]^T (+ bias), A and B bf16 row-major (K contiguous), as k_gemm_bf16 with the
+// same epilogues (EPI 0: C only; 1: also Aout = SiLU(C) in bf16; 2: Aout = bf16(C)).  N is 16 or a
+// multiple of 128 up to the grid's reach, K a multiple of 16, M anything.  One CTA of 128 threads per
+// output tile of 128 rows x NT = min(128, N - n0) columns: each K stage of up to 128 columns of A and B
+// goes to shared memory in the K-major core-matrix layout, one thread issues its K / 16 MMAs
+// (M = 128, N = NT, K = 16) into the tile's TMEM accumulator and commits them to the CTA's barrier;
+// after the last stage thread r reads row r of the accumulator (tcgen05.ld) into shared memory, from where
+// the CTA writes the outputs in runs of consecutive columns.  A
+// wait that runs out adds one to flag and ends the tile without output.
+constexpr int kGemmKc = 128;
+struct __align__(16) GemmTcSmem {
+    uint8_t A[kGemmKc / 8 * 2048];  // 128 rows x kGemmKc bf16
+    uint8_t B[kGemmKc / 8 * 2048];  // NT rows x kGemmKc bf16
+    unsigned long long mbar;
+    unsigned tmem;
+};
+// The epilogue of the tile's columns col0 .. col0 + NC - 1 (k_gemm_bf16's: v = accumulator + bias to C,
+// and SiLU(v) or v in bf16 to Aout).  Thread r puts row r's accumulators (v) into shared memory st (pitch
+// NC + 1 floats: no bank conflicts either way), then the 128 threads write whole row segments: C and Aout
+// are written in runs of consecutive columns.
+template <int EPI, int NC>
+__device__ __forceinline__ void gemm_tc_out(const uint32_t (&v)[NC], float *st, int m0, int M, int col0, int N,
+                                            const float *bias, float *C, __nv_bfloat16 *Aout) {
+    const int r = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < NC; c++) st[r * (NC + 1) + c] = __uint_as_float(v[c]);
+    __syncthreads();
+    constexpr int NP = NC / 2;  // column pairs of a row
+    for (int e = r; e < 128 * NP; e += 128) {
+        const int row = e / NP, cp = e - row * NP, c = 2 * cp, col = col0 + c;
+        if (m0 + row >= M) continue;
+        const float a0 = st[row * (NC + 1) + c], a1 = st[row * (NC + 1) + c + 1];
+        const float v0 = bias ? a0 + bias[col] : a0, v1 = bias ? a1 + bias[col + 1] : a1;
+        *reinterpret_cast<float2 *>(C + (size_t)(m0 + row) * N + col) = make_float2(v0, v1);
+        if (EPI == 1) *reinterpret_cast<uint32_t *>(Aout + (size_t)(m0 + row) * N + col) = silu_bf16x2(v0, v1);
+        else if (EPI == 2) *reinterpret_cast<uint32_t *>(Aout + (size_t)(m0 + row) * N + col) = pack_bf16(v0, v1);
+    }
+    __syncthreads();
+}
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
+                                                 const float *bias, float *C, __nv_bfloat16 *Aout, int *flag) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GemmTcSmem &sm = *reinterpret_cast<GemmTcSmem *>(smraw);
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128, r = threadIdx.x;
+    const int NT = min(128, N - n0);
+    const unsigned ncols = NT > 32 ? 128u : 32u;
+    if (r == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&sm.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    if (r < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&sm.tmem)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const unsigned tmem = sm.tmem;
+    const uint32_t idesc = tc_idesc_bf16(128, NT);
+    const unsigned lbo_b = (unsigned)NT * 16u;
+    unsigned phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K && ok; k0 += kGemmKc) {
+        const int kc = min(kGemmKc, K - k0), kb8 = kc / 8;
+        for (int u = r; u < 128 * kb8; u += 128) {
+            const int row = u / kb8, kb = u - row * kb8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m0 + row < M) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + row) * K + k0 + 8 * kb);
+            *reinterpret_cast<uint4 *>(sm.A + kb * 2048 + row * 16) = v;
+        }
+        for (int u = r; u < NT * kb8; u += 128) {
+            const int row = u / kb8, kb = u - row * kb8;
+            const uint4 v = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + row) * K + k0 + 8 * kb);
+            *reinterpret_cast<uint4 *>(sm.B + kb * lbo_b + row * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+        if (r == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            for (int kk = 0; kk < kc / 16; kk++)
+                tc_mma(tmem, tc_sdesc(sm.A + kk * 4096, 2048, 128), tc_sdesc(sm.B + kk * 2 * lbo_b, lbo_b, 128), idesc,
+                       (k0 > 0 || kk > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_addr(&sm.mbar)));
+        }
+        ok = __syncthreads_and(tc_wait(&sm.mbar, phase & 1u));
+        phase++;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+    }
+    if (ok) {  // all MMAs are done: the operand buffers hold the output stage
+        const unsigned tl = tmem + ((unsigned)(32 * (r >> 5)) << 16);
+        float *st = reinterpret_cast<float *>(sm.A);
+        if (NT == 16) {
+            uint32_t v[16];
+            tc_ld16(v, tl);
+            gemm_tc_out<EPI, 16>(v, st, m0, M, n0, N, bias, C, Aout);
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < NT; c0 += 32) {
+                uint32_t v[32];
+                tc_ld32(v, tl + (unsigned)c0);
+                gemm_tc_out<EPI, 32>(v, st, m0, M, n0 + c0, N, bias, C, Aout);
+            }
+        }
+    } else {
+        if (r == 0) atomicAdd(flag, 1);
+        tc_wait(&sm.mbar, (phase - 1u) & 1u);  // the last MMAs may still be in flight: wait once more (bounded)
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (r < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+    }
+}
+
 }  // namespace tl

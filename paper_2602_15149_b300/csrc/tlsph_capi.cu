@@ -2437,6 +2437,7 @@ struct tlsph_mlp {
     double *stat_d;
     float *stat_f;
     int *tc_flag;           // tensor-core waits that ran out in the last forward
+    int *gemm_flag;         // tensor-core waits of the training GEMMs that ran out (cleared when reported)
     int tensor_path = TLSPH_TENSOR_TCGEN05;
     int64_t t = 0;
 };
@@ -2491,11 +2492,27 @@ tlsph_status mlp_refresh(tlsph_mlp *m) {
     return TLSPH_OK;
 }
 
+// The training GEMMs on the network's tensor path: tcgen05 (k_gemm_tc, one CTA per 128 x 128 output tile)
+// or warp-level mma.sync (k_gemm_bf16).
 template <int EPI>
 void gemm(tlsph_mlp *m, int M, int N, int K, const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias,
           float *C, __nv_bfloat16 *Aout) {
+    if (m->tensor_path == TLSPH_TENSOR_TCGEN05) {
+        const dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
+        k_gemm_tc<EPI><<<grid, 128, sizeof(GemmTcSmem), m->stream>>>(M, N, K, A, B, bias, C, Aout, m->gemm_flag);
+        return;
+    }
     const int warps = (M / 16) * ((N + 31) / 32);
     k_gemm_bf16<EPI><<<(unsigned)((warps + 3) / 4), 128, 0, m->stream>>>(M, N, K, A, B, bias, C, Aout);
+}
+// TLSPH_ERR_TIMEOUT (and the flag cleared) when a training GEMM's wait on the tensor cores ran out; the
+// stream must be synchronised.
+tlsph_status gemm_check(tlsph_mlp *m) {
+    int h = 0;
+    MK(cudaMemcpy(&h, m->gemm_flag, sizeof h, cudaMemcpyDeviceToHost));
+    if (!h) return TLSPH_OK;
+    MK(cudaMemset(m->gemm_flag, 0, sizeof h));
+    return mfail(m, TLSPH_ERR_TIMEOUT, "a tensor-core wait of a training GEMM ran out");
 }
 void transpose(tlsph_mlp *m, int rows, int cols, const __nv_bfloat16 *in, __nv_bfloat16 *out) {
     k_transpose_bf16<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, m->stream>>>(rows, cols, in, out);
@@ -2568,11 +2585,22 @@ tlsph_status tlsph_mlp_create(int device, void *cuda_stream, int batch, tlsph_ml
     MAX(m->doutb, B * kOut * 2) MAX(m->doutT, B * kOut * 2)
     MAX(m->Yn, B * kOut * 4) MAX(m->Z0, B * kHid * 4) MAX(m->Z1, B * kHid * 4) MAX(m->Z2, B * kHid * 4)
     MAX(m->out, B * kOut * 4) MAX(m->dout, B * kOut * 4) MAX(m->dA, B * kHid * 4) MAX(m->dZf, B * kHid * 4)
-    MAX(m->loss, 4) MAX(m->stat_d, 64 * 8) MAX(m->stat_f, 64 * 4) MAX(m->tc_flag, 4)
+    MAX(m->loss, 4) MAX(m->stat_d, 64 * 8) MAX(m->stat_f, 64 * 4) MAX(m->tc_flag, 4) MAX(m->gemm_flag, 4)
 #undef MAX
     if (st != TLSPH_OK) {
         tlsph_mlp_destroy(m);
         return st;
+    }
+    cudaMemsetAsync(m->gemm_flag, 0, sizeof(int), m->stream);
+    if (cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmTcSmem)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmTcSmem)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmTcSmem)) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        tlsph_mlp_destroy(m);
+        return TLSPH_ERR_CUDA;
     }
     cudaMemsetAsync(m->P, 0, kNumParams * 4, m->stream);
     cudaMemsetAsync(m->m, 0, kNumParams * 4, m->stream);
@@ -2714,7 +2742,7 @@ tlsph_status tlsph_mlp_gradients(tlsph_mlp *m, const float *x, const float *y, f
     if (grads) MK(cudaMemcpyAsync(grads, m->G, kNumParams * 4, cudaMemcpyDeviceToHost, m->stream));
     if (loss) MK(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
     MK(cudaStreamSynchronize(m->stream));
-    return TLSPH_OK;
+    return gemm_check(m);
 }
 
 tlsph_status tlsph_mlp_train_step(tlsph_mlp *m, const float *x, const float *y, float lr, float *loss) {
@@ -2732,6 +2760,7 @@ tlsph_status tlsph_mlp_train_step(tlsph_mlp *m, const float *x, const float *y, 
     if (loss) {
         MK(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
         MK(cudaStreamSynchronize(m->stream));
+        return gemm_check(m);
     }
     return TLSPH_OK;
 }

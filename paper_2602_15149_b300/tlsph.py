@@ -421,7 +421,7 @@ class MLP:
         self._ck(self.lib.tlsph_mlp_load(self.h, os.fsencode(path)), "load")
 
     def set_tensor_path(self, path):
-        """TENSOR_TCGEN05 (default) or TENSOR_MMA_SYNC for the inference kernels."""
+        """TENSOR_TCGEN05 (default) or TENSOR_MMA_SYNC for the inference kernels and the training GEMMs."""
         self._ck(self.lib.tlsph_mlp_set_tensor_path(self.h, int(path)), "set_tensor_path")
 
     def set_normalization(self, norm):

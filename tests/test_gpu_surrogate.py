@@ -86,6 +86,31 @@ def test_gradients_match_reference(torch):
             assert cos > 0.999 and rel < 5e-2, (cos, rel)
 
 
+@pytest.mark.parametrize("batch", [2048, 512, 272])
+def test_training_gemm_paths_agree(torch, batch):
+    """The training GEMMs on tcgen05 (TMEM accumulators, one CTA per 128 x 128 tile; a batch of 272 rows
+    leaves a ragged last tile) and on mma.sync give the same loss and gradients up to summation order,
+    and a few Adam steps on either path move the parameters alike."""
+    params = ref.init_params(seed=7)
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.normal(size=(batch, 16)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.normal(size=(batch, 16)).astype(np.float32)).cuda()
+    out = {}
+    for path in (tlsph.TENSOR_TCGEN05, tlsph.TENSOR_MMA_SYNC):
+        net = tlsph.MLP(batch=batch)
+        net.set_tensor_path(path)
+        net.set_params(tlsph.pack_params(params))
+        net.set_normalization(identity_norm())
+        loss, g = net.gradients(x, y)
+        for _ in range(5):
+            net.train_step(x, y, lr=1e-3)
+        out[path] = (loss, g, net.get_params())
+    (l0, g0, p0), (l1, g1, p1) = out[tlsph.TENSOR_TCGEN05], out[tlsph.TENSOR_MMA_SYNC]
+    assert abs(l0 - l1) <= 1e-3 * abs(l1)
+    assert np.linalg.norm(g0 - g1) <= 1e-2 * np.linalg.norm(g1)
+    assert np.linalg.norm(p0 - p1) <= 1e-3 * np.linalg.norm(p1)
+
+
 @pytest.fixture(scope="module")
 def trained(torch):
     """A network trained on return-map samples of a small J2 block (same recipe as the 1M block)."""
