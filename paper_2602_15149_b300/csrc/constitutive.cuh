@@ -413,43 +413,6 @@ template <typename T> TL_HD M3<T> j2_stress(const Kin<T> &k, const M3<T> &dev, c
 
 // J2 update.  K6 = (xx, yy, zz, xy, xz, yz) of C_p^-1 - I.  Returns 0, or 1 if the
 // bracket / iteration did not converge (the state is still updated with the last iterate).
-// Golden-section search for the minimum of r on [a, b] that stops at the first point with r <= 0 (in R,
-// rR; true), or returns false after 80 steps.  Taken only when a doubling of the bracket stepped over the
-// negative interval, so it is kept out of line: its four evaluations of r stay out of the J2 update's
-// inlined code.
-template <typename T>
-__host__ __device__ __noinline__ bool j2_golden_search(const J2Res<T> &r, T a, T b, T &R, T &rR) {
-    const T g = T(0.6180339887498949);
-    T c1 = b - g * (b - a), d1 = a + g * (b - a);
-    T rc = r(c1), rd = r(d1);
-    for (int k = 0; k < 80; k++) {
-        if (rc <= T(0)) {
-            R = c1;
-            rR = rc;
-            return true;
-        }
-        if (rd <= T(0)) {
-            R = d1;
-            rR = rd;
-            return true;
-        }
-        if (rc < rd) {
-            b = d1;
-            d1 = c1;
-            rd = rc;
-            c1 = b - g * (b - a);
-            rc = r(c1);
-        } else {
-            a = c1;
-            c1 = d1;
-            rc = rd;
-            d1 = a + g * (b - a);
-            rd = r(d1);
-        }
-    }
-    return false;
-}
-
 template <typename T>
 TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6out[6], T &ep_out,
                                          M3<T> &S, T &dgamma) {
@@ -491,7 +454,39 @@ TL_HD int j2_update(const Kin<T> &k, const T K6[6], T ep, const MatT<T> &m, T K6
             const T Rn = T(2) * R;
             const T rn = r(Rn);
             if (rn > T(0) && rn >= rR) {
-                if (j2_golden_search(r, Rp, Rn, R, rR)) break;
+                const T g = T(0.6180339887498949);
+                T a = Rp, b = Rn;
+                T c1 = b - g * (b - a), d1 = a + g * (b - a);
+                T rc = r(c1), rd = r(d1);
+                bool found = false;
+                for (int k = 0; k < 80; k++) {
+                    if (rc <= T(0)) {
+                        R = c1;
+                        rR = rc;
+                        found = true;
+                        break;
+                    }
+                    if (rd <= T(0)) {
+                        R = d1;
+                        rR = rd;
+                        found = true;
+                        break;
+                    }
+                    if (rc < rd) {
+                        b = d1;
+                        d1 = c1;
+                        rd = rc;
+                        c1 = b - g * (b - a);
+                        rc = r(c1);
+                    } else {
+                        a = c1;
+                        c1 = d1;
+                        rc = rd;
+                        d1 = a + g * (b - a);
+                        rd = r(d1);
+                    }
+                }
+                if (found) break;
                 // no point below zero (r rose only by rounding near r = 0): keep doubling
             }
             Rp = R;
