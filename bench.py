@@ -53,9 +53,9 @@ FLOP_PER_PAIR = {"gradient": 39.0 + 28.0, "pass2": 35.0}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 # DRAM bytes per launch of each kernel (k_pass2 = "pass2", k_gradient, k_stress) from one ncu capture
-# of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
-# profiles/dram_traffic__block_3d_j2_128x128x64.md), keyed by the hash of the kernel sources it
-# was taken on; reported as null once the kernels change.
+# of the 1M-particle block at full size (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
+# launches of step 6), keyed by the hash of the kernel sources it was taken on; reported as null once
+# the kernels change.
 NCU_TRAFFIC = {"sources": "e37e6252d9d9a465", "pass2": 216789504.0, "gradient": 140532992.0, "stress": 154042624.0}
 
 
